@@ -1,0 +1,507 @@
+/*
+ * pa_oracle.c -- plain CPU oracle of population annealing (PA).
+ * TEST INFRASTRUCTURE ONLY (see pa_oracle.h): tests, smoke() and the
+ * cpu_baseline leg of bench.py call it; the product path never does.
+ *
+ * Every floating-point step is IEEE double with contraction disabled at build
+ * time (-ffp-contract=off), so each expression below is rounded exactly as it
+ * is written.
+ */
+#include "pa_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------
+ * Philox4x32-10 (Salmon et al., SC'11, "Parallel random numbers: as easy as
+ * 1, 2, 3").  State (x0,x1,x2,x3), key (k0,k1).  One round multiplies x0 and
+ * x2 by two fixed odd constants, keeps the four 32-bit halves, mixes the high
+ * halves with the other words and the key, and advances the key by the two
+ * Weyl constants.  Ten rounds.
+ * ---------------------------------------------------------------------- */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)M0 * (uint64_t)x0;
+        uint64_t p1 = (uint64_t)M1 * (uint64_t)x2;
+        uint32_t y0 = (uint32_t)(p1 >> 32) ^ x1 ^ k0;
+        uint32_t y1 = (uint32_t)p1;
+        uint32_t y2 = (uint32_t)(p0 >> 32) ^ x3 ^ k1;
+        uint32_t y3 = (uint32_t)p0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+        k0 += W0; k1 += W1;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+static void draw(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t tag,
+                 int32_t instance, uint32_t out[4])
+{
+    uint32_t ctr[4] = { c0, c1, c2, (tag << 28) | (uint32_t)instance };
+    uint32_t key[2] = { (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32) };
+    or_philox4x32_10(ctr, key, out);
+}
+
+/* ------------------------------------------------------------------------
+ * Schedule and tables.
+ * beta_i = beta0 + (beta_max - beta0) * i / K  (Sec. 3: constant step).
+ * Metropolis threshold T(beta, dE) = floor(exp(-beta dE) * 2^32), so that a
+ * uniform 32-bit u accepts with probability exp(-beta dE) when u < T.
+ * Weight D[j] = exp(-dbeta * 4 j): the factor exp[-(beta_i - beta_{i-1}) E]
+ * of Eq. 3 relative to the lowest occupied energy (energies are 4 apart).
+ * ---------------------------------------------------------------------- */
+double or_beta(const or_config* c, int32_t i)
+{
+    return c->beta0 + ((c->beta_max - c->beta0) * (double)i) / (double)c->K;
+}
+
+uint64_t or_threshold(double beta, int32_t dE)
+{
+    double x = -(beta * (double)dE);
+    double t = floor(exp(x) * 4294967296.0);
+    return (uint64_t)t;
+}
+
+double or_weight(double dbeta, int64_t j)
+{
+    return exp(-(dbeta * (double)(4 * j)));
+}
+
+/* Number of energy levels: U (unsatisfied bonds) runs over 0..dim*N in steps
+ * of two, so k = U >> 1 runs over 0..dim*N/2. */
+int64_t or_num_bins(int32_t dim, int32_t L)
+{
+    int64_t N = 1;
+    for (int d = 0; d < dim; ++d) N *= L;
+    return (int64_t)dim * N / 2 + 1;
+}
+
+/* ------------------------------------------------------------------------
+ * Lattice (Eq. 6).  Site s = x + L y (+ L^2 z); bond (s, d) joins s and
+ * s + e_d (mod L) with coupling J[s*dim + d].  H = -sum_{s,d} J sigma sigma',
+ * which is the -(J/2) sum' of Eq. 6 with its double count removed.
+ * ---------------------------------------------------------------------- */
+static int64_t site_count(int32_t dim, int32_t L)
+{
+    int64_t N = 1;
+    for (int d = 0; d < dim; ++d) N *= L;
+    return N;
+}
+
+static int64_t coord(int32_t L, int64_t s, int d)
+{
+    for (int k = 0; k < d; ++k) s /= L;
+    return s % L;
+}
+
+static int64_t neighbour(int32_t L, int64_t s, int d, int dir)
+{
+    int64_t stride = 1;
+    for (int k = 0; k < d; ++k) stride *= L;
+    int64_t x = coord(L, s, d);
+    int64_t xn = (x + dir + L) % L;
+    return s + (xn - x) * stride;
+}
+
+static int colour_of(int32_t dim, int32_t L, int64_t s)
+{
+    int64_t sum = 0;
+    for (int d = 0; d < dim; ++d) sum += coord(L, s, d);
+    return (int)(sum & 1);
+}
+
+/* Neighbour table nb[(s*dim + d)*2 + 0/1] = s + e_d / s - e_d and the colour
+ * of every site, built from neighbour()/colour_of() and kept for the last
+ * (dim, L) asked for (the oracle is single-threaded). */
+static struct { int32_t dim, L; int64_t* nb; int8_t* col; } geo = { 0, 0, NULL, NULL };
+
+static void geometry(int32_t dim, int32_t L)
+{
+    if (geo.nb && geo.dim == dim && geo.L == L) return;
+    free(geo.nb); free(geo.col);
+    int64_t N = site_count(dim, L);
+    geo.nb = (int64_t*)malloc(sizeof(int64_t) * (size_t)(N * dim * 2));
+    geo.col = (int8_t*)malloc((size_t)N);
+    for (int64_t s = 0; s < N; ++s) {
+        geo.col[s] = (int8_t)colour_of(dim, L, s);
+        for (int d = 0; d < dim; ++d) {
+            geo.nb[(s * dim + d) * 2 + 0] = neighbour(L, s, d, +1);
+            geo.nb[(s * dim + d) * 2 + 1] = neighbour(L, s, d, -1);
+        }
+    }
+    geo.dim = dim; geo.L = L;
+}
+
+void or_init_couplings(const or_config* c, int8_t* J)
+{
+    int64_t N = site_count(c->dim, c->L);
+    for (int64_t s = 0; s < N; ++s)
+        for (int d = 0; d < c->dim; ++d) {
+            int8_t j = 1;
+            if (c->model == OR_MODEL_PMJ) {
+                uint32_t out[4];
+                draw(c->coupling_seed, (uint32_t)(s >> 2), (uint32_t)d, 0u,
+                     OR_TAG_COUPLING, c->instance_id, out);
+                j = (out[s & 3] >> 31) ? -1 : 1;
+            }
+            J[s * c->dim + d] = j;
+        }
+}
+
+/* Initial state at beta0 = 0: every state equally likely (Sec. 2), one
+ * independent uniform bit per site.  The top bit of the draw set => -1. */
+void or_init_replica(const or_config* c, int64_t slot, int8_t* spins)
+{
+    int64_t N = site_count(c->dim, c->L);
+    for (int64_t s = 0; s < N; ++s) {
+        uint32_t out[4];
+        draw(c->seed, (uint32_t)(s >> 2), 0u, (uint32_t)slot, OR_TAG_INIT,
+             c->instance_id, out);
+        spins[s] = (out[s & 3] >> 31) ? -1 : 1;
+    }
+}
+
+void or_energy(int32_t dim, int32_t L, const int8_t* J, const int8_t* spins,
+               int64_t* U, int64_t* M)
+{
+    int64_t N = site_count(dim, L);
+    int64_t u = 0, m = 0;
+    geometry(dim, L);
+    for (int64_t s = 0; s < N; ++s) {
+        m += spins[s];
+        for (int d = 0; d < dim; ++d) {
+            int64_t t = geo.nb[(s * dim + d) * 2 + 0];
+            if (J[s * dim + d] * spins[s] * spins[t] < 0) ++u;
+        }
+    }
+    *U = u;
+    *M = m;
+}
+
+/* Energy change of flipping site s: 2 sigma_s sum_j J_sj sigma_j. */
+int64_t or_delta_e(int32_t dim, int32_t L, const int8_t* J, const int8_t* spins, int64_t s)
+{
+    int64_t local = 0;
+    geometry(dim, L);
+    for (int d = 0; d < dim; ++d) {
+        int64_t up = geo.nb[(s * dim + d) * 2 + 0];
+        int64_t dn = geo.nb[(s * dim + d) * 2 + 1];
+        local += J[s * dim + d] * spins[up];
+        local += J[dn * dim + d] * spins[dn];
+    }
+    return 2 * spins[s] * local;
+}
+
+/* ------------------------------------------------------------------------
+ * Metropolis equilibration (Sec. 2, theta sweeps at the new temperature).
+ * One sweep = colour 0 sites (even coordinate sum) in ascending s, then
+ * colour 1.  The random number of colour site s is word (h & 3) of the Philox
+ * block (h >> 2, 2g + colour, slot, SWEEP|id) with h = s >> 1, where g is the
+ * global index of the sweep in the run.  It is drawn only when dE > 0.
+ * ---------------------------------------------------------------------- */
+int64_t or_sweep_replica(const or_config* c, const int8_t* J, int8_t* spins,
+                         int64_t slot, int64_t g0, int32_t nsweeps, const uint64_t T[3])
+{
+    int64_t N = site_count(c->dim, c->L);
+    int64_t dU = 0;
+    for (int32_t t = 0; t < nsweeps; ++t) {
+        int64_t g = g0 + t;
+        for (int colour = 0; colour < 2; ++colour) {
+            int64_t cached = -1;
+            uint32_t out[4] = { 0, 0, 0, 0 };
+            for (int64_t s = 0; s < N; ++s) {
+                geometry(c->dim, c->L);
+                if (geo.col[s] != colour) continue;
+                int64_t dE = or_delta_e(c->dim, c->L, J, spins, s);
+                int accept;
+                if (dE <= 0) {
+                    accept = 1;
+                } else {
+                    int64_t h = s >> 1;
+                    if ((h >> 2) != cached) {
+                        cached = h >> 2;
+                        draw(c->seed, (uint32_t)(h >> 2), (uint32_t)(2 * g + colour),
+                             (uint32_t)slot, OR_TAG_SWEEP, c->instance_id, out);
+                    }
+                    uint64_t u = out[h & 3];
+                    accept = u < T[dE / 4 - 1];
+                }
+                if (accept) {
+                    spins[s] = (int8_t)-spins[s];
+                    dU += dE / 2;
+                }
+            }
+        }
+    }
+    return dU;
+}
+
+/* ------------------------------------------------------------------------
+ * Eq. 3 / Eq. 4 on the energy histogram H (levels 4 apart).
+ *   kref = lowest occupied level, S = sum_k H_k D[k - kref]  (fixed order:
+ *   256 contiguous chunks of ceil(bins/256) levels, each summed left to right
+ *   from 0.0, then the 256 partial sums combined pairwise, level by level).
+ *   tau_k = R0 D[k - kref] / S: Eq. 4 renormalised to the initial population
+ *   R0, so that the expected population stays at R0 (Sec. 2 asks to keep it
+ *   close to the original one).
+ *   n_k = floor(tau_k), F_k = floor(frac(tau_k) * 2^32).
+ * ---------------------------------------------------------------------- */
+double or_tau_table(const uint32_t* H, int64_t bins, const double* Dtab, int64_t R0,
+                    uint32_t* n, uint32_t* F, int64_t* kref_out)
+{
+    int64_t kref = -1;
+    for (int64_t k = 0; k < bins; ++k)
+        if (H[k] > 0) { kref = k; break; }
+    *kref_out = kref;
+    if (kref < 0) {
+        for (int64_t k = 0; k < bins; ++k) n[k] = F[k] = 0;
+        return 0.0;
+    }
+    double part[256];
+    int64_t ch = (bins + 255) / 256;
+    for (int64_t ci = 0; ci < 256; ++ci) {
+        double acc = 0.0;
+        for (int64_t k = ci * ch; k < (ci + 1) * ch && k < bins; ++k)
+            if (k >= kref) acc = acc + (double)H[k] * Dtab[k - kref];
+        part[ci] = acc;
+    }
+    for (int w = 256; w > 1; w /= 2)
+        for (int j = 0; j < w / 2; ++j) part[j] = part[2 * j] + part[2 * j + 1];
+    double S = part[0];
+    for (int64_t k = 0; k < bins; ++k) {
+        if (k < kref) { n[k] = F[k] = 0; continue; }
+        double tau = ((double)R0 * Dtab[k - kref]) / S;
+        double nk = floor(tau);
+        n[k] = (uint32_t)nk;
+        F[k] = (uint32_t)floor((tau - nk) * 4294967296.0);
+    }
+    return S;
+}
+
+/* Nearest-integer resampling (the Poisson draw of Sec. 2 replaced by one of
+ * its variants): r_i = n_k + [u_i < F_k], u_i = word (i & 3) of the Philox
+ * block (i >> 2, step, 0, RESAMPLE|id).  E[r_i] = tau_k. */
+void or_copy_counts(const or_config* c, int32_t step, const uint32_t* ebin, int64_t R,
+                    const uint32_t* n, const uint32_t* F, uint32_t* r)
+{
+    for (int64_t i = 0; i < R; ++i) {
+        uint32_t out[4];
+        draw(c->seed, (uint32_t)(i >> 2), (uint32_t)step, 0u, OR_TAG_RESAMPLE,
+             c->instance_id, out);
+        uint32_t u = out[i & 3];
+        uint32_t k = ebin[i];
+        r[i] = n[k] + (u < F[k] ? 1u : 0u);
+    }
+}
+
+/* Population averages (Sec. 2) from exact integer sums. */
+void or_derive_obs(or_obs* o, int64_t N)
+{
+    double Rd = (double)o->R, Nd = (double)N;
+    double mE = (double)o->sumE / Rd;
+    double mE2 = (double)o->sumE2 / Rd;
+    double mA = (double)o->sumAbsM / Rd;
+    double mM2 = (double)o->sumM2 / Rd;
+    o->e = mE / Nd;
+    o->cv = ((o->beta * o->beta) * (mE2 - mE * mE)) / Nd;
+    o->m_abs = mA / Nd;
+    o->chi = (o->beta * (mM2 - mA * mA)) / Nd;
+}
+
+/* ------------------------------------------------------------------------
+ * A whole run.
+ * ---------------------------------------------------------------------- */
+struct or_run {
+    or_config c;
+    int64_t N, bins, cap, R, R_prev, g, kref, parity, fails;
+    int32_t step;
+    int8_t *J, *spins, *spins2;
+    uint32_t *ebin, *ebin2, *H, *r, *o, *tn, *tF;
+    int32_t *M, *M2;
+    int64_t *U, *U2;       /* energies tracked through the sweeps */
+    uint64_t *T;           /* [(K+1) * 3] */
+    double S, lnQ, lnZ;
+    or_obs obs;
+};
+
+static void measure(or_run* r)
+{
+    memset(r->H, 0, sizeof(uint32_t) * (size_t)r->bins);
+    or_obs* o = &r->obs;
+    o->step = r->step;
+    o->R = r->R;
+    o->sumE = o->sumE2 = o->sumAbsM = o->sumM2 = 0;
+    for (int64_t i = 0; i < r->R; ++i) {
+        int64_t U, M;
+        or_energy(r->c.dim, r->c.L, r->J, r->spins + i * r->N, &U, &M);
+        if (U != r->U[i]) ++r->fails;            /* from scratch == tracked */
+        if ((U & 1) != r->parity) ++r->fails;    /* parity is a constant   */
+        r->U[i] = U;
+        r->ebin[i] = (uint32_t)(U >> 1);
+        r->M[i] = (int32_t)M;
+        r->H[U >> 1] += 1;
+        int64_t E = 2 * U - (int64_t)r->c.dim * r->N;
+        o->sumE += E;
+        o->sumE2 += E * E;
+        o->sumAbsM += M < 0 ? -M : M;
+        o->sumM2 += M * M;
+    }
+    o->beta = or_beta(&r->c, r->step);
+    o->lnQ = r->lnQ;
+    o->lnZ = r->lnZ;
+    or_derive_obs(o, r->N);
+}
+
+or_run* or_create(const or_config* c)
+{
+    if (c->dim != 2 && c->dim != 3) return NULL;
+    if (c->L < 2 || (c->L & 1)) return NULL;
+    if (c->K < 1 || c->theta < 0 || c->R0 < 1) return NULL;
+    if (c->instance_id < 0 || c->instance_id >= (1 << 28)) return NULL;
+    if (c->beta_max < c->beta0) return NULL;
+    or_run* r = (or_run*)calloc(1, sizeof(or_run));
+    r->c = *c;
+    r->N = site_count(c->dim, c->L);
+    r->bins = or_num_bins(c->dim, c->L);
+    r->cap = c->capacity > 0 ? c->capacity
+                             : c->R0 + 16 * (int64_t)ceil(sqrt((double)c->R0)) + 1024;
+    if (r->cap < c->R0) { free(r); return NULL; }
+    size_t cap = (size_t)r->cap, N = (size_t)r->N, bins = (size_t)r->bins;
+    r->J = (int8_t*)malloc(N * (size_t)c->dim);
+    r->spins = (int8_t*)malloc(cap * N);
+    r->spins2 = (int8_t*)malloc(cap * N);
+    r->ebin = (uint32_t*)calloc(cap, 4);
+    r->ebin2 = (uint32_t*)calloc(cap, 4);
+    r->M = (int32_t*)calloc(cap, 4);
+    r->M2 = (int32_t*)calloc(cap, 4);
+    r->U = (int64_t*)calloc(cap, 8);
+    r->U2 = (int64_t*)calloc(cap, 8);
+    r->r = (uint32_t*)calloc(cap, 4);
+    r->o = (uint32_t*)calloc(cap, 4);
+    r->H = (uint32_t*)calloc(bins, 4);
+    r->tn = (uint32_t*)calloc(bins, 4);
+    r->tF = (uint32_t*)calloc(bins, 4);
+    r->T = (uint64_t*)calloc((size_t)(c->K + 1) * 3, 8);
+    for (int32_t i = 0; i <= c->K; ++i)
+        for (int cl = 0; cl < 3; ++cl)
+            r->T[i * 3 + cl] = or_threshold(or_beta(c, i), 4 * (cl + 1));
+    or_init_couplings(c, r->J);
+    r->R = c->R0;
+    r->kref = -1;
+    for (int64_t i = 0; i < r->R; ++i) or_init_replica(c, i, r->spins + i * r->N);
+    /* the parity of U is fixed by the couplings: read it off replica 0 */
+    {
+        int64_t U, M;
+        or_energy(c->dim, c->L, r->J, r->spins, &U, &M);
+        r->parity = U & 1;
+    }
+    for (int64_t i = 0; i < r->R; ++i) {
+        int64_t U, M;
+        or_energy(c->dim, c->L, r->J, r->spins + i * r->N, &U, &M);
+        r->U[i] = U;
+    }
+    r->lnQ = 0.0;
+    r->lnZ = (double)r->N * log(2.0);
+    measure(r);
+    return r;
+}
+
+void or_destroy(or_run* r)
+{
+    if (!r) return;
+    free(r->J); free(r->spins); free(r->spins2); free(r->ebin); free(r->ebin2);
+    free(r->M); free(r->M2); free(r->U); free(r->U2); free(r->r); free(r->o);
+    free(r->H); free(r->tn); free(r->tF); free(r->T);
+    free(r);
+}
+
+int or_resample(or_run* r)
+{
+    const or_config* c = &r->c;
+    int32_t i = r->step + 1;
+    if (i > c->K) return -2;
+    if (r->R < 1) return -4;
+    double dbeta = or_beta(c, i) - or_beta(c, i - 1);
+    double* Dtab = (double*)malloc(sizeof(double) * (size_t)r->bins);
+    for (int64_t j = 0; j < r->bins; ++j) Dtab[j] = or_weight(dbeta, j);
+    int64_t hsum = 0;
+    for (int64_t k = 0; k < r->bins; ++k) hsum += r->H[k];
+    if (hsum != r->R) ++r->fails;                /* sum_k H_k = R */
+    r->S = or_tau_table(r->H, r->bins, Dtab, c->R0, r->tn, r->tF, &r->kref);
+    free(Dtab);
+    int64_t Eref = 2 * (2 * r->kref + r->parity) - (int64_t)c->dim * r->N;
+    r->lnQ = (log(r->S) - log((double)r->R)) - dbeta * (double)Eref;   /* Eq. 3 */
+    r->lnZ = r->lnZ + r->lnQ;                                          /* Eq. 5 */
+    or_copy_counts(c, i, r->ebin, r->R, r->tn, r->tF, r->r);
+    int64_t total = 0;
+    for (int64_t j = 0; j < r->R; ++j) {
+        r->o[j] = (uint32_t)total;
+        total += r->r[j];
+    }
+    r->R_prev = r->R;
+    r->step = i;
+    if (total > r->cap) return -3;
+    /* exact copies (Sec. 2): copy j of replica i lands in slot o_i + j */
+    for (int64_t j = 0; j < r->R; ++j)
+        for (uint32_t k = 0; k < r->r[j]; ++k) {
+            int64_t dst = (int64_t)r->o[j] + k;
+            memcpy(r->spins2 + dst * r->N, r->spins + j * r->N, (size_t)r->N);
+            r->ebin2[dst] = r->ebin[j];
+            r->M2[dst] = r->M[j];
+            r->U2[dst] = r->U[j];
+        }
+    int8_t* ts = r->spins; r->spins = r->spins2; r->spins2 = ts;
+    uint32_t* te = r->ebin; r->ebin = r->ebin2; r->ebin2 = te;
+    int32_t* tm = r->M; r->M = r->M2; r->M2 = tm;
+    int64_t* tu = r->U; r->U = r->U2; r->U2 = tu;
+    r->R = total;
+    if (total < 1) return -4;
+    return 0;
+}
+
+int or_sweep(or_run* r, int32_t nsweeps)
+{
+    if (nsweeps < 0) return -1;
+    const uint64_t* T = r->T + (size_t)r->step * 3;
+    for (int64_t i = 0; i < r->R; ++i)
+        r->U[i] += or_sweep_replica(&r->c, r->J, r->spins + i * r->N, i, r->g, nsweeps, T);
+    r->g += nsweeps;
+    measure(r);
+    return 0;
+}
+
+int or_step(or_run* r)
+{
+    int rc = or_resample(r);
+    if (rc) return rc;
+    return or_sweep(r, r->c.theta);
+}
+
+void or_observables(const or_run* r, or_obs* out) { *out = r->obs; }
+
+int64_t or_R(const or_run* r) { return r->R; }
+int64_t or_N(const or_run* r) { return r->N; }
+int64_t or_bins(const or_run* r) { return r->bins; }
+int32_t or_step_index(const or_run* r) { return r->step; }
+int64_t or_sweep_counter(const or_run* r) { return r->g; }
+const int8_t* or_spins(const or_run* r) { return r->spins; }
+const uint32_t* or_ebin(const or_run* r) { return r->ebin; }
+const int32_t* or_mag(const or_run* r) { return r->M; }
+const uint32_t* or_hist(const or_run* r) { return r->H; }
+const uint32_t* or_counts(const or_run* r) { return r->r; }
+const uint32_t* or_offsets(const or_run* r) { return r->o; }
+const uint32_t* or_tab_n(const or_run* r) { return r->tn; }
+const uint32_t* or_tab_F(const or_run* r) { return r->tF; }
+const int8_t* or_couplings(const or_run* r) { return r->J; }
+int64_t or_R_prev(const or_run* r) { return r->R_prev; }
+int64_t or_kref(const or_run* r) { return r->kref; }
+double or_S(const or_run* r) { return r->S; }
+int64_t or_parity(const or_run* r) { return r->parity; }
+int64_t or_check_failures(const or_run* r) { return r->fails; }
+double or_lnQ(const or_run* r) { return r->lnQ; }
+double or_lnZ(const or_run* r) { return r->lnZ; }

@@ -1,0 +1,81 @@
+"""Planted mistakes: each one is applied to a copy of oracle/pa_oracle.c on the
+CPU, compiled, and the pins of test_oracle_pins.py / test_oracle_pa_statistics.py
+are run against it.  Every plausible slip listed here must make a pin fail; a
+mutant that passes means a hole in the pins."""
+from __future__ import annotations
+
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+SRC = os.path.join(ROOT, "oracle", "pa_oracle.c")
+
+# (name, original text, planted mistake, pins to run)
+MUTANTS = [
+    ("philox_swapped_multipliers", "uint64_t p0 = (uint64_t)M0 * (uint64_t)x0;",
+     "uint64_t p0 = (uint64_t)M1 * (uint64_t)x0;", "philox"),
+    ("philox_key_bumped_first", "    for (int round = 0; round < 10; ++round) {\n        uint64_t p0",
+     "    for (int round = 0; round < 10; ++round) {\n        k0 += W0; k1 += W1;\n        uint64_t p0",
+     "philox"),
+    ("delta_e_sign", "return 2 * spins[s] * local;", "return -2 * spins[s] * local;",
+     "delta_e or zero_temperature or boltzmann"),
+    ("delta_e_drops_backward_bond", "        local += J[dn * dim + d] * spins[dn];\n", "",
+     "delta_e"),
+    ("delta_e_wrong_backward_coupling", "local += J[dn * dim + d] * spins[dn];",
+     "local += J[s * dim + d] * spins[dn];", "delta_e or gauge or boltzmann"),
+    ("energy_counts_satisfied_bonds", "if (J[s * dim + d] * spins[s] * spins[t] < 0) ++u;",
+     "if (J[s * dim + d] * spins[s] * spins[t] > 0) ++u;", "kaufman or delta_e"),
+    ("energy_wrong_coupling_index", "if (J[s * dim + d] * spins[s] * spins[t] < 0) ++u;",
+     "if (J[t * dim + d] * spins[s] * spins[t] < 0) ++u;", "gauge or delta_e"),
+    ("threshold_one_class_for_all", "accept = u < T[dE / 4 - 1];", "accept = u < T[0];",
+     "boltzmann"),
+    ("threshold_compare_reversed", "accept = u < T[dE / 4 - 1];",
+     "accept = u >= T[dE / 4 - 1];", "beta_zero or boltzmann"),
+    ("weight_wrong_level_spacing", "return exp(-(dbeta * (double)(4 * j)));",
+     "return exp(-(dbeta * (double)(2 * j)));", "weights or tau_table or lnQ"),
+    ("lnQ_sign_of_reference_energy", "- dbeta * (double)Eref;", "+ dbeta * (double)Eref;",
+     "lnQ"),
+    ("tau_normalised_by_current_R", "r->S = or_tau_table(r->H, r->bins, Dtab, c->R0,",
+     "r->S = or_tau_table(r->H, r->bins, Dtab, r->R,", "lnZ_and_energy_match_kaufman"),
+    ("tau_missing_reference_shift", "acc = acc + (double)H[k] * Dtab[k - kref];",
+     "acc = acc + (double)H[k] * Dtab[k];", "tau_table"),
+    ("counts_compare_reversed", "r[i] = n[k] + (u < F[k] ? 1u : 0u);",
+     "r[i] = n[k] + (u > F[k] ? 1u : 0u);", "copy_counts"),
+    ("offsets_inclusive", "        r->o[j] = (uint32_t)total;\n        total += r->r[j];",
+     "        total += r->r[j];\n        r->o[j] = (uint32_t)total;", "copies_are_exact"),
+    ("init_one_word_per_block", "spins[s] = (out[s & 3] >> 31) ? -1 : 1;",
+     "spins[s] = (out[0] >> 31) ? -1 : 1;", "fair_coins"),
+    ("cv_sign", "(mE2 - mE * mE)", "(mE2 + mE * mE)", "observables"),
+]
+
+
+def _build_mutant(tmp, old, new):
+    src = open(SRC).read()
+    assert src.count(old) == 1, old
+    d = tmp
+    shutil.copy(os.path.join(ROOT, "oracle", "pa_oracle.h"), d)
+    with open(os.path.join(d, "pa_oracle.c"), "w") as f:
+        f.write(src.replace(old, new))
+    lib = os.path.join(d, "libmutant.so")
+    subprocess.run(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared", "-o", lib,
+                    os.path.join(d, "pa_oracle.c"), "-lm"], check=True)
+    return lib
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name,old,new,keys", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_planted_mistake_is_caught(tmp_path, name, old, new, keys):
+    lib = _build_mutant(str(tmp_path), old, new)
+    env = dict(os.environ, PA_ORACLE_LIB=lib)
+    cmd = [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+           os.path.join(HERE, "test_oracle_pins.py"),
+           os.path.join(HERE, "test_oracle_pa_statistics.py"), "-k", keys]
+    proc = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=900, cwd=ROOT)
+    tail = proc.stdout[-400:]
+    assert "passed" in tail or "failed" in tail, tail + proc.stderr[-400:]
+    assert proc.returncode == 1 and "failed" in tail, f"mutant {name} survived:\n{tail}"

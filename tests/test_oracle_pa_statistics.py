@@ -1,0 +1,104 @@
+"""End-to-end pins of the oracle's whole PA run against exact thermodynamics.
+
+Population annealing estimates ln Z(beta_i) = N ln 2 + sum_l ln Q_l (Eq. 3,
+Eq. 5 read as -beta F) and population averages (Sec. 2).  Over M independent
+seeds the mean estimate must sit within 3 standard errors of:
+  * Kaufman's exact ln Z of the 16 x 16 torus (the paper's model, Eq. 6, at the
+    config-1 workload: R0 = 1000, beta 0 -> 1 in 100 steps, theta = 10),
+  * brute-force ln Z of the 4 x 4 torus and of a 2 x 2 x 2 +-J instance.
+The runs also check the invariants the oracle tracks: energies recomputed from
+scratch equal the tracked ones and sum_k H_k = R after every step, and the
+population stays within a few sqrt(R0) of R0.
+"""
+from __future__ import annotations
+
+import multiprocessing as mpc
+import os
+
+import numpy as np
+import pytest
+
+import exact
+
+CHECK_STEPS_L16 = (20, 44, 60, 100)
+
+
+def _run_seed(args):
+    kind, seed = args
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    from oracle import oracle as O
+    if kind == "L16":
+        cfg = O.make_config(dim=2, L=16, R0=1000, K=100, theta=10, seed=seed)
+        checks = CHECK_STEPS_L16
+    elif kind == "L4":
+        cfg = O.make_config(dim=2, L=4, R0=3000, K=40, theta=4, beta_max=1.2, seed=seed)
+        checks = (10, 20, 40)
+    else:
+        cfg = O.make_config(dim=3, L=2, model=O.MODEL_PMJ, R0=3000, K=40, theta=4,
+                            beta_max=2.0, seed=seed, coupling_seed=6)
+        checks = (10, 20, 40)
+    run = O.Run(cfg)
+    out, Rs = {}, []
+    for i in range(1, cfg.K + 1):
+        assert run.step() == 0
+        o = run.observables()
+        Rs.append(o["R"])
+        if i in checks:
+            out[i] = (o["beta"], o["lnZ"], o["sumE"] / o["R"])
+    return out, run.check_failures, Rs
+
+
+def _runs(kind, seeds):
+    ctx = mpc.get_context("spawn")
+    with ctx.Pool(min(len(seeds), os.cpu_count() or 1)) as pool:
+        return pool.map(_run_seed, [(kind, s) for s in seeds])
+
+
+def _assert_within(vals, want, nsig=3.0):
+    vals = np.asarray(vals, dtype=np.float64)
+    se = vals.std(ddof=1) / np.sqrt(vals.size)
+    assert abs(vals.mean() - want) < nsig * se + 1e-12 * abs(want), (vals.mean(), want, se)
+
+
+@pytest.mark.slow
+def test_pa_lnZ_and_energy_match_kaufman_L16():
+    res = _runs("L16", list(range(100, 120)))
+    R0 = 1000
+    for out, fails, Rs in res:
+        assert fails == 0
+        assert max(abs(r - R0) for r in Rs) <= 2.5 * np.sqrt(R0)
+    for i in CHECK_STEPS_L16:
+        beta = res[0][0][i][0]
+        _assert_within([r[0][i][1] for r in res], float(exact.kaufman_lnZ(16, beta)))
+        _assert_within([r[0][i][2] / 256 for r in res], exact.kaufman_energy_per_site(16, beta))
+
+
+def _pa_vs_dos(kind, dos):
+    res = _runs(kind, list(range(40, 56)))
+    for out, fails, Rs in res:
+        assert fails == 0
+        assert max(abs(r - 3000) for r in Rs) <= 2.5 * np.sqrt(3000)
+    for i in res[0][0]:
+        beta = res[0][0][i][0]
+        _assert_within([r[0][i][1] for r in res], float(exact.lnZ_from_dos(dos, beta)))
+        _assert_within([r[0][i][2] for r in res], exact.mean_energy_from_dos(dos, beta))
+
+
+@pytest.mark.slow
+def test_pa_lnZ_matches_bruteforce_2d_L4():
+    from oracle import oracle as O
+    J = np.ones(32, dtype=np.int8)
+    dos = exact.density_of_states(2 * O.energy(2, 4, J, s)[0] - 32 for s in exact.all_states(16))
+    _pa_vs_dos("L4", dos)
+
+
+@pytest.mark.slow
+def test_pa_lnZ_matches_bruteforce_3d_L2_pm_j():
+    from oracle import oracle as O
+    cfg = O.make_config(dim=3, L=2, model=O.MODEL_PMJ, coupling_seed=6)
+    J = O.couplings(cfg)
+    dos = exact.density_of_states(2 * O.energy(3, 2, J, s)[0] - 24 for s in exact.all_states(8))
+    _pa_vs_dos("L2_3d", dos)

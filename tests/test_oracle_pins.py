@@ -1,0 +1,479 @@
+"""Pins of the CPU oracle to results fixed by the paper and by mathematics.
+
+Each test names what it pins and the passage of the paper the oracle function
+follows (Russkov, Chulkevich & Shchur, Sec. 2 / Sec. 3 and Eqs. 3-6).  None of
+them compares the oracle with itself: the references are closed forms
+(Kaufman's partition function, high-precision exp), brute-force enumeration,
+an independent library (Triton's Philox, run by its CPU interpreter),
+invariants (gauge symmetry, local vs global energy) and special cases
+(beta = 0, zero temperature, zero temperature step).
+"""
+from __future__ import annotations
+
+import json
+import os
+import subprocess
+import sys
+
+import mpmath as mp
+import numpy as np
+import pytest
+
+import exact
+from oracle import oracle as O
+
+pytestmark = pytest.mark.filterwarnings("ignore::DeprecationWarning")
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+# ---------------------------------------------------------------------------
+# Philox4x32-10 (random numbers of Sec. 2; generator of Salmon et al. 2011)
+# ---------------------------------------------------------------------------
+_TRITON_SCRIPT = r"""
+import os, sys, json
+os.environ["TRITON_INTERPRET"] = "1"
+import torch, triton, triton.language as tl
+
+@triton.jit
+def k(seed_ptr, c0p, c1p, c2p, c3p, o0, o1, o2, o3, n: tl.constexpr):
+    i = tl.arange(0, n)
+    seed = tl.load(seed_ptr)
+    r0, r1, r2, r3 = tl.philox(seed, tl.load(c0p + i), tl.load(c1p + i), tl.load(c2p + i),
+                               tl.load(c3p + i), 10)
+    tl.store(o0 + i, r0); tl.store(o1 + i, r1); tl.store(o2 + i, r2); tl.store(o3 + i, r3)
+
+cases = json.loads(sys.stdin.read())
+res = []
+for key, ctrs in cases:
+    n = len(ctrs)
+    seed = torch.tensor([key], dtype=torch.int64)
+    cs = [torch.tensor([c[j] for c in ctrs], dtype=torch.int64).to(torch.uint32) for j in range(4)]
+    outs = [torch.zeros(n, dtype=torch.uint32) for _ in range(4)]
+    k[(1,)](seed, *cs, *outs, n=n)
+    res.append([[int(outs[j][i].item()) & 0xffffffff for j in range(4)] for i in range(n)])
+print(json.dumps(res))
+"""
+
+
+def test_philox_matches_independent_library():
+    """Oracle Philox4x32-10 == Triton's tl.philox (key = seed lo/hi words)."""
+    pytest.importorskip("triton")
+    rng = np.random.default_rng(2006_00561)
+    cases = []
+    for key in [0, 0xFFFFFFFFFFFFFFFF - (1 << 63), 0x299F31D0A4093822, 1, 3]:
+        ctrs = [[0, 0, 0, 0], [0xFFFFFFFF] * 4]
+        ctrs += rng.integers(0, 2**32, size=(14, 4), dtype=np.uint64).tolist()
+        cases.append([int(key), [[int(x) for x in c] for c in ctrs]])
+    # Triton takes the key as a signed int64 seed; the key words are its lo/hi halves
+    proc = subprocess.run([sys.executable, "-c", _TRITON_SCRIPT], input=json.dumps(cases),
+                          capture_output=True, text=True, timeout=600)
+    if proc.returncode != 0:
+        pytest.skip("triton interpreter unavailable: " + proc.stderr[-300:])
+    ref = json.loads(proc.stdout.strip().splitlines()[-1])
+    for (key, ctrs), outs in zip(cases, ref):
+        k = key & 0xFFFFFFFFFFFFFFFF
+        for c, want in zip(ctrs, outs):
+            got = O.philox(c, [k & 0xFFFFFFFF, k >> 32]).tolist()
+            assert got == want, (hex(k), c)
+
+
+def test_philox_counter_words_all_matter():
+    """Changing any counter or key bit changes the block (no word is dropped)."""
+    base = O.philox([1, 2, 3, 4], [5, 6])
+    for w in range(4):
+        c = [1, 2, 3, 4]
+        c[w] ^= 1 << 17
+        assert not np.array_equal(O.philox(c, [5, 6]), base)
+    assert not np.array_equal(O.philox([1, 2, 3, 4], [5, 7]), base)
+    assert not np.array_equal(O.philox([1, 2, 3, 4], [5 | (1 << 31), 6]), base)
+
+
+# ---------------------------------------------------------------------------
+# Energy (Eq. 6) -- Kaufman's closed form and brute force
+# ---------------------------------------------------------------------------
+def _dos_2d(L: int) -> dict:
+    N = L * L
+    J = np.ones(2 * N, dtype=np.int8)
+    states = exact.all_states(N)
+    energies = []
+    for s in states:
+        U, _ = O.energy(2, L, J, s)
+        energies.append(2 * U - 2 * N)
+    return exact.density_of_states(energies)
+
+
+@pytest.fixture(scope="module")
+def dos_L4():
+    return _dos_2d(4)
+
+
+def test_energy_L4_partition_function_matches_kaufman(dos_L4):
+    """Z(beta) summed over all 2^16 states with the oracle's Eq. 6 energy equals
+    Kaufman's exact finite-torus Z (L = 4) to 1e-14."""
+    assert sum(dos_L4.values()) == 1 << 16
+    assert dos_L4[-32] == 2 and min(dos_L4) == -32 and max(dos_L4) == 32
+    for beta in [0.05, 0.2, 0.4406868, 0.6, 1.0, 2.0]:
+        got = exact.lnZ_from_dos(dos_L4, beta)
+        want = exact.kaufman_lnZ(4, beta)
+        assert abs(got - want) <= 1e-14 * abs(want), beta
+
+
+def test_energy_levels_are_four_apart(dos_L4):
+    """E = 2U - dim N and U is even on the even torus: levels step by 4 (the
+    spacing the weight table D of Eq. 3 assumes)."""
+    assert all((E + 32) % 4 == 0 for E in dos_L4)
+
+
+@pytest.mark.parametrize("dim,L,model", [(2, 4, 0), (2, 6, 1), (3, 2, 1), (3, 4, 1), (3, 6, 0)])
+def test_delta_e_equals_energy_difference(dim, L, model):
+    """Local field rule dE = 2 s_i sum_j J_ij s_j equals E(after) - E(before)."""
+    cfg = O.make_config(dim=dim, L=L, model=model, coupling_seed=77, seed=5)
+    J = O.couplings(cfg)
+    N = L ** dim
+    rng = np.random.default_rng(dim * 100 + L)
+    for _ in range(4):
+        s = np.where(rng.random(N) < 0.5, -1, 1).astype(np.int8)
+        U0, M0 = O.energy(dim, L, J, s)
+        for site in range(N):
+            dE = O.delta_e(dim, L, J, s, site)
+            t = s.copy()
+            t[site] = -t[site]
+            U1, M1 = O.energy(dim, L, J, t)
+            assert (2 * U1 - 2 * U0) == dE
+            assert M1 - M0 == -2 * s[site]
+
+
+def _bond_partner(L, dim, s, d):
+    x = [(s // L ** k) % L for k in range(dim)]
+    x[d] = (x[d] + 1) % L
+    return sum(x[k] * L ** k for k in range(dim))
+
+
+@pytest.mark.parametrize("L", [2, 4, 6])
+def test_gauge_invariance_3d_pm_j(L):
+    """E(J, s) = E(J', s') for the gauge map J'_(s,d) = e_s J_(s,d) e_(s+e_d),
+    s' = e s: the +-J energy uses each bond's own coupling on the right pair."""
+    dim, N = 3, L ** 3
+    cfg = O.make_config(dim=3, L=L, model=O.MODEL_PMJ, coupling_seed=1234 + L)
+    J = O.couplings(cfg)
+    rng = np.random.default_rng(L)
+    eps = np.where(rng.random(N) < 0.5, -1, 1).astype(np.int8)
+    Jg = J.copy()
+    for s in range(N):
+        for d in range(dim):
+            Jg[s * dim + d] = eps[s] * J[s * dim + d] * eps[_bond_partner(L, dim, s, d)]
+    for _ in range(5):
+        sp = np.where(rng.random(N) < 0.5, -1, 1).astype(np.int8)
+        assert O.energy(3, L, J, sp)[0] == O.energy(3, L, Jg, (eps * sp).astype(np.int8))[0]
+    # a pure gauge of the ferromagnet is unfrustrated: its ground state s = e has U = 0
+    Jf = np.array([eps[s] * eps[_bond_partner(L, dim, s, d)] for s in range(N) for d in range(3)],
+                  dtype=np.int8)
+    assert O.energy(3, L, Jf, eps)[0] == 0
+    assert O.energy(3, L, Jf, (-eps).astype(np.int8))[0] == 0
+
+
+def test_3d_states_constant_along_z_reduce_to_2d(dos_L4):
+    """A 3D ferromagnet state s(x,y,z) = t(x,y) has U_3D = L U_2D(t): the 3D
+    energy reduces to L copies of the Kaufman-pinned 2D energy."""
+    L = 4
+    J3 = np.ones(3 * L ** 3, dtype=np.int8)
+    J2 = np.ones(2 * L ** 2, dtype=np.int8)
+    rng = np.random.default_rng(9)
+    for _ in range(20):
+        t = np.where(rng.random(L * L) < 0.5, -1, 1).astype(np.int8)
+        s = np.tile(t, L).astype(np.int8)
+        assert O.energy(3, L, J3, s)[0] == L * O.energy(2, L, J2, t)[0]
+
+
+def test_pm_j_couplings_and_init_are_fair_coins():
+    """Couplings (p = 1/2) and initial spins (Sec. 2: uniform at beta0 = 0)."""
+    cfg = O.make_config(dim=3, L=10, model=O.MODEL_PMJ, coupling_seed=4)
+    J = O.couplings(cfg)
+    n = J.size
+    assert abs((J == -1).sum() - n / 2) < 5 * np.sqrt(n / 4)
+    assert set(np.unique(J)) == {-1, 1}
+    cfg2 = O.make_config(dim=2, L=16, seed=1)
+    spins = np.stack([O.init_replica(cfg2, i) for i in range(200)])
+    m = spins.size
+    assert abs((spins == -1).sum() - m / 2) < 5 * np.sqrt(m / 4)
+    # distinct replicas get distinct states; sites are not copies of each other
+    assert len({s.tobytes() for s in spins}) == 200
+    assert abs(np.corrcoef(spins[:, 0], spins[:, 1])[0, 1]) < 0.3
+
+
+# ---------------------------------------------------------------------------
+# Tables: schedule (Sec. 3), Metropolis thresholds, Eq. 3 weights
+# ---------------------------------------------------------------------------
+def test_paper_schedule_step():
+    """beta 0 -> 1 in K = 200 steps has the constant step 0.005 of Sec. 3."""
+    with open(os.path.join(GOLDEN, "paper_workload.json")) as f:
+        w = json.load(f)
+    cfg = O.make_config(L=w["L"], K=w["K"], beta0=w["beta0"], beta_max=w["beta_K"])
+    steps = [O.beta(cfg, i) - O.beta(cfg, i - 1) for i in range(1, w["K"] + 1)]
+    assert max(abs(s - w["delta_beta"]) for s in steps) < 1e-15
+    assert O.beta(cfg, 0) == 0.0 and O.beta(cfg, w["K"]) == 1.0
+
+
+def test_thresholds_against_high_precision_exp():
+    """T(beta, dE) = floor(2^32 exp(-beta dE)), compared with 40-digit exp."""
+    mp.mp.dps = 40
+    for beta in [0.0, 1e-9, 0.005, 0.1, 0.2216, 0.4406868, 1.0, 3.0, 12.0]:
+        prev = None
+        for dE in (4, 8, 12):
+            T = O.threshold(beta, dE)
+            want = int(mp.floor(mp.exp(-mp.mpf(beta) * dE) * 2 ** 32))
+            assert abs(T - want) <= 1, (beta, dE)
+            assert 0 <= T <= 2 ** 32
+            if prev is not None:
+                assert T <= prev
+            prev = T
+    assert O.threshold(0.0, 4) == 2 ** 32 and O.threshold(0.0, 12) == 2 ** 32
+    assert O.threshold(30.0, 4) == 0
+
+
+def test_weights_against_high_precision_exp():
+    mp.mp.dps = 40
+    for dbeta in [0.0, 0.005, 0.0025, 0.02, 0.5]:
+        for j in [0, 1, 2, 7, 100, 4096]:
+            x = mp.mpf(dbeta) * 4 * j
+            want = mp.exp(-x)
+            got = O.weight(dbeta, j)
+            # the rounded product dbeta*4j shifts the exponent by <= |x| 2^-53
+            assert abs(got - want) <= 2.3e-16 * (1 + x) * want + mp.mpf(1e-300)
+
+
+# ---------------------------------------------------------------------------
+# Metropolis sweep (Sec. 2: MCMC equilibration at the new temperature)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dim,L,model", [(2, 16, 0), (3, 6, 1), (2, 4, 0)])
+def test_sweep_at_beta_zero_flips_every_site_once(dim, L, model):
+    """T = 2^32 accepts every proposal: one sweep negates every spin."""
+    cfg = O.make_config(dim=dim, L=L, model=model, coupling_seed=3, seed=11)
+    J = O.couplings(cfg)
+    s = O.init_replica(cfg, 5)
+    before = s.copy()
+    U0 = O.energy(dim, L, J, s)[0]
+    dU = O.sweep_replica(cfg, J, s, slot=5, g0=0, nsweeps=1, T=[2 ** 32] * 3)
+    assert np.array_equal(s, -before)
+    assert O.energy(dim, L, J, s)[0] == U0 + dU == U0  # global flip keeps E
+
+
+@pytest.mark.parametrize("dim,L,model", [(2, 16, 0), (3, 6, 1)])
+def test_sweep_at_zero_temperature_never_raises_energy(dim, L, model):
+    """T = 0 rejects every dE > 0: U never increases and only dE <= 0 moves."""
+    cfg = O.make_config(dim=dim, L=L, model=model, coupling_seed=8, seed=2)
+    J = O.couplings(cfg)
+    s = O.init_replica(cfg, 0)
+    U = O.energy(dim, L, J, s)[0]
+    for g in range(20):
+        dU = O.sweep_replica(cfg, J, s, slot=0, g0=g, nsweeps=1, T=[0, 0, 0])
+        U1 = O.energy(dim, L, J, s)[0]
+        assert dU <= 0 and U1 == U + dU
+        U = U1
+    assert U < O.energy(dim, L, J, O.init_replica(cfg, 0))[0]
+
+
+def _metropolis_energy_samples(cfg, J, beta, nrep, nsweeps, burn):
+    dim, L = cfg.dim, cfg.L
+    N = L ** dim
+    T = [O.threshold(beta, 4), O.threshold(beta, 8), O.threshold(beta, 12)]
+    samples = np.zeros((nrep, nsweeps), dtype=np.int64)
+    for r in range(nrep):
+        s = O.init_replica(cfg, r)
+        U = O.energy(dim, L, J, s)[0]
+        U += O.sweep_replica(cfg, J, s, slot=r, g0=0, nsweeps=burn, T=T)
+        for t in range(nsweeps):
+            U += O.sweep_replica(cfg, J, s, slot=r, g0=burn + t, nsweeps=1, T=T)
+            samples[r, t] = 2 * U - dim * N
+    return samples
+
+
+def _check_boltzmann(samples, dos, beta):
+    p = exact.boltzmann_from_dos(dos, beta)
+    nrep = samples.shape[0]
+    # replicas are independent chains: per-chain level frequencies give the SE
+    for E, pE in p.items():
+        f = (samples == E).mean(axis=1)
+        se = max(f.std(ddof=1) / np.sqrt(nrep), 1e-4)
+        assert abs(f.mean() - pE) < 5 * se, (E, f.mean(), pE, se)
+    e = samples.mean(axis=1)
+    assert abs(e.mean() - exact.mean_energy_from_dos(dos, beta)) < 4 * e.std(ddof=1) / np.sqrt(
+        nrep)
+
+
+def test_sweep_samples_boltzmann_2d_L4(dos_L4):
+    """Checkerboard Metropolis with u < T samples exp(-beta E): the energy
+    distribution at beta = 0.35 matches the brute-force (Kaufman-pinned) one."""
+    cfg = O.make_config(dim=2, L=4, seed=21)
+    J = np.ones(32, dtype=np.int8)
+    samples = _metropolis_energy_samples(cfg, J, 0.35, nrep=48, nsweeps=1500, burn=50)
+    _check_boltzmann(samples, dos_L4, 0.35)
+
+
+def test_sweep_samples_boltzmann_3d_L2_pm_j():
+    """Same for a +-J 3D instance (L = 2, 2^8 states by brute force), beta = 0.5,
+    which exercises the dE = 12 threshold."""
+    cfg = O.make_config(dim=3, L=2, model=O.MODEL_PMJ, coupling_seed=6, seed=31)
+    J = O.couplings(cfg)
+    states = exact.all_states(8)
+    dos = exact.density_of_states(2 * O.energy(3, 2, J, s)[0] - 24 for s in states)
+    samples = _metropolis_energy_samples(cfg, J, 0.5, nrep=48, nsweeps=1500, burn=50)
+    _check_boltzmann(samples, dos, 0.5)
+
+
+# ---------------------------------------------------------------------------
+# Resampling: Eq. 3 (Q), Eq. 4 (tau), nearest-integer copy counts
+# ---------------------------------------------------------------------------
+def _random_hist(rng, bins, R, lo, width):
+    H = np.zeros(bins, dtype=np.uint32)
+    ks = np.clip(np.round(rng.normal(lo + width / 2, width / 6, size=R)).astype(int), 0, bins - 1)
+    np.add.at(H, ks, 1)
+    return H
+
+
+@pytest.mark.parametrize("bins,R0,R,dbeta", [(257, 1000, 1013, 0.01), (4097, 2 ** 17, 131000, 0.005),
+                                            (1501, 2 ** 14, 2 ** 14, 0.02), (9, 50, 47, 0.3),
+                                            (257, 1000, 990, 0.0)])
+def test_tau_table_against_eq4_high_precision(bins, R0, R, dbeta):
+    """tau_k = R0 exp(-dbeta E_k) / sum_j exp(-dbeta E_j) (Eq. 4 renormalised to
+    R0) in 40-digit arithmetic; n_k + F_k/2^32 reproduces it to < 2^-32."""
+    mp.mp.dps = 40
+    rng = np.random.default_rng(bins + R)
+    H = _random_hist(rng, bins, R, lo=bins // 5, width=max(bins // 10, 3))
+    Dtab = np.array([O.weight(dbeta, j) for j in range(bins)])
+    S, kref, n, F = O.tau_table(H, Dtab, R0)
+    assert kref == int(np.nonzero(H)[0][0])
+    w = {k: mp.exp(-mp.mpf(dbeta) * 4 * k) for k in range(bins) if H[k]}
+    Z = mp.fsum(H[k] * w[k] for k in w)
+    S_exact = Z / w[kref]
+    assert abs(S - S_exact) <= 1e-13 * S_exact
+    total = mp.mpf(0)
+    for k in w:
+        tau = R0 * w[k] / Z
+        got = int(n[k]) + mp.mpf(int(F[k])) / 2 ** 32
+        assert abs(got - tau) <= mp.mpf(2) ** -32 + 1e-13 * tau, k
+        total += H[k] * tau
+    assert abs(total - R0) < 1e-9 * R0  # sum_k H_k tau_k = R0
+    assert (n[:kref] == 0).all() and (F[:kref] == 0).all()
+
+
+def test_copy_counts_are_nearest_integers_with_the_right_mean():
+    """r_i in {floor tau, floor tau + 1}, and P(r = floor tau + 1) = frac tau."""
+    cfg = O.make_config(seed=123)
+    bins = 4
+    n = np.array([0, 2, 1, 5], dtype=np.uint32)
+    frac = np.array([0.3, 0.75, 0.0, 0.5])
+    F = np.floor(frac * 2 ** 32).astype(np.uint32)
+    R = 40000
+    ebin = (np.arange(R) % bins).astype(np.uint32)
+    r = O.copy_counts(cfg, 7, ebin, n, F)
+    for k in range(bins):
+        rk = r[ebin == k].astype(np.int64)
+        assert set(np.unique(rk)) <= {int(n[k]), int(n[k]) + 1}
+        p = (rk == n[k] + 1).mean()
+        m = rk.size
+        assert abs(p - frac[k]) <= 5 * np.sqrt(max(frac[k] * (1 - frac[k]), 1e-12) / m) + 1e-12
+    # another step index draws different numbers
+    r2 = O.copy_counts(cfg, 8, ebin, n, F)
+    assert not np.array_equal(r, r2)
+
+
+def test_zero_temperature_step_resample_is_identity():
+    """beta_i = beta_{i-1} and R = R0: tau = 1 everywhere, every replica is
+    copied once into its own slot (Eq. 4 with a zero temperature step)."""
+    cfg = O.make_config(dim=2, L=8, R0=300, K=3, theta=0, beta0=0.3, beta_max=0.3, seed=4)
+    run = O.Run(cfg)
+    before = run.spins()
+    eb = run.ebin()
+    for _ in range(3):
+        assert run.resample() == 0
+        assert (run.counts() == 1).all()
+        assert np.array_equal(run.offsets(), np.arange(300))
+        assert np.array_equal(run.spins(), before)
+        assert np.array_equal(run.ebin(), eb)
+        assert abs(run.lnQ) < 1e-15
+
+
+def test_lnQ_against_eq3_high_precision():
+    """ln Q = ln[(1/R) sum_j exp(-(beta_i - beta_{i-1}) E_j)] (Eq. 3) from the
+    population's own energies, in 40-digit arithmetic; ln Z accumulates it."""
+    mp.mp.dps = 40
+    cfg = O.make_config(dim=2, L=8, R0=400, K=20, theta=3, seed=8)
+    run = O.Run(cfg)
+    N = 64
+    lnZ = run.lnZ
+    assert abs(lnZ - N * np.log(2)) < 1e-12
+    for i in range(1, 12):
+        U = 2 * run.ebin().astype(np.int64) + run.parity
+        E = 2 * U - 2 * N
+        db = mp.mpf(O.beta(cfg, i)) - mp.mpf(O.beta(cfg, i - 1))
+        want = mp.log(mp.fsum(mp.exp(-db * int(e)) for e in E) / len(E))
+        assert run.resample() == 0
+        assert abs(run.lnQ - want) <= 1e-12 * max(1.0, abs(float(want)))
+        assert abs(run.lnZ - (lnZ + run.lnQ)) <= 1e-12 * abs(lnZ)
+        lnZ = run.lnZ
+        assert run.sweep(cfg.theta) == 0
+
+
+def test_resample_copies_are_exact_and_ordered():
+    """Sec. 2: offspring are exact copies; copy j of replica i sits in slot
+    o_i + j, o = exclusive prefix sum of the counts (order is stable)."""
+    cfg = O.make_config(dim=2, L=8, R0=500, K=10, theta=2, beta_max=2.0, seed=17)
+    run = O.Run(cfg)
+    for _ in range(6):
+        old = run.spins()
+        old_e = run.ebin()
+        old_m = run.mag()
+        assert run.resample() == 0
+        r, o = run.counts(), run.offsets()
+        assert np.array_equal(o, np.concatenate([[0], np.cumsum(r)[:-1]]).astype(np.uint32))
+        assert run.R == int(r.sum())
+        new = run.spins()
+        src = np.repeat(np.arange(old.shape[0]), r)
+        assert np.array_equal(new, old[src])
+        assert np.array_equal(run.ebin(), old_e[src])
+        assert np.array_equal(run.mag(), old_m[src])
+        assert run.sweep(cfg.theta) == 0
+
+
+def test_capacity_overflow_is_an_error():
+    cfg = O.make_config(dim=2, L=8, R0=200, capacity=200, K=50, theta=1, beta_max=3.0, seed=1)
+    run = O.Run(cfg)
+    rc = 0
+    for _ in range(50):
+        rc = run.step()
+        if rc:
+            break
+    assert rc == -3
+
+
+def test_bad_configurations_are_rejected():
+    for kw in [dict(L=5), dict(L=0), dict(dim=4), dict(K=0), dict(R0=0), dict(theta=-1),
+               dict(beta0=1.0, beta_max=0.5), dict(instance_id=1 << 28)]:
+        with pytest.raises(ValueError):
+            O.Run(O.make_config(**kw))
+
+
+# ---------------------------------------------------------------------------
+# Observables (Sec. 2: averages over the population)
+# ---------------------------------------------------------------------------
+def test_observables_are_population_averages():
+    cfg = O.make_config(dim=2, L=8, R0=300, K=5, theta=2, seed=3)
+    run = O.Run(cfg)
+    for _ in range(3):
+        assert run.step() == 0
+    o = run.observables()
+    N = 64
+    U = 2 * run.ebin().astype(np.int64) + run.parity
+    E = 2 * U - 2 * N
+    M = run.mag().astype(np.int64)
+    assert o["R"] == run.R == E.size
+    assert o["sumE"] == E.sum() and o["sumE2"] == (E * E).sum()
+    assert o["sumAbsM"] == np.abs(M).sum() and o["sumM2"] == (M * M).sum()
+    b = o["beta"]
+    assert o["e"] == pytest.approx(E.mean() / N, rel=1e-14)
+    assert o["cv"] == pytest.approx(b * b * E.var() / N, rel=1e-10)
+    assert o["m_abs"] == pytest.approx(np.abs(M).mean() / N, rel=1e-14)
+    assert o["chi"] == pytest.approx(b * (np.mean(M * M) - np.abs(M).mean() ** 2) / N, rel=1e-10)
+    assert np.array_equal(run.hist(), np.bincount(run.ebin(), minlength=run.bins))
