@@ -1,0 +1,217 @@
+/*
+ * pa.h -- C ABI of the GB300 population-annealing (PA) engine.
+ *
+ * Method: population annealing as stated in Russkov, Chulkevich & Shchur,
+ * "Algorithm for the replica redistribution in the implementation of parallel
+ * annealing method on the hybrid supercomputer architecture", Sec. 2:
+ *   - start from R0 replicas at beta0 (Sec. 2, uniform states at beta0 = 0),
+ *   - each step i moves the population from beta_{i-1} to beta_i: the
+ *     partition-function ratio Q (Eq. 3), normalised weights tau (Eq. 4),
+ *     resampling into exact copies (Sec. 2), theta Metropolis sweeps,
+ *     observables, and the free-energy recursion (Eq. 5),
+ * for the Ising model of Eq. 6 (2D ferromagnet) and its +-J Edwards-Anderson
+ * variant (2D or 3D).  Everything runs on one GPU; the population never
+ * leaves device memory except through pa_dump / pa_observables.
+ *
+ * Conventions for every entry point:
+ *   - Return value: PA_OK (0) or a negative PA_ERR_* code; pa_strerror() names
+ *     it.  A call that returns an error changes no state.
+ *   - Device errors that happen inside an asynchronous step (population above
+ *     capacity, a lookback wait that ran out, an invariant that failed) are
+ *     recorded in a sticky status word in device memory; the next
+ *     synchronising call (pa_observables, pa_status, pa_dump) reports them.
+ *   - Memory: the library never allocates device memory.  The caller passes
+ *     one device buffer of pa_workspace_size() bytes (256-byte aligned) and
+ *     keeps it alive until pa_free(); the library owns only a small host
+ *     handle.  Streams are plain cudaStream_t values passed as void*.
+ *   - Threads: one pa_run must not be used from two host threads at once.
+ */
+#ifndef PA_H
+#define PA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define PA_OK               0
+#define PA_ERR_INVALID_ARG (-1)  /* NULL pointer, K < 1, R0 < 1, beta_max < beta0 ... */
+#define PA_ERR_ODD_L       (-2)  /* the checkerboard update needs an even L           */
+#define PA_ERR_UNSUPPORTED (-3)  /* (dim, L, layout) has no compiled kernel           */
+#define PA_ERR_CAPACITY    (-4)  /* population above the configured capacity         */
+#define PA_ERR_TIMEOUT     (-5)  /* a bounded device-side wait gave up                 */
+#define PA_ERR_CUDA        (-6)  /* a CUDA runtime call failed                         */
+#define PA_ERR_WORKSPACE   (-7)  /* workspace NULL, too small or not 256-B aligned     */
+#define PA_ERR_DONE        (-8)  /* resample asked beyond step K                       */
+#define PA_ERR_EMPTY       (-9)  /* the population died out (R = 0)                    */
+#define PA_ERR_INVARIANT   (-10) /* device check failed: sum_k H_k != R                */
+
+/* ---- models and layouts ------------------------------------------------ */
+#define PA_MODEL_FERRO   0  /* J_ij = +1 on every bond: Eq. 6                           */
+#define PA_MODEL_PMJ     1  /* J_ij = +-1, p = 1/2 per bond, drawn from coupling_seed   */
+
+#define PA_LAYOUT_INT8   0  /* one int8 (+1/-1) per site, row-major s = x + L y (+L^2 z) */
+#define PA_LAYOUT_PACKED 1  /* one bit per site (1 = spin -1); rows along x of
+                               ceil(L/32) little-endian 32-bit words             */
+
+/* Supported sizes (anything else returns PA_ERR_UNSUPPORTED):
+ *   dim 2: L in {4, 8, 16, 32, 64, 128};  dim 3: L in {2, 4, 6, 8, 10, 12, 16}. */
+
+/* One PA run.  beta_i = beta0 + (beta_max - beta0) * i / K, i = 0..K (Sec. 3
+ * uses a constant step).  capacity = largest population the workspace holds;
+ * 0 selects R0 + 16 ceil(sqrt(R0)) + 1024.  instance_id < 2^28 separates the
+ * random streams of runs that share a seed. */
+typedef struct {
+    int32_t  dim;           /* 2 or 3                                  */
+    int32_t  L;             /* linear size, even                        */
+    int32_t  model;         /* PA_MODEL_*                               */
+    int32_t  layout;        /* PA_LAYOUT_*                              */
+    int32_t  K;             /* number of annealing steps, >= 1          */
+    int32_t  theta;         /* Metropolis sweeps per step, >= 0         */
+    int32_t  instance_id;   /* 0 .. 2^28-1                              */
+    int32_t  reserved;      /* must be 0                                */
+    int64_t  R0;            /* initial population, 1 .. 2^31            */
+    int64_t  capacity;      /* 0 = default                              */
+    double   beta0, beta_max;
+    uint64_t seed;          /* Philox key: init, sweeps, resampling     */
+    uint64_t coupling_seed; /* Philox key of the +-J couplings          */
+} pa_config;
+
+/* Population averages after the sweeps at beta_i (Sec. 2), from exact
+ * integer sums over the population: E = 2U - dim N (U = unsatisfied bonds),
+ * M = sum of spins.
+ *   e     = <E>/N                  cv  = beta^2 (<E^2> - <E>^2) / N
+ *   m_abs = <|M|>/N                chi = beta (<M^2> - <|M|>^2) / N
+ *   lnQ   = ln Q(beta_{i-1}, beta_i) of Eq. 3 (0 at step 0)
+ *   lnZ   = N ln 2 + sum_{l<=i} ln Q_l, i.e. -beta_i F(beta_i) of Eq. 5 when
+ *           beta0 = 0 (ln of the number of states at infinite temperature). */
+typedef struct {
+    int64_t step, R;
+    int64_t sumE, sumE2, sumAbsM, sumM2;
+    double  beta, lnQ, lnZ;
+    double  e, cv, m_abs, chi;
+} pa_obs;
+
+typedef struct pa_run pa_run;
+
+/* Bytes of device workspace one run needs; 0 if the config is invalid. */
+size_t pa_workspace_size(const pa_config* cfg);
+
+/* Creates a run in the caller's workspace and enqueues, on `stream`, the
+ * initial population at beta0 (uniform random states), the couplings, and
+ * the measurement of step 0.  The host tables (Metropolis thresholds and the
+ * Eq. 3 weights of every step) are built here in IEEE double and copied to
+ * the workspace; this is the only host-to-device copy of a run.
+ * *out receives the handle.  Returns PA_ERR_WORKSPACE if `bytes` is too small
+ * or the pointer is not 256-byte aligned. */
+int pa_init(const pa_config* cfg, void* dev_workspace, size_t bytes, void* stream,
+            pa_run** out);
+
+/* Step i = current + 1 of the annealing (beta_{i-1} -> beta_i), first half:
+ * energy histogram -> Q (Eq. 3) and the per-energy tau table (Eq. 4) ->
+ * nearest-integer copy counts r_j = floor(tau) + [u_j < frac(tau)] ->
+ * exclusive scan -> gather of exact copies into the other population buffer.
+ * Asynchronous on the run's stream; needs a measured population (a sweep,
+ * possibly of 0 sweeps, since the last resample). */
+int pa_resample(pa_run* run);
+
+/* nsweeps checkerboard Metropolis sweeps at the current beta_i, then the
+ * energy/magnetisation of every replica, the energy histogram and the
+ * observables record of step i.  nsweeps = 0 only measures.  Asynchronous. */
+int pa_sweep(pa_run* run, int32_t nsweeps);
+
+/* pa_resample followed by pa_sweep(theta). */
+int pa_step(pa_run* run);
+
+/* nsteps calls of pa_step, replayed from a CUDA graph of one step that is
+ * captured on first use (on a private stream, then launched on the run's
+ * stream).  Same results as nsteps pa_step calls. */
+int pa_run_steps(pa_run* run, int32_t nsteps);
+
+/* Synchronises the run's stream and copies the observables of the latest
+ * measured step into *out.  Reports sticky device errors. */
+int pa_observables(pa_run* run, pa_obs* out);
+
+/* Copies the records of steps first .. first+n-1 (each written when that step
+ * was measured) into out[0..n-1].  Synchronises. */
+int pa_observables_history(pa_run* run, int32_t first, int32_t n, pa_obs* out);
+
+/* Synchronises and returns the sticky device status as a PA_ERR_* code. */
+int pa_status(pa_run* run);
+
+/* Test / inspection hook: synchronises and copies one array of the current
+ * state into host memory.  `bytes` must be at least the size pa_dump_size()
+ * reports.  The spin dump PA_DUMP_SPINS is converted to int8 +-1 in site
+ * order s = x + L y (+ L^2 z), whatever the layout. */
+#define PA_DUMP_SPINS      0  /* int8  [R][N]                                  */
+#define PA_DUMP_EBIN       1  /* u32   [R]   energy level k = U >> 1           */
+#define PA_DUMP_MAG        2  /* i32   [R]   magnetisation M                   */
+#define PA_DUMP_HIST       3  /* u32   [bins] histogram of k (last measurement)*/
+#define PA_DUMP_COUNTS     4  /* u32   [R_prev] copy counts r of last resample */
+#define PA_DUMP_OFFSETS    5  /* u32   [R_prev] exclusive scan o of the counts */
+#define PA_DUMP_TAB_N      6  /* u32   [bins] floor(tau_k) of last resample    */
+#define PA_DUMP_TAB_F      7  /* u32   [bins] floor(frac(tau_k) 2^32)          */
+#define PA_DUMP_COUPLINGS  8  /* int8  [N][dim] J of bond (s, s + e_d)         */
+#define PA_DUMP_SPINS_RAW  9  /* bytes [R][stride] device layout               */
+#define PA_DUMP_STATE     10  /* pa_state                                       */
+int64_t pa_dump_size(pa_run* run, int32_t what);
+int pa_dump(pa_run* run, int32_t what, void* host_dst, size_t bytes);
+
+/* pa_dump restricted to replicas first .. first+count-1 of a per-replica array
+ * (PA_DUMP_SPINS, _SPINS_RAW, _EBIN, _MAG: slots of the current population;
+ * _COUNTS, _OFFSETS: slots of the population that entered the last resample).
+ * bytes >= count * (N, stride or 4).  PA_ERR_INVALID_ARG if the range leaves
+ * the population.  Synchronises. */
+int pa_dump_range(pa_run* run, int32_t what, int64_t first, int64_t count, void* host_dst,
+                  size_t bytes);
+
+/* Scalar run state as seen by the device. */
+typedef struct {
+    int64_t step, R, R_prev, kref, sweeps_done, status_bits;
+    double  lnQ, lnZ, S;
+    int64_t N, bins, stride, capacity, parity;
+} pa_state;
+
+/* Host-side tables the engine uploads, for bitwise comparison before any
+ * kernel runs (no GPU needed): T[c] = floor(2^32 exp(-beta_i 4(c+1))), c=0..2,
+ * the Metropolis acceptance thresholds at beta_i, and D[j] = exp(-(beta_i -
+ * beta_{i-1}) 4 j), j = 0..bins-1, the Eq. 3 weights relative to the lowest
+ * occupied energy level (levels are 4 apart).  D is not written for step 0. */
+int pa_tables(const pa_config* cfg, int32_t step, uint64_t T[3], double* D, int64_t bins);
+
+/* Energy levels of (dim, L): dim L^dim / 2 + 1. */
+int64_t pa_num_bins(int32_t dim, int32_t L);
+
+/* Replaces the current population with `count` replicas read from host memory
+ * (what = PA_DUMP_SPINS: int8 +-1 per site in site order; PA_DUMP_SPINS_RAW:
+ * the device layout, `stride` bytes per replica as pa_dump gives it), then
+ * measures it (energy levels, magnetisations, histogram, observables record
+ * of the current step) exactly as pa_sweep(run, 0) does.  count must lie in
+ * 1 .. capacity; bytes >= count * (N or stride).  The step index, ln Z and
+ * the sweep counter are kept, so dump + load round-trips a population.
+ * With pinned host memory the copy is asynchronous on the run's stream; the
+ * caller keeps host_src alive until the stream reaches it. */
+int pa_load(pa_run* run, int32_t what, const void* host_src, int64_t count, size_t bytes);
+
+/* Kernel timing (for benchmarks): while enabled, every kernel the run
+ * enqueues outside a CUDA graph is bracketed by CUDA events on the run's
+ * stream.  pa_profile_read synchronises and returns, per kernel kind
+ * (0 reweight/tau, 1 resample: counts + scan + gather, 2 sweep, 3 observables),
+ * the number of launches and their summed device time in ms since the last
+ * reset. */
+int pa_profile(pa_run* run, int32_t enable);
+int pa_profile_read(pa_run* run, int64_t launches[4], double ms[4], int32_t reset);
+
+/* Releases the host handle (and its CUDA graph).  The workspace stays the
+ * caller's. */
+void pa_free(pa_run* run);
+
+const char* pa_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PA_H */

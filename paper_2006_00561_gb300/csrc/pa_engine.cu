@@ -1,0 +1,709 @@
+// pa_engine.cu -- host side of the C ABI declared in include/pa.h.
+//
+// The engine validates a run's configuration, lays the run out in the
+// caller's device workspace, builds the per-step host tables (beta schedule,
+// Metropolis thresholds, Eq. 3 weights) in IEEE double, and enqueues the
+// kernels of pa_sweep.cu / pa_resample.cu on the caller's stream.  It never
+// allocates device memory.
+#include <cmath>
+#include <cstddef>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "pa_internal.cuh"
+
+using pa::RunDev;
+using pa::DevState;
+
+struct pa_run {
+    pa_config cfg;
+    cudaStream_t stream;
+    RunDev d;
+    int sweep_grid;
+    std::vector<uint32_t> thr;
+    std::vector<double> beta, dbeta, dtab;
+    std::vector<uint32_t> dsel;
+    DevState init_state;
+    cudaStream_t cap_stream;
+    cudaGraphExec_t graph;
+    size_t hist_bytes;  // accum (16 B) + histogram
+    // kernel timing
+    bool prof;
+    struct Pending {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<Pending> pending;
+    int64_t prof_n[4];
+    double prof_ms[4];
+    uint32_t load_R;  // source of the population size written by pa_load
+};
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+
+size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
+
+struct Layout {
+    int64_t N, bins, nrows, NW, nwords, stride, cap, tiles, ndist;
+    size_t state, obs, thr, beta, dbeta, dsel, dtab, accum, tabn, tabF, desc, coup, ebin[2], mag[2],
+        counts, offsets, spins[2], total;
+};
+
+// beta_i = beta0 + (beta_max - beta0) * i / K (constant step, Sec. 3).
+double beta_of(const pa_config* c, int32_t i) {
+    return c->beta0 + ((c->beta_max - c->beta0) * (double)i) / (double)c->K;
+}
+
+// floor(2^32 exp(-beta dE)): u < T accepts with probability exp(-beta dE).
+uint64_t threshold_of(double beta, int32_t dE) {
+    const double x = -(beta * (double)dE);
+    return (uint64_t)std::floor(std::exp(x) * 4294967296.0);
+}
+
+// exp(-dbeta 4 j): Eq. 3 weight of level kref + j relative to level kref.
+double weight_of(double dbeta, int64_t j) { return std::exp(-(dbeta * (double)(4 * j))); }
+
+int64_t ipow(int64_t a, int b) {
+    int64_t r = 1;
+    for (int i = 0; i < b; ++i) r *= a;
+    return r;
+}
+
+int validate(const pa_config* c) {
+    if (!c) return PA_ERR_INVALID_ARG;
+    if (c->dim != 2 && c->dim != 3) return PA_ERR_INVALID_ARG;
+    if (c->L < 2) return PA_ERR_INVALID_ARG;
+    if (c->L & 1) return PA_ERR_ODD_L;
+    if (c->layout != PA_LAYOUT_INT8 && c->layout != PA_LAYOUT_PACKED) return PA_ERR_INVALID_ARG;
+    if (c->model != PA_MODEL_FERRO && c->model != PA_MODEL_PMJ) return PA_ERR_INVALID_ARG;
+    if (c->K < 1 || c->theta < 0 || c->reserved != 0) return PA_ERR_INVALID_ARG;
+    if (c->instance_id < 0 || c->instance_id >= (1 << 28)) return PA_ERR_INVALID_ARG;
+    if (c->R0 < 1 || c->R0 > (int64_t(1) << 31)) return PA_ERR_INVALID_ARG;
+    if (!std::isfinite(c->beta0) || !std::isfinite(c->beta_max) || c->beta_max < c->beta0)
+        return PA_ERR_INVALID_ARG;
+    if (c->capacity != 0 && (c->capacity < c->R0 || c->capacity > (int64_t(1) << 31)))
+        return PA_ERR_INVALID_ARG;
+    if (!pa::sweep_supported(c->layout, c->dim, c->L)) return PA_ERR_UNSUPPORTED;
+    return PA_OK;
+}
+
+// Schedule and deduplicated weight tables (one per distinct dbeta bit pattern).
+void schedule(const pa_config* c, int64_t bins, std::vector<double>& beta,
+              std::vector<double>& dbeta, std::vector<uint32_t>& dsel, std::vector<double>* dtab,
+              int64_t* ndist) {
+    beta.assign(c->K + 1, 0.0);
+    dbeta.assign(c->K + 1, 0.0);
+    dsel.assign(c->K + 1, 0u);
+    for (int32_t i = 0; i <= c->K; ++i) beta[i] = beta_of(c, i);
+    std::vector<double> uniq;
+    for (int32_t i = 1; i <= c->K; ++i) {
+        dbeta[i] = beta[i] - beta[i - 1];
+        size_t j = 0;
+        while (j < uniq.size() && std::memcmp(&uniq[j], &dbeta[i], sizeof(double)) != 0) ++j;
+        if (j == uniq.size()) uniq.push_back(dbeta[i]);
+        dsel[i] = (uint32_t)j;
+    }
+    if (uniq.empty()) uniq.push_back(0.0);
+    *ndist = (int64_t)uniq.size();
+    if (dtab) {
+        dtab->assign((size_t)(uniq.size() * bins), 0.0);
+        for (size_t u = 0; u < uniq.size(); ++u)
+            for (int64_t j = 0; j < bins; ++j) (*dtab)[u * bins + j] = weight_of(uniq[u], j);
+    }
+}
+
+int make_layout(const pa_config* c, Layout* Lo, std::vector<double>* beta, std::vector<double>* dbeta,
+                std::vector<uint32_t>* dsel, std::vector<double>* dtab) {
+    int rc = validate(c);
+    if (rc) return rc;
+    Layout& l = *Lo;
+    l.N = ipow(c->L, c->dim);
+    l.bins = (int64_t)c->dim * l.N / 2 + 1;
+    l.nrows = c->dim == 2 ? c->L : (int64_t)c->L * c->L;
+    l.NW = (c->L + 31) / 32;
+    l.nwords = l.nrows * l.NW;
+    l.stride = c->layout == PA_LAYOUT_PACKED ? (l.nwords * 4 + 15) / 16 * 16 : (l.N + 15) / 16 * 16;
+    l.cap = c->capacity > 0 ? c->capacity
+                            : c->R0 + 16 * (int64_t)std::ceil(std::sqrt((double)c->R0)) + 1024;
+    if (l.cap > (int64_t(1) << 31)) return PA_ERR_INVALID_ARG;
+    l.tiles = (l.cap + pa::RS_TILE - 1) / pa::RS_TILE;
+    std::vector<double> b, db;
+    std::vector<uint32_t> ds;
+    schedule(c, l.bins, beta ? *beta : b, dbeta ? *dbeta : db, dsel ? *dsel : ds, dtab, &l.ndist);
+    const size_t K1 = (size_t)c->K + 1;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = off;
+        off = align_up(off + bytes);
+        return at;
+    };
+    l.state = take(256);
+    l.obs = take(K1 * sizeof(pa_obs));
+    l.thr = take(K1 * 16);
+    l.beta = take(K1 * 8);
+    l.dbeta = take(K1 * 8);
+    l.dsel = take(K1 * 4);
+    l.dtab = take((size_t)(l.ndist * l.bins * 8));
+    l.accum = take(16 + (size_t)l.bins * 4);
+    l.tabn = take((size_t)l.bins * 4);
+    l.tabF = take((size_t)l.bins * 4);
+    l.desc = take((size_t)l.tiles * 8);
+    if (c->model == PA_MODEL_PMJ)
+        l.coup = take(c->layout == PA_LAYOUT_PACKED ? (size_t)(c->dim * l.nwords * 4)
+                                                    : (size_t)(l.N * c->dim));
+    else
+        l.coup = 0;
+    for (int b2 = 0; b2 < 2; ++b2) l.ebin[b2] = take((size_t)l.cap * 4);
+    for (int b2 = 0; b2 < 2; ++b2) l.mag[b2] = take((size_t)l.cap * 4);
+    l.counts = take((size_t)l.cap * 4);
+    l.offsets = take((size_t)l.cap * 4);
+    for (int b2 = 0; b2 < 2; ++b2) l.spins[b2] = take((size_t)(l.cap * l.stride));
+    l.total = off;
+    return PA_OK;
+}
+
+#define CK(call)                                   \
+    do {                                           \
+        if ((call) != cudaSuccess) return PA_ERR_CUDA; \
+    } while (0)
+
+int sticky_to_code(uint32_t bits) {
+    if (bits & pa::ST_TIMEOUT) return PA_ERR_TIMEOUT;
+    if (bits & pa::ST_CAPACITY) return PA_ERR_CAPACITY;
+    if (bits & pa::ST_INVARIANT) return PA_ERR_INVARIANT;
+    if (bits & pa::ST_EMPTY) return PA_ERR_EMPTY;
+    if (bits & pa::ST_DONE) return PA_ERR_DONE;
+    return PA_OK;
+}
+
+int read_state(pa_run* r, DevState* out) {
+    CK(cudaStreamSynchronize(r->stream));
+    CK(cudaMemcpy(out, r->d.st, sizeof(DevState), cudaMemcpyDeviceToHost));
+    return PA_OK;
+}
+
+cudaEvent_t take_event(pa_run* r) {
+    if (!r->ev_pool.empty()) {
+        cudaEvent_t e = r->ev_pool.back();
+        r->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Launches one kernel; brackets it with events when timing is on and the
+// launch goes to the run's own stream (not into a graph capture).
+template <class F>
+int timed(pa_run* r, cudaStream_t s, int kind, F&& launch) {
+    if (!r->prof || s != r->stream) {
+        CK(launch());
+        return PA_OK;
+    }
+    cudaEvent_t a = take_event(r), b = take_event(r);
+    if (!a || !b) return PA_ERR_CUDA;
+    CK(cudaEventRecord(a, s));
+    CK(launch());
+    CK(cudaEventRecord(b, s));
+    r->pending.push_back({kind, a, b});
+    return PA_OK;
+}
+
+int enqueue_sweep(pa_run* r, cudaStream_t s, int32_t nsweeps) {
+    CK(cudaMemsetAsync(r->d.accum, 0, r->hist_bytes, s));
+    int rc = timed(r, s, 2, [&] { return pa::launch_sweep(r->d, nsweeps, r->sweep_grid, s); });
+    if (rc) return rc;
+    return timed(r, s, 3, [&] { return pa::launch_obs(r->d, nsweeps, s); });
+}
+
+int enqueue_resample(pa_run* r, cudaStream_t s) {
+    int rc = timed(r, s, 0, [&] { return pa::launch_tau(r->d, s); });
+    if (rc) return rc;
+    return timed(r, s, 1, [&] { return pa::launch_resample(r->d, s); });
+}
+
+int enqueue_step(pa_run* r, cudaStream_t s) {
+    int rc = enqueue_resample(r, s);
+    if (rc) return rc;
+    return enqueue_sweep(r, s, r->cfg.theta);
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t pa_num_bins(int32_t dim, int32_t L) {
+    if ((dim != 2 && dim != 3) || L < 1) return 0;
+    return (int64_t)dim * ipow(L, dim) / 2 + 1;
+}
+
+size_t pa_workspace_size(const pa_config* cfg) {
+    Layout l;
+    if (make_layout(cfg, &l, nullptr, nullptr, nullptr, nullptr)) return 0;
+    return l.total;
+}
+
+int pa_tables(const pa_config* cfg, int32_t step, uint64_t T[3], double* D, int64_t bins) {
+    int rc = validate(cfg);
+    if (rc) return rc;
+    if (step < 0 || step > cfg->K || !T) return PA_ERR_INVALID_ARG;
+    const double b = beta_of(cfg, step);
+    for (int c = 0; c < 3; ++c) T[c] = threshold_of(b, 4 * (c + 1));
+    if (D && step >= 1) {
+        const double db = b - beta_of(cfg, step - 1);
+        for (int64_t j = 0; j < bins; ++j) D[j] = weight_of(db, j);
+    }
+    return PA_OK;
+}
+
+int pa_init(const pa_config* cfg, void* ws, size_t bytes, void* stream, pa_run** out) {
+    if (!out) return PA_ERR_INVALID_ARG;
+    *out = nullptr;
+    Layout l;
+    std::vector<double> beta, dbeta, dtab;
+    std::vector<uint32_t> dsel;
+    int rc = make_layout(cfg, &l, &beta, &dbeta, &dsel, &dtab);
+    if (rc) return rc;
+    if (!ws || ((uintptr_t)ws % ALIGN) != 0 || bytes < l.total) return PA_ERR_WORKSPACE;
+
+    pa_run* r = new (std::nothrow) pa_run();
+    if (!r) return PA_ERR_INVALID_ARG;
+    r->cfg = *cfg;
+    r->stream = (cudaStream_t)stream;
+    r->beta = beta;
+    r->dbeta = dbeta;
+    r->dsel = dsel;
+    r->dtab = dtab;
+    r->cap_stream = nullptr;
+    r->graph = nullptr;
+    r->prof = false;
+    for (int k = 0; k < 4; ++k) {
+        r->prof_n[k] = 0;
+        r->prof_ms[k] = 0.0;
+    }
+    r->load_R = 0;
+    r->thr.assign((size_t)(cfg->K + 1) * 4, 0u);
+    for (int32_t i = 0; i <= cfg->K; ++i) {
+        uint32_t full = 0;
+        for (int c = 0; c < 3; ++c) {
+            const uint64_t T = threshold_of(beta[i], 4 * (c + 1));
+            if (T >= 4294967296ull) {
+                full |= 1u << c;
+                r->thr[i * 4 + c] = 0xffffffffu;
+            } else {
+                r->thr[i * 4 + c] = (uint32_t)T;
+            }
+        }
+        r->thr[i * 4 + 3] = full;
+    }
+
+    uint8_t* base = (uint8_t*)ws;
+    RunDev& d = r->d;
+    std::memset(&d, 0, sizeof(d));
+    d.st = (DevState*)(base + l.state);
+    for (int b2 = 0; b2 < 2; ++b2) {
+        d.spins[b2] = base + l.spins[b2];
+        d.ebin[b2] = (uint32_t*)(base + l.ebin[b2]);
+        d.mag[b2] = (int32_t*)(base + l.mag[b2]);
+    }
+    d.counts = (uint32_t*)(base + l.counts);
+    d.offsets = (uint32_t*)(base + l.offsets);
+    d.accum = (unsigned long long*)(base + l.accum);
+    d.hist = (uint32_t*)(base + l.accum + 16);
+    d.tab_n = (uint32_t*)(base + l.tabn);
+    d.tab_F = (uint32_t*)(base + l.tabF);
+    d.thr = (const uint32_t*)(base + l.thr);
+    d.dtab = (const double*)(base + l.dtab);
+    d.dsel = (const uint32_t*)(base + l.dsel);
+    d.beta = (const double*)(base + l.beta);
+    d.dbeta = (const double*)(base + l.dbeta);
+    d.desc = (unsigned long long*)(base + l.desc);
+    d.obs = (pa_obs*)(base + l.obs);
+    if (cfg->model == PA_MODEL_PMJ) {
+        if (cfg->layout == PA_LAYOUT_PACKED) d.jpk = (uint32_t*)(base + l.coup);
+        else d.j8 = (int8_t*)(base + l.coup);
+    }
+    d.seed = cfg->seed;
+    d.coupling_seed = cfg->coupling_seed;
+    d.instance = (uint32_t)cfg->instance_id;
+    d.dim = cfg->dim;
+    d.L = cfg->L;
+    d.layout = cfg->layout;
+    d.model = cfg->model;
+    d.K = cfg->K;
+    d.N = l.N;
+    d.bins = l.bins;
+    d.stride = (uint32_t)l.stride;
+    d.nwords = (uint32_t)l.nwords;
+    d.cap = (uint32_t)l.cap;
+    d.cap_alloc = (uint32_t)l.cap;
+    d.R0 = (uint32_t)cfg->R0;
+    d.tiles = (uint32_t)l.tiles;
+    r->hist_bytes = 16 + (size_t)l.bins * 4;
+
+    r->sweep_grid = pa::sweep_grid(d);
+    if (r->sweep_grid <= 0) {
+        delete r;
+        return PA_ERR_CUDA;
+    }
+
+    std::memset(&r->init_state, 0, sizeof(DevState));
+    r->init_state.R = (uint32_t)cfg->R0;
+    r->init_state.lnZ = (double)l.N * std::log(2.0);
+    cudaStream_t s = r->stream;
+    const size_t K1 = (size_t)cfg->K + 1;
+    bool ok = cudaMemcpyAsync(d.st, &r->init_state, sizeof(DevState), cudaMemcpyHostToDevice, s) ==
+                  cudaSuccess &&
+              cudaMemsetAsync(d.desc, 0, (size_t)l.tiles * 8, s) == cudaSuccess &&
+              cudaMemsetAsync(d.obs, 0, K1 * sizeof(pa_obs), s) == cudaSuccess &&
+              cudaMemsetAsync(d.counts, 0, (size_t)l.cap * 4, s) == cudaSuccess &&
+              cudaMemsetAsync(d.offsets, 0, (size_t)l.cap * 4, s) == cudaSuccess &&
+              cudaMemsetAsync(d.tab_n, 0, (size_t)l.bins * 4, s) == cudaSuccess &&
+              cudaMemsetAsync(d.tab_F, 0, (size_t)l.bins * 4, s) == cudaSuccess &&
+              cudaMemcpyAsync((void*)d.thr, r->thr.data(), K1 * 16, cudaMemcpyHostToDevice, s) ==
+                  cudaSuccess &&
+              cudaMemcpyAsync((void*)d.beta, r->beta.data(), K1 * 8, cudaMemcpyHostToDevice, s) ==
+                  cudaSuccess &&
+              cudaMemcpyAsync((void*)d.dbeta, r->dbeta.data(), K1 * 8, cudaMemcpyHostToDevice,
+                              s) == cudaSuccess &&
+              cudaMemcpyAsync((void*)d.dsel, r->dsel.data(), K1 * 4, cudaMemcpyHostToDevice, s) ==
+                  cudaSuccess &&
+              cudaMemcpyAsync((void*)d.dtab, r->dtab.data(), r->dtab.size() * 8,
+                              cudaMemcpyHostToDevice, s) == cudaSuccess &&
+              pa::launch_init(d, s) == cudaSuccess && enqueue_sweep(r, s, 0) == PA_OK;
+    if (!ok) {
+        delete r;
+        return PA_ERR_CUDA;
+    }
+    *out = r;
+    return PA_OK;
+}
+
+int pa_resample(pa_run* r) {
+    if (!r) return PA_ERR_INVALID_ARG;
+    return enqueue_resample(r, r->stream);
+}
+
+int pa_sweep(pa_run* r, int32_t nsweeps) {
+    if (!r || nsweeps < 0) return PA_ERR_INVALID_ARG;
+    return enqueue_sweep(r, r->stream, nsweeps);
+}
+
+int pa_step(pa_run* r) {
+    if (!r) return PA_ERR_INVALID_ARG;
+    return enqueue_step(r, r->stream);
+}
+
+int pa_run_steps(pa_run* r, int32_t nsteps) {
+    if (!r || nsteps < 0) return PA_ERR_INVALID_ARG;
+    if (!r->graph) {
+        if (!r->cap_stream) CK(cudaStreamCreateWithFlags(&r->cap_stream, cudaStreamNonBlocking));
+        CK(cudaStreamBeginCapture(r->cap_stream, cudaStreamCaptureModeThreadLocal));
+        const int rc = enqueue_step(r, r->cap_stream);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(r->cap_stream, &g);
+        if (rc || e != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            return rc ? rc : PA_ERR_CUDA;
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&r->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) {
+            r->graph = nullptr;
+            return PA_ERR_CUDA;
+        }
+    }
+    for (int32_t i = 0; i < nsteps; ++i) CK(cudaGraphLaunch(r->graph, r->stream));
+    return PA_OK;
+}
+
+int pa_status(pa_run* r) {
+    if (!r) return PA_ERR_INVALID_ARG;
+    DevState st;
+    int rc = read_state(r, &st);
+    if (rc) return rc;
+    return sticky_to_code(st.status);
+}
+
+int pa_observables(pa_run* r, pa_obs* out) {
+    if (!r || !out) return PA_ERR_INVALID_ARG;
+    DevState st;
+    int rc = read_state(r, &st);
+    if (rc) return rc;
+    CK(cudaMemcpy(out, r->d.obs + st.step, sizeof(pa_obs), cudaMemcpyDeviceToHost));
+    return sticky_to_code(st.status);
+}
+
+int pa_observables_history(pa_run* r, int32_t first, int32_t n, pa_obs* out) {
+    if (!r || !out || first < 0 || n < 0 || (int64_t)first + n > (int64_t)r->cfg.K + 1)
+        return PA_ERR_INVALID_ARG;
+    DevState st;
+    int rc = read_state(r, &st);
+    if (rc) return rc;
+    if (n) CK(cudaMemcpy(out, r->d.obs + first, (size_t)n * sizeof(pa_obs), cudaMemcpyDeviceToHost));
+    return sticky_to_code(st.status);
+}
+
+int64_t pa_dump_size(pa_run* r, int32_t what) {
+    if (!r) return -1;
+    DevState st;
+    if (read_state(r, &st)) return -1;
+    const RunDev& d = r->d;
+    switch (what) {
+        case PA_DUMP_SPINS: return (int64_t)st.R * d.N;
+        case PA_DUMP_SPINS_RAW: return (int64_t)st.R * d.stride;
+        case PA_DUMP_EBIN:
+        case PA_DUMP_MAG: return (int64_t)st.R * 4;
+        case PA_DUMP_HIST:
+        case PA_DUMP_TAB_N:
+        case PA_DUMP_TAB_F: return d.bins * 4;
+        case PA_DUMP_COUNTS:
+        case PA_DUMP_OFFSETS: return (int64_t)st.R_prev * 4;
+        case PA_DUMP_COUPLINGS: return d.N * d.dim;
+        case PA_DUMP_STATE: return (int64_t)sizeof(pa_state);
+        default: return -1;
+    }
+}
+
+int pa_dump(pa_run* r, int32_t what, void* dst, size_t bytes) {
+    if (!r || !dst) return PA_ERR_INVALID_ARG;
+    const int64_t need = pa_dump_size(r, what);
+    if (need < 0 || (int64_t)bytes < need) return PA_ERR_INVALID_ARG;
+    DevState st;
+    int rc = read_state(r, &st);
+    if (rc) return rc;
+    const RunDev& d = r->d;
+    const int NW = (d.L + 31) / 32;
+    switch (what) {
+        case PA_DUMP_SPINS: {
+            std::vector<uint8_t> raw((size_t)st.R * d.stride);
+            if (!raw.empty())
+                CK(cudaMemcpy(raw.data(), d.spins[st.cur], raw.size(), cudaMemcpyDeviceToHost));
+            int8_t* o = (int8_t*)dst;
+            for (uint32_t rep = 0; rep < st.R; ++rep) {
+                const uint8_t* p = raw.data() + (size_t)rep * d.stride;
+                int8_t* q = o + (size_t)rep * d.N;
+                if (d.layout == PA_LAYOUT_INT8) {
+                    std::memcpy(q, p, (size_t)d.N);
+                } else {
+                    const uint32_t* w = (const uint32_t*)p;
+                    for (int64_t s = 0; s < d.N; ++s) {
+                        const int64_t row = s / d.L, x = s % d.L;
+                        const uint32_t bit = (w[row * NW + x / 32] >> (x % 32)) & 1u;
+                        q[s] = bit ? (int8_t)-1 : (int8_t)1;
+                    }
+                }
+            }
+            break;
+        }
+        case PA_DUMP_SPINS_RAW:
+            if (need) CK(cudaMemcpy(dst, d.spins[st.cur], (size_t)need, cudaMemcpyDeviceToHost));
+            break;
+        case PA_DUMP_EBIN:
+            if (need) CK(cudaMemcpy(dst, d.ebin[st.cur], (size_t)need, cudaMemcpyDeviceToHost));
+            break;
+        case PA_DUMP_MAG:
+            if (need) CK(cudaMemcpy(dst, d.mag[st.cur], (size_t)need, cudaMemcpyDeviceToHost));
+            break;
+        case PA_DUMP_HIST: CK(cudaMemcpy(dst, d.hist, (size_t)need, cudaMemcpyDeviceToHost)); break;
+        case PA_DUMP_TAB_N: CK(cudaMemcpy(dst, d.tab_n, (size_t)need, cudaMemcpyDeviceToHost)); break;
+        case PA_DUMP_TAB_F: CK(cudaMemcpy(dst, d.tab_F, (size_t)need, cudaMemcpyDeviceToHost)); break;
+        case PA_DUMP_COUNTS:
+            if (need) CK(cudaMemcpy(dst, d.counts, (size_t)need, cudaMemcpyDeviceToHost));
+            break;
+        case PA_DUMP_OFFSETS:
+            if (need) CK(cudaMemcpy(dst, d.offsets, (size_t)need, cudaMemcpyDeviceToHost));
+            break;
+        case PA_DUMP_COUPLINGS: {
+            int8_t* o = (int8_t*)dst;
+            if (d.model != PA_MODEL_PMJ) {
+                std::memset(o, 1, (size_t)need);
+            } else if (d.layout == PA_LAYOUT_INT8) {
+                CK(cudaMemcpy(o, d.j8, (size_t)need, cudaMemcpyDeviceToHost));
+            } else {
+                std::vector<uint32_t> pk((size_t)d.dim * d.nwords);
+                CK(cudaMemcpy(pk.data(), d.jpk, pk.size() * 4, cudaMemcpyDeviceToHost));
+                for (int64_t s = 0; s < d.N; ++s)
+                    for (int dd = 0; dd < d.dim; ++dd) {
+                        const int64_t row = s / d.L, x = s % d.L;
+                        const uint32_t bit =
+                            (pk[(size_t)dd * d.nwords + row * NW + x / 32] >> (x % 32)) & 1u;
+                        o[s * d.dim + dd] = bit ? (int8_t)-1 : (int8_t)1;
+                    }
+            }
+            break;
+        }
+        case PA_DUMP_STATE: {
+            pa_state ps;
+            ps.step = st.step;
+            ps.R = st.R;
+            ps.R_prev = st.R_prev;
+            ps.kref = st.kref;
+            ps.sweeps_done = (int64_t)st.sweeps_done;
+            ps.status_bits = st.status;
+            ps.lnQ = st.lnQ;
+            ps.lnZ = st.lnZ;
+            ps.S = st.S;
+            ps.N = d.N;
+            ps.bins = d.bins;
+            ps.stride = d.stride;
+            ps.capacity = d.cap;
+            ps.parity = st.negbonds & 1u;
+            std::memcpy(dst, &ps, sizeof(ps));
+            break;
+        }
+        default: return PA_ERR_INVALID_ARG;
+    }
+    return PA_OK;
+}
+
+int pa_dump_range(pa_run* r, int32_t what, int64_t first, int64_t count, void* dst,
+                  size_t bytes) {
+    if (!r || !dst || first < 0 || count < 0) return PA_ERR_INVALID_ARG;
+    DevState st;
+    int rc = read_state(r, &st);
+    if (rc) return rc;
+    const RunDev& d = r->d;
+    const int NW = (d.L + 31) / 32;
+    int64_t limit = st.R, elem = 4;
+    const uint8_t* src = nullptr;
+    switch (what) {
+        case PA_DUMP_SPINS: elem = d.N; src = d.spins[st.cur]; break;
+        case PA_DUMP_SPINS_RAW: elem = d.stride; src = d.spins[st.cur]; break;
+        case PA_DUMP_EBIN: src = (const uint8_t*)d.ebin[st.cur]; break;
+        case PA_DUMP_MAG: src = (const uint8_t*)d.mag[st.cur]; break;
+        case PA_DUMP_COUNTS: limit = st.R_prev; src = (const uint8_t*)d.counts; break;
+        case PA_DUMP_OFFSETS: limit = st.R_prev; src = (const uint8_t*)d.offsets; break;
+        default: return PA_ERR_INVALID_ARG;
+    }
+    if (first + count > limit || (int64_t)bytes < count * elem) return PA_ERR_INVALID_ARG;
+    if (count == 0) return PA_OK;
+    if (what != PA_DUMP_SPINS) {
+        const size_t per = what == PA_DUMP_SPINS_RAW ? d.stride : 4;
+        CK(cudaMemcpy(dst, src + (size_t)first * per, (size_t)count * per, cudaMemcpyDeviceToHost));
+        return PA_OK;
+    }
+    std::vector<uint8_t> raw((size_t)count * d.stride);
+    CK(cudaMemcpy(raw.data(), src + (size_t)first * d.stride, raw.size(), cudaMemcpyDeviceToHost));
+    int8_t* o = (int8_t*)dst;
+    for (int64_t rep = 0; rep < count; ++rep) {
+        const uint8_t* p = raw.data() + (size_t)rep * d.stride;
+        int8_t* q = o + (size_t)rep * d.N;
+        if (d.layout == PA_LAYOUT_INT8) {
+            std::memcpy(q, p, (size_t)d.N);
+        } else {
+            const uint32_t* w = (const uint32_t*)p;
+            for (int64_t s = 0; s < d.N; ++s) {
+                const int64_t row = s / d.L, x = s % d.L;
+                q[s] = ((w[row * NW + x / 32] >> (x % 32)) & 1u) ? (int8_t)-1 : (int8_t)1;
+            }
+        }
+    }
+    return PA_OK;
+}
+
+int pa_load(pa_run* r, int32_t what, const void* src, int64_t count, size_t bytes) {
+    if (!r || !src || count < 1 || count > (int64_t)r->d.cap) return PA_ERR_INVALID_ARG;
+    const RunDev& d = r->d;
+    if (what != PA_DUMP_SPINS && what != PA_DUMP_SPINS_RAW) return PA_ERR_INVALID_ARG;
+    const int64_t per = what == PA_DUMP_SPINS ? d.N : d.stride;
+    if ((int64_t)bytes < count * per) return PA_ERR_INVALID_ARG;
+    DevState st;
+    int rc = read_state(r, &st);
+    if (rc) return rc;
+    uint8_t* dst = d.spins[st.cur];
+    if (what == PA_DUMP_SPINS_RAW) {
+        CK(cudaMemcpyAsync(dst, src, (size_t)(count * d.stride), cudaMemcpyHostToDevice, r->stream));
+    } else {
+        std::vector<uint8_t> stage((size_t)(count * d.stride), 0);
+        const int8_t* in = (const int8_t*)src;
+        const int NW = (d.L + 31) / 32;
+        for (int64_t rep = 0; rep < count; ++rep) {
+            const int8_t* p = in + rep * d.N;
+            uint8_t* q = stage.data() + rep * d.stride;
+            if (d.layout == PA_LAYOUT_INT8) {
+                for (int64_t s2 = 0; s2 < d.N; ++s2) {
+                    if (p[s2] != 1 && p[s2] != -1) return PA_ERR_INVALID_ARG;
+                    q[s2] = (uint8_t)p[s2];
+                }
+            } else {
+                uint32_t* w = (uint32_t*)q;
+                for (int64_t s2 = 0; s2 < d.N; ++s2) {
+                    if (p[s2] != 1 && p[s2] != -1) return PA_ERR_INVALID_ARG;
+                    if (p[s2] < 0) w[(s2 / d.L) * NW + (s2 % d.L) / 32] |= 1u << ((s2 % d.L) % 32);
+                }
+            }
+        }
+        CK(cudaMemcpyAsync(dst, stage.data(), stage.size(), cudaMemcpyHostToDevice, r->stream));
+        CK(cudaStreamSynchronize(r->stream));
+    }
+    r->load_R = (uint32_t)count;
+    CK(cudaMemcpyAsync((uint8_t*)d.st + offsetof(DevState, R), &r->load_R, 4,
+                       cudaMemcpyHostToDevice, r->stream));
+    return enqueue_sweep(r, r->stream, 0);
+}
+
+int pa_profile(pa_run* r, int32_t enable) {
+    if (!r) return PA_ERR_INVALID_ARG;
+    r->prof = enable != 0;
+    return PA_OK;
+}
+
+int pa_profile_read(pa_run* r, int64_t launches[4], double ms[4], int32_t reset) {
+    if (!r) return PA_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(r->stream));
+    for (const auto& p : r->pending) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, p.a, p.b));
+        r->prof_n[p.kind] += 1;
+        r->prof_ms[p.kind] += t;
+        r->ev_pool.push_back(p.a);
+        r->ev_pool.push_back(p.b);
+    }
+    r->pending.clear();
+    for (int k = 0; k < 4; ++k) {
+        if (launches) launches[k] = r->prof_n[k];
+        if (ms) ms[k] = r->prof_ms[k];
+        if (reset) {
+            r->prof_n[k] = 0;
+            r->prof_ms[k] = 0.0;
+        }
+    }
+    return PA_OK;
+}
+
+void pa_free(pa_run* r) {
+    if (!r) return;
+    for (const auto& p : r->pending) {
+        r->ev_pool.push_back(p.a);
+        r->ev_pool.push_back(p.b);
+    }
+    for (cudaEvent_t e : r->ev_pool) cudaEventDestroy(e);
+    if (r->graph) cudaGraphExecDestroy(r->graph);
+    if (r->cap_stream) cudaStreamDestroy(r->cap_stream);
+    delete r;
+}
+
+const char* pa_strerror(int code) {
+    switch (code) {
+        case PA_OK: return "ok";
+        case PA_ERR_INVALID_ARG: return "invalid argument";
+        case PA_ERR_ODD_L: return "L must be even for the checkerboard update";
+        case PA_ERR_UNSUPPORTED: return "no compiled kernel for this (dim, L, layout)";
+        case PA_ERR_CAPACITY: return "population exceeded the configured capacity";
+        case PA_ERR_TIMEOUT: return "a bounded device-side wait gave up";
+        case PA_ERR_CUDA: return "CUDA runtime error";
+        case PA_ERR_WORKSPACE: return "workspace missing, too small or not 256-byte aligned";
+        case PA_ERR_DONE: return "annealing schedule already finished";
+        case PA_ERR_EMPTY: return "population died out";
+        case PA_ERR_INVARIANT: return "device invariant failed (histogram sum != R)";
+        default: return "unknown error";
+    }
+}
+
+}  // extern "C"

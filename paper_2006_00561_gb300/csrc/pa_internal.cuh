@@ -1,0 +1,121 @@
+// pa_internal.cuh -- device-side data of one population-annealing run and the
+// launchers the host engine (pa_engine.cu) calls.  Every array lives in the
+// caller's workspace; the kernels read the run's scalars (population size,
+// step index, buffer parity, sweep counter) from device memory, so a step can
+// be enqueued or replayed from a CUDA graph without any host round trip.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/pa.h"
+
+namespace pa {
+
+// Counter tags: top four bits of Philox counter word 3 (low 28 bits: instance).
+constexpr uint32_t TAG_INIT = 1u;
+constexpr uint32_t TAG_SWEEP = 2u;
+constexpr uint32_t TAG_RESAMPLE = 3u;
+constexpr uint32_t TAG_COUPLING = 4u;
+
+// Sticky status bits of DevState::status.
+constexpr uint32_t ST_CAPACITY = 1u;
+constexpr uint32_t ST_TIMEOUT = 2u;
+constexpr uint32_t ST_EMPTY = 4u;
+constexpr uint32_t ST_DONE = 8u;
+constexpr uint32_t ST_INVARIANT = 16u;
+
+// Scalars of a run, in device memory (first 256 bytes of the workspace).
+struct DevState {
+    uint32_t step;          // current beta index i
+    uint32_t R;             // current population size
+    uint32_t R_prev;        // population entering the last resample
+    uint32_t epoch;         // bumped by every reweight; tags lookback descriptors
+    uint32_t tile_counter;  // dynamic tile ids of the resample kernel
+    uint32_t status;        // sticky ST_* bits
+    uint32_t cur;           // population buffer holding the current replicas
+    uint32_t src;           // buffer the last resample read from
+    uint32_t sweep_base;    // global index of the next Metropolis sweep
+    uint32_t active;        // 1 if the reweight of this step succeeded
+    uint32_t kref;          // lowest occupied energy level at the last reweight
+    uint32_t negbonds;      // number of J = -1 bonds (U mod 2 = negbonds mod 2)
+    double lnQ, lnZ, S;
+    unsigned long long sweeps_done;
+    unsigned long long pad[3];
+};
+static_assert(sizeof(DevState) <= 256, "DevState must fit its slot");
+
+// Per-step record, same layout as pa_obs.
+static_assert(sizeof(pa_obs) == 104, "pa_obs layout");
+
+// Everything a kernel needs, passed by value.
+struct RunDev {
+    DevState* st;
+    uint8_t* spins[2];          // population buffers, cap_alloc * stride bytes each
+    uint32_t* ebin[2];          // energy level k = U >> 1 per replica
+    int32_t* mag[2];            // magnetisation per replica
+    uint32_t* counts;           // copy counts of the last resample
+    uint32_t* offsets;          // exclusive scan of the counts
+    unsigned long long* accum;  // [2] = sum |M|, sum M^2 of the running measurement
+    uint32_t* hist;             // [bins] energy histogram of the running measurement
+    uint32_t* tab_n;            // [bins] floor(tau_k)
+    uint32_t* tab_F;            // [bins] floor(frac(tau_k) * 2^32)
+    const uint32_t* thr;        // [(K+1)*4]: T0, T1, T2 (clamped to u32), bit c of [3] = T_c is 2^32
+    const double* dtab;         // [ndist * bins] Eq. 3 weights
+    const uint32_t* dsel;       // [K+1] weight table of step i
+    const double* beta;         // [K+1]
+    const double* dbeta;        // [K+1] beta_i - beta_{i-1}
+    unsigned long long* desc;   // [tiles] lookback descriptors
+    pa_obs* obs;                // [K+1] per-step records
+    uint32_t* jpk;              // packed couplings [dim][nwords] (bit set: J = -1), PMJ only
+    int8_t* j8;                 // int8 couplings [N][dim], PMJ only
+    uint64_t seed, coupling_seed;
+    uint32_t instance;          // instance id (< 2^28)
+    int32_t dim, L, layout, model, K;
+    int64_t N, bins;
+    uint32_t stride;            // bytes per replica (multiple of 16)
+    uint32_t nwords;            // packed: 32-bit words per replica
+    uint32_t cap;               // logical capacity
+    uint32_t cap_alloc;         // slots in each buffer
+    uint32_t R0;
+    uint32_t tiles;             // descriptors available
+};
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32
+// multiplies whose high halves are xored with the other words and the key;
+// the key advances by the two Weyl constants after every round.
+__device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                        uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t a = c0, b = c2;
+        const uint32_t hiA = __umulhi(0xD2511F53u, a), loA = 0xD2511F53u * a;
+        const uint32_t hiB = __umulhi(0xCD9E8D57u, b), loB = 0xCD9E8D57u * b;
+        c0 = hiB ^ c1 ^ k0;
+        c1 = loB;
+        c2 = hiA ^ c3 ^ k1;
+        c3 = loA;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+__device__ __forceinline__ uint32_t pick(const uint4& v, uint32_t j) {
+    return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
+}
+
+// ---- launchers (defined in the kernel translation units) ----------------
+bool sweep_supported(int layout, int dim, int L);
+cudaError_t launch_init(const RunDev& d, cudaStream_t s);
+cudaError_t launch_sweep(const RunDev& d, int nsweeps, int grid, cudaStream_t s);
+int sweep_grid(const RunDev& d);
+cudaError_t launch_tau(const RunDev& d, cudaStream_t s);
+cudaError_t launch_resample(const RunDev& d, cudaStream_t s);
+cudaError_t launch_obs(const RunDev& d, int nsweeps, cudaStream_t s);
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_ITEMS = 8;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
+
+}  // namespace pa

@@ -1,0 +1,359 @@
+// pa_resample.cu -- reweighting and resampling of the population (Sec. 2,
+// Eq. 3 and Eq. 4) and the per-step observables (Sec. 2, Eq. 5).
+//
+//  k_tau       one CTA: the energy histogram H of the population at beta_{i-1}
+//              gives kref (lowest occupied level), S = sum_k H_k D[k - kref]
+//              with D[j] = exp(-(beta_i - beta_{i-1}) 4 j), Q = S exp(-dbeta
+//              E(kref)) / R (Eq. 3) and the per-level weights
+//              tau_k = R0 D[k - kref] / S (Eq. 4, renormalised to R0), kept as
+//              n_k = floor(tau_k), F_k = floor(frac(tau_k) 2^32).
+//  k_resample  one pass over the population, one tile of RS_TILE replicas per
+//              CTA: copy counts r_j = n_k + [u_j < F_k] (nearest-integer rule),
+//              a single-pass exclusive scan with decoupled lookback across
+//              tiles, and the gather of r_j exact copies of replica j into slots
+//              o_j .. o_j + r_j - 1 of the other population buffer.
+//  k_obs       one CTA: exact integer sums over the histogram and the
+//              magnetisation accumulators, then the FP64 averages.
+//
+// Floating point: IEEE double with explicit _rn intrinsics (no contraction),
+// summed in a fixed order, so the tables are the same bits as any other
+// implementation of the same order; log() only feeds ln Q, never a decision.
+#include "pa_internal.cuh"
+
+namespace pa {
+namespace {
+
+constexpr unsigned long long DESC_AGG = 1ull;
+constexpr unsigned long long DESC_PREFIX = 2ull;
+constexpr unsigned LOOKBACK_SPIN_LIMIT = 1u << 22;
+
+__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long desc_make(unsigned long long flag, uint32_t epoch,
+                                                         uint32_t value) {
+    return (flag << 62) | ((unsigned long long)(epoch & 0x3fffffffu) << 32) | value;
+}
+
+__global__ void __launch_bounds__(256) k_tau(RunDev d) {
+    DevState* st = d.st;
+    __shared__ double part[256];
+    __shared__ uint32_t s_kref;
+    __shared__ unsigned long long s_sum;
+    const int t = threadIdx.x;
+    const uint32_t i = st->step + 1;
+    const uint32_t R = st->R;
+    const uint32_t bins = (uint32_t)d.bins;
+    if (i > (uint32_t)d.K || R == 0) {
+        if (t == 0) {
+            st->active = 0;
+            atomicOr(&st->status, i > (uint32_t)d.K ? ST_DONE : ST_EMPTY);
+        }
+        return;
+    }
+    if (t == 0) {
+        s_kref = 0xffffffffu;
+        s_sum = 0;
+    }
+    __syncthreads();
+    uint32_t kmin = 0xffffffffu;
+    unsigned long long hs = 0;
+    for (uint32_t k = t; k < bins; k += 256) {
+        const uint32_t h = d.hist[k];
+        if (h && k < kmin) kmin = k;
+        hs += h;
+    }
+    atomicMin(&s_kref, kmin);
+    atomicAdd(&s_sum, hs);
+    __syncthreads();
+    const uint32_t kref = s_kref;
+    const double* D = d.dtab + (size_t)d.dsel[i] * bins;
+    // S in the fixed order: 256 contiguous chunks summed left to right, then a
+    // pairwise tree over the chunk sums.
+    const uint32_t ch = (bins + 255) / 256;
+    double acc = 0.0;
+    for (uint32_t k = t * ch; k < (t + 1) * ch && k < bins; ++k)
+        if (k >= kref) acc = __dadd_rn(acc, __dmul_rn((double)d.hist[k], D[k - kref]));
+    part[t] = acc;
+    __syncthreads();
+    for (int w = 256; w > 1; w >>= 1) {
+        double v = 0.0;
+        if (t < w / 2) v = __dadd_rn(part[2 * t], part[2 * t + 1]);
+        __syncthreads();
+        if (t < w / 2) part[t] = v;
+        __syncthreads();
+    }
+    const double S = part[0];
+    const double R0d = (double)d.R0;
+    for (uint32_t k = t; k < bins; k += 256) {
+        uint32_t n = 0, F = 0;
+        if (k >= kref) {
+            const double tau = __ddiv_rn(__dmul_rn(R0d, D[k - kref]), S);
+            const double nk = floor(tau);
+            n = (uint32_t)nk;
+            F = (uint32_t)floor(__dmul_rn(__dsub_rn(tau, nk), 4294967296.0));
+        }
+        d.tab_n[k] = n;
+        d.tab_F[k] = F;
+    }
+    if (t == 0) {
+        if (s_sum != (unsigned long long)R) atomicOr(&st->status, ST_INVARIANT);
+        const long long parity = st->negbonds & 1u;
+        const long long Eref = 2 * (2 * (long long)kref + parity) - (long long)d.dim * d.N;
+        const double lnQ =
+            __dsub_rn(__dsub_rn(log(S), log((double)R)), __dmul_rn(d.dbeta[i], (double)Eref));
+        st->lnQ = lnQ;
+        st->lnZ = __dadd_rn(st->lnZ, lnQ);
+        st->S = S;
+        st->kref = kref;
+        st->step = i;
+        st->R_prev = R;
+        st->epoch = st->epoch + 1;
+        st->tile_counter = 0;
+        st->src = st->cur;
+        st->cur = st->cur ^ 1u;
+        st->active = 1;
+    }
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_resample(RunDev d) {
+    DevState* st = d.st;
+    __shared__ uint32_t s_r[RS_TILE];
+    __shared__ uint32_t s_o[RS_TILE];
+    __shared__ uint32_t s_warp[RS_THREADS / 32];
+    __shared__ uint32_t s_tile, s_excl;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    if (!st->active) return;
+    const uint32_t R = st->R_prev, epoch = st->epoch, src = st->src, step = st->step;
+    if (t == 0) s_tile = atomicAdd(&st->tile_counter, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const uint32_t base = tile * RS_TILE;
+    if (base >= R) return;
+    const uint32_t n_in = min((uint32_t)RS_TILE, R - base);
+
+    // copy counts, RS_ITEMS consecutive replicas per thread
+    const uint32_t* eb = d.ebin[src];
+    const uint32_t ctr3 = (TAG_RESAMPLE << 28) | d.instance;
+    const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
+    uint32_t r[RS_ITEMS];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int j0 = 0; j0 < RS_ITEMS; j0 += 4) {
+        const uint32_t i0 = base + (uint32_t)t * RS_ITEMS + j0;
+        uint4 u = make_uint4(0, 0, 0, 0);
+        if (i0 < R) u = philox(i0 >> 2, step, 0u, ctr3, k0, k1);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t i = i0 + j;
+            uint32_t v = 0;
+            if (i < R) {
+                const uint32_t k = eb[i];
+                v = d.tab_n[k] + (pick(u, (uint32_t)j) < d.tab_F[k] ? 1u : 0u);
+            }
+            r[j0 + j] = v;
+            sum += v;
+        }
+    }
+    // block-wide exclusive scan of the per-thread sums
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t w = lane < RS_THREADS / 32 ? s_warp[lane] : 0u;
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < RS_THREADS / 32) s_warp[lane] = wi - w;  // exclusive warp offsets
+        const uint32_t total = __shfl_sync(0xffffffffu, wi, RS_THREADS / 32 - 1);
+        // decoupled lookback across tiles (one thread)
+        if (lane == 0) {
+            uint32_t excl = 0;
+            if (tile == 0) {
+                st_release(&d.desc[0], desc_make(DESC_PREFIX, epoch, total));
+            } else {
+                st_release(&d.desc[tile], desc_make(DESC_AGG, epoch, total));
+                int p = (int)tile - 1;
+                for (;;) {
+                    unsigned long long v = 0;
+                    unsigned spins = 0;
+                    bool ok = false;
+                    for (;;) {
+                        v = ld_acquire(&d.desc[p]);
+                        if ((v >> 62) != 0 && ((v >> 32) & 0x3fffffffu) == (epoch & 0x3fffffffu)) {
+                            ok = true;
+                            break;
+                        }
+                        if (++spins >= LOOKBACK_SPIN_LIMIT) break;
+                        if (spins > 64) __nanosleep(64);
+                    }
+                    if (!ok) {
+                        atomicOr(&st->status, ST_TIMEOUT);
+                        break;
+                    }
+                    excl += (uint32_t)(v & 0xffffffffu);
+                    if ((v >> 62) == DESC_PREFIX || p == 0) break;
+                    --p;
+                }
+                st_release(&d.desc[tile], desc_make(DESC_PREFIX, epoch, excl + total));
+            }
+            s_excl = excl;
+        }
+    }
+    __syncthreads();
+    uint32_t o = s_excl + s_warp[wid] + (incl - sum);
+#pragma unroll
+    for (int j = 0; j < RS_ITEMS; ++j) {
+        const uint32_t li = (uint32_t)t * RS_ITEMS + j;
+        const uint32_t i = base + li;
+        if (i < R) {
+            s_r[li] = r[j];
+            s_o[li] = o;
+            d.counts[i] = r[j];
+            d.offsets[i] = o;
+            if (i == R - 1) {
+                const uint32_t Rnew = o + r[j];
+                if (Rnew > d.cap) atomicOr(&st->status, ST_CAPACITY);
+                if (Rnew == 0) atomicOr(&st->status, ST_EMPTY);
+                st->R = Rnew > d.cap ? d.cap : Rnew;
+            }
+        }
+        o += r[j];
+    }
+    __syncthreads();
+
+    // gather: 16-byte chunks, consecutive threads on consecutive chunks
+    const uint32_t CH = d.stride >> 4;
+    const uint4* srcp = reinterpret_cast<const uint4*>(d.spins[src]) + (size_t)base * CH;
+    uint4* dstp = reinterpret_cast<uint4*>(d.spins[src ^ 1u]);
+    const uint32_t items = n_in * CH;
+    const bool pow2 = (CH & (CH - 1)) == 0;
+    const int shift = __ffs(CH) - 1;
+    for (uint32_t it = t; it < items; it += RS_THREADS) {
+        const uint32_t li = pow2 ? (it >> shift) : (it / CH);
+        const uint32_t c = it - li * CH;
+        const uint32_t rr = s_r[li];
+        if (rr == 0) continue;
+        const uint32_t dst0 = s_o[li];
+        const uint4 v = srcp[(size_t)li * CH + c];
+        for (uint32_t k = 0; k < rr; ++k) {
+            const uint32_t dst = dst0 + k;
+            if (dst < d.cap) dstp[(size_t)dst * CH + c] = v;
+        }
+    }
+    const uint32_t* esrc = d.ebin[src] + base;
+    const int32_t* msrc = d.mag[src] + base;
+    uint32_t* edst = d.ebin[src ^ 1u];
+    int32_t* mdst = d.mag[src ^ 1u];
+    for (uint32_t li = t; li < n_in; li += RS_THREADS) {
+        const uint32_t rr = s_r[li];
+        if (rr == 0) continue;
+        const uint32_t e = esrc[li];
+        const int32_t m = msrc[li];
+        for (uint32_t k = 0; k < rr; ++k) {
+            const uint32_t dst = s_o[li] + k;
+            if (dst < d.cap) {
+                edst[dst] = e;
+                mdst[dst] = m;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(256) k_obs(RunDev d, int nsweeps) {
+    DevState* st = d.st;
+    __shared__ long long s_part[3][8];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const uint32_t step = st->step;
+    const long long parity = st->negbonds & 1u;
+    const long long dimN = (long long)d.dim * d.N;
+    long long cnt = 0, sE = 0, sE2 = 0;
+    for (uint32_t k = t; k < (uint32_t)d.bins; k += 256) {
+        const long long h = d.hist[k];
+        if (!h) continue;
+        const long long E = 2 * (2 * (long long)k + parity) - dimN;
+        cnt += h;
+        sE += h * E;
+        sE2 += h * E * E;
+    }
+    cnt = warp_sum_ll(cnt);
+    sE = warp_sum_ll(sE);
+    sE2 = warp_sum_ll(sE2);
+    if (lane == 0) {
+        s_part[0][wid] = cnt;
+        s_part[1][wid] = sE;
+        s_part[2][wid] = sE2;
+    }
+    __syncthreads();
+    if (t == 0) {
+        for (int w = 1; w < 8; ++w) {
+            cnt += s_part[0][w];
+            sE += s_part[1][w];
+            sE2 += s_part[2][w];
+        }
+        const uint32_t R = st->R;
+        if (cnt != (long long)R) atomicOr(&st->status, ST_INVARIANT);
+        pa_obs o;
+        o.step = step;
+        o.R = R;
+        o.sumE = sE;
+        o.sumE2 = sE2;
+        o.sumAbsM = (long long)d.accum[0];
+        o.sumM2 = (long long)d.accum[1];
+        o.beta = d.beta[step];
+        o.lnQ = st->lnQ;
+        o.lnZ = st->lnZ;
+        const double Rd = (double)R, Nd = (double)d.N;
+        const double mE = __ddiv_rn((double)o.sumE, Rd);
+        const double mE2 = __ddiv_rn((double)o.sumE2, Rd);
+        const double mA = __ddiv_rn((double)o.sumAbsM, Rd);
+        const double mM2 = __ddiv_rn((double)o.sumM2, Rd);
+        o.e = __ddiv_rn(mE, Nd);
+        o.cv = __ddiv_rn(__dmul_rn(__dmul_rn(o.beta, o.beta), __dsub_rn(mE2, __dmul_rn(mE, mE))), Nd);
+        o.m_abs = __ddiv_rn(mA, Nd);
+        o.chi = __ddiv_rn(__dmul_rn(o.beta, __dsub_rn(mM2, __dmul_rn(mA, mA))), Nd);
+        d.obs[step] = o;
+        st->sweep_base = st->sweep_base + (uint32_t)nsweeps;
+        st->sweeps_done = st->sweeps_done + (unsigned long long)nsweeps;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_tau(const RunDev& d, cudaStream_t s) {
+    k_tau<<<1, 256, 0, s>>>(d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resample(const RunDev& d, cudaStream_t s) {
+    k_resample<<<d.tiles, RS_THREADS, 0, s>>>(d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_obs(const RunDev& d, int nsweeps, cudaStream_t s) {
+    k_obs<<<1, 256, 0, s>>>(d, nsweeps);
+    return cudaGetLastError();
+}
+
+}  // namespace pa
