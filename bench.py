@@ -33,15 +33,17 @@ sys.path.insert(0, ROOT)
 METRIC = ("spin-flip attempts/ns + resampled replicas/s at R0=2^21; batched vs plain, 1 GB300")
 UNIT = "spin-flip attempts/ns"
 WORKLOAD = dict(dim=2, L=64, R0=1 << 21, K=400, theta=10, beta0=0.0, beta_max=1.0, seed=3)
-# Algorithmic integer work of one Metropolis attempt in the bit-sliced kernel
-# (32-bit ALU operations): a quarter of one Philox4x32-10 block (10 rounds of
-# 2 wide multiplies + 2 three-input xors = 40 per block, 4 sites per block)
-# = 10, threshold select + compare + flip-bit set = 3, and the site's share of
-# the bit-sliced neighbour count and class masks (~48 word operations per 32
-# sites of a colour) = 1.5.
-OPS_PER_ATTEMPT = 14.5
-# Issue peak of 32-bit integer lanes: 152 SMs x 4 schedulers x 32 lanes per
-# clock at the 2070 MHz maximum SM clock.
+# Algorithmic integer work of one Metropolis attempt, in 32-bit integer
+# operations (a three-input logic op counts one, a 32x32 -> 64 multiply two:
+# its high and low products):
+#   Philox4x32-10, 10 rounds x (2 multiplies = 4 + 2 three-input xors = 2)
+#     = 60 per block of 4 uniforms                                    -> 15.0
+#   acceptance: select the class threshold, compare, merge the bit     ->  3.0
+#   lattice: bit-sliced unsatisfied-bond count and class masks, ~48 word
+#     operations per 32 sites of one colour in a 64-site row          ->  1.5
+OPS_PER_ATTEMPT = 19.5
+# Integer issue peak: per SM and clock, 64 lanes on the ALU pipe plus 64 on
+# the FMA-heavy pipe (integer multiply-add), 152 SMs, 2070 MHz maximum clock.
 ALU_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12
 
 
@@ -333,7 +335,8 @@ def main():
                      "unit": "Tops/s (32-bit int)", "frac": achieved_tops / ALU_PEAK_TOPS,
                      "traffic": None, "kernel": "k_sweep (theta=10 sweeps + measurement)",
                      "ops_per_attempt": OPS_PER_ATTEMPT,
-                     "peak_note": "152 SMs x 128 int32 lanes x 2070 MHz (derived)"},
+                     "peak_note": "152 SMs x (64 ALU + 64 FMA-heavy) int32 lanes x 2070 MHz "
+                                  "(derived from unit counts and the maximum clock)"},
         "resample_roofline": {"bound": "hbm", "achieved": res_gbs, "peak": hbm, "unit": "GB/s",
                               "frac": res_gbs / hbm, "traffic": None,
                               "bytes_per_step": res_bytes,

@@ -330,6 +330,11 @@ int pa_init(const pa_config* cfg, void* ws, size_t bytes, void* stream, pa_run**
     }
     d.seed = cfg->seed;
     d.coupling_seed = cfg->coupling_seed;
+    d.one = 1u;
+    for (int k = 0; k < 10; ++k) {
+        d.rk0[k] = (uint32_t)cfg->seed + (uint32_t)k * 0x9E3779B9u;
+        d.rk1[k] = (uint32_t)(cfg->seed >> 32) + (uint32_t)k * 0xBB67AE85u;
+    }
     d.instance = (uint32_t)cfg->instance_id;
     d.dim = cfg->dim;
     d.L = cfg->L;

@@ -79,6 +79,8 @@ struct RunDev {
     uint32_t cap_alloc;         // slots in each buffer
     uint32_t R0;
     uint32_t tiles;             // descriptors available
+    uint32_t rk0[10], rk1[10];  // Philox round keys of `seed` (key + r * Weyl constant)
+    uint32_t one;               // the value 1, opaque to the compiler (multiply-add tests)
 };
 
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32
@@ -101,6 +103,23 @@ __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, u
     return make_uint4(c0, c1, c2, c3);
 }
 
+// Same generator with the ten round keys taken from precomputed tables (the
+// kernel-parameter copy of RunDev::rk0/rk1), so no key addition is issued.
+__device__ __forceinline__ uint4 philox_rk(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                           const uint32_t* rk0, const uint32_t* rk1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t a = c0, b = c2;
+        const uint32_t hiA = __umulhi(0xD2511F53u, a), loA = 0xD2511F53u * a;
+        const uint32_t hiB = __umulhi(0xCD9E8D57u, b), loB = 0xCD9E8D57u * b;
+        c0 = hiB ^ c1 ^ rk0[r];
+        c1 = loB;
+        c2 = hiA ^ c3 ^ rk1[r];
+        c3 = loA;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
 __device__ __forceinline__ uint32_t pick(const uint4& v, uint32_t j) {
     return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
 }
@@ -113,6 +132,10 @@ int sweep_grid(const RunDev& d);
 cudaError_t launch_tau(const RunDev& d, cudaStream_t s);
 cudaError_t launch_resample(const RunDev& d, cudaStream_t s);
 cudaError_t launch_obs(const RunDev& d, int nsweeps, cudaStream_t s);
+// specialised 2D ferromagnet, L = 64, packed (pa_sweep_l64.cu)
+bool l64_applies(const RunDev& d);
+int l64_grid(const RunDev& d);
+cudaError_t launch_sweep_l64(const RunDev& d, int nsweeps, int grid, cudaStream_t s);
 
 constexpr int RS_THREADS = 256;
 constexpr int RS_ITEMS = 8;

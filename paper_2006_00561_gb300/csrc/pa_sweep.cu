@@ -505,6 +505,7 @@ bool sweep_supported(int layout, int dim, int L) {
 }
 
 int sweep_grid(const RunDev& d) {
+    if (l64_applies(d)) return l64_grid(d);
     const KInfo k = find_kernel(d.layout, d.dim, d.L, d.model == PA_MODEL_PMJ);
     if (!k.fn) return 0;
     if (cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, k.smem) !=
@@ -523,6 +524,7 @@ int sweep_grid(const RunDev& d) {
 }
 
 cudaError_t launch_sweep(const RunDev& d, int nsweeps, int grid, cudaStream_t s) {
+    if (l64_applies(d)) return launch_sweep_l64(d, nsweeps, grid, s);
     const KInfo k = find_kernel(d.layout, d.dim, d.L, d.model == PA_MODEL_PMJ);
     if (!k.fn) return cudaErrorInvalidValue;
     RunDev dd = d;

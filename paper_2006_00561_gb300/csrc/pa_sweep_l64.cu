@@ -1,0 +1,314 @@
+// pa_sweep_l64.cu -- Metropolis sweeps of the 2D Ising ferromagnet (Eq. 6) at
+// L = 64, the workload of the paper's tests (Sec. 3 and 4), bit-packed one
+// 64-site row per 64-bit word.
+//
+// Same update rule and random numbers as the generic kernels of pa_sweep.cu
+// (checkerboard order, dE = 4 (2 - c_u), u = word h & 3 of the Philox block
+// (h >> 2, 2 g + colour, slot, SWEEP | instance), h = s >> 1, accept iff
+// dE <= 0 or u < T(beta_i, dE)), mapped for throughput:
+//   * one warp holds one replica for all theta sweeps, entirely in registers:
+//     lane l owns rows 2l and 2l+1 (one 16-byte load per lane, coalesced);
+//   * vertical neighbours come from the adjacent lanes by warp shuffle,
+//     horizontal ones by a 64-bit rotate; the unsatisfied-bond count of all
+//     64 sites of a row is evaluated bit-sliced (a handful of word ops);
+//   * a row holds 32 sites of each colour = 8 Philox blocks, each block
+//     covering 4 sites of that row, and both acceptance tests (dE = 4 and 8)
+//     are folded into two bit masks, so no shared memory and no atomics;
+//   * the Philox round keys come from the kernel parameters, and the products
+//     shared by all blocks of a half-sweep are formed once.
+// Grid-stride (persistent) over replicas; the population size is read from
+// device memory.  The measurement epilogue is the one of the generic kernel.
+#include "pa_internal.cuh"
+
+namespace pa {
+namespace {
+
+// Tuning knobs (compile time): warps per block, resident blocks per SM the
+// register budget is sized for, and which pipe evaluates the threshold tests u < T:
+//   PA_L64_CMP_MODE 0: both tests as compare + predicated OR (ALU pipe);
+//                   1: the dE = 4 test on the FMA pipe, dE = 8 on the ALU;
+//                   2: both on the FMA pipe;
+//                   3: the dE = 4 test of half of the blocks on the FMA pipe.
+// On the FMA pipe, u < T is the high word of the 32x32+64 multiply-add
+// u * 1 + (2^64 - T) (all ones iff no carry out, i.e. u < T), and the site's
+// bit is added to the mask by a second multiply-add with -(1 << bit).  The
+// Philox multiplies already load the FMA pipe and its xors the ALU pipe, so
+// moving the tests balances the two.
+#ifndef PA_L64_MIN_BLOCKS
+#define PA_L64_MIN_BLOCKS 1
+#endif
+#ifndef PA_L64_CMP_MODE
+#define PA_L64_CMP_MODE 3
+#endif
+
+#ifndef PA_L64_WARPS
+#define PA_L64_WARPS 16
+#endif
+constexpr int WARPS64 = PA_L64_WARPS;
+
+__device__ __forceinline__ uint64_t shfl64(uint64_t v, int src) {
+    const uint32_t lo = __shfl_sync(0xffffffffu, (uint32_t)v, src);
+    const uint32_t hi = __shfl_sync(0xffffffffu, (uint32_t)(v >> 32), src);
+    return ((uint64_t)hi << 32) | lo;
+}
+
+__device__ __forceinline__ uint32_t warp_sum(uint32_t v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Threshold of one energy class for the current step.
+struct Thr {
+    uint32_t T;       // threshold, u < T accepts
+    uint64_t cneg;    // 2^64 - T (0 when T = 0)
+};
+
+// acc + (u < T ? bit : 0), on the FMA pipe (see the knob comment).
+__device__ __forceinline__ uint32_t add_if_below_fma(uint32_t acc, uint32_t u, uint32_t one,
+                                                     uint64_t cneg, uint32_t negbit) {
+    uint64_t r;
+    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(r) : "r"(u), "r"(one), "l"(cneg));
+    uint32_t out;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(out) : "r"((uint32_t)(r >> 32)), "r"(negbit), "r"(acc));
+    return out;
+}
+
+template <bool FMA>
+__device__ __forceinline__ uint32_t add_if_below(uint32_t acc, uint32_t u, const Thr& t,
+                                                 uint32_t one, int bit) {
+    if constexpr (FMA) {
+        return add_if_below_fma(acc, u, one, t.cneg, 0u - (1u << bit));
+    } else {
+        return u < t.T ? (acc | (1u << bit)) : acc;
+    }
+}
+
+// Philox4x32-10 of the blocks (c0, c1, slot, ctr3) of one half-sweep.  Round 1
+// multiplies c0 and slot, round 2 multiplies the round-1 word built from slot
+// and c1 and the one built from c0: the slot/c1 products are the same for
+// every block of the half-sweep, so they are formed once (HalfSweepGen), and
+// M0 * c0 of consecutive blocks is one product plus multiples of M0.  Rounds
+// 3..10 are the plain rounds.  Same bits as philox_rk().
+constexpr uint32_t PM0 = 0xD2511F53u, PM1 = 0xCD9E8D57u;
+
+struct HalfSweepGen {
+    uint32_t x1k;   // round-1 word 1 (low product of slot) ^ round-2 key 0
+    uint32_t hiA2k; // high half of M0 * (round-1 word 0) ^ round-2 key 1
+    uint32_t loA2;  // low half of M0 * (round-1 word 0)
+    uint32_t c3k;   // counter word 3 ^ round-1 key 1
+};
+
+__device__ __forceinline__ HalfSweepGen half_sweep_gen(const RunDev& d, uint32_t c1, uint32_t slot,
+                                                      uint32_t ctr3) {
+    HalfSweepGen g;
+    const uint32_t x0 = __umulhi(PM1, slot) ^ c1 ^ d.rk0[0];
+    g.x1k = (PM1 * slot) ^ d.rk0[1];
+    g.hiA2k = __umulhi(PM0, x0) ^ d.rk1[1];
+    g.loA2 = PM0 * x0;
+    g.c3k = ctr3 ^ d.rk1[0];
+    return g;
+}
+
+// pA = M0 * c0 (64-bit) of the block.
+__device__ __forceinline__ uint4 philox_block(const RunDev& d, const HalfSweepGen& g, uint64_t pA) {
+    const uint32_t x2 = (uint32_t)(pA >> 32) ^ g.c3k;
+    const uint32_t x3 = (uint32_t)pA;
+    uint32_t c0 = __umulhi(PM1, x2) ^ g.x1k;
+    uint32_t c1 = PM1 * x2;
+    uint32_t c2 = g.hiA2k ^ x3;
+    uint32_t c3 = g.loA2;
+#pragma unroll
+    for (int r = 2; r < 10; ++r) {
+        const uint32_t a = c0, b = c2;
+        const uint32_t hiA = __umulhi(PM0, a), loA = PM0 * a;
+        const uint32_t hiB = __umulhi(PM1, b), loB = PM1 * b;
+        c0 = hiB ^ c1 ^ d.rk0[r];
+        c1 = loB;
+        c2 = hiA ^ c3 ^ d.rk1[r];
+        c3 = loA;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+// Acceptance masks of the 32 colour-c sites of row y, P = (y + c) & 1: sites
+// x = 8j + 2m + P take word m of Philox block 8y + j; bit x of a4 / a8 is set
+// when that uniform is below T4 / T8.  Four blocks per iteration fill one
+// 32-bit half of each mask.
+template <int P>
+__device__ __forceinline__ void row_accepts(const RunDev& d, const HalfSweepGen& gen, uint32_t y,
+                                            const Thr& t4, const Thr& t8, uint64_t& a4,
+                                            uint64_t& a8) {
+    const uint32_t one = d.one;
+    uint32_t h4[2], h8[2];
+#pragma unroll 1
+    for (uint32_t q = 0; q < 2; ++q) {
+        uint32_t k4 = 0, k8 = 0;
+        const uint64_t base = (uint64_t)PM0 * (8u * y + 4u * q);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const uint4 u = philox_block(d, gen, base + (uint64_t)PM0 * (uint64_t)h);
+            const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+            constexpr int M = PA_L64_CMP_MODE;
+            const bool f4 = M == 1 || M == 2 || (M == 3 && h < 2);
+            const bool f8 = M == 2;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const int bit = 8 * h + 2 * m + P;
+                k4 = f4 ? add_if_below<true>(k4, w[m], t4, one, bit)
+                        : add_if_below<false>(k4, w[m], t4, one, bit);
+                k8 = f8 ? add_if_below<true>(k8, w[m], t8, one, bit)
+                        : add_if_below<false>(k8, w[m], t8, one, bit);
+            }
+        }
+        if (q == 0) {
+            h4[0] = k4;
+            h8[0] = k8;
+        } else {
+            h4[1] = k4;
+            h8[1] = k8;
+        }
+    }
+    a4 = ((uint64_t)h4[1] << 32) | h4[0];
+    a8 = ((uint64_t)h8[1] << 32) | h8[0];
+}
+
+// Flip mask of the colour sites (parity P) of one row, given the rows above
+// and below.  c_u >= 2 flips outright (dE <= 0); c_u = 1 needs u < T4; c_u = 0
+// needs u < T8.  full bit 0 / 1: T4 / T8 equal 2^32 (beta = 0), always accept.
+template <int P>
+__device__ __forceinline__ uint64_t row_flips(const RunDev& d, const HalfSweepGen& gen,
+                                              uint64_t own, uint64_t up, uint64_t dn, uint32_t y,
+                                              const Thr& t4, const Thr& t8, uint32_t full) {
+    constexpr uint64_t cm = P ? 0xAAAAAAAAAAAAAAAAull : 0x5555555555555555ull;
+    uint64_t a4, a8;
+    row_accepts<P>(d, gen, y, t4, t8, a4, a8);
+    const uint64_t a = own ^ ((own >> 1) | (own << 63));  // bond to x + 1
+    const uint64_t b = own ^ ((own << 1) | (own >> 63));  // bond to x - 1
+    const uint64_t e = own ^ up;
+    const uint64_t f = own ^ dn;
+    const uint64_t s1 = a ^ b, s2 = e ^ f;
+    const uint64_t ge2 = (a & b) | (e & f) | (s1 & s2);
+    const uint64_t zero = ~(a | b | e | f);
+    const uint64_t one = (s1 ^ s2) & ~ge2;
+    if (full & 1u) a4 = ~0ull;
+    if (full & 2u) a8 = ~0ull;
+    return (ge2 | (one & a4) | (zero & a8)) & cm;
+}
+
+__device__ __forceinline__ void hist_flush(uint32_t* hist, uint32_t level, int n, int lane) {
+    if (n <= 0) return;
+    const unsigned valid = n >= 32 ? 0xffffffffu : ((1u << n) - 1u);
+    if (lane < n) {
+        const unsigned peers = __match_any_sync(valid, level);
+        if (lane == __ffs(peers) - 1) atomicAdd(&hist[level], (uint32_t)__popc(peers));
+    }
+}
+
+__global__ void __launch_bounds__(WARPS64 * 32, PA_L64_MIN_BLOCKS) k_sweep_l64(__grid_constant__ const RunDev d, int nsweeps) {
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    DevState* st = d.st;
+    const uint32_t R = st->R;
+    const uint32_t cur = st->cur;
+    const uint32_t step = st->step;
+    const uint32_t g0 = st->sweep_base;
+    Thr t4, t8;
+    t4.T = d.thr[step * 4 + 0];
+    t8.T = d.thr[step * 4 + 1];
+    t4.cneg = t4.T ? (0ull - (uint64_t)t4.T) : 0ull;
+    t8.cneg = t8.T ? (0ull - (uint64_t)t8.T) : 0ull;
+    const uint32_t full = d.thr[step * 4 + 3];
+    const uint32_t ctr3 = (TAG_SWEEP << 28) | d.instance;
+    const uint32_t ya = 2u * (uint32_t)lane, yb = ya + 1u;
+    const int lup = (lane + 31) & 31, ldn = (lane + 1) & 31;
+
+    const uint4* spins = reinterpret_cast<const uint4*>(d.spins[cur]);
+    uint4* spins_w = reinterpret_cast<uint4*>(d.spins[cur]);
+    uint32_t* ebin = d.ebin[cur];
+    int32_t* mag = d.mag[cur];
+
+    long long sumAbsM = 0, sumM2 = 0;
+    uint32_t mylevel = 0;
+    int nlev = 0;
+    const uint32_t nwarps = gridDim.x * WARPS64;
+    for (uint32_t slot = blockIdx.x * WARPS64 + wib; slot < R; slot += nwarps) {
+        const uint4 v = spins[(size_t)slot * 32 + lane];
+        uint64_t ra = ((uint64_t)v.y << 32) | v.x;  // row ya
+        uint64_t rb = ((uint64_t)v.w << 32) | v.z;  // row yb
+        for (int t = 0; t < nsweeps; ++t) {
+            const uint32_t g = g0 + (uint32_t)t;
+            {  // colour 0: even rows have parity 0, odd rows parity 1
+                const uint64_t up = shfl64(rb, lup);  // row ya - 1
+                const uint64_t dn = shfl64(ra, ldn);  // row yb + 1
+                const HalfSweepGen gen = half_sweep_gen(d, 2u * g, slot, ctr3);
+                const uint64_t fa = row_flips<0>(d, gen, ra, up, rb, ya, t4, t8, full);
+                const uint64_t fb = row_flips<1>(d, gen, rb, ra, dn, yb, t4, t8, full);
+                ra ^= fa;
+                rb ^= fb;
+            }
+            {  // colour 1
+                const uint64_t up = shfl64(rb, lup);
+                const uint64_t dn = shfl64(ra, ldn);
+                const HalfSweepGen gen = half_sweep_gen(d, 2u * g + 1u, slot, ctr3);
+                const uint64_t fa = row_flips<1>(d, gen, ra, up, rb, ya, t4, t8, full);
+                const uint64_t fb = row_flips<0>(d, gen, rb, ra, dn, yb, t4, t8, full);
+                ra ^= fa;
+                rb ^= fb;
+            }
+        }
+        // measurement: bonds to x + 1 and to y + 1 of both rows
+        const uint64_t dn = shfl64(ra, ldn);
+        uint32_t U = __popcll(ra ^ ((ra >> 1) | (ra << 63))) + __popcll(ra ^ rb) +
+                     __popcll(rb ^ ((rb >> 1) | (rb << 63))) + __popcll(rb ^ dn);
+        uint32_t down = __popcll(ra) + __popcll(rb);
+        U = warp_sum(U);
+        down = warp_sum(down);
+        const int M = 4096 - 2 * (int)down;
+        spins_w[(size_t)slot * 32 + lane] =
+            make_uint4((uint32_t)ra, (uint32_t)(ra >> 32), (uint32_t)rb, (uint32_t)(rb >> 32));
+        if (lane == 0) {
+            ebin[slot] = U >> 1;
+            mag[slot] = M;
+            if (U & 1u) atomicOr(&st->status, ST_INVARIANT);
+            sumAbsM += M < 0 ? -M : M;
+            sumM2 += (long long)M * M;
+        }
+        if (lane == nlev) mylevel = U >> 1;
+        if (++nlev == 32) {
+            hist_flush(d.hist, mylevel, 32, lane);
+            nlev = 0;
+        }
+    }
+    hist_flush(d.hist, mylevel, nlev, lane);
+    if (lane == 0 && (sumAbsM | sumM2)) {
+        atomicAdd(&d.accum[0], (unsigned long long)sumAbsM);
+        atomicAdd(&d.accum[1], (unsigned long long)sumM2);
+    }
+}
+
+}  // namespace
+
+bool l64_applies(const RunDev& d) {
+    return d.layout == PA_LAYOUT_PACKED && d.dim == 2 && d.L == 64 && d.model == PA_MODEL_FERRO &&
+           d.stride == 512;
+}
+
+int l64_grid(const RunDev& d) {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_l64, WARPS64 * 32, 0) !=
+        cudaSuccess)
+        return 0;
+    if (per_sm < 1) return 0;
+    const int64_t need = ((int64_t)d.cap + WARPS64 - 1) / WARPS64;
+    const int64_t full = (int64_t)sms * per_sm;
+    return (int)(need < full ? need : full);
+}
+
+cudaError_t launch_sweep_l64(const RunDev& d, int nsweeps, int grid, cudaStream_t s) {
+    k_sweep_l64<<<grid, WARPS64 * 32, 0, s>>>(d, nsweeps);
+    return cudaGetLastError();
+}
+
+}  // namespace pa
