@@ -205,6 +205,40 @@ int pa_load(pa_run* run, int32_t what, const void* host_src, int64_t count, size
 int pa_profile(pa_run* run, int32_t enable);
 int pa_profile_read(pa_run* run, int64_t launches[4], double ms[4], int32_t reset);
 
+/* ---- copy counts and scan without device allocation ---------------------
+ * The paper has no counterpart to this entry point: it exists for callers that
+ * cannot allocate device memory at all -- code that runs while a CUDA graph is
+ * being captured, plugins whose host process owns every allocation, embedded
+ * callers with a fixed memory budget -- and so cannot provide pa_init's
+ * workspace.
+ *
+ * For R replicas with energy levels d_ebin[0..R-1] (device memory) and the
+ * per-level tables d_tab_n / d_tab_F [bins] of a resample (as PA_DUMP_TAB_N /
+ * PA_DUMP_TAB_F give them), it writes the nearest-integer copy counts
+ * d_counts[i] = n[k] + [u_i < F[k]], their exclusive scan d_offsets[i], and
+ * the new population size *d_total, all in device memory, asynchronously on
+ * `stream`.  u_i is the resampling uniform of replica i at annealing step
+ * `step` under `seed` and `instance_id`, so the output equals the counts and
+ * offsets pa_resample computes for the same population.
+ *
+ * It allocates nothing: the scratch of its single-pass scan lives in a static
+ * device array of about 33 KB that every GPU loading this library holds until
+ * the process exits.  R may be at most PA_NOALLOC_MAX_REPLICAS; larger R (or a
+ * negative one, NULL pointers, bins < 1, a negative step or an instance id
+ * >= 2^28) returns PA_ERR_INVALID_ARG before anything is enqueued.
+ * The first call on each device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  Every call
+ * reuses the same array (the call clears what must start at zero), so two
+ * calls whose kernels overlap on the GPU -- on different streams, or from
+ * different threads -- race and give wrong results; serialise them.
+ * *d_total reads 0xFFFFFFFF if a level was >= bins (that replica counts 0
+ * copies) or if a bounded wait inside the scan gave up. */
+#define PA_NOALLOC_MAX_REPLICAS 8388608
+int pa_copy_counts_scan_noalloc(const uint32_t* d_ebin, int64_t R, const uint32_t* d_tab_n,
+                                const uint32_t* d_tab_F, int64_t bins, uint64_t seed,
+                                int32_t step, int32_t instance_id, uint32_t* d_counts,
+                                uint32_t* d_offsets, uint32_t* d_total, void* stream);
+
 /* Releases the host handle (and its CUDA graph).  The workspace stays the
  * caller's. */
 void pa_free(pa_run* run);

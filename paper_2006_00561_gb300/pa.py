@@ -32,8 +32,9 @@ EXPORTS = [
     "pa_workspace_size", "pa_init", "pa_resample", "pa_sweep", "pa_step", "pa_run_steps",
     "pa_observables", "pa_observables_history", "pa_status", "pa_dump_size", "pa_dump",
     "pa_dump_range", "pa_load", "pa_profile", "pa_profile_read",
-    "pa_tables", "pa_num_bins", "pa_free", "pa_strerror",
+    "pa_tables", "pa_num_bins", "pa_free", "pa_strerror", "pa_copy_counts_scan_noalloc",
 ]
+NOALLOC_MAX_REPLICAS = 8388608
 
 
 class PaError(RuntimeError):
@@ -118,6 +119,8 @@ def lib():
         L.pa_num_bins.restype = C.c_int64
         L.pa_free.argtypes = [vp]
         L.pa_free.restype = None
+        L.pa_copy_counts_scan_noalloc.argtypes = [vp, C.c_int64, vp, vp, C.c_int64, C.c_uint64,
+                                                   C.c_int32, C.c_int32, vp, vp, vp, vp]
         L.pa_strerror.argtypes = [C.c_int]
         L.pa_strerror.restype = C.c_char_p
         _lib = L
@@ -253,6 +256,17 @@ def pa_profile_read(h: int, reset: bool = True):
 def pa_free(h: int):
     if h:
         lib().pa_free(C.c_void_p(h))
+
+
+def pa_copy_counts_scan_noalloc(ebin_ptr: int, R: int, tab_n_ptr: int, tab_F_ptr: int, bins: int,
+                                seed: int, step: int, instance_id: int, counts_ptr: int,
+                                offsets_ptr: int, total_ptr: int, stream_handle: int):
+    """Copy counts + exclusive scan into caller-owned device buffers (device
+    pointers as ints); allocates nothing.  See include/pa.h."""
+    _check(lib().pa_copy_counts_scan_noalloc(
+        C.c_void_p(ebin_ptr), R, C.c_void_p(tab_n_ptr), C.c_void_p(tab_F_ptr), bins, seed, step,
+        instance_id, C.c_void_p(counts_ptr), C.c_void_p(offsets_ptr), C.c_void_p(total_ptr),
+        C.c_void_p(stream_handle)), "pa_copy_counts_scan_noalloc")
 
 
 # ---- convenience: a run that owns its torch workspace ------------------------
