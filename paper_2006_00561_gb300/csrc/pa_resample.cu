@@ -237,23 +237,36 @@ __global__ void __launch_bounds__(RS_THREADS) k_resample(RunDev d) {
     }
     __syncthreads();
 
-    // gather: 16-byte chunks, consecutive threads on consecutive chunks
+    // gather: 16-byte chunks, consecutive threads on consecutive chunks; GU
+    // independent loads in flight per thread before their stores
+    constexpr int GU = 4;
     const uint32_t CH = d.stride >> 4;
-    const uint4* srcp = reinterpret_cast<const uint4*>(d.spins[src]) + (size_t)base * CH;
-    uint4* dstp = reinterpret_cast<uint4*>(d.spins[src ^ 1u]);
+    const uint4* __restrict__ srcp = reinterpret_cast<const uint4*>(d.spins[src]) + (size_t)base * CH;
+    uint4* __restrict__ dstp = reinterpret_cast<uint4*>(d.spins[src ^ 1u]);
     const uint32_t items = n_in * CH;
     const bool pow2 = (CH & (CH - 1)) == 0;
     const int shift = __ffs(CH) - 1;
-    for (uint32_t it = t; it < items; it += RS_THREADS) {
-        const uint32_t li = pow2 ? (it >> shift) : (it / CH);
-        const uint32_t c = it - li * CH;
-        const uint32_t rr = s_r[li];
-        if (rr == 0) continue;
-        const uint32_t dst0 = s_o[li];
-        const uint4 v = srcp[(size_t)li * CH + c];
-        for (uint32_t k = 0; k < rr; ++k) {
-            const uint32_t dst = dst0 + k;
-            if (dst < d.cap) dstp[(size_t)dst * CH + c] = v;
+    for (uint32_t it0 = t; it0 < items; it0 += RS_THREADS * GU) {
+        uint4 v[GU];
+        uint32_t rr[GU], d0[GU], cc[GU];
+#pragma unroll
+        for (int u = 0; u < GU; ++u) {
+            const uint32_t it = it0 + (uint32_t)u * RS_THREADS;
+            rr[u] = 0;
+            if (it < items) {
+                const uint32_t li = pow2 ? (it >> shift) : (it / CH);
+                cc[u] = it - li * CH;
+                rr[u] = s_r[li];
+                d0[u] = s_o[li];
+                if (rr[u]) v[u] = __ldg(srcp + (size_t)li * CH + cc[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < GU; ++u) {
+            for (uint32_t k = 0; k < rr[u]; ++k) {
+                const uint32_t dst = d0[u] + k;
+                if (dst < d.cap) __stcs(dstp + (size_t)dst * CH + cc[u], v[u]);
+            }
         }
     }
     const uint32_t* esrc = d.ebin[src] + base;

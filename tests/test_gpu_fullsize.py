@@ -1,0 +1,104 @@
+"""Parity at the benchmark sizes, in the launch configuration bench.py times.
+
+2D Ising L = 64 bit-packed with R0 = 2^21 (the paper-scale population, two
+1 GiB buffers) and R0 = 2^17.  After every checked step:
+  * reweight, on the whole population: tau tables (n, F), kref and S of
+    Eq. 3 / 4 recomputed by the oracle from the dumped histogram;
+  * copy counts and offsets of every replica, recomputed by the oracle from
+    the dumped energy levels (bit for bit), and the new population size;
+  * gather: sampled output slots hold exact copies of their source replica;
+  * sweep: theta = 10 Metropolis sweeps of sampled replicas recomputed by the
+    oracle from their dumped pre-sweep state (each replica's sweep is a pure
+    function of its state, slot, sweep index and beta);
+  * measurement: histogram == bincount(levels), integer observables == the
+    sums over the dumped levels and magnetisations.
+Graph-replayed steps (pa_run_steps) run between the checked ones.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2006_00561_gb300 import build as B
+    B.build()
+    from paper_2006_00561_gb300 import pa
+    return pa
+
+
+def check_step(P, run, ocfg, rng, nsample=48):
+    N = 4096
+    st0 = run.state()
+    R_prev = st0["R"]
+    ebin = run.dump(P.DUMP_EBIN)
+    mag = run.dump(P.DUMP_MAG)
+    hist = run.dump(P.DUMP_HIST)
+    assert np.array_equal(hist, np.bincount(ebin, minlength=st0["bins"]))
+    obs = run.observables()
+    E = 2 * (2 * ebin.astype(np.int64)) - 2 * N
+    assert obs["sumE"] == E.sum() and obs["sumE2"] == (E * E).sum()
+    assert obs["sumAbsM"] == np.abs(mag.astype(np.int64)).sum()
+    assert obs["sumM2"] == (mag.astype(np.int64) ** 2).sum()
+    src_sample = rng.choice(R_prev, size=nsample, replace=False)
+    pre_src = {int(i): run.dump_range(P.DUMP_SPINS_RAW, int(i), 1)[0] for i in src_sample}
+
+    run.resample()
+    st = run.state()
+    assert st["status_bits"] == 0
+    step = st["step"]
+    Dtab = np.array([O.weight(O.beta(ocfg, step) - O.beta(ocfg, step - 1), j)
+                     for j in range(st["bins"])])
+    S, kref, n, F = O.tau_table(hist, Dtab, ocfg.R0)
+    assert st["kref"] == kref and st["S"] == S
+    assert np.array_equal(run.dump(P.DUMP_TAB_N), n)
+    assert np.array_equal(run.dump(P.DUMP_TAB_F), F)
+    counts = run.dump(P.DUMP_COUNTS)
+    assert np.array_equal(counts, O.copy_counts(ocfg, step, ebin, n, F))
+    offsets = run.dump(P.DUMP_OFFSETS)
+    csum = np.cumsum(counts.astype(np.int64))
+    assert np.array_equal(offsets.astype(np.int64), csum - counts)
+    assert st["R"] == csum[-1]
+    # gather: output slots copy their sources
+    for i in src_sample:
+        i = int(i)
+        for k in range(int(counts[i])):
+            got = run.dump_range(P.DUMP_SPINS_RAW, int(offsets[i]) + k, 1)[0]
+            assert np.array_equal(got, pre_src[i])
+    # sweep of sampled replicas
+    R = st["R"]
+    slots = rng.choice(R, size=nsample, replace=False)
+    pre = {int(s): run.dump_range(P.DUMP_SPINS, int(s), 1)[0].copy() for s in slots}
+    g0 = st["sweeps_done"]
+    run.sweep(ocfg.theta)
+    T = [O.threshold(O.beta(ocfg, step), 4 * (c + 1)) for c in range(3)]
+    J = np.ones(2 * N, dtype=np.int8)
+    for s, spins in pre.items():
+        O.sweep_replica(ocfg, J, spins, s, g0, ocfg.theta, T)
+        assert np.array_equal(run.dump_range(P.DUMP_SPINS, s, 1)[0], spins), (step, s)
+    assert run.status() == 0
+
+
+@pytest.mark.parametrize("R0,seed,checks", [(1 << 21, 3, 3), (1 << 17, 2, 4)])
+def test_fullsize_parity(P, R0, seed, checks):
+    K = 400 if R0 == 1 << 21 else 200
+    ocfg = O.make_config(dim=2, L=64, R0=R0, K=K, theta=10, seed=seed)
+    run = P.Run(P.make_config(dim=2, L=64, layout=P.LAYOUT_PACKED, R0=R0, K=K, theta=10,
+                              seed=seed))
+    rng = np.random.default_rng(R0)
+    # initial population: sampled replicas equal the oracle's uniform init
+    for s in rng.choice(R0, size=16, replace=False):
+        assert np.array_equal(run.dump_range(P.DUMP_SPINS, int(s), 1)[0],
+                              O.init_replica(ocfg, int(s)))
+    for c in range(checks):
+        check_step(P, run, ocfg, rng)
+        run.run_steps(2 + 3 * c)
+        assert run.status() == 0
+    st = run.state()
+    assert abs(st["R"] - R0) < 5 * np.sqrt(R0)
+    run.close()
