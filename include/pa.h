@@ -205,6 +205,37 @@ int pa_load(pa_run* run, int32_t what, const void* host_src, int64_t count, size
 int pa_profile(pa_run* run, int32_t enable);
 int pa_profile_read(pa_run* run, int64_t launches[4], double ms[4], int32_t reset);
 
+/* ---- batched form ---------------------------------------------------------
+ * Many independent runs (for example a disorder ensemble of +-J instances of
+ * mixed L and R0) advanced together: one step of every run costs one launch
+ * per phase -- reweight (one CTA per run), resample (one global tile space in
+ * which each run's tiles are claimed in order), one sweep launch per class of
+ * runs sharing (layout, dim, L, model), observables (one CTA per run) --
+ * instead of four launches per run.  Every run gives exactly the bits it gives
+ * when stepped alone with pa_step.  The runs keep their own workspaces; the
+ * batch holds only their descriptors, in a workspace of
+ * pa_batch_workspace_size(nruns) bytes.  While a batch steps its runs, do not
+ * call pa_step/pa_sweep/pa_resample on them; pa_batch_sync() waits for the
+ * batch stream and returns the first sticky error of any run, after which the
+ * per-run read calls (pa_observables, pa_dump, ...) see the batch's results. */
+typedef struct pa_batch pa_batch;
+size_t pa_batch_workspace_size(int32_t nruns);
+int pa_batch_init(pa_run* const* runs, int32_t nruns, void* dev_workspace, size_t bytes,
+                  void* stream, pa_batch** out);
+/* One annealing step of every run (PA_ERR_DONE once any run reached K). */
+int pa_batch_step(pa_batch* batch);
+/* nsteps steps replayed from a CUDA graph of one batched step. */
+int pa_batch_run_steps(pa_batch* batch, int32_t nsteps);
+int pa_batch_sync(pa_batch* batch);
+/* Sweep classes and their launch shape: info = {layout, dim, L, model,
+ * number of runs, warps per block, slots}.  pa_batch_set_warps chooses the
+ * warps per block (2, 4 or 8; the L = 64 register kernel has 16 only) of one
+ * class; results do not depend on it. */
+int pa_batch_num_classes(pa_batch* batch);
+int pa_batch_class_info(pa_batch* batch, int32_t cls, int32_t info[7]);
+int pa_batch_set_warps(pa_batch* batch, int32_t cls, int32_t warps);
+void pa_batch_free(pa_batch* batch);
+
 /* ---- copy counts and scan without device allocation ---------------------
  * The paper has no counterpart to this entry point: it exists for callers that
  * cannot allocate device memory at all -- code that runs while a CUDA graph is

@@ -7,6 +7,7 @@
 // allocates device memory.
 #include <cmath>
 #include <cstddef>
+#include <cstdint>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -331,6 +332,7 @@ int pa_init(const pa_config* cfg, void* ws, size_t bytes, void* stream, pa_run**
     d.seed = cfg->seed;
     d.coupling_seed = cfg->coupling_seed;
     d.one = 1u;
+    d.theta = cfg->theta;
     for (int k = 0; k < 10; ++k) {
         d.rk0[k] = (uint32_t)cfg->seed + (uint32_t)k * 0x9E3779B9u;
         d.rk1[k] = (uint32_t)(cfg->seed >> 32) + (uint32_t)k * 0xBB67AE85u;
@@ -709,6 +711,256 @@ const char* pa_strerror(int code) {
         case PA_ERR_INVARIANT: return "device invariant failed (histogram sum != R)";
         default: return "unknown error";
     }
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched form
+// ---------------------------------------------------------------------------
+struct pa_batch {
+    std::vector<pa_run*> runs;
+    cudaStream_t stream;
+    pa::BatchDev bd;
+    struct Cls {
+        int layout, dim, L, model;
+        std::vector<uint32_t> ids;
+        pa::BatchSweepArgs args;
+        pa::RunDev proto;
+        int warps, grid;
+    };
+    std::vector<Cls> cls;
+    cudaStream_t cap_stream;
+    cudaGraphExec_t graph;
+    int64_t steps_left;
+};
+
+namespace {
+size_t batch_layout(int32_t nruns, size_t off[5]) {
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = align_up(o + bytes);
+        return at;
+    };
+    off[0] = take((size_t)nruns * sizeof(pa::RunDev));     // runs
+    off[1] = take((size_t)(nruns + 1) * 4);                 // tile_base
+    off[2] = take((size_t)(nruns + 1) * 4);                 // counters
+    off[3] = take((size_t)nruns * 4);                       // run ids by class
+    off[4] = take((size_t)(2 * nruns) * 4);                 // slot bases
+    return o;
+}
+
+int enqueue_batch_step(pa_batch* b, cudaStream_t s) {
+    CK(pa::launch_tau_batched(b->bd, s));
+    CK(pa::launch_resample_batched(b->bd, s));
+    for (const auto& c : b->cls) CK(pa::launch_sweep_batched(c.args, c.proto, c.warps, c.grid, s));
+    CK(pa::launch_obs_batched(b->bd, s));
+    return PA_OK;
+}
+}  // namespace
+
+extern "C" {
+
+size_t pa_batch_workspace_size(int32_t nruns) {
+    if (nruns < 1) return 0;
+    size_t off[5];
+    return batch_layout(nruns, off);
+}
+
+int pa_batch_init(pa_run* const* runs, int32_t nruns, void* ws, size_t bytes, void* stream,
+                  pa_batch** out) {
+    if (!out || !runs || nruns < 1) return PA_ERR_INVALID_ARG;
+    *out = nullptr;
+    size_t off[5];
+    const size_t need = batch_layout(nruns, off);
+    if (!ws || ((uintptr_t)ws % ALIGN) != 0 || bytes < need) return PA_ERR_WORKSPACE;
+    pa_batch* b = new (std::nothrow) pa_batch();
+    if (!b) return PA_ERR_INVALID_ARG;
+    b->stream = (cudaStream_t)stream;
+    b->cap_stream = nullptr;
+    b->graph = nullptr;
+    b->steps_left = INT64_MAX;
+    std::vector<pa::RunDev> h_runs;
+    std::vector<uint32_t> tile_base(1, 0u);
+    for (int32_t i = 0; i < nruns; ++i) {
+        pa_run* r = runs[i];
+        if (!r) {
+            delete b;
+            return PA_ERR_INVALID_ARG;
+        }
+        for (int32_t j = 0; j < i; ++j)
+            if (runs[j] == r) {
+                delete b;
+                return PA_ERR_INVALID_ARG;
+            }
+        DevState st;
+        if (read_state(r, &st) != PA_OK) {
+            delete b;
+            return PA_ERR_CUDA;
+        }
+        const int64_t left = (int64_t)r->cfg.K - (int64_t)st.step;
+        if (left < b->steps_left) b->steps_left = left;
+        b->runs.push_back(r);
+        h_runs.push_back(r->d);
+        tile_base.push_back(tile_base.back() + r->d.tiles);
+    }
+    // classes: one sweep kernel instantiation per (layout, dim, L, model)
+    for (int32_t i = 0; i < nruns; ++i) {
+        const pa::RunDev& d = h_runs[i];
+        size_t c = 0;
+        while (c < b->cls.size() &&
+               !(b->cls[c].layout == d.layout && b->cls[c].dim == d.dim && b->cls[c].L == d.L &&
+                 b->cls[c].model == d.model))
+            ++c;
+        if (c == b->cls.size()) {
+            pa_batch::Cls k;
+            k.layout = d.layout;
+            k.dim = d.dim;
+            k.L = d.L;
+            k.model = d.model;
+            k.proto = d;
+            k.warps = pa::l64_batched_applies(d) ? 16 : 4;
+            b->cls.push_back(k);
+        }
+        b->cls[c].ids.push_back((uint32_t)i);
+    }
+    std::vector<uint32_t> ids, bases;
+    uint8_t* base = (uint8_t*)ws;
+    pa::RunDev* d_runs = (pa::RunDev*)(base + off[0]);
+    uint32_t* d_tile_base = (uint32_t*)(base + off[1]);
+    uint32_t* d_counters = (uint32_t*)(base + off[2]);
+    uint32_t* d_ids = (uint32_t*)(base + off[3]);
+    uint32_t* d_bases = (uint32_t*)(base + off[4]);
+    for (size_t c = 0; c < b->cls.size(); ++c) {
+        auto& k = b->cls[c];
+        const size_t id0 = ids.size(), base0 = bases.size();
+        uint32_t slots = 0;
+        for (uint32_t i : k.ids) {
+            ids.push_back(i);
+            bases.push_back(slots);
+            slots += (h_runs[i].cap + 31u) / 32u * 32u;
+        }
+        bases.push_back(slots);
+        k.args.runs = d_runs;
+        k.args.run_ids = d_ids + id0;
+        k.args.slot_base = d_bases + base0;
+        k.args.n = (uint32_t)k.ids.size();
+        k.args.total_slots = slots;
+        k.args.counter = d_counters + 1 + c;
+        k.grid = pa::batched_sweep_grid(k.proto, k.warps);
+        if (k.grid <= 0) {
+            delete b;
+            return PA_ERR_CUDA;
+        }
+    }
+    b->bd.runs = d_runs;
+    b->bd.nruns = (uint32_t)nruns;
+    b->bd.tile_base = d_tile_base;
+    b->bd.total_tiles = tile_base.back();
+    b->bd.counters = d_counters;
+    b->bd.ncounters = (uint32_t)(1 + b->cls.size());
+    cudaStream_t s = b->stream;
+    const bool ok =
+        cudaMemcpyAsync(d_runs, h_runs.data(), h_runs.size() * sizeof(pa::RunDev),
+                        cudaMemcpyHostToDevice, s) == cudaSuccess &&
+        cudaMemcpyAsync(d_tile_base, tile_base.data(), tile_base.size() * 4, cudaMemcpyHostToDevice,
+                        s) == cudaSuccess &&
+        cudaMemsetAsync(d_counters, 0, (size_t)(nruns + 1) * 4, s) == cudaSuccess &&
+        cudaMemcpyAsync(d_ids, ids.data(), ids.size() * 4, cudaMemcpyHostToDevice, s) ==
+            cudaSuccess &&
+        cudaMemcpyAsync(d_bases, bases.data(), bases.size() * 4, cudaMemcpyHostToDevice, s) ==
+            cudaSuccess &&
+        cudaStreamSynchronize(s) == cudaSuccess;
+    if (!ok) {
+        delete b;
+        return PA_ERR_CUDA;
+    }
+    *out = b;
+    return PA_OK;
+}
+
+int pa_batch_step(pa_batch* b) {
+    if (!b) return PA_ERR_INVALID_ARG;
+    if (b->steps_left <= 0) return PA_ERR_DONE;
+    const int rc = enqueue_batch_step(b, b->stream);
+    if (rc == PA_OK) --b->steps_left;
+    return rc;
+}
+
+int pa_batch_run_steps(pa_batch* b, int32_t nsteps) {
+    if (!b || nsteps < 0) return PA_ERR_INVALID_ARG;
+    if (nsteps > b->steps_left) return PA_ERR_DONE;
+    if (!b->graph) {
+        if (!b->cap_stream) CK(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+        CK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+        const int rc = enqueue_batch_step(b, b->cap_stream);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
+        if (rc || e != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            return rc ? rc : PA_ERR_CUDA;
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) {
+            b->graph = nullptr;
+            return PA_ERR_CUDA;
+        }
+    }
+    for (int32_t i = 0; i < nsteps; ++i) CK(cudaGraphLaunch(b->graph, b->stream));
+    b->steps_left -= nsteps;
+    return PA_OK;
+}
+
+int pa_batch_sync(pa_batch* b) {
+    if (!b) return PA_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(b->stream));
+    int worst = PA_OK;
+    for (pa_run* r : b->runs) {
+        const int rc = pa_status(r);
+        if (rc != PA_OK && worst == PA_OK) worst = rc;
+    }
+    return worst;
+}
+
+int pa_batch_num_classes(pa_batch* b) { return b ? (int)b->cls.size() : PA_ERR_INVALID_ARG; }
+
+int pa_batch_class_info(pa_batch* b, int32_t c, int32_t info[7]) {
+    if (!b || !info || c < 0 || c >= (int32_t)b->cls.size()) return PA_ERR_INVALID_ARG;
+    const auto& k = b->cls[c];
+    info[0] = k.layout;
+    info[1] = k.dim;
+    info[2] = k.L;
+    info[3] = k.model;
+    info[4] = (int32_t)k.ids.size();
+    info[5] = k.warps;
+    info[6] = (int32_t)k.args.total_slots;
+    return PA_OK;
+}
+
+int pa_batch_set_warps(pa_batch* b, int32_t c, int32_t warps) {
+    if (!b || c < 0 || c >= (int32_t)b->cls.size()) return PA_ERR_INVALID_ARG;
+    auto& k = b->cls[c];
+    if (pa::l64_batched_applies(k.proto)) return warps == 16 ? PA_OK : PA_ERR_INVALID_ARG;
+    if (warps != 2 && warps != 4 && warps != 8) return PA_ERR_INVALID_ARG;
+    if (!pa::batched_warps_valid(k.proto, warps)) return PA_ERR_INVALID_ARG;
+    const int grid = pa::batched_sweep_grid(k.proto, warps);
+    if (grid <= 0) return PA_ERR_CUDA;
+    k.warps = warps;
+    k.grid = grid;
+    if (b->graph) {  // the captured step used the old shape
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    return PA_OK;
+}
+
+void pa_batch_free(pa_batch* b) {
+    if (!b) return;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    delete b;
 }
 
 }  // extern "C"

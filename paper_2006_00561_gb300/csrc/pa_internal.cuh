@@ -81,6 +81,31 @@ struct RunDev {
     uint32_t tiles;             // descriptors available
     uint32_t rk0[10], rk1[10];  // Philox round keys of `seed` (key + r * Weyl constant)
     uint32_t one;               // the value 1, opaque to the compiler (multiply-add tests)
+    int32_t theta;              // sweeps per annealing step
+};
+
+// A batch of runs stepped together (pa_batch_* in include/pa.h).  Arrays in
+// the batch workspace; counters are cleared by the batched reweight kernel at
+// the start of every step.
+struct BatchDev {
+    const RunDev* runs;          // [nruns]
+    uint32_t nruns;
+    const uint32_t* tile_base;   // [nruns + 1] prefix sums of each run's resample tiles
+    uint32_t total_tiles;
+    uint32_t* counters;          // [0]: resample tiles, [1 + c]: sweep chunks of class c
+    uint32_t ncounters;
+};
+
+// One (layout, dim, L, model) class of a batch: the runs one sweep kernel
+// instantiation serves.  Global slot g of the class lies in run run_ids[j]
+// when slot_base[j] <= g < slot_base[j + 1] (capacities rounded up to 32).
+struct BatchSweepArgs {
+    const RunDev* runs;
+    const uint32_t* run_ids;     // [n]
+    const uint32_t* slot_base;   // [n + 1]
+    uint32_t n;
+    uint32_t total_slots;
+    uint32_t* counter;           // chunk counter of this class
 };
 
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32
@@ -136,6 +161,20 @@ cudaError_t launch_obs(const RunDev& d, int nsweeps, cudaStream_t s);
 bool l64_applies(const RunDev& d);
 int l64_grid(const RunDev& d);
 cudaError_t launch_sweep_l64(const RunDev& d, int nsweeps, int grid, cudaStream_t s);
+// batched forms (one launch for every run of a batch, or of one class)
+cudaError_t launch_tau_batched(const BatchDev& b, cudaStream_t s);
+cudaError_t launch_resample_batched(const BatchDev& b, cudaStream_t s);
+cudaError_t launch_obs_batched(const BatchDev& b, cudaStream_t s);
+// sweep of one class; `warps` selects the block shape (an autotuned knob:
+// 2, 4 or 8 warps per block for the shared-memory kernels; the L = 64
+// register kernel has one shape), grid 0 = one wave of resident blocks
+cudaError_t launch_sweep_batched(const BatchSweepArgs& a, const RunDev& proto, int warps, int grid,
+                                 cudaStream_t s);
+int batched_sweep_grid(const RunDev& proto, int warps);
+bool batched_warps_valid(const RunDev& proto, int warps);
+bool l64_batched_applies(const RunDev& proto);
+cudaError_t launch_sweep_l64_batched(const BatchSweepArgs& a, int grid, cudaStream_t s);
+int l64_batched_grid();
 
 constexpr int RS_THREADS = 256;
 constexpr int RS_ITEMS = 8;

@@ -42,7 +42,9 @@ __device__ __forceinline__ unsigned long long desc_make(unsigned long long flag,
     return (flag << 62) | ((unsigned long long)(epoch & 0x3fffffffu) << 32) | value;
 }
 
-__global__ void __launch_bounds__(256) k_tau(RunDev d) {
+// Reweight of one run by one 256-thread CTA (plain: k_tau, batched: one CTA
+// per run of k_tau_batched).
+__device__ __forceinline__ void tau_run(const RunDev& d) {
     DevState* st = d.st;
     __shared__ double part[256];
     __shared__ uint32_t s_kref;
@@ -123,18 +125,36 @@ __global__ void __launch_bounds__(256) k_tau(RunDev d) {
     }
 }
 
-__global__ void __launch_bounds__(RS_THREADS) k_resample(RunDev d) {
-    DevState* st = d.st;
-    __shared__ uint32_t s_r[RS_TILE];
-    __shared__ uint32_t s_o[RS_TILE];
-    __shared__ uint32_t s_warp[RS_THREADS / 32];
-    __shared__ uint32_t s_tile, s_excl;
-    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    if (!st->active) return;
-    const uint32_t R = st->R_prev, epoch = st->epoch, src = st->src, step = st->step;
-    if (t == 0) s_tile = atomicAdd(&st->tile_counter, 1u);
+__global__ void __launch_bounds__(256) k_tau(RunDev d) { tau_run(d); }
+
+// Batched reweight: CTA r handles run r, then clears that run's histogram and
+// magnetisation sums for the coming sweep (the reweight is their last
+// reader); CTA 0 clears the batch's work counters.
+__global__ void __launch_bounds__(256) k_tau_batched(BatchDev b) {
+    if (blockIdx.x == 0 && threadIdx.x < b.ncounters) b.counters[threadIdx.x] = 0u;
+    const RunDev& d = b.runs[blockIdx.x];
+    tau_run(d);
     __syncthreads();
-    const uint32_t tile = s_tile;
+    for (uint32_t k = threadIdx.x; k < (uint32_t)d.bins; k += blockDim.x) d.hist[k] = 0u;
+    if (threadIdx.x < 2) d.accum[threadIdx.x] = 0ull;
+}
+
+struct ResampleSmem {
+    uint32_t r[RS_TILE];
+    uint32_t o[RS_TILE];
+    uint32_t warp[RS_THREADS / 32];
+    uint32_t tile, excl;
+};
+
+// Counts, scan and gather of tile `tile` of one run (all threads of the CTA).
+__device__ __forceinline__ void resample_tile(const RunDev& d, uint32_t tile, ResampleSmem& sm) {
+    DevState* st = d.st;
+    uint32_t* s_r = sm.r;
+    uint32_t* s_o = sm.o;
+    uint32_t* s_warp = sm.warp;
+    uint32_t& s_excl = sm.excl;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const uint32_t R = st->R_prev, epoch = st->epoch, src = st->src, step = st->step;
     const uint32_t base = tile * RS_TILE;
     if (base >= R) return;
     const uint32_t n_in = min((uint32_t)RS_TILE, R - base);
@@ -288,13 +308,44 @@ __global__ void __launch_bounds__(RS_THREADS) k_resample(RunDev d) {
     }
 }
 
+__global__ void __launch_bounds__(RS_THREADS) k_resample(RunDev d) {
+    __shared__ ResampleSmem sm;
+    if (!d.st->active) return;
+    if (threadIdx.x == 0) sm.tile = atomicAdd(&d.st->tile_counter, 1u);
+    __syncthreads();
+    resample_tile(d, sm.tile, sm);
+}
+
+// Batched: global tile ids are claimed in increasing order; run r owns ids
+// tile_base[r] .. tile_base[r+1]-1, so within a run tiles are claimed in order
+// and the lookback only ever waits on tiles already running.
+__global__ void __launch_bounds__(RS_THREADS) k_resample_batched(BatchDev b) {
+    __shared__ ResampleSmem sm;
+    __shared__ uint32_t s_run;
+    if (threadIdx.x == 0) {
+        const uint32_t g = atomicAdd(&b.counters[0], 1u);
+        uint32_t lo = 0, hi = b.nruns;  // tile_base[lo] <= g < tile_base[hi]
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (b.tile_base[mid] <= g) lo = mid;
+            else hi = mid;
+        }
+        s_run = lo;
+        sm.tile = g - b.tile_base[lo];
+    }
+    __syncthreads();
+    const RunDev& d = b.runs[s_run];
+    if (!d.st->active) return;
+    resample_tile(d, sm.tile, sm);
+}
+
 __device__ __forceinline__ long long warp_sum_ll(long long v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
-__global__ void __launch_bounds__(256) k_obs(RunDev d, int nsweeps) {
+__device__ __forceinline__ void obs_run(const RunDev& d, int nsweeps) {
     DevState* st = d.st;
     __shared__ long long s_part[3][8];
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
@@ -352,6 +403,13 @@ __global__ void __launch_bounds__(256) k_obs(RunDev d, int nsweeps) {
     }
 }
 
+__global__ void __launch_bounds__(256) k_obs(RunDev d, int nsweeps) { obs_run(d, nsweeps); }
+
+__global__ void __launch_bounds__(256) k_obs_batched(BatchDev b) {
+    const RunDev& d = b.runs[blockIdx.x];
+    obs_run(d, d.theta);
+}
+
 }  // namespace
 
 cudaError_t launch_tau(const RunDev& d, cudaStream_t s) {
@@ -366,6 +424,21 @@ cudaError_t launch_resample(const RunDev& d, cudaStream_t s) {
 
 cudaError_t launch_obs(const RunDev& d, int nsweeps, cudaStream_t s) {
     k_obs<<<1, 256, 0, s>>>(d, nsweeps);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tau_batched(const BatchDev& b, cudaStream_t s) {
+    k_tau_batched<<<b.nruns, 256, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resample_batched(const BatchDev& b, cudaStream_t s) {
+    k_resample_batched<<<b.total_tiles, RS_THREADS, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_obs_batched(const BatchDev& b, cudaStream_t s) {
+    k_obs_batched<<<b.nruns, 256, 0, s>>>(b);
     return cudaGetLastError();
 }
 

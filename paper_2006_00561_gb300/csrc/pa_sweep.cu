@@ -12,14 +12,16 @@
 // threshold T(beta_i, dE) = floor(2^32 exp(-beta_i dE)).
 //
 // One warp owns one replica at a time; the replica is staged whole in shared
-// memory for all sweeps and written back once.  Grid-stride over replicas, the
-// population size is read from device memory.
+// memory for all sweeps and written back once.  The plain kernels grid-stride
+// over the replicas of one run; the batched kernels claim chunks of 32
+// replicas of one run at a time from the global slot space of a batch class.
+// Both call the same per-replica device functions, so they give the same bits.
 #include "pa_internal.cuh"
 
 namespace pa {
 namespace {
 
-constexpr int WARPS = 4;  // warps per block of the generic sweep kernels
+constexpr int WARPS = 4;  // warps per block of the plain generic sweep kernels
 
 template <int DIM, int L>
 struct Geo {
@@ -112,161 +114,193 @@ __device__ __forceinline__ void count_add(uint32_t& b0, uint32_t& b1, uint32_t& 
     b2 |= c1;
 }
 
-template <int DIM, int L, bool PMJ>
-__global__ void __launch_bounds__(WARPS * 32) k_sweep_packed(RunDev d, int nsweeps) {
-    using G = Geo<DIM, L>;
-    constexpr int NW = G::NW, NWORDS = G::NWORDS;
-    extern __shared__ uint32_t smem[];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    uint32_t* S = smem + wib * 5 * NWORDS;
-    uint32_t* ALW = S + NWORDS;
-    uint32_t* CB0 = ALW + NWORDS;
-    uint32_t* CB1 = CB0 + NWORDS;
-    uint32_t* FLIP = CB1 + NWORDS;
 
-    DevState* st = d.st;
-    const uint32_t R = st->R;
-    const uint32_t cur = st->cur;
-    const uint32_t step = st->step;
-    const uint32_t g0 = st->sweep_base;
-    const uint32_t parity = st->negbonds & 1u;
-    const uint32_t T0 = d.thr[step * 4 + 0], T1 = d.thr[step * 4 + 1], T2 = d.thr[step * 4 + 2];
-    const uint32_t full = d.thr[step * 4 + 3];
-    const uint32_t ctr3 = (TAG_SWEEP << 28) | d.instance;
-    const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
-    const uint32_t* Jp = d.jpk;  // plane dd at Jp + dd*NWORDS
+// Per-run scalars of one sweep launch, read from the run's device state.
+struct SweepCtx {
+    uint32_t R, cur, step, g0, parity, T0, T1, T2, full, ctr3, k0, k1;
+};
 
-    uint8_t* spins = d.spins[cur];
-    uint32_t* ebin = d.ebin[cur];
-    int32_t* mag = d.mag[cur];
+__device__ __forceinline__ SweepCtx sweep_ctx(const RunDev& d) {
+    SweepCtx x;
+    const DevState* st = d.st;
+    x.R = st->R;
+    x.cur = st->cur;
+    x.step = st->step;
+    x.g0 = st->sweep_base;
+    x.parity = st->negbonds & 1u;
+    x.T0 = d.thr[x.step * 4 + 0];
+    x.T1 = d.thr[x.step * 4 + 1];
+    x.T2 = d.thr[x.step * 4 + 2];
+    x.full = d.thr[x.step * 4 + 3];
+    x.ctr3 = (TAG_SWEEP << 28) | d.instance;
+    x.k0 = (uint32_t)d.seed;
+    x.k1 = (uint32_t)(d.seed >> 32);
+    return x;
+}
 
-    for (int w = lane; w < NWORDS; w += 32) FLIP[w] = 0u;
-
+// Per-warp bookkeeping of the measurement: energy levels of up to 32
+// replicas (one per lane) for one warp-aggregated histogram flush, and the
+// magnetisation sums.
+struct Tally {
     long long sumAbsM = 0, sumM2 = 0;
-    uint32_t mylevel = 0;
-    int nlev = 0;
-    const uint32_t nwarps = gridDim.x * WARPS;
-    for (uint32_t slot = blockIdx.x * WARPS + wib; slot < R; slot += nwarps) {
-        const uint32_t* src = reinterpret_cast<const uint32_t*>(spins + (size_t)slot * d.stride);
-        for (int w = lane; w < NWORDS; w += 32) S[w] = src[w];
-        __syncwarp();
-        for (int t = 0; t < nsweeps; ++t) {
-            const uint32_t g = g0 + (uint32_t)t;
-            for (int c = 0; c < 2; ++c) {
-                // phase A: classify every site of colour c (bit-sliced, 32 sites per word)
-                for (int w = lane; w < NWORDS; w += 32) {
-                    const int r = w / NW, k = w % NW;
-                    int yp, ym, zp, zm;
-                    row_nbrs<DIM, L>(r, yp, ym, zp, zm);
-                    const uint32_t own = S[w];
-                    uint32_t jx = 0, jxm = 0, jyp = 0, jym = 0, jzp = 0, jzm = 0;
-                    if constexpr (PMJ) {
-                        jx = __ldg(Jp + w);
-                        jxm = xminus<DIM, L>(Jp + r * NW, k);
-                        jyp = __ldg(Jp + NWORDS + w);
-                        jym = __ldg(Jp + NWORDS + ym * NW + k);
-                        if constexpr (DIM == 3) {
-                            jzp = __ldg(Jp + 2 * NWORDS + w);
-                            jzm = __ldg(Jp + 2 * NWORDS + zm * NW + k);
-                        }
-                    }
-                    uint32_t b0 = 0, b1 = 0, b2 = 0;
-                    count_add(b0, b1, b2, own ^ xplus<DIM, L>(S + r * NW, k) ^ jx);
-                    count_add(b0, b1, b2, own ^ xminus<DIM, L>(S + r * NW, k) ^ jxm);
-                    count_add(b0, b1, b2, own ^ S[yp * NW + k] ^ jyp);
-                    count_add(b0, b1, b2, own ^ S[ym * NW + k] ^ jym);
-                    if constexpr (DIM == 3) {
-                        count_add(b0, b1, b2, own ^ S[zp * NW + k] ^ jzp);
-                        count_add(b0, b1, b2, own ^ S[zm * NW + k] ^ jzm);
-                    }
-                    const int rowpar = DIM == 2 ? (r & 1) : ((r % L + r / L) & 1);
-                    uint32_t cm = ((c + rowpar) & 1) ? 0xAAAAAAAAu : 0x55555555u;
-                    if (k == NW - 1) cm &= G::LASTMASK;
-                    const uint32_t zero = ~(b0 | b1 | b2);
-                    if constexpr (DIM == 2) {
-                        ALW[w] = (b1 | b2) & cm;  // c_u >= 2: dE <= 0
-                        CB0[w] = zero;            // c_u = 0: dE = 8 (class 1)
-                        CB1[w] = 0u;
-                    } else {
-                        ALW[w] = (b2 | (b1 & b0)) & cm;  // c_u >= 3
-                        CB0[w] = b0 & ~b1 & ~b2;         // c_u = 1: dE = 8 (class 1)
-                        CB1[w] = zero;                   // c_u = 0: dE = 12 (class 2)
-                    }
-                }
-                __syncwarp();
-                // phase B: one Philox block per 4 colour sites
-                for (int q = lane; q < G::NCALLS; q += 32) {
-                    const uint4 u = philox((uint32_t)q, 2u * g + (uint32_t)c, slot, ctr3, k0, k1);
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const int h = 4 * q + j;
-                        if (h >= G::HALF) break;
-                        int r, x;
-                        site_of<DIM, L>(h, c, r, x);
-                        const int w = r * NW + (x >> 5);
-                        const uint32_t bit = 1u << (x & 31);
-                        if (ALW[w] & bit) continue;
-                        const uint32_t idx = ((CB0[w] & bit) ? 1u : 0u) | ((CB1[w] & bit) ? 2u : 0u);
-                        const uint32_t T = idx == 0 ? T0 : (idx == 1 ? T1 : T2);
-                        if (((full >> idx) & 1u) || pick(u, (uint32_t)j) < T) atomicOr(&FLIP[w], bit);
-                    }
-                }
-                __syncwarp();
-                // phase C: apply
-                for (int w = lane; w < NWORDS; w += 32) {
-                    S[w] ^= ALW[w] | FLIP[w];
-                    FLIP[w] = 0u;
-                }
-                __syncwarp();
-            }
-        }
-        // measurement: U = unsatisfied bonds, M = N - 2 * (number of -1 spins)
-        uint32_t U = 0, down = 0;
-        for (int w = lane; w < NWORDS; w += 32) {
-            const int r = w / NW, k = w % NW;
-            int yp, ym, zp, zm;
-            row_nbrs<DIM, L>(r, yp, ym, zp, zm);
-            const uint32_t vm = (k == NW - 1) ? G::LASTMASK : 0xffffffffu;
-            const uint32_t own = S[w];
-            uint32_t jx = 0, jy = 0, jz = 0;
-            if constexpr (PMJ) {
-                jx = __ldg(Jp + w);
-                jy = __ldg(Jp + NWORDS + w);
-                if constexpr (DIM == 3) jz = __ldg(Jp + 2 * NWORDS + w);
-            }
-            U += __popc((own ^ xplus<DIM, L>(S + r * NW, k) ^ jx) & vm);
-            U += __popc((own ^ S[yp * NW + k] ^ jy) & vm);
-            if constexpr (DIM == 3) U += __popc((own ^ S[zp * NW + k] ^ jz) & vm);
-            down += __popc(own & vm);
-        }
-        U = warp_sum_u32(U);
-        down = warp_sum_u32(down);
-        const int M = G::N - 2 * (int)down;
-        uint32_t* dst = reinterpret_cast<uint32_t*>(spins + (size_t)slot * d.stride);
-        for (int w = lane; w < NWORDS; w += 32) dst[w] = S[w];
+    uint32_t level = 0;
+    int n = 0;
+
+    __device__ __forceinline__ void add(uint32_t* hist, uint32_t U, int M, int lane) {
         if (lane == 0) {
-            ebin[slot] = U >> 1;
-            mag[slot] = M;
-            if ((U & 1u) != parity) atomicOr(&st->status, ST_INVARIANT);
             sumAbsM += M < 0 ? -M : M;
             sumM2 += (long long)M * M;
         }
-        if (lane == nlev) mylevel = U >> 1;
-        if (++nlev == 32) {
-            hist_flush(d.hist, mylevel, 32, lane);
-            nlev = 0;
+        if (lane == n) level = U >> 1;
+        if (++n == 32) {
+            hist_flush(hist, level, 32, lane);
+            n = 0;
         }
-        __syncwarp();
     }
-    hist_flush(d.hist, mylevel, nlev, lane);
-    if (lane == 0 && (sumAbsM | sumM2)) {
-        atomicAdd(&d.accum[0], (unsigned long long)sumAbsM);
-        atomicAdd(&d.accum[1], (unsigned long long)sumM2);
+    __device__ __forceinline__ void finish(uint32_t* hist, unsigned long long* accum, int lane) {
+        hist_flush(hist, level, n, lane);
+        n = 0;
+        if (lane == 0 && (sumAbsM | sumM2)) {
+            atomicAdd(&accum[0], (unsigned long long)sumAbsM);
+            atomicAdd(&accum[1], (unsigned long long)sumM2);
+        }
+        sumAbsM = sumM2 = 0;
+    }
+};
+
+// Stores the measured level and magnetisation of a replica (lane 0) and
+// checks that U has the instance's parity.
+__device__ __forceinline__ void record(const RunDev& d, const SweepCtx& x, uint32_t slot,
+                                       uint32_t U, int M, int lane) {
+    if (lane == 0) {
+        d.ebin[x.cur][slot] = U >> 1;
+        d.mag[x.cur][slot] = M;
+        if ((U & 1u) != x.parity) atomicOr(&d.st->status, ST_INVARIANT);
     }
 }
 
 // --------------------------------------------------------------------------
-// int8 layout: one byte (+1 / -1) per site, site s = x + L y (+ L^2 z).
+// One replica, packed layout: theta sweeps in shared memory (S and the four
+// class / flip arrays of NWORDS words each), then the measurement.  Returns
+// U; M through the reference.  FLIP must be zero on entry and is on exit.
+// --------------------------------------------------------------------------
+template <int DIM, int L, bool PMJ>
+__device__ __forceinline__ uint32_t packed_replica(const RunDev& d, const SweepCtx& x,
+                                                   uint32_t slot, int nsweeps, uint32_t* S,
+                                                   int lane, int& M) {
+    using G = Geo<DIM, L>;
+    constexpr int NW = G::NW, NWORDS = G::NWORDS;
+    uint32_t* ALW = S + NWORDS;
+    uint32_t* CB0 = ALW + NWORDS;
+    uint32_t* CB1 = CB0 + NWORDS;
+    uint32_t* FLIP = CB1 + NWORDS;
+    const uint32_t* Jp = d.jpk;  // plane dd at Jp + dd*NWORDS
+    uint8_t* spins = d.spins[x.cur];
+
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(spins + (size_t)slot * d.stride);
+    for (int w = lane; w < NWORDS; w += 32) S[w] = src[w];
+    __syncwarp();
+    for (int t = 0; t < nsweeps; ++t) {
+        const uint32_t g = x.g0 + (uint32_t)t;
+        for (int c = 0; c < 2; ++c) {
+            // phase A: classify every site of colour c (bit-sliced, 32 sites per word)
+            for (int w = lane; w < NWORDS; w += 32) {
+                const int r = w / NW, k = w % NW;
+                int yp, ym, zp, zm;
+                row_nbrs<DIM, L>(r, yp, ym, zp, zm);
+                const uint32_t own = S[w];
+                uint32_t jx = 0, jxm = 0, jyp = 0, jym = 0, jzp = 0, jzm = 0;
+                if constexpr (PMJ) {
+                    jx = __ldg(Jp + w);
+                    jxm = xminus<DIM, L>(Jp + r * NW, k);
+                    jyp = __ldg(Jp + NWORDS + w);
+                    jym = __ldg(Jp + NWORDS + ym * NW + k);
+                    if constexpr (DIM == 3) {
+                        jzp = __ldg(Jp + 2 * NWORDS + w);
+                        jzm = __ldg(Jp + 2 * NWORDS + zm * NW + k);
+                    }
+                }
+                uint32_t b0 = 0, b1 = 0, b2 = 0;
+                count_add(b0, b1, b2, own ^ xplus<DIM, L>(S + r * NW, k) ^ jx);
+                count_add(b0, b1, b2, own ^ xminus<DIM, L>(S + r * NW, k) ^ jxm);
+                count_add(b0, b1, b2, own ^ S[yp * NW + k] ^ jyp);
+                count_add(b0, b1, b2, own ^ S[ym * NW + k] ^ jym);
+                if constexpr (DIM == 3) {
+                    count_add(b0, b1, b2, own ^ S[zp * NW + k] ^ jzp);
+                    count_add(b0, b1, b2, own ^ S[zm * NW + k] ^ jzm);
+                }
+                const int rowpar = DIM == 2 ? (r & 1) : ((r % L + r / L) & 1);
+                uint32_t cm = ((c + rowpar) & 1) ? 0xAAAAAAAAu : 0x55555555u;
+                if (k == NW - 1) cm &= G::LASTMASK;
+                const uint32_t zero = ~(b0 | b1 | b2);
+                if constexpr (DIM == 2) {
+                    ALW[w] = (b1 | b2) & cm;  // c_u >= 2: dE <= 0
+                    CB0[w] = zero;            // c_u = 0: dE = 8 (class 1)
+                    CB1[w] = 0u;
+                } else {
+                    ALW[w] = (b2 | (b1 & b0)) & cm;  // c_u >= 3
+                    CB0[w] = b0 & ~b1 & ~b2;         // c_u = 1: dE = 8 (class 1)
+                    CB1[w] = zero;                   // c_u = 0: dE = 12 (class 2)
+                }
+            }
+            __syncwarp();
+            // phase B: one Philox block per 4 colour sites
+            for (int q = lane; q < G::NCALLS; q += 32) {
+                const uint4 u = philox((uint32_t)q, 2u * g + (uint32_t)c, slot, x.ctr3, x.k0, x.k1);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int h = 4 * q + j;
+                    if (h >= G::HALF) break;
+                    int r, xx;
+                    site_of<DIM, L>(h, c, r, xx);
+                    const int w = r * NW + (xx >> 5);
+                    const uint32_t bit = 1u << (xx & 31);
+                    if (ALW[w] & bit) continue;
+                    const uint32_t idx = ((CB0[w] & bit) ? 1u : 0u) | ((CB1[w] & bit) ? 2u : 0u);
+                    const uint32_t T = idx == 0 ? x.T0 : (idx == 1 ? x.T1 : x.T2);
+                    if (((x.full >> idx) & 1u) || pick(u, (uint32_t)j) < T) atomicOr(&FLIP[w], bit);
+                }
+            }
+            __syncwarp();
+            // phase C: apply
+            for (int w = lane; w < NWORDS; w += 32) {
+                S[w] ^= ALW[w] | FLIP[w];
+                FLIP[w] = 0u;
+            }
+            __syncwarp();
+        }
+    }
+    // measurement: U = unsatisfied bonds, M = N - 2 * (number of -1 spins)
+    uint32_t U = 0, down = 0;
+    for (int w = lane; w < NWORDS; w += 32) {
+        const int r = w / NW, k = w % NW;
+        int yp, ym, zp, zm;
+        row_nbrs<DIM, L>(r, yp, ym, zp, zm);
+        const uint32_t vm = (k == NW - 1) ? G::LASTMASK : 0xffffffffu;
+        const uint32_t own = S[w];
+        uint32_t jx = 0, jy = 0, jz = 0;
+        if constexpr (PMJ) {
+            jx = __ldg(Jp + w);
+            jy = __ldg(Jp + NWORDS + w);
+            if constexpr (DIM == 3) jz = __ldg(Jp + 2 * NWORDS + w);
+        }
+        U += __popc((own ^ xplus<DIM, L>(S + r * NW, k) ^ jx) & vm);
+        U += __popc((own ^ S[yp * NW + k] ^ jy) & vm);
+        if constexpr (DIM == 3) U += __popc((own ^ S[zp * NW + k] ^ jz) & vm);
+        down += __popc(own & vm);
+    }
+    U = warp_sum_u32(U);
+    down = warp_sum_u32(down);
+    M = G::N - 2 * (int)down;
+    uint32_t* dst = reinterpret_cast<uint32_t*>(spins + (size_t)slot * d.stride);
+    for (int w = lane; w < NWORDS; w += 32) dst[w] = S[w];
+    __syncwarp();
+    return U;
+}
+
+// --------------------------------------------------------------------------
+// One replica, int8 layout: one byte (+1 / -1) per site, s = x + L y (+L^2 z).
+// Same-colour sites are independent, so a lane flips its site in place.
 // --------------------------------------------------------------------------
 template <int DIM, int L>
 __device__ __forceinline__ int nbr(int s, int dd, int dir) {
@@ -277,108 +311,143 @@ __device__ __forceinline__ int nbr(int s, int dd, int dir) {
 }
 
 template <int DIM, int L, bool PMJ>
-__global__ void __launch_bounds__(WARPS * 32) k_sweep_i8(RunDev d, int nsweeps) {
+__device__ __forceinline__ uint32_t i8_replica(const RunDev& d, const SweepCtx& x, uint32_t slot,
+                                               int nsweeps, int8_t* S, int lane, int& M) {
     using G = Geo<DIM, L>;
-    extern __shared__ uint32_t smem[];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    int8_t* S = reinterpret_cast<int8_t*>(smem) + wib * G::I8BYTES;
-
-    DevState* st = d.st;
-    const uint32_t R = st->R;
-    const uint32_t cur = st->cur;
-    const uint32_t step = st->step;
-    const uint32_t g0 = st->sweep_base;
-    const uint32_t parity = st->negbonds & 1u;
-    const uint32_t T0 = d.thr[step * 4 + 0], T1 = d.thr[step * 4 + 1], T2 = d.thr[step * 4 + 2];
-    const uint32_t full = d.thr[step * 4 + 3];
-    const uint32_t ctr3 = (TAG_SWEEP << 28) | d.instance;
-    const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
     const int8_t* J = d.j8;
-
-    uint8_t* spins = d.spins[cur];
-    uint32_t* ebin = d.ebin[cur];
-    int32_t* mag = d.mag[cur];
-
-    long long sumAbsM = 0, sumM2 = 0;
-    uint32_t mylevel = 0;
-    int nlev = 0;
-    const uint32_t nwarps = gridDim.x * WARPS;
-    for (uint32_t slot = blockIdx.x * WARPS + wib; slot < R; slot += nwarps) {
-        const uint32_t* src = reinterpret_cast<const uint32_t*>(spins + (size_t)slot * d.stride);
-        uint32_t* S32 = reinterpret_cast<uint32_t*>(S);
-        for (int w = lane; w < G::I8BYTES / 4; w += 32) S32[w] = src[w];
-        __syncwarp();
-        for (int t = 0; t < nsweeps; ++t) {
-            const uint32_t g = g0 + (uint32_t)t;
-            for (int c = 0; c < 2; ++c) {
-                for (int q = lane; q < G::NCALLS; q += 32) {
-                    const uint4 u = philox((uint32_t)q, 2u * g + (uint32_t)c, slot, ctr3, k0, k1);
+    uint8_t* spins = d.spins[x.cur];
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(spins + (size_t)slot * d.stride);
+    uint32_t* S32 = reinterpret_cast<uint32_t*>(S);
+    for (int w = lane; w < G::I8BYTES / 4; w += 32) S32[w] = src[w];
+    __syncwarp();
+    for (int t = 0; t < nsweeps; ++t) {
+        const uint32_t g = x.g0 + (uint32_t)t;
+        for (int c = 0; c < 2; ++c) {
+            for (int q = lane; q < G::NCALLS; q += 32) {
+                const uint4 u = philox((uint32_t)q, 2u * g + (uint32_t)c, slot, x.ctr3, x.k0, x.k1);
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const int h = 4 * q + j;
-                        if (h >= G::HALF) break;
-                        int r, x;
-                        site_of<DIM, L>(h, c, r, x);
-                        const int s = x + L * r;
-                        int local = 0;
+                for (int j = 0; j < 4; ++j) {
+                    const int h = 4 * q + j;
+                    if (h >= G::HALF) break;
+                    int r, xx;
+                    site_of<DIM, L>(h, c, r, xx);
+                    const int s = xx + L * r;
+                    int local = 0;
 #pragma unroll
-                        for (int dd = 0; dd < DIM; ++dd) {
-                            const int up = nbr<DIM, L>(s, dd, +1), dn = nbr<DIM, L>(s, dd, -1);
-                            if constexpr (PMJ) {
-                                local += __ldg(J + s * DIM + dd) * S[up];
-                                local += __ldg(J + dn * DIM + dd) * S[dn];
-                            } else {
-                                local += S[up] + S[dn];
-                            }
+                    for (int dd = 0; dd < DIM; ++dd) {
+                        const int up = nbr<DIM, L>(s, dd, +1), dn = nbr<DIM, L>(s, dd, -1);
+                        if constexpr (PMJ) {
+                            local += __ldg(J + s * DIM + dd) * S[up];
+                            local += __ldg(J + dn * DIM + dd) * S[dn];
+                        } else {
+                            local += S[up] + S[dn];
                         }
-                        const int dE = 2 * S[s] * local;
-                        bool acc = dE <= 0;
-                        if (!acc) {
-                            const uint32_t idx = (uint32_t)(dE / 4 - 1);
-                            const uint32_t T = idx == 0 ? T0 : (idx == 1 ? T1 : T2);
-                            acc = ((full >> idx) & 1u) || pick(u, (uint32_t)j) < T;
-                        }
-                        if (acc) S[s] = (int8_t)-S[s];
                     }
+                    const int dE = 2 * S[s] * local;
+                    bool acc = dE <= 0;
+                    if (!acc) {
+                        const uint32_t idx = (uint32_t)(dE / 4 - 1);
+                        const uint32_t T = idx == 0 ? x.T0 : (idx == 1 ? x.T1 : x.T2);
+                        acc = ((x.full >> idx) & 1u) || pick(u, (uint32_t)j) < T;
+                    }
+                    if (acc) S[s] = (int8_t)-S[s];
                 }
-                __syncwarp();
             }
+            __syncwarp();
         }
-        uint32_t U = 0, down = 0;
-        for (int s = lane; s < G::N; s += 32) {
-            const int sv = S[s];
-            down += sv < 0;
-#pragma unroll
-            for (int dd = 0; dd < DIM; ++dd) {
-                const int up = nbr<DIM, L>(s, dd, +1);
-                int prod = sv * S[up];
-                if constexpr (PMJ) prod *= __ldg(J + s * DIM + dd);
-                U += prod < 0;
-            }
-        }
-        U = warp_sum_u32(U);
-        down = warp_sum_u32(down);
-        const int M = G::N - 2 * (int)down;
-        uint32_t* dst = reinterpret_cast<uint32_t*>(spins + (size_t)slot * d.stride);
-        for (int w = lane; w < G::I8BYTES / 4; w += 32) dst[w] = S32[w];
-        if (lane == 0) {
-            ebin[slot] = U >> 1;
-            mag[slot] = M;
-            if ((U & 1u) != parity) atomicOr(&st->status, ST_INVARIANT);
-            sumAbsM += M < 0 ? -M : M;
-            sumM2 += (long long)M * M;
-        }
-        if (lane == nlev) mylevel = U >> 1;
-        if (++nlev == 32) {
-            hist_flush(d.hist, mylevel, 32, lane);
-            nlev = 0;
-        }
-        __syncwarp();
     }
-    hist_flush(d.hist, mylevel, nlev, lane);
-    if (lane == 0 && (sumAbsM | sumM2)) {
-        atomicAdd(&d.accum[0], (unsigned long long)sumAbsM);
-        atomicAdd(&d.accum[1], (unsigned long long)sumM2);
+    uint32_t U = 0, down = 0;
+    for (int s = lane; s < G::N; s += 32) {
+        const int sv = S[s];
+        down += sv < 0;
+#pragma unroll
+        for (int dd = 0; dd < DIM; ++dd) {
+            const int up = nbr<DIM, L>(s, dd, +1);
+            int prod = sv * S[up];
+            if constexpr (PMJ) prod *= __ldg(J + s * DIM + dd);
+            U += prod < 0;
+        }
+    }
+    U = warp_sum_u32(U);
+    down = warp_sum_u32(down);
+    M = G::N - 2 * (int)down;
+    uint32_t* dst = reinterpret_cast<uint32_t*>(spins + (size_t)slot * d.stride);
+    for (int w = lane; w < G::I8BYTES / 4; w += 32) dst[w] = S32[w];
+    __syncwarp();
+    return U;
+}
+
+// Shared memory per warp of each layout, in 32-bit words.
+template <int DIM, int L, int LAYOUT>
+__host__ __device__ constexpr int warp_words() {
+    return LAYOUT == PA_LAYOUT_PACKED ? 5 * Geo<DIM, L>::NWORDS : Geo<DIM, L>::I8BYTES / 4;
+}
+
+template <int DIM, int L, int LAYOUT, bool PMJ>
+__device__ __forceinline__ uint32_t one_replica(const RunDev& d, const SweepCtx& x, uint32_t slot,
+                                                int nsweeps, uint32_t* wsmem, int lane, int& M) {
+    if constexpr (LAYOUT == PA_LAYOUT_PACKED)
+        return packed_replica<DIM, L, PMJ>(d, x, slot, nsweeps, wsmem, lane, M);
+    else
+        return i8_replica<DIM, L, PMJ>(d, x, slot, nsweeps, reinterpret_cast<int8_t*>(wsmem), lane,
+                                       M);
+}
+
+// Plain: every replica of one run, grid-stride.
+template <int DIM, int L, int LAYOUT, bool PMJ>
+__global__ void __launch_bounds__(WARPS * 32) k_sweep(RunDev d, int nsweeps) {
+    extern __shared__ uint32_t smem[];
+    constexpr int WW = warp_words<DIM, L, LAYOUT>();
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint32_t* ws = smem + wib * WW;
+    if constexpr (LAYOUT == PA_LAYOUT_PACKED)
+        for (int w = lane; w < Geo<DIM, L>::NWORDS; w += 32) ws[4 * Geo<DIM, L>::NWORDS + w] = 0u;
+    __syncwarp();
+    const SweepCtx x = sweep_ctx(d);
+    Tally tally;
+    const uint32_t nwarps = gridDim.x * WARPS;
+    for (uint32_t slot = blockIdx.x * WARPS + wib; slot < x.R; slot += nwarps) {
+        int M = 0;
+        const uint32_t U = one_replica<DIM, L, LAYOUT, PMJ>(d, x, slot, nsweeps, ws, lane, M);
+        record(d, x, slot, U, M, lane);
+        tally.add(d.hist, U, M, lane);
+    }
+    tally.finish(d.hist, d.accum, lane);
+}
+
+// Batched: chunks of 32 slots of one run, claimed from the class's slot space.
+template <int DIM, int L, int LAYOUT, bool PMJ, int BW>
+__global__ void __launch_bounds__(BW * 32) k_sweep_batched(BatchSweepArgs a) {
+    extern __shared__ uint32_t smem[];
+    constexpr int WW = warp_words<DIM, L, LAYOUT>();
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint32_t* ws = smem + wib * WW;
+    if constexpr (LAYOUT == PA_LAYOUT_PACKED)
+        for (int w = lane; w < Geo<DIM, L>::NWORDS; w += 32) ws[4 * Geo<DIM, L>::NWORDS + w] = 0u;
+    __syncwarp();
+    Tally tally;
+    for (;;) {
+        uint32_t chunk = 0;
+        if (lane == 0) chunk = atomicAdd(a.counter, 1u);
+        chunk = __shfl_sync(0xffffffffu, chunk, 0);
+        const uint32_t g = chunk * 32u;
+        if (g >= a.total_slots) break;
+        uint32_t lo = 0, hi = a.n;  // slot_base[lo] <= g < slot_base[hi]
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (a.slot_base[mid] <= g) lo = mid;
+            else hi = mid;
+        }
+        const RunDev& d = a.runs[a.run_ids[lo]];
+        const SweepCtx x = sweep_ctx(d);
+        const uint32_t first = g - a.slot_base[lo];
+        for (uint32_t slot = first; slot < first + 32u && slot < x.R; ++slot) {
+            int M = 0;
+            const uint32_t U = one_replica<DIM, L, LAYOUT, PMJ>(d, x, slot, d.theta, ws, lane, M);
+            record(d, x, slot, U, M, lane);
+            tally.add(d.hist, U, M, lane);
+        }
+        tally.finish(d.hist, d.accum, lane);
     }
 }
 
@@ -474,27 +543,75 @@ struct KInfo {
 };
 
 template <int DIM, int L>
-KInfo pick_kernel(int layout, bool pmj) {
-    using G = Geo<DIM, L>;
+KInfo pick_plain(int layout, bool pmj) {
     if (layout == PA_LAYOUT_PACKED) {
-        const int smem = WARPS * 5 * G::NWORDS * 4;
-        return {pmj ? (const void*)k_sweep_packed<DIM, L, true>
-                    : (const void*)k_sweep_packed<DIM, L, false>,
+        const int smem = WARPS * warp_words<DIM, L, PA_LAYOUT_PACKED>() * 4;
+        return {pmj ? (const void*)k_sweep<DIM, L, PA_LAYOUT_PACKED, true>
+                    : (const void*)k_sweep<DIM, L, PA_LAYOUT_PACKED, false>,
                 smem};
     }
-    const int smem = WARPS * G::I8BYTES;
-    return {pmj ? (const void*)k_sweep_i8<DIM, L, true> : (const void*)k_sweep_i8<DIM, L, false>,
+    const int smem = WARPS * warp_words<DIM, L, PA_LAYOUT_INT8>() * 4;
+    return {pmj ? (const void*)k_sweep<DIM, L, PA_LAYOUT_INT8, true>
+                : (const void*)k_sweep<DIM, L, PA_LAYOUT_INT8, false>,
             smem};
 }
 
+template <int DIM, int L, int LAYOUT, int BW>
+KInfo pick_batched_w(bool pmj) {
+    const int smem = BW * warp_words<DIM, L, LAYOUT>() * 4;
+    return {pmj ? (const void*)k_sweep_batched<DIM, L, LAYOUT, true, BW>
+                : (const void*)k_sweep_batched<DIM, L, LAYOUT, false, BW>,
+            smem};
+}
+
+template <int DIM, int L>
+KInfo pick_batched(int layout, bool pmj, int warps) {
+    if (layout == PA_LAYOUT_PACKED) {
+        if (warps == 2) return pick_batched_w<DIM, L, PA_LAYOUT_PACKED, 2>(pmj);
+        if (warps == 4) return pick_batched_w<DIM, L, PA_LAYOUT_PACKED, 4>(pmj);
+        if (warps == 8) return pick_batched_w<DIM, L, PA_LAYOUT_PACKED, 8>(pmj);
+    } else {
+        if (warps == 2) return pick_batched_w<DIM, L, PA_LAYOUT_INT8, 2>(pmj);
+        if (warps == 4) return pick_batched_w<DIM, L, PA_LAYOUT_INT8, 4>(pmj);
+        if (warps == 8) return pick_batched_w<DIM, L, PA_LAYOUT_INT8, 8>(pmj);
+    }
+    return {nullptr, 0};
+}
+
+#define PA_SIZES(X) X(2, 4) X(2, 8) X(2, 16) X(2, 32) X(2, 64) X(2, 128) \
+    X(3, 2) X(3, 4) X(3, 6) X(3, 8) X(3, 10) X(3, 12) X(3, 16)
+
 KInfo find_kernel(int layout, int dim, int L, bool pmj) {
 #define PA_CASE(D_, L_) \
-    if (dim == D_ && L == L_) return pick_kernel<D_, L_>(layout, pmj);
-    PA_CASE(2, 4) PA_CASE(2, 8) PA_CASE(2, 16) PA_CASE(2, 32) PA_CASE(2, 64) PA_CASE(2, 128)
-    PA_CASE(3, 2) PA_CASE(3, 4) PA_CASE(3, 6) PA_CASE(3, 8) PA_CASE(3, 10) PA_CASE(3, 12)
-    PA_CASE(3, 16)
+    if (dim == D_ && L == L_) return pick_plain<D_, L_>(layout, pmj);
+    PA_SIZES(PA_CASE)
 #undef PA_CASE
     return {nullptr, 0};
+}
+
+KInfo find_batched(int layout, int dim, int L, bool pmj, int warps) {
+#define PA_CASE(D_, L_) \
+    if (dim == D_ && L == L_) return pick_batched<D_, L_>(layout, pmj, warps);
+    PA_SIZES(PA_CASE)
+#undef PA_CASE
+    return {nullptr, 0};
+}
+
+int grid_for(const KInfo& k, int threads, int64_t need_blocks) {
+    if (!k.fn) return 0;
+    if (cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, k.smem) !=
+        cudaSuccess)
+        return 0;
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k.fn, threads, k.smem) !=
+        cudaSuccess)
+        return 0;
+    if (per_sm < 1) return 0;
+    const int64_t full = (int64_t)sms * per_sm;
+    if (need_blocks > 0 && need_blocks < full) return (int)need_blocks;
+    return (int)full;
 }
 
 }  // namespace
@@ -507,20 +624,7 @@ bool sweep_supported(int layout, int dim, int L) {
 int sweep_grid(const RunDev& d) {
     if (l64_applies(d)) return l64_grid(d);
     const KInfo k = find_kernel(d.layout, d.dim, d.L, d.model == PA_MODEL_PMJ);
-    if (!k.fn) return 0;
-    if (cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, k.smem) !=
-        cudaSuccess)
-        return 0;
-    int dev = 0, sms = 0, per_sm = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k.fn, WARPS * 32, k.smem) !=
-        cudaSuccess)
-        return 0;
-    if (per_sm < 1) return 0;
-    const int64_t need = ((int64_t)d.cap + WARPS - 1) / WARPS;
-    const int64_t full = (int64_t)sms * per_sm;
-    return (int)(need < full ? need : full);
+    return grid_for(k, WARPS * 32, ((int64_t)d.cap + WARPS - 1) / WARPS);
 }
 
 cudaError_t launch_sweep(const RunDev& d, int nsweeps, int grid, cudaStream_t s) {
@@ -531,6 +635,28 @@ cudaError_t launch_sweep(const RunDev& d, int nsweeps, int grid, cudaStream_t s)
     int n = nsweeps;
     void* args[] = {&dd, &n};
     return cudaLaunchKernel(k.fn, dim3(grid), dim3(WARPS * 32), args, (size_t)k.smem, s);
+}
+
+bool batched_warps_valid(const RunDev& proto, int warps) {
+    if (l64_batched_applies(proto)) return true;
+    return find_batched(proto.layout, proto.dim, proto.L, proto.model == PA_MODEL_PMJ, warps).fn !=
+           nullptr;
+}
+
+int batched_sweep_grid(const RunDev& proto, int warps) {
+    if (l64_batched_applies(proto)) return l64_batched_grid();
+    const KInfo k = find_batched(proto.layout, proto.dim, proto.L, proto.model == PA_MODEL_PMJ, warps);
+    return grid_for(k, warps * 32, 0);
+}
+
+cudaError_t launch_sweep_batched(const BatchSweepArgs& a, const RunDev& proto, int warps, int grid,
+                                 cudaStream_t s) {
+    if (l64_batched_applies(proto)) return launch_sweep_l64_batched(a, grid, s);
+    const KInfo k = find_batched(proto.layout, proto.dim, proto.L, proto.model == PA_MODEL_PMJ, warps);
+    if (!k.fn) return cudaErrorInvalidValue;
+    BatchSweepArgs aa = a;
+    void* args[] = {&aa};
+    return cudaLaunchKernel(k.fn, dim3(grid), dim3(warps * 32), args, (size_t)k.smem, s);
 }
 
 cudaError_t launch_init(const RunDev& d, cudaStream_t s) {

@@ -92,6 +92,15 @@ __device__ __forceinline__ uint32_t add_if_below(uint32_t acc, uint32_t u, const
 // 3..10 are the plain rounds.  Same bits as philox_rk().
 constexpr uint32_t PM0 = 0xD2511F53u, PM1 = 0xCD9E8D57u;
 
+// Round keys of the run's seed and the opaque 1 of the multiply-add tests:
+// kernel parameters in the plain kernel, a per-warp shared-memory copy of the
+// chunk's run in the batched one.
+struct Keys {
+    const uint32_t* rk0;
+    const uint32_t* rk1;
+    uint32_t one;
+};
+
 struct HalfSweepGen {
     uint32_t x1k;   // round-1 word 1 (low product of slot) ^ round-2 key 0
     uint32_t hiA2k; // high half of M0 * (round-1 word 0) ^ round-2 key 1
@@ -99,7 +108,7 @@ struct HalfSweepGen {
     uint32_t c3k;   // counter word 3 ^ round-1 key 1
 };
 
-__device__ __forceinline__ HalfSweepGen half_sweep_gen(const RunDev& d, uint32_t c1, uint32_t slot,
+__device__ __forceinline__ HalfSweepGen half_sweep_gen(const Keys& d, uint32_t c1, uint32_t slot,
                                                       uint32_t ctr3) {
     HalfSweepGen g;
     const uint32_t x0 = __umulhi(PM1, slot) ^ c1 ^ d.rk0[0];
@@ -111,7 +120,7 @@ __device__ __forceinline__ HalfSweepGen half_sweep_gen(const RunDev& d, uint32_t
 }
 
 // pA = M0 * c0 (64-bit) of the block.
-__device__ __forceinline__ uint4 philox_block(const RunDev& d, const HalfSweepGen& g, uint64_t pA) {
+__device__ __forceinline__ uint4 philox_block(const Keys& d, const HalfSweepGen& g, uint64_t pA) {
     const uint32_t x2 = (uint32_t)(pA >> 32) ^ g.c3k;
     const uint32_t x3 = (uint32_t)pA;
     uint32_t c0 = __umulhi(PM1, x2) ^ g.x1k;
@@ -136,7 +145,7 @@ __device__ __forceinline__ uint4 philox_block(const RunDev& d, const HalfSweepGe
 // when that uniform is below T4 / T8.  Four blocks per iteration fill one
 // 32-bit half of each mask.
 template <int P>
-__device__ __forceinline__ void row_accepts(const RunDev& d, const HalfSweepGen& gen, uint32_t y,
+__device__ __forceinline__ void row_accepts(const Keys& d, const HalfSweepGen& gen, uint32_t y,
                                             const Thr& t4, const Thr& t8, uint64_t& a4,
                                             uint64_t& a8) {
     const uint32_t one = d.one;
@@ -177,7 +186,7 @@ __device__ __forceinline__ void row_accepts(const RunDev& d, const HalfSweepGen&
 // and below.  c_u >= 2 flips outright (dE <= 0); c_u = 1 needs u < T4; c_u = 0
 // needs u < T8.  full bit 0 / 1: T4 / T8 equal 2^32 (beta = 0), always accept.
 template <int P>
-__device__ __forceinline__ uint64_t row_flips(const RunDev& d, const HalfSweepGen& gen,
+__device__ __forceinline__ uint64_t row_flips(const Keys& d, const HalfSweepGen& gen,
                                               uint64_t own, uint64_t up, uint64_t dn, uint32_t y,
                                               const Thr& t4, const Thr& t8, uint32_t full) {
     constexpr uint64_t cm = P ? 0xAAAAAAAAAAAAAAAAull : 0x5555555555555555ull;
@@ -205,84 +214,158 @@ __device__ __forceinline__ void hist_flush(uint32_t* hist, uint32_t level, int n
     }
 }
 
-__global__ void __launch_bounds__(WARPS64 * 32, PA_L64_MIN_BLOCKS) k_sweep_l64(__grid_constant__ const RunDev d, int nsweeps) {
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    DevState* st = d.st;
-    const uint32_t R = st->R;
-    const uint32_t cur = st->cur;
-    const uint32_t step = st->step;
-    const uint32_t g0 = st->sweep_base;
-    Thr t4, t8;
+// One replica: theta sweeps in registers, then the measurement.  Returns U
+// (all lanes), M through the reference; writes the replica back.
+__device__ __forceinline__ uint32_t l64_replica(const Keys& K, uint4* spins, uint32_t slot,
+                                                int nsweeps, uint32_t g0, uint32_t ctr3,
+                                                const Thr& t4, const Thr& t8, uint32_t full,
+                                                int lane, int& M) {
+    const uint32_t ya = 2u * (uint32_t)lane, yb = ya + 1u;
+    const int lup = (lane + 31) & 31, ldn = (lane + 1) & 31;
+    const uint4 v = spins[(size_t)slot * 32 + lane];
+    uint64_t ra = ((uint64_t)v.y << 32) | v.x;  // row ya
+    uint64_t rb = ((uint64_t)v.w << 32) | v.z;  // row yb
+    for (int t = 0; t < nsweeps; ++t) {
+        const uint32_t g = g0 + (uint32_t)t;
+        {  // colour 0: even rows have parity 0, odd rows parity 1
+            const uint64_t up = shfl64(rb, lup);  // row ya - 1
+            const uint64_t dn = shfl64(ra, ldn);  // row yb + 1
+            const HalfSweepGen gen = half_sweep_gen(K, 2u * g, slot, ctr3);
+            const uint64_t fa = row_flips<0>(K, gen, ra, up, rb, ya, t4, t8, full);
+            const uint64_t fb = row_flips<1>(K, gen, rb, ra, dn, yb, t4, t8, full);
+            ra ^= fa;
+            rb ^= fb;
+        }
+        {  // colour 1
+            const uint64_t up = shfl64(rb, lup);
+            const uint64_t dn = shfl64(ra, ldn);
+            const HalfSweepGen gen = half_sweep_gen(K, 2u * g + 1u, slot, ctr3);
+            const uint64_t fa = row_flips<1>(K, gen, ra, up, rb, ya, t4, t8, full);
+            const uint64_t fb = row_flips<0>(K, gen, rb, ra, dn, yb, t4, t8, full);
+            ra ^= fa;
+            rb ^= fb;
+        }
+    }
+    // measurement: bonds to x + 1 and to y + 1 of both rows
+    const uint64_t dn = shfl64(ra, ldn);
+    uint32_t U = __popcll(ra ^ ((ra >> 1) | (ra << 63))) + __popcll(ra ^ rb) +
+                 __popcll(rb ^ ((rb >> 1) | (rb << 63))) + __popcll(rb ^ dn);
+    uint32_t down = __popcll(ra) + __popcll(rb);
+    U = warp_sum(U);
+    down = warp_sum(down);
+    M = 4096 - 2 * (int)down;
+    spins[(size_t)slot * 32 + lane] =
+        make_uint4((uint32_t)ra, (uint32_t)(ra >> 32), (uint32_t)rb, (uint32_t)(rb >> 32));
+    return U;
+}
+
+struct L64Tally {
+    long long sumAbsM = 0, sumM2 = 0;
+    uint32_t level = 0;
+    int n = 0;
+    __device__ __forceinline__ void add(uint32_t* hist, uint32_t U, int M, int lane) {
+        if (lane == 0) {
+            sumAbsM += M < 0 ? -M : M;
+            sumM2 += (long long)M * M;
+        }
+        if (lane == n) level = U >> 1;
+        if (++n == 32) {
+            hist_flush(hist, level, 32, lane);
+            n = 0;
+        }
+    }
+    __device__ __forceinline__ void finish(uint32_t* hist, unsigned long long* accum, int lane) {
+        hist_flush(hist, level, n, lane);
+        n = 0;
+        if (lane == 0 && (sumAbsM | sumM2)) {
+            atomicAdd(&accum[0], (unsigned long long)sumAbsM);
+            atomicAdd(&accum[1], (unsigned long long)sumM2);
+        }
+        sumAbsM = sumM2 = 0;
+    }
+};
+
+__device__ __forceinline__ void thresholds(const RunDev& d, uint32_t step, Thr& t4, Thr& t8,
+                                           uint32_t& full) {
     t4.T = d.thr[step * 4 + 0];
     t8.T = d.thr[step * 4 + 1];
     t4.cneg = t4.T ? (0ull - (uint64_t)t4.T) : 0ull;
     t8.cneg = t8.T ? (0ull - (uint64_t)t8.T) : 0ull;
-    const uint32_t full = d.thr[step * 4 + 3];
+    full = d.thr[step * 4 + 3];
+}
+
+__global__ void __launch_bounds__(WARPS64 * 32, PA_L64_MIN_BLOCKS)
+    k_sweep_l64(__grid_constant__ const RunDev d, int nsweeps) {
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    DevState* st = d.st;
+    const uint32_t R = st->R;
+    const uint32_t cur = st->cur;
+    const uint32_t g0 = st->sweep_base;
+    Thr t4, t8;
+    uint32_t full;
+    thresholds(d, st->step, t4, t8, full);
     const uint32_t ctr3 = (TAG_SWEEP << 28) | d.instance;
-    const uint32_t ya = 2u * (uint32_t)lane, yb = ya + 1u;
-    const int lup = (lane + 31) & 31, ldn = (lane + 1) & 31;
-
-    const uint4* spins = reinterpret_cast<const uint4*>(d.spins[cur]);
-    uint4* spins_w = reinterpret_cast<uint4*>(d.spins[cur]);
-    uint32_t* ebin = d.ebin[cur];
-    int32_t* mag = d.mag[cur];
-
-    long long sumAbsM = 0, sumM2 = 0;
-    uint32_t mylevel = 0;
-    int nlev = 0;
+    const Keys K{d.rk0, d.rk1, d.one};
+    uint4* spins = reinterpret_cast<uint4*>(d.spins[cur]);
+    L64Tally tally;
     const uint32_t nwarps = gridDim.x * WARPS64;
     for (uint32_t slot = blockIdx.x * WARPS64 + wib; slot < R; slot += nwarps) {
-        const uint4 v = spins[(size_t)slot * 32 + lane];
-        uint64_t ra = ((uint64_t)v.y << 32) | v.x;  // row ya
-        uint64_t rb = ((uint64_t)v.w << 32) | v.z;  // row yb
-        for (int t = 0; t < nsweeps; ++t) {
-            const uint32_t g = g0 + (uint32_t)t;
-            {  // colour 0: even rows have parity 0, odd rows parity 1
-                const uint64_t up = shfl64(rb, lup);  // row ya - 1
-                const uint64_t dn = shfl64(ra, ldn);  // row yb + 1
-                const HalfSweepGen gen = half_sweep_gen(d, 2u * g, slot, ctr3);
-                const uint64_t fa = row_flips<0>(d, gen, ra, up, rb, ya, t4, t8, full);
-                const uint64_t fb = row_flips<1>(d, gen, rb, ra, dn, yb, t4, t8, full);
-                ra ^= fa;
-                rb ^= fb;
-            }
-            {  // colour 1
-                const uint64_t up = shfl64(rb, lup);
-                const uint64_t dn = shfl64(ra, ldn);
-                const HalfSweepGen gen = half_sweep_gen(d, 2u * g + 1u, slot, ctr3);
-                const uint64_t fa = row_flips<1>(d, gen, ra, up, rb, ya, t4, t8, full);
-                const uint64_t fb = row_flips<0>(d, gen, rb, ra, dn, yb, t4, t8, full);
-                ra ^= fa;
-                rb ^= fb;
-            }
-        }
-        // measurement: bonds to x + 1 and to y + 1 of both rows
-        const uint64_t dn = shfl64(ra, ldn);
-        uint32_t U = __popcll(ra ^ ((ra >> 1) | (ra << 63))) + __popcll(ra ^ rb) +
-                     __popcll(rb ^ ((rb >> 1) | (rb << 63))) + __popcll(rb ^ dn);
-        uint32_t down = __popcll(ra) + __popcll(rb);
-        U = warp_sum(U);
-        down = warp_sum(down);
-        const int M = 4096 - 2 * (int)down;
-        spins_w[(size_t)slot * 32 + lane] =
-            make_uint4((uint32_t)ra, (uint32_t)(ra >> 32), (uint32_t)rb, (uint32_t)(rb >> 32));
+        int M = 0;
+        const uint32_t U = l64_replica(K, spins, slot, nsweeps, g0, ctr3, t4, t8, full, lane, M);
         if (lane == 0) {
-            ebin[slot] = U >> 1;
-            mag[slot] = M;
+            d.ebin[cur][slot] = U >> 1;
+            d.mag[cur][slot] = M;
             if (U & 1u) atomicOr(&st->status, ST_INVARIANT);
-            sumAbsM += M < 0 ? -M : M;
-            sumM2 += (long long)M * M;
         }
-        if (lane == nlev) mylevel = U >> 1;
-        if (++nlev == 32) {
-            hist_flush(d.hist, mylevel, 32, lane);
-            nlev = 0;
-        }
+        tally.add(d.hist, U, M, lane);
     }
-    hist_flush(d.hist, mylevel, nlev, lane);
-    if (lane == 0 && (sumAbsM | sumM2)) {
-        atomicAdd(&d.accum[0], (unsigned long long)sumAbsM);
-        atomicAdd(&d.accum[1], (unsigned long long)sumM2);
+    tally.finish(d.hist, d.accum, lane);
+}
+
+// Batched: chunks of 32 slots of one run from a class's slot space.
+__global__ void __launch_bounds__(WARPS64 * 32, PA_L64_MIN_BLOCKS) k_sweep_l64_batched(BatchSweepArgs a) {
+    __shared__ uint32_t s_keys[WARPS64][24];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    L64Tally tally;
+    for (;;) {
+        uint32_t chunk = 0;
+        if (lane == 0) chunk = atomicAdd(a.counter, 1u);
+        chunk = __shfl_sync(0xffffffffu, chunk, 0);
+        const uint32_t g = chunk * 32u;
+        if (g >= a.total_slots) break;
+        uint32_t lo = 0, hi = a.n;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (a.slot_base[mid] <= g) lo = mid;
+            else hi = mid;
+        }
+        const RunDev& d = a.runs[a.run_ids[lo]];
+        DevState* st = d.st;
+        const uint32_t R = st->R, cur = st->cur, g0 = st->sweep_base;
+        Thr t4, t8;
+        uint32_t full;
+        thresholds(d, st->step, t4, t8, full);
+        if (lane < 10) {
+            s_keys[wib][lane] = d.rk0[lane];
+            s_keys[wib][10 + lane] = d.rk1[lane];
+        }
+        __syncwarp();
+        const Keys K{&s_keys[wib][0], &s_keys[wib][10], d.one};
+        const uint32_t ctr3 = (TAG_SWEEP << 28) | d.instance;
+        uint4* spins = reinterpret_cast<uint4*>(d.spins[cur]);
+        const uint32_t first = g - a.slot_base[lo];
+        for (uint32_t slot = first; slot < first + 32u && slot < R; ++slot) {
+            int M = 0;
+            const uint32_t U = l64_replica(K, spins, slot, d.theta, g0, ctr3, t4, t8, full, lane, M);
+            if (lane == 0) {
+                d.ebin[cur][slot] = U >> 1;
+                d.mag[cur][slot] = M;
+                if (U & 1u) atomicOr(&st->status, ST_INVARIANT);
+            }
+            tally.add(d.hist, U, M, lane);
+        }
+        tally.finish(d.hist, d.accum, lane);
+        __syncwarp();
     }
 }
 
@@ -308,6 +391,23 @@ int l64_grid(const RunDev& d) {
 
 cudaError_t launch_sweep_l64(const RunDev& d, int nsweeps, int grid, cudaStream_t s) {
     k_sweep_l64<<<grid, WARPS64 * 32, 0, s>>>(d, nsweeps);
+    return cudaGetLastError();
+}
+
+bool l64_batched_applies(const RunDev& proto) { return l64_applies(proto); }
+
+int l64_batched_grid() {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_l64_batched, WARPS64 * 32,
+                                                      0) != cudaSuccess)
+        return 0;
+    return per_sm < 1 ? 0 : sms * per_sm;
+}
+
+cudaError_t launch_sweep_l64_batched(const BatchSweepArgs& a, int grid, cudaStream_t s) {
+    k_sweep_l64_batched<<<grid, WARPS64 * 32, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -33,6 +33,9 @@ EXPORTS = [
     "pa_observables", "pa_observables_history", "pa_status", "pa_dump_size", "pa_dump",
     "pa_dump_range", "pa_load", "pa_profile", "pa_profile_read",
     "pa_tables", "pa_num_bins", "pa_free", "pa_strerror", "pa_copy_counts_scan_noalloc",
+    "pa_batch_workspace_size", "pa_batch_init", "pa_batch_step", "pa_batch_run_steps",
+    "pa_batch_sync", "pa_batch_num_classes", "pa_batch_class_info", "pa_batch_set_warps",
+    "pa_batch_free",
 ]
 NOALLOC_MAX_REPLICAS = 8388608
 
@@ -121,6 +124,16 @@ def lib():
         L.pa_free.restype = None
         L.pa_copy_counts_scan_noalloc.argtypes = [vp, C.c_int64, vp, vp, C.c_int64, C.c_uint64,
                                                    C.c_int32, C.c_int32, vp, vp, vp, vp]
+        L.pa_batch_workspace_size.argtypes = [C.c_int32]
+        L.pa_batch_workspace_size.restype = C.c_size_t
+        L.pa_batch_init.argtypes = [C.POINTER(vp), C.c_int32, vp, C.c_size_t, vp, C.POINTER(vp)]
+        for n in ("pa_batch_step", "pa_batch_sync", "pa_batch_num_classes"):
+            getattr(L, n).argtypes = [vp]
+        L.pa_batch_run_steps.argtypes = [vp, C.c_int32]
+        L.pa_batch_class_info.argtypes = [vp, C.c_int32, C.POINTER(C.c_int32)]
+        L.pa_batch_set_warps.argtypes = [vp, C.c_int32, C.c_int32]
+        L.pa_batch_free.argtypes = [vp]
+        L.pa_batch_free.restype = None
         L.pa_strerror.argtypes = [C.c_int]
         L.pa_strerror.restype = C.c_char_p
         _lib = L
@@ -341,3 +354,56 @@ class Run:
     def dump_range(self, what: int, first: int, count: int) -> np.ndarray:
         stride = self.state()["stride"] if what == DUMP_SPINS_RAW else 0
         return pa_dump_range(self.h, what, first, count, self.N, stride)
+
+
+# ---- batched form ---------------------------------------------------------------
+class Batch:
+    """Several runs stepped together (pa_batch_* of include/pa.h)."""
+
+    def __init__(self, runs, stream=None):
+        import torch
+        self.runs = list(runs)
+        n = len(self.runs)
+        nbytes = int(lib().pa_batch_workspace_size(n))
+        if nbytes == 0:
+            raise PaError(-1, "pa_batch_workspace_size")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        handles = (C.c_void_p * n)(*[r.h for r in self.runs])
+        h = C.c_void_p()
+        _check(lib().pa_batch_init(handles, n, C.c_void_p(self.workspace.data_ptr()), nbytes,
+                                   C.c_void_p(self.stream.cuda_stream), C.byref(h)),
+               "pa_batch_init")
+        self.h = h.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().pa_batch_free(C.c_void_p(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self):
+        _check(lib().pa_batch_step(C.c_void_p(self.h)), "pa_batch_step")
+
+    def run_steps(self, n: int):
+        _check(lib().pa_batch_run_steps(C.c_void_p(self.h), n), "pa_batch_run_steps")
+
+    def sync(self) -> int:
+        return int(lib().pa_batch_sync(C.c_void_p(self.h)))
+
+    def classes(self) -> list:
+        out = []
+        for c in range(int(lib().pa_batch_num_classes(C.c_void_p(self.h)))):
+            info = (C.c_int32 * 7)()
+            _check(lib().pa_batch_class_info(C.c_void_p(self.h), c, info), "pa_batch_class_info")
+            out.append(dict(zip(("layout", "dim", "L", "model", "runs", "warps", "slots"),
+                                list(info))))
+        return out
+
+    def set_warps(self, cls: int, warps: int):
+        _check(lib().pa_batch_set_warps(C.c_void_p(self.h), cls, warps), "pa_batch_set_warps")
