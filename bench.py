@@ -51,6 +51,25 @@ ALU_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12
 SWEEP_TRAFFIC_BYTES_2P21 = 210.2e6 * 8
 
 
+def rank_workload(rank: int, R0: int) -> dict:
+    """Replicas only: every rank runs an independent population of the same
+    workload, separated by its instance id (the Philox counter's instance
+    field), so no data-path collective is needed."""
+    return dict(WORKLOAD, R0=R0, instance_id=rank)
+
+
+def aggregate(dist, ms: float, work: float, device) -> tuple:
+    """(max time over ranks, total work over ranks); plain values without a
+    process group."""
+    if dist is None:
+        return ms, work
+    import torch
+    t = torch.tensor([ms, work], dtype=torch.float64, device=device)
+    ts = [torch.zeros_like(t) for _ in range(dist.get_world_size())]
+    dist.all_gather(ts, t)
+    return max(float(x[0]) for x in ts), sum(float(x[1]) for x in ts)
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -133,6 +152,99 @@ def oracle_rate(seconds: float, L=64, R0=512, theta=10):
             "seconds": total, "resampled_replicas_per_s": resampled / t_res if t_res else None}
 
 
+def ensemble_compare(P, steps: int, tune_cache=None) -> dict:
+    """Config 4: 256 +-J instances (L in {6,8,10}, R0 in {2^14..2^16}, beta
+    0 -> 3, K = 150, theta = 10) stepped plain (four launches per run per step)
+    and batched (one CUDA graph per step, autotuned sweep shapes).  Both sets
+    start from the same seeds; throughput = attempts / device time."""
+    import torch
+    from paper_2006_00561_gb300 import autotune, workloads
+    specs = workloads.ea_ensemble(256, seed=4)
+    stream = torch.cuda.Stream()
+    out = {"workload": "256 3D +-J EA instances, L in {6,8,10}, R0 in {2^14,2^15,2^16}, "
+                       "beta 0->3, K=150, theta=10 (numpy PCG64 seed 4)"}
+
+    def attempts(runs, first, n):
+        tot = 0
+        for r, sp in zip(runs, specs):
+            h = r.history(first, n)
+            tot += sum(x["R"] for x in h) * sp["L"] ** 3 * sp["theta"]
+        return tot
+
+    plain = [P.Run(P.make_config(layout=P.LAYOUT_PACKED, **sp), stream=stream) for sp in specs]
+    for r in plain:
+        r.step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    first = plain[0].state()["step"] + 1
+    e0.record(stream)
+    for _ in range(steps):
+        for r in plain:
+            r.step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_plain = e0.elapsed_time(e1)
+    a_plain = attempts(plain, first, steps)
+    for r in plain:
+        r.close()
+    del plain
+    torch.cuda.empty_cache()
+
+    runs = [P.Run(P.make_config(layout=P.LAYOUT_PACKED, **sp), stream=stream) for sp in specs]
+    batch = P.Batch(runs, stream=stream)
+    tuned = autotune.tune(batch, steps_left=specs[0]["K"] - steps - 2, cache_path=tune_cache)
+    batch.run_steps(1)
+    assert batch.sync() == 0
+    first = runs[0].state()["step"] + 1
+    torch.cuda.synchronize()
+    e0.record(stream)
+    batch.run_steps(steps)
+    e1.record(stream)
+    assert batch.sync() == 0
+    ms_b = e0.elapsed_time(e1)
+    a_b = attempts(runs, first, steps)
+    out.update({
+        "plain_attempts_per_ns": a_plain / (ms_plain * 1e6),
+        "batched_attempts_per_ns": a_b / (ms_b * 1e6),
+        "plain_ms_per_step": ms_plain / steps, "batched_ms_per_step": ms_b / steps,
+        "speedup": (a_b / ms_b) / (a_plain / ms_plain),
+        "launches_per_step": {"plain": 4 * len(specs), "batched": 3 + len(batch.classes())},
+        "autotune": {"choice": tuned["choice"], "steps_used": tuned["steps_used"],
+                     "classes": batch.classes()},
+        "replicas": sum(r.state()["R"] for r in runs),
+    })
+    batch.close()
+    for r in runs:
+        r.close()
+    return out
+
+
+def serving_measure(P, n: int = 48, rates=(400.0, 40.0)) -> dict:
+    """Config 5 in miniature: the serving mix (2D L in {16,32,64,128}, 3D +-J
+    L in {6,8,10}, beta_max in {1,3}, theta = 10, Poisson arrivals) with R0 =
+    2^U, U in 8..14 and K in 25..75 (the full trace's R0 2^12..2^18 and K
+    100..300 scaled down so a run ends in seconds).  Served through the
+    continuous-batching loop with an HBM budget of 8 GB, at an offered rate
+    above and one below the GPU's capacity."""
+    from paper_2006_00561_gb300 import serve, workloads
+    out = {"workload": f"{n} requests, serving mix, R0=2^8..2^14, K=25..75, theta=10",
+           "hbm_budget_bytes": 8 << 30}
+    for rate in rates:
+        trace = workloads.serving_trace(n, rate=rate, seed=5, R0_exp=(8, 14), K_range=(25, 75))
+        offered = sum(t["R0"] * t["L"] ** t["dim"] * t["theta"] * t["K"] for t in trace)
+        span = trace[-1]["arrival"]
+        srv = serve.Server(hbm_budget=8 << 30, quantum=4)
+        st = srv.run_trace(trace)
+        out[f"rate_{int(rate)}_per_s"] = {
+            "offered_attempts_per_ns": offered / (span * 1e9),
+            "served_attempts_per_ns": st.get("served_attempts_per_ns"),
+            "p50_latency_s": st.get("p50_latency_s"), "p99_latency_s": st.get("p99_latency_s"),
+            "served": st["served"], "max_resident": st["max_resident"],
+            "iterations": st["iterations"], "wall_s": st["wall_s"],
+            "host_phase_s": st["host_phase_s"]}
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -172,6 +284,8 @@ def main():
     ap.add_argument("--R0", type=int, default=WORKLOAD["R0"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -190,9 +304,8 @@ def main():
 
     from paper_2006_00561_gb300 import pa as P
 
-    wl = dict(WORKLOAD, R0=args.R0)
-    # replicas only: every rank runs its own independent population
-    cfg = P.make_config(layout=P.LAYOUT_PACKED, instance_id=rank, **wl)
+    wl = rank_workload(rank, args.R0)
+    cfg = P.make_config(layout=P.LAYOUT_PACKED, **wl)
     stream = torch.cuda.Stream()
     run = P.Run(cfg, stream=stream)
     N = wl["L"] ** 2
@@ -222,14 +335,7 @@ def main():
     Rs = [h["R"] for h in hist]
     attempts = sum(Rs[1:]) * N * theta
     resampled = sum(Rs[:-1])
-    if dist is not None:
-        t = torch.tensor([ms_graph, attempts], dtype=torch.float64, device="cuda")
-        ts = [torch.zeros_like(t) for _ in range(world)]
-        dist.all_gather(ts, t)
-        ms_graph = max(float(x[0]) for x in ts)
-        attempts_all = sum(float(x[1]) for x in ts)
-    else:
-        attempts_all = attempts
+    ms_graph, attempts_all = aggregate(dist, ms_graph, attempts, "cuda")
     value = attempts_all / (ms_graph * 1e6)
     run.observables()  # raises on a sticky device error
 
@@ -296,16 +402,21 @@ def main():
             d2h += R_now * stride + 104
         barrier()
         dt = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([dt, e2e_attempts], dtype=torch.float64, device="cuda")
-            ts = [torch.zeros_like(t) for _ in range(world)]
-            dist.all_gather(ts, t)
-            dt = max(float(x[0]) for x in ts)
-            e2e_attempts = sum(float(x[1]) for x in ts)
+        dt, e2e_attempts = aggregate(dist, dt, e2e_attempts, "cuda")
         e2e = {"value": e2e_attempts / (dt * 1e9), "unit": UNIT,
                "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps,
                "path": "pa_load(pinned host population) + pa_step + pa_observables + "
                        "pa_dump_range(pinned host) every step"}
+
+    ens = None
+    if not args.no_ensemble and world == 1:
+        run.close()
+        del run
+        torch.cuda.empty_cache()
+        ens = ensemble_compare(P, steps=3)
+    srv = None
+    if not args.no_serving and world == 1:
+        srv = serving_measure(P)
 
     if rank != 0:
         if dist is not None:
@@ -347,11 +458,17 @@ def main():
                               "frac": res_gbs / hbm, "traffic": None,
                               "bytes_per_step": res_bytes,
                               "peak_note": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
-        "gpu_launches": 4 * args.steps * (3 if e2e else 2) + (args.steps if e2e else 0),
+        # kernels inside the headline timed region: k_tau, k_resample, the sweep
+        # kernel and k_obs per graph-replayed step
+        "gpu_launches": 4 * args.steps,
         "clocks": clk.result,
     }
     if e2e:
         line["e2e"] = e2e
+    if ens:
+        line["batched_ensemble"] = ens
+    if srv:
+        line["serving"] = srv
     if cpu:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)

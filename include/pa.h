@@ -228,12 +228,15 @@ int pa_batch_step(pa_batch* batch);
 int pa_batch_run_steps(pa_batch* batch, int32_t nsteps);
 int pa_batch_sync(pa_batch* batch);
 /* Sweep classes and their launch shape: info = {layout, dim, L, model,
- * number of runs, warps per block, slots}.  pa_batch_set_warps chooses the
- * warps per block (2, 4 or 8; the L = 64 register kernel has 16 only) of one
- * class; results do not depend on it. */
+ * number of runs, warps per block, slots, slots per claim}.  The classes of
+ * one step run as parallel branches.  pa_batch_set_shape chooses one class's
+ * warps per block (2, 4 or 8; the L = 64 register kernel has 16 only; 0 keeps
+ * the current value) and slots per claim (1, 2, 4, 8, 16 or 32; 0 picks the
+ * largest that leaves about four claims per resident warp).  Results do not
+ * depend on the shape. */
 int pa_batch_num_classes(pa_batch* batch);
-int pa_batch_class_info(pa_batch* batch, int32_t cls, int32_t info[7]);
-int pa_batch_set_warps(pa_batch* batch, int32_t cls, int32_t warps);
+int pa_batch_class_info(pa_batch* batch, int32_t cls, int32_t info[8]);
+int pa_batch_set_shape(pa_batch* batch, int32_t cls, int32_t warps, int32_t chunk);
 void pa_batch_free(pa_batch* batch);
 
 /* ---- copy counts and scan without device allocation ---------------------

@@ -728,8 +728,11 @@ struct pa_batch {
         pa::BatchSweepArgs args;
         pa::RunDev proto;
         int warps, grid;
+        cudaStream_t stream;  // the class's branch of a step (fork / join)
+        cudaEvent_t done;
     };
     std::vector<Cls> cls;
+    cudaEvent_t fork;
     cudaStream_t cap_stream;
     cudaGraphExec_t graph;
     int64_t steps_left;
@@ -751,12 +754,46 @@ size_t batch_layout(int32_t nruns, size_t off[5]) {
     return o;
 }
 
+// Slots per claim: the largest power of two <= 32 that still leaves about
+// four claims per resident warp, so small classes spread over the GPU.
+uint32_t auto_chunk(uint32_t total_slots, int grid, int warps) {
+    uint32_t chunk = 32;
+    const uint64_t want = 4ull * (uint64_t)grid * (uint64_t)warps;
+    while (chunk > 1 && (uint64_t)(total_slots / chunk) < want) chunk >>= 1;
+    return chunk;
+}
+
+// One batched step: reweight and resample of every run on s, then the sweep
+// classes as parallel branches (fork / join through events), then the
+// observables of every run on s.
 int enqueue_batch_step(pa_batch* b, cudaStream_t s) {
     CK(pa::launch_tau_batched(b->bd, s));
     CK(pa::launch_resample_batched(b->bd, s));
-    for (const auto& c : b->cls) CK(pa::launch_sweep_batched(c.args, c.proto, c.warps, c.grid, s));
+    if (b->cls.size() == 1) {
+        const auto& c = b->cls[0];
+        CK(pa::launch_sweep_batched(c.args, c.proto, c.warps, c.grid, s));
+    } else {
+        CK(cudaEventRecord(b->fork, s));
+        for (const auto& c : b->cls) {
+            CK(cudaStreamWaitEvent(c.stream, b->fork, 0));
+            CK(pa::launch_sweep_batched(c.args, c.proto, c.warps, c.grid, c.stream));
+            CK(cudaEventRecord(c.done, c.stream));
+        }
+        for (const auto& c : b->cls) CK(cudaStreamWaitEvent(s, c.done, 0));
+    }
     CK(pa::launch_obs_batched(b->bd, s));
     return PA_OK;
+}
+
+void batch_release(pa_batch* b) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    for (auto& c : b->cls) {
+        if (c.stream) cudaStreamDestroy(c.stream);
+        if (c.done) cudaEventDestroy(c.done);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
+    delete b;
 }
 }  // namespace
 
@@ -780,23 +817,24 @@ int pa_batch_init(pa_run* const* runs, int32_t nruns, void* ws, size_t bytes, vo
     b->stream = (cudaStream_t)stream;
     b->cap_stream = nullptr;
     b->graph = nullptr;
+    b->fork = nullptr;
     b->steps_left = INT64_MAX;
     std::vector<pa::RunDev> h_runs;
     std::vector<uint32_t> tile_base(1, 0u);
     for (int32_t i = 0; i < nruns; ++i) {
         pa_run* r = runs[i];
         if (!r) {
-            delete b;
+            batch_release(b);
             return PA_ERR_INVALID_ARG;
         }
         for (int32_t j = 0; j < i; ++j)
             if (runs[j] == r) {
-                delete b;
+                batch_release(b);
                 return PA_ERR_INVALID_ARG;
             }
         DevState st;
         if (read_state(r, &st) != PA_OK) {
-            delete b;
+            batch_release(b);
             return PA_ERR_CUDA;
         }
         const int64_t left = (int64_t)r->cfg.K - (int64_t)st.step;
@@ -821,6 +859,8 @@ int pa_batch_init(pa_run* const* runs, int32_t nruns, void* ws, size_t bytes, vo
             k.model = d.model;
             k.proto = d;
             k.warps = pa::l64_batched_applies(d) ? 16 : 4;
+            k.stream = nullptr;
+            k.done = nullptr;
             b->cls.push_back(k);
         }
         b->cls[c].ids.push_back((uint32_t)i);
@@ -849,10 +889,16 @@ int pa_batch_init(pa_run* const* runs, int32_t nruns, void* ws, size_t bytes, vo
         k.args.total_slots = slots;
         k.args.counter = d_counters + 1 + c;
         k.grid = pa::batched_sweep_grid(k.proto, k.warps);
-        if (k.grid <= 0) {
-            delete b;
+        if (k.grid <= 0 || cudaStreamCreateWithFlags(&k.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&k.done, cudaEventDisableTiming) != cudaSuccess) {
+            batch_release(b);
             return PA_ERR_CUDA;
         }
+        k.args.chunk = auto_chunk(slots, k.grid, k.warps);
+    }
+    if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) {
+        batch_release(b);
+        return PA_ERR_CUDA;
     }
     b->bd.runs = d_runs;
     b->bd.nruns = (uint32_t)nruns;
@@ -873,7 +919,7 @@ int pa_batch_init(pa_run* const* runs, int32_t nruns, void* ws, size_t bytes, vo
             cudaSuccess &&
         cudaStreamSynchronize(s) == cudaSuccess;
     if (!ok) {
-        delete b;
+        batch_release(b);
         return PA_ERR_CUDA;
     }
     *out = b;
@@ -926,7 +972,7 @@ int pa_batch_sync(pa_batch* b) {
 
 int pa_batch_num_classes(pa_batch* b) { return b ? (int)b->cls.size() : PA_ERR_INVALID_ARG; }
 
-int pa_batch_class_info(pa_batch* b, int32_t c, int32_t info[7]) {
+int pa_batch_class_info(pa_batch* b, int32_t c, int32_t info[8]) {
     if (!b || !info || c < 0 || c >= (int32_t)b->cls.size()) return PA_ERR_INVALID_ARG;
     const auto& k = b->cls[c];
     info[0] = k.layout;
@@ -936,19 +982,25 @@ int pa_batch_class_info(pa_batch* b, int32_t c, int32_t info[7]) {
     info[4] = (int32_t)k.ids.size();
     info[5] = k.warps;
     info[6] = (int32_t)k.args.total_slots;
+    info[7] = (int32_t)k.args.chunk;
     return PA_OK;
 }
 
-int pa_batch_set_warps(pa_batch* b, int32_t c, int32_t warps) {
+int pa_batch_set_shape(pa_batch* b, int32_t c, int32_t warps, int32_t chunk) {
     if (!b || c < 0 || c >= (int32_t)b->cls.size()) return PA_ERR_INVALID_ARG;
+    if (chunk < 0 || chunk > 32 || (chunk & (chunk - 1))) return PA_ERR_INVALID_ARG;
     auto& k = b->cls[c];
-    if (pa::l64_batched_applies(k.proto)) return warps == 16 ? PA_OK : PA_ERR_INVALID_ARG;
-    if (warps != 2 && warps != 4 && warps != 8) return PA_ERR_INVALID_ARG;
-    if (!pa::batched_warps_valid(k.proto, warps)) return PA_ERR_INVALID_ARG;
-    const int grid = pa::batched_sweep_grid(k.proto, warps);
+    int w = warps == 0 ? k.warps : warps;
+    if (pa::l64_batched_applies(k.proto)) {
+        if (w != 16) return PA_ERR_INVALID_ARG;
+    } else if ((w != 2 && w != 4 && w != 8) || !pa::batched_warps_valid(k.proto, w)) {
+        return PA_ERR_INVALID_ARG;
+    }
+    const int grid = pa::batched_sweep_grid(k.proto, w);
     if (grid <= 0) return PA_ERR_CUDA;
-    k.warps = warps;
+    k.warps = w;
     k.grid = grid;
+    k.args.chunk = chunk ? (uint32_t)chunk : auto_chunk(k.args.total_slots, grid, w);
     if (b->graph) {  // the captured step used the old shape
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
@@ -958,9 +1010,7 @@ int pa_batch_set_warps(pa_batch* b, int32_t c, int32_t warps) {
 
 void pa_batch_free(pa_batch* b) {
     if (!b) return;
-    if (b->graph) cudaGraphExecDestroy(b->graph);
-    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
-    delete b;
+    batch_release(b);
 }
 
 }  // extern "C"

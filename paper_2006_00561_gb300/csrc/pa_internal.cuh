@@ -98,7 +98,8 @@ struct BatchDev {
 
 // One (layout, dim, L, model) class of a batch: the runs one sweep kernel
 // instantiation serves.  Global slot g of the class lies in run run_ids[j]
-// when slot_base[j] <= g < slot_base[j + 1] (capacities rounded up to 32).
+// when slot_base[j] <= g < slot_base[j + 1] (capacities rounded up to 32, so
+// a chunk of `chunk` slots never straddles two runs).
 struct BatchSweepArgs {
     const RunDev* runs;
     const uint32_t* run_ids;     // [n]
@@ -106,6 +107,7 @@ struct BatchSweepArgs {
     uint32_t n;
     uint32_t total_slots;
     uint32_t* counter;           // chunk counter of this class
+    uint32_t chunk;              // slots per claim: 1, 2, 4, 8, 16 or 32
 };
 
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32

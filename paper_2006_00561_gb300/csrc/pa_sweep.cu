@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_sweep(RunDev d, int nsweeps) {
     tally.finish(d.hist, d.accum, lane);
 }
 
-// Batched: chunks of 32 slots of one run, claimed from the class's slot space.
+// Batched: chunks of a.chunk slots of one run, claimed from the class's slot space.
 template <int DIM, int L, int LAYOUT, bool PMJ, int BW>
 __global__ void __launch_bounds__(BW * 32) k_sweep_batched(BatchSweepArgs a) {
     extern __shared__ uint32_t smem[];
@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(BW * 32) k_sweep_batched(BatchSweepArgs a) {
         uint32_t chunk = 0;
         if (lane == 0) chunk = atomicAdd(a.counter, 1u);
         chunk = __shfl_sync(0xffffffffu, chunk, 0);
-        const uint32_t g = chunk * 32u;
+        const uint32_t g = chunk * a.chunk;
         if (g >= a.total_slots) break;
         uint32_t lo = 0, hi = a.n;  // slot_base[lo] <= g < slot_base[hi]
         while (hi - lo > 1) {
@@ -441,7 +441,7 @@ __global__ void __launch_bounds__(BW * 32) k_sweep_batched(BatchSweepArgs a) {
         const RunDev& d = a.runs[a.run_ids[lo]];
         const SweepCtx x = sweep_ctx(d);
         const uint32_t first = g - a.slot_base[lo];
-        for (uint32_t slot = first; slot < first + 32u && slot < x.R; ++slot) {
+        for (uint32_t slot = first; slot < first + a.chunk && slot < x.R; ++slot) {
             int M = 0;
             const uint32_t U = one_replica<DIM, L, LAYOUT, PMJ>(d, x, slot, d.theta, ws, lane, M);
             record(d, x, slot, U, M, lane);

@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(WARPS64 * 32, PA_L64_MIN_BLOCKS)
     tally.finish(d.hist, d.accum, lane);
 }
 
-// Batched: chunks of 32 slots of one run from a class's slot space.
+// Batched: chunks of a.chunk slots of one run from a class's slot space.
 __global__ void __launch_bounds__(WARPS64 * 32, PA_L64_MIN_BLOCKS) k_sweep_l64_batched(BatchSweepArgs a) {
     __shared__ uint32_t s_keys[WARPS64][24];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(WARPS64 * 32, PA_L64_MIN_BLOCKS) k_sweep_l64_b
         uint32_t chunk = 0;
         if (lane == 0) chunk = atomicAdd(a.counter, 1u);
         chunk = __shfl_sync(0xffffffffu, chunk, 0);
-        const uint32_t g = chunk * 32u;
+        const uint32_t g = chunk * a.chunk;
         if (g >= a.total_slots) break;
         uint32_t lo = 0, hi = a.n;
         while (hi - lo > 1) {
@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(WARPS64 * 32, PA_L64_MIN_BLOCKS) k_sweep_l64_b
         const uint32_t ctr3 = (TAG_SWEEP << 28) | d.instance;
         uint4* spins = reinterpret_cast<uint4*>(d.spins[cur]);
         const uint32_t first = g - a.slot_base[lo];
-        for (uint32_t slot = first; slot < first + 32u && slot < R; ++slot) {
+        for (uint32_t slot = first; slot < first + a.chunk && slot < R; ++slot) {
             int M = 0;
             const uint32_t U = l64_replica(K, spins, slot, d.theta, g0, ctr3, t4, t8, full, lane, M);
             if (lane == 0) {

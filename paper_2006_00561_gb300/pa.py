@@ -34,7 +34,7 @@ EXPORTS = [
     "pa_dump_range", "pa_load", "pa_profile", "pa_profile_read",
     "pa_tables", "pa_num_bins", "pa_free", "pa_strerror", "pa_copy_counts_scan_noalloc",
     "pa_batch_workspace_size", "pa_batch_init", "pa_batch_step", "pa_batch_run_steps",
-    "pa_batch_sync", "pa_batch_num_classes", "pa_batch_class_info", "pa_batch_set_warps",
+    "pa_batch_sync", "pa_batch_num_classes", "pa_batch_class_info", "pa_batch_set_shape",
     "pa_batch_free",
 ]
 NOALLOC_MAX_REPLICAS = 8388608
@@ -131,7 +131,7 @@ def lib():
             getattr(L, n).argtypes = [vp]
         L.pa_batch_run_steps.argtypes = [vp, C.c_int32]
         L.pa_batch_class_info.argtypes = [vp, C.c_int32, C.POINTER(C.c_int32)]
-        L.pa_batch_set_warps.argtypes = [vp, C.c_int32, C.c_int32]
+        L.pa_batch_set_shape.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32]
         L.pa_batch_free.argtypes = [vp]
         L.pa_batch_free.restype = None
         L.pa_strerror.argtypes = [C.c_int]
@@ -399,11 +399,15 @@ class Batch:
     def classes(self) -> list:
         out = []
         for c in range(int(lib().pa_batch_num_classes(C.c_void_p(self.h)))):
-            info = (C.c_int32 * 7)()
+            info = (C.c_int32 * 8)()
             _check(lib().pa_batch_class_info(C.c_void_p(self.h), c, info), "pa_batch_class_info")
-            out.append(dict(zip(("layout", "dim", "L", "model", "runs", "warps", "slots"),
-                                list(info))))
+            out.append(dict(zip(("layout", "dim", "L", "model", "runs", "warps", "slots",
+                                 "chunk"), list(info))))
         return out
 
+    def set_shape(self, cls: int, warps: int = 0, chunk: int = 0):
+        _check(lib().pa_batch_set_shape(C.c_void_p(self.h), cls, warps, chunk),
+               "pa_batch_set_shape")
+
     def set_warps(self, cls: int, warps: int):
-        _check(lib().pa_batch_set_warps(C.c_void_p(self.h), cls, warps), "pa_batch_set_warps")
+        self.set_shape(cls, warps, 0)

@@ -1,0 +1,223 @@
+"""Serving loop: continuous batching of population-annealing runs.
+
+Requests (one PA run each) arrive over time.  A request is admitted when its
+workspace fits the HBM budget; its population then stays resident in device
+memory until it finishes.  Every iteration advances all resident runs together
+with the batched form (one launch per phase for all of them, each run at its
+own step of its own schedule), so requests that arrive while others are
+running join the device work at the next iteration.  A finished run's final
+observables are read back, its workspace is released, and waiting requests
+take the freed memory.  Results do not depend on which runs shared a batch:
+every run gives the bits it gives when stepped alone.
+
+The loop is host code around the C ABI (pa_init, pa_batch_*, pa_observables);
+PyTorch provides the device memory and the stream.
+"""
+from __future__ import annotations
+
+import dataclasses
+import time
+
+import numpy as np
+
+from . import pa as P
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    spec: dict                   # make_config keyword arguments (plus 'arrival' seconds)
+    arrival: float               # seconds after the server's start
+    admitted: float | None = None
+    finished: float | None = None
+    result: dict | None = None   # final observables
+    history: list | None = None  # observables of every step, if kept
+    error: str | None = None
+    run: object = None
+    step: int = 0                # annealing steps done (tracked on the host)
+    spins: object = None         # final population (int8), if kept
+
+    @property
+    def latency(self):
+        return None if self.finished is None else self.finished - self.arrival
+
+    def attempts(self) -> int:
+        N = self.spec["L"] ** self.spec["dim"]
+        return sum(h["R"] for h in (self.history or [])[1:]) * N * self.spec["theta"]
+
+
+class Server:
+    """Continuous-batching server over one GPU.
+
+    hbm_budget: bytes of device memory the resident runs' workspaces may use.
+    quantum: most steps run between two admission / retirement points.
+    layout: spin layout of every admitted run.
+    """
+
+    def __init__(self, hbm_budget: int, quantum: int = 8, layout: int = P.LAYOUT_PACKED,
+                 keep_history: bool = True, keep_spins: bool = False, stream=None):
+        import torch
+        self.budget = int(hbm_budget)
+        self.quantum = int(quantum)
+        self.layout = layout
+        self.keep_history = keep_history
+        self.keep_spins = keep_spins
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.queue: list[Request] = []
+        self.resident: list[Request] = []
+        self.done: list[Request] = []
+        self.rejected: list[Request] = []
+        self.used = 0
+        self.max_used = 0
+        self.batch = None
+        self.batch_members: tuple = ()
+        self.iterations = 0
+        self.max_resident = 0
+        self.t0 = None
+        self.phase_s = {"admit": 0.0, "batch": 0.0, "steps": 0.0, "retire": 0.0}
+
+    # -- requests --------------------------------------------------------------
+    def _cfg(self, spec: dict) -> P.Config:
+        keys = ("dim", "L", "model", "K", "theta", "instance_id", "R0", "beta0", "beta_max",
+                "seed", "coupling_seed")
+        return P.make_config(layout=self.layout, **{k: spec[k] for k in keys if k in spec})
+
+    def footprint(self, spec: dict) -> int:
+        return P.pa_workspace_size(self._cfg(spec))
+
+    def submit(self, rid: int, spec: dict, arrival: float):
+        req = Request(rid, dict(spec), arrival)
+        need = self.footprint(spec)
+        if need == 0 or need > self.budget:
+            req.error = "rejected: footprint above the HBM budget" if need else "invalid config"
+            self.rejected.append(req)
+        else:
+            self.queue.append(req)
+        return req
+
+    # -- one iteration ---------------------------------------------------------
+    def _now(self) -> float:
+        return time.perf_counter() - self.t0
+
+    def _admit(self, now: float) -> bool:
+        changed = False
+        self.queue.sort(key=lambda r: r.arrival)
+        i = 0
+        while i < len(self.queue):
+            req = self.queue[i]
+            if req.arrival > now:
+                break
+            need = self.footprint(req.spec)
+            if self.used + need > self.budget:
+                break  # first come, first served: later requests wait too
+            req.run = P.Run(self._cfg(req.spec), stream=self.stream)
+            req.admitted = now
+            self.used += need
+            self.max_used = max(self.max_used, self.used)
+            self.resident.append(req)
+            self.queue.pop(i)
+            changed = True
+        self.max_resident = max(self.max_resident, len(self.resident))
+        return changed
+
+    def _retire(self) -> bool:
+        keep, changed = [], False
+        for req in self.resident:
+            if req.step >= req.spec["K"]:
+                if self.keep_spins:
+                    req.spins = req.run.spins()
+                if self.keep_history:
+                    req.history = req.run.history(0, req.spec["K"] + 1)
+                req.result = req.run.observables()
+                req.finished = self._now()
+                self.used -= self.footprint(req.spec)
+                req.run.close()
+                req.run = None
+                self.done.append(req)
+                changed = True
+            else:
+                keep.append(req)
+        self.resident = keep
+        return changed
+
+    def step(self) -> int:
+        """Admit, advance every resident run by up to `quantum` steps, retire.
+        Returns the number of steps advanced."""
+        if self.t0 is None:
+            self.t0 = time.perf_counter()
+        t = time.perf_counter()
+        now = t - self.t0
+        self._admit(now)
+        t1 = time.perf_counter()
+        self.phase_s["admit"] += t1 - t
+        if not self.resident:
+            return 0
+        members = tuple(id(r) for r in self.resident)
+        if self.batch is None or members != self.batch_members:
+            if self.batch is not None:
+                self.batch.close()
+            self.batch = P.Batch([r.run for r in self.resident], stream=self.stream)
+            self.batch_members = members
+        t2 = time.perf_counter()
+        self.phase_s["batch"] += t2 - t1
+        left = min(r.spec["K"] - r.step for r in self.resident)
+        n = max(1, min(self.quantum, left))
+        self.batch.run_steps(n)
+        rc = self.batch.sync()
+        if rc != 0:
+            raise P.PaError(rc, "batched step")
+        for r in self.resident:
+            r.step += n
+        self.iterations += 1
+        t3 = time.perf_counter()
+        self.phase_s["steps"] += t3 - t2
+        if self._retire():
+            self.batch.close()
+            self.batch = None
+            self.batch_members = ()
+        self.phase_s["retire"] += time.perf_counter() - t3
+        return n
+
+    def idle(self) -> bool:
+        return not self.resident and not self.queue
+
+    def run_trace(self, trace: list, time_scale: float = 1.0, max_seconds: float = 1e9) -> dict:
+        """Serves a list of request specs with an 'arrival' key (seconds, scaled
+        by time_scale) in real time and returns latency / throughput stats."""
+        self.t0 = time.perf_counter()
+        pending = sorted(enumerate(trace), key=lambda x: x[1]["arrival"])
+        k = 0
+        while k < len(pending) or not self.idle():
+            now = self._now()
+            while k < len(pending) and pending[k][1]["arrival"] * time_scale <= now:
+                rid, spec = pending[k]
+                self.submit(rid, spec, spec["arrival"] * time_scale)
+                k += 1
+            if self.resident or (self.queue and self.queue[0].arrival <= now):
+                self.step()
+            elif k < len(pending):
+                time.sleep(min(0.001, max(0.0, pending[k][1]["arrival"] * time_scale - now)))
+            if now > max_seconds:
+                break
+        if self.batch is not None:
+            self.batch.close()
+            self.batch = None
+        return self.stats()
+
+    def stats(self) -> dict:
+        lat = np.array([r.latency for r in self.done if r.latency is not None])
+        wall = self._now() if self.t0 is not None else 0.0
+        attempts = sum(r.attempts() for r in self.done) if self.keep_history else None
+        out = {"served": len(self.done), "rejected": len(self.rejected),
+               "waiting": len(self.queue), "resident": len(self.resident),
+               "max_resident": self.max_resident, "iterations": self.iterations,
+               "max_hbm_bytes": self.max_used, "hbm_budget": self.budget,
+               "host_phase_s": dict(self.phase_s),
+               "wall_s": wall}
+        if lat.size:
+            out.update({"p50_latency_s": float(np.percentile(lat, 50)),
+                        "p99_latency_s": float(np.percentile(lat, 99)),
+                        "mean_latency_s": float(lat.mean())})
+        if attempts is not None and wall > 0:
+            out["served_attempts_per_ns"] = attempts / (wall * 1e9)
+        return out

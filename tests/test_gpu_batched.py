@@ -75,11 +75,14 @@ def test_launch_shape_does_not_change_results(P):
     plain = _runs(P, specs)
     batched = _runs(P, specs)
     batch = P.Batch(batched)
-    shapes = [2, 8, 4, 8, 2]
-    for step, w in enumerate(shapes, start=1):
+    shapes = [(2, 1), (8, 32), (4, 4), (8, 2), (2, 0)]
+    for step, (w, chunk) in enumerate(shapes, start=1):
         for c, info in enumerate(batch.classes()):
             if info["warps"] != 16:
-                batch.set_warps(c, w)
+                batch.set_shape(c, w, chunk)
+                assert batch.classes()[c]["warps"] == w
+                if chunk:
+                    assert batch.classes()[c]["chunk"] == chunk
         batch.run_steps(1)
         for r in plain:
             r.step()
