@@ -377,16 +377,180 @@ __device__ __forceinline__ uint32_t i8_replica(const RunDev& d, const SweepCtx& 
     return U;
 }
 
+// --------------------------------------------------------------------------
+// One replica, packed layout with one 32-bit word per row (L <= 32) and at
+// most 128 rows (2D L <= 32, 3D L <= 10): rows resident in registers.
+// Lane l owns rows l, l + 32, ... and keeps their spins and couplings in
+// registers; the rows are also published in shared memory (S) for the
+// neighbours.  Per half-sweep: (1) Philox blocks in counter order into U
+// (shared), (2) every owned row takes the uniforms of its L/2 colour sites
+// from U at compile-time offsets, tests them against all class thresholds at
+// once (bit j of mask t set iff u_j < T_t) and combines them with the row's
+// bit-sliced classes, (3) the rows are flipped and re-published.  Same
+// counters and thresholds as packed_replica(), hence the same bits.
+// --------------------------------------------------------------------------
+template <int DIM, int L>
+struct RowGeo {
+    static constexpr int NROWS = DIM == 2 ? L : L * L;
+    static constexpr int RPL = (NROWS + 31) / 32;
+    static constexpr int HR = L / 2;  // colour sites per row
+    static constexpr uint32_t MASK = L == 32 ? 0xffffffffu : ((1u << L) - 1u);
+    static constexpr bool OK = L <= 32 && NROWS <= 128;
+};
+
+template <int DIM, int L>
+__device__ __forceinline__ uint32_t rot_plus(uint32_t v) {  // bit x <- bit x+1 (mod L)
+    if constexpr (L == 32) return (v >> 1) | (v << 31);
+    else return ((v >> 1) | (v << (L - 1))) & RowGeo<DIM, L>::MASK;
+}
+template <int DIM, int L>
+__device__ __forceinline__ uint32_t rot_minus(uint32_t v) {  // bit x <- bit x-1 (mod L)
+    if constexpr (L == 32) return (v << 1) | (v >> 31);
+    else return ((v << 1) | (v >> (L - 1))) & RowGeo<DIM, L>::MASK;
+}
+
+template <int DIM, int L, bool PMJ>
+__device__ __forceinline__ uint32_t rows_replica(const RunDev& d, const SweepCtx& x, uint32_t slot,
+                                                 int nsweeps, uint32_t* S, int lane, int& M) {
+    using RG = RowGeo<DIM, L>;
+    using G = Geo<DIM, L>;
+    constexpr int NROWS = RG::NROWS, RPL = RG::RPL, HR = RG::HR;
+    uint32_t* U = S + ((NROWS + 3) & ~3);  // uniforms of the half-sweep, in counter order
+    const uint32_t* Jp = d.jpk;
+    uint8_t* spins = d.spins[x.cur];
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(spins + (size_t)slot * d.stride);
+
+    uint32_t own[RPL], jx[RPL], jxm[RPL], jyp[RPL], jym[RPL], jzp[RPL], jzm[RPL];
+    int yp[RPL], ym[RPL], zp[RPL], zm[RPL], par[RPL];
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) {
+        const int r = lane + 32 * k;
+        own[k] = 0u;
+        jx[k] = jxm[k] = jyp[k] = jym[k] = jzp[k] = jzm[k] = 0u;
+        yp[k] = ym[k] = zp[k] = zm[k] = par[k] = 0;
+        if (r < NROWS) {
+            row_nbrs<DIM, L>(r, yp[k], ym[k], zp[k], zm[k]);
+            par[k] = DIM == 2 ? (r & 1) : ((r % L + r / L) & 1);
+            own[k] = src[r];
+            S[r] = own[k];
+            if constexpr (PMJ) {
+                jx[k] = __ldg(Jp + r);
+                jxm[k] = rot_minus<DIM, L>(jx[k]);
+                jyp[k] = __ldg(Jp + NROWS + r);
+                jym[k] = __ldg(Jp + NROWS + ym[k]);
+                if constexpr (DIM == 3) {
+                    jzp[k] = __ldg(Jp + 2 * NROWS + r);
+                    jzm[k] = __ldg(Jp + 2 * NROWS + zm[k]);
+                }
+            }
+        }
+    }
+    __syncwarp();
+    for (int t = 0; t < nsweeps; ++t) {
+        const uint32_t g = x.g0 + (uint32_t)t;
+        for (int c = 0; c < 2; ++c) {
+            for (int q = lane; q < G::NCALLS; q += 32) {
+                const uint4 u = philox((uint32_t)q, 2u * g + (uint32_t)c, slot, x.ctr3, x.k0, x.k1);
+                reinterpret_cast<uint4*>(U)[q] = u;
+            }
+            __syncwarp();
+            uint32_t flip[RPL];
+#pragma unroll
+            for (int k = 0; k < RPL; ++k) {
+                flip[k] = 0u;
+                const int r = lane + 32 * k;
+                if (r >= NROWS) continue;
+                const uint32_t o = own[k];
+                uint32_t b0 = 0, b1 = 0, b2 = 0;
+                count_add(b0, b1, b2, o ^ rot_plus<DIM, L>(o) ^ jx[k]);
+                count_add(b0, b1, b2, o ^ rot_minus<DIM, L>(o) ^ jxm[k]);
+                count_add(b0, b1, b2, o ^ S[yp[k]] ^ jyp[k]);
+                count_add(b0, b1, b2, o ^ S[ym[k]] ^ jym[k]);
+                if constexpr (DIM == 3) {
+                    count_add(b0, b1, b2, o ^ S[zp[k]] ^ jzp[k]);
+                    count_add(b0, b1, b2, o ^ S[zm[k]] ^ jzm[k]);
+                }
+                const uint32_t zero = ~(b0 | b1 | b2);
+                uint32_t alw, m0, m1, m2;
+                if constexpr (DIM == 2) {
+                    alw = b1 | b2;            // c_u >= 2: dE <= 0
+                    m1 = zero;                // c_u = 0: dE = 8
+                    m0 = b0 & ~b1 & ~b2;      // c_u = 1: dE = 4
+                    m2 = 0u;
+                } else {
+                    alw = b2 | (b1 & b0);     // c_u >= 3
+                    m2 = zero;                // c_u = 0: dE = 12
+                    m1 = b0 & ~b1 & ~b2;      // c_u = 1: dE = 8
+                    m0 = b1 & ~b0 & ~b2;      // c_u = 2: dE = 4
+                }
+                // site frame: bit 2j <-> colour site j of the row (x = 2j + p)
+                const int p = (c + par[k]) & 1;
+                const uint32_t* ur = U + HR * r;
+                uint32_t a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll
+                for (int j = 0; j < HR; ++j) {
+                    const uint32_t u = ur[j];
+                    const uint32_t bit = 1u << (2 * j);
+                    if (u < x.T0) a0 |= bit;
+                    if (u < x.T1) a1 |= bit;
+                    if constexpr (DIM == 3)
+                        if (u < x.T2) a2 |= bit;
+                }
+                if (x.full & 1u) a0 = ~0u;
+                if (x.full & 2u) a1 = ~0u;
+                if (x.full & 4u) a2 = ~0u;
+                constexpr uint32_t EVEN = 0x55555555u;
+                const uint32_t acc = ((alw >> p) | ((m0 >> p) & a0) | ((m1 >> p) & a1) |
+                                      ((m2 >> p) & a2)) & EVEN;
+                flip[k] = (acc << p) & RG::MASK;
+            }
+            __syncwarp();  // every lane is done reading S and U
+#pragma unroll
+            for (int k = 0; k < RPL; ++k) {
+                const int r = lane + 32 * k;
+                if (r < NROWS) {
+                    own[k] ^= flip[k];
+                    S[r] = own[k];
+                }
+            }
+            __syncwarp();
+        }
+    }
+    uint32_t Uc = 0, down = 0;
+    uint32_t* dst = reinterpret_cast<uint32_t*>(spins + (size_t)slot * d.stride);
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) {
+        const int r = lane + 32 * k;
+        if (r >= NROWS) continue;
+        const uint32_t o = own[k];
+        Uc += __popc((o ^ rot_plus<DIM, L>(o) ^ jx[k]) & RG::MASK);
+        Uc += __popc((o ^ S[yp[k]] ^ jyp[k]) & RG::MASK);
+        if constexpr (DIM == 3) Uc += __popc((o ^ S[zp[k]] ^ jzp[k]) & RG::MASK);
+        down += __popc(o & RG::MASK);
+        dst[r] = o;
+    }
+    Uc = warp_sum_u32(Uc);
+    down = warp_sum_u32(down);
+    M = G::N - 2 * (int)down;
+    __syncwarp();
+    return Uc;
+}
+
 // Shared memory per warp of each layout, in 32-bit words.
 template <int DIM, int L, int LAYOUT>
 __host__ __device__ constexpr int warp_words() {
-    return LAYOUT == PA_LAYOUT_PACKED ? 5 * Geo<DIM, L>::NWORDS : Geo<DIM, L>::I8BYTES / 4;
+    if constexpr (LAYOUT != PA_LAYOUT_PACKED) return Geo<DIM, L>::I8BYTES / 4;
+    else if constexpr (RowGeo<DIM, L>::OK)
+        return ((RowGeo<DIM, L>::NROWS + 3) & ~3) + 4 * Geo<DIM, L>::NCALLS;
+    else return 5 * Geo<DIM, L>::NWORDS;
 }
 
 template <int DIM, int L, int LAYOUT, bool PMJ>
 __device__ __forceinline__ uint32_t one_replica(const RunDev& d, const SweepCtx& x, uint32_t slot,
                                                 int nsweeps, uint32_t* wsmem, int lane, int& M) {
-    if constexpr (LAYOUT == PA_LAYOUT_PACKED)
+    if constexpr (LAYOUT == PA_LAYOUT_PACKED && RowGeo<DIM, L>::OK)
+        return rows_replica<DIM, L, PMJ>(d, x, slot, nsweeps, wsmem, lane, M);
+    else if constexpr (LAYOUT == PA_LAYOUT_PACKED)
         return packed_replica<DIM, L, PMJ>(d, x, slot, nsweeps, wsmem, lane, M);
     else
         return i8_replica<DIM, L, PMJ>(d, x, slot, nsweeps, reinterpret_cast<int8_t*>(wsmem), lane,
@@ -400,7 +564,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_sweep(RunDev d, int nsweeps) {
     constexpr int WW = warp_words<DIM, L, LAYOUT>();
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     uint32_t* ws = smem + wib * WW;
-    if constexpr (LAYOUT == PA_LAYOUT_PACKED)
+    if constexpr (LAYOUT == PA_LAYOUT_PACKED && !RowGeo<DIM, L>::OK)
         for (int w = lane; w < Geo<DIM, L>::NWORDS; w += 32) ws[4 * Geo<DIM, L>::NWORDS + w] = 0u;
     __syncwarp();
     const SweepCtx x = sweep_ctx(d);
@@ -422,7 +586,7 @@ __global__ void __launch_bounds__(BW * 32) k_sweep_batched(BatchSweepArgs a) {
     constexpr int WW = warp_words<DIM, L, LAYOUT>();
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     uint32_t* ws = smem + wib * WW;
-    if constexpr (LAYOUT == PA_LAYOUT_PACKED)
+    if constexpr (LAYOUT == PA_LAYOUT_PACKED && !RowGeo<DIM, L>::OK)
         for (int w = lane; w < Geo<DIM, L>::NWORDS; w += 32) ws[4 * Geo<DIM, L>::NWORDS + w] = 0u;
     __syncwarp();
     Tally tally;
