@@ -308,12 +308,21 @@ __device__ __forceinline__ void resample_tile(const RunDev& d, uint32_t tile, Re
     }
 }
 
+// Persistent: one wave of CTAs, each claiming tiles until none is left.
+// Claims come in increasing order, so a tile's lookback only waits on tiles
+// already claimed by running CTAs.
 __global__ void __launch_bounds__(RS_THREADS) k_resample(RunDev d) {
     __shared__ ResampleSmem sm;
     if (!d.st->active) return;
-    if (threadIdx.x == 0) sm.tile = atomicAdd(&d.st->tile_counter, 1u);
-    __syncthreads();
-    resample_tile(d, sm.tile, sm);
+    const uint32_t R = d.st->R_prev;
+    for (;;) {
+        if (threadIdx.x == 0) sm.tile = atomicAdd(&d.st->tile_counter, 1u);
+        __syncthreads();
+        const uint32_t tile = sm.tile;
+        if (tile * (uint32_t)RS_TILE >= R) break;
+        resample_tile(d, tile, sm);
+        __syncthreads();  // sm is reused by the next tile
+    }
 }
 
 // Batched: global tile ids are claimed in increasing order; run r owns ids
@@ -322,21 +331,28 @@ __global__ void __launch_bounds__(RS_THREADS) k_resample(RunDev d) {
 __global__ void __launch_bounds__(RS_THREADS) k_resample_batched(BatchDev b) {
     __shared__ ResampleSmem sm;
     __shared__ uint32_t s_run;
-    if (threadIdx.x == 0) {
-        const uint32_t g = atomicAdd(&b.counters[0], 1u);
-        uint32_t lo = 0, hi = b.nruns;  // tile_base[lo] <= g < tile_base[hi]
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (b.tile_base[mid] <= g) lo = mid;
-            else hi = mid;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const uint32_t g = atomicAdd(&b.counters[0], 1u);
+            if (g >= b.total_tiles) {
+                s_run = 0xffffffffu;
+            } else {
+                uint32_t lo = 0, hi = b.nruns;  // tile_base[lo] <= g < tile_base[hi]
+                while (hi - lo > 1) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (b.tile_base[mid] <= g) lo = mid;
+                    else hi = mid;
+                }
+                s_run = lo;
+                sm.tile = g - b.tile_base[lo];
+            }
         }
-        s_run = lo;
-        sm.tile = g - b.tile_base[lo];
+        __syncthreads();
+        if (s_run == 0xffffffffu) break;
+        const RunDev& d = b.runs[s_run];
+        if (d.st->active) resample_tile(d, sm.tile, sm);
+        __syncthreads();
     }
-    __syncthreads();
-    const RunDev& d = b.runs[s_run];
-    if (!d.st->active) return;
-    resample_tile(d, sm.tile, sm);
 }
 
 __device__ __forceinline__ long long warp_sum_ll(long long v) {
@@ -417,8 +433,28 @@ cudaError_t launch_tau(const RunDev& d, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// One wave of resident CTAs (capped by the number of tiles), looked up once
+// per device and kernel.
+static int resample_wave(const void* fn, int which, uint32_t tiles) {
+    static int cache[64][2];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    int wave = cache[dev][which];
+    if (wave <= 0) {
+        int sms = 0, per_sm = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, RS_THREADS, 0) != cudaSuccess)
+            return 0;
+        wave = sms * (per_sm < 1 ? 1 : per_sm);
+        cache[dev][which] = wave;
+    }
+    return (int)((int64_t)tiles < wave ? (int64_t)tiles : wave);
+}
+
 cudaError_t launch_resample(const RunDev& d, cudaStream_t s) {
-    k_resample<<<d.tiles, RS_THREADS, 0, s>>>(d);
+    const int grid = resample_wave((const void*)k_resample, 0, d.tiles);
+    if (grid <= 0) return cudaErrorInvalidValue;
+    k_resample<<<grid, RS_THREADS, 0, s>>>(d);
     return cudaGetLastError();
 }
 
@@ -433,7 +469,9 @@ cudaError_t launch_tau_batched(const BatchDev& b, cudaStream_t s) {
 }
 
 cudaError_t launch_resample_batched(const BatchDev& b, cudaStream_t s) {
-    k_resample_batched<<<b.total_tiles, RS_THREADS, 0, s>>>(b);
+    const int grid = resample_wave((const void*)k_resample_batched, 1, b.total_tiles);
+    if (grid <= 0) return cudaErrorInvalidValue;
+    k_resample_batched<<<grid, RS_THREADS, 0, s>>>(b);
     return cudaGetLastError();
 }
 
