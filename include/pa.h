@@ -196,6 +196,19 @@ int64_t pa_num_bins(int32_t dim, int32_t L);
  * caller keeps host_src alive until the stream reaches it. */
 int pa_load(pa_run* run, int32_t what, const void* host_src, int64_t count, size_t bytes);
 
+/* Checkpoint / resume.  Random numbers are keyed by step, sweep index, slot
+ * and site, so the complete state of a run at a step boundary is its
+ * population (spins, energy levels, magnetisations), its energy histogram,
+ * the per-step records and a few scalars (step, population sizes, sweep
+ * counter, ln Z, ln Q, S).  pa_checkpoint writes them to host memory
+ * (pa_checkpoint_size bytes; synchronises; refuses a run with a sticky error).
+ * pa_restore loads such a checkpoint into a run created with the same
+ * pa_config (compared byte for byte; PA_ERR_INVALID_ARG otherwise), after
+ * which the run continues exactly as the checkpointed one would have. */
+int64_t pa_checkpoint_size(pa_run* run);
+int pa_checkpoint(pa_run* run, void* host_dst, size_t bytes);
+int pa_restore(pa_run* run, const void* host_src, size_t bytes);
+
 /* Kernel timing (for benchmarks): while enabled, every kernel the run
  * enqueues outside a CUDA graph is bracketed by CUDA events on the run's
  * stream.  pa_profile_read synchronises and returns, per kernel kind

@@ -655,6 +655,104 @@ int pa_load(pa_run* r, int32_t what, const void* src, int64_t count, size_t byte
     return enqueue_sweep(r, r->stream, 0);
 }
 
+// Checkpoint layout: header | records [step+1] | spins [R][stride] | levels [R]
+// | magnetisations [R] | histogram [bins].  The couplings are not stored: they
+// follow from the configuration.
+struct CkptHeader {
+    char magic[8];
+    uint32_t version, pad;
+    pa_config cfg;
+    DevState st;
+    uint64_t R, bins, stride, nrec;
+};
+
+static const char kCkptMagic[8] = {'P', 'A', 'G', 'B', '3', '0', '0', '1'};
+
+int64_t pa_checkpoint_size(pa_run* r) {
+    if (!r) return -1;
+    DevState st;
+    if (read_state(r, &st)) return -1;
+    const RunDev& d = r->d;
+    return (int64_t)sizeof(CkptHeader) + (int64_t)(st.step + 1) * (int64_t)sizeof(pa_obs) +
+           (int64_t)st.R * ((int64_t)d.stride + 8) + d.bins * 4;
+}
+
+int pa_checkpoint(pa_run* r, void* dst, size_t bytes) {
+    if (!r || !dst) return PA_ERR_INVALID_ARG;
+    const int64_t need = pa_checkpoint_size(r);
+    if (need < 0 || (int64_t)bytes < need) return PA_ERR_INVALID_ARG;
+    DevState st;
+    int rc = read_state(r, &st);
+    if (rc) return rc;
+    if (st.status) return sticky_to_code(st.status);
+    const RunDev& d = r->d;
+    CkptHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, kCkptMagic, 8);
+    h.version = 1;
+    h.cfg = r->cfg;
+    h.st = st;
+    h.R = st.R;
+    h.bins = (uint64_t)d.bins;
+    h.stride = d.stride;
+    h.nrec = (uint64_t)st.step + 1;
+    uint8_t* o = (uint8_t*)dst;
+    std::memcpy(o, &h, sizeof(h));
+    o += sizeof(h);
+    CK(cudaMemcpy(o, d.obs, h.nrec * sizeof(pa_obs), cudaMemcpyDeviceToHost));
+    o += h.nrec * sizeof(pa_obs);
+    if (st.R) {
+        CK(cudaMemcpy(o, d.spins[st.cur], (size_t)st.R * d.stride, cudaMemcpyDeviceToHost));
+        o += (size_t)st.R * d.stride;
+        CK(cudaMemcpy(o, d.ebin[st.cur], (size_t)st.R * 4, cudaMemcpyDeviceToHost));
+        o += (size_t)st.R * 4;
+        CK(cudaMemcpy(o, d.mag[st.cur], (size_t)st.R * 4, cudaMemcpyDeviceToHost));
+        o += (size_t)st.R * 4;
+    }
+    CK(cudaMemcpy(o, d.hist, (size_t)d.bins * 4, cudaMemcpyDeviceToHost));
+    return PA_OK;
+}
+
+int pa_restore(pa_run* r, const void* src, size_t bytes) {
+    if (!r || !src || bytes < sizeof(CkptHeader)) return PA_ERR_INVALID_ARG;
+    CkptHeader h;
+    std::memcpy(&h, src, sizeof(h));
+    const RunDev& d = r->d;
+    if (std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 1) return PA_ERR_INVALID_ARG;
+    if (std::memcmp(&h.cfg, &r->cfg, sizeof(pa_config)) != 0) return PA_ERR_INVALID_ARG;
+    if (h.bins != (uint64_t)d.bins || h.stride != d.stride || h.R > d.cap ||
+        h.nrec != (uint64_t)h.st.step + 1 || h.st.step > (uint32_t)r->cfg.K)
+        return PA_ERR_INVALID_ARG;
+    const size_t need = sizeof(h) + h.nrec * sizeof(pa_obs) + h.R * (h.stride + 8) + h.bins * 4;
+    if (bytes < need) return PA_ERR_INVALID_ARG;
+    DevState now;
+    int rc = read_state(r, &now);
+    if (rc) return rc;
+    // the run's own lookback epoch keeps counting; the population goes to buffer 0
+    DevState st = h.st;
+    st.cur = 0;
+    st.src = 0;
+    st.epoch = now.epoch;
+    st.tile_counter = 0;
+    st.active = 0;
+    st.status = 0;
+    r->init_state = st;
+    const uint8_t* in = (const uint8_t*)src + sizeof(h);
+    CK(cudaMemcpy(d.obs, in, h.nrec * sizeof(pa_obs), cudaMemcpyHostToDevice));
+    in += h.nrec * sizeof(pa_obs);
+    if (h.R) {
+        CK(cudaMemcpy(d.spins[0], in, h.R * d.stride, cudaMemcpyHostToDevice));
+        in += h.R * d.stride;
+        CK(cudaMemcpy(d.ebin[0], in, h.R * 4, cudaMemcpyHostToDevice));
+        in += h.R * 4;
+        CK(cudaMemcpy(d.mag[0], in, h.R * 4, cudaMemcpyHostToDevice));
+        in += h.R * 4;
+    }
+    CK(cudaMemcpy(d.hist, in, h.bins * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d.st, &r->init_state, sizeof(DevState), cudaMemcpyHostToDevice));
+    return PA_OK;
+}
+
 int pa_profile(pa_run* r, int32_t enable) {
     if (!r) return PA_ERR_INVALID_ARG;
     r->prof = enable != 0;

@@ -35,7 +35,7 @@ EXPORTS = [
     "pa_tables", "pa_num_bins", "pa_free", "pa_strerror", "pa_copy_counts_scan_noalloc",
     "pa_batch_workspace_size", "pa_batch_init", "pa_batch_step", "pa_batch_run_steps",
     "pa_batch_sync", "pa_batch_num_classes", "pa_batch_class_info", "pa_batch_set_shape",
-    "pa_batch_free",
+    "pa_batch_free", "pa_checkpoint_size", "pa_checkpoint", "pa_restore",
 ]
 NOALLOC_MAX_REPLICAS = 8388608
 
@@ -134,6 +134,10 @@ def lib():
         L.pa_batch_set_shape.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32]
         L.pa_batch_free.argtypes = [vp]
         L.pa_batch_free.restype = None
+        L.pa_checkpoint_size.argtypes = [vp]
+        L.pa_checkpoint_size.restype = C.c_int64
+        L.pa_checkpoint.argtypes = [vp, vp, C.c_size_t]
+        L.pa_restore.argtypes = [vp, vp, C.c_size_t]
         L.pa_strerror.argtypes = [C.c_int]
         L.pa_strerror.restype = C.c_char_p
         _lib = L
@@ -347,6 +351,20 @@ class Run:
 
     def dump(self, what: int) -> np.ndarray:
         return pa_dump(self.h, what)
+
+    def checkpoint(self) -> bytes:
+        n = int(lib().pa_checkpoint_size(C.c_void_p(self.h)))
+        if n < 0:
+            raise PaError(-1, "pa_checkpoint_size")
+        buf = np.zeros(n, dtype=np.uint8)
+        _check(lib().pa_checkpoint(C.c_void_p(self.h), C.c_void_p(buf.ctypes.data), n),
+               "pa_checkpoint")
+        return buf.tobytes()
+
+    def restore(self, blob: bytes):
+        buf = np.frombuffer(blob, dtype=np.uint8).copy()
+        _check(lib().pa_restore(C.c_void_p(self.h), C.c_void_p(buf.ctypes.data), buf.size),
+               "pa_restore")
 
     def load(self, what: int, src: np.ndarray, count: int):
         pa_load(self.h, what, src, count)
