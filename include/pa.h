@@ -61,9 +61,16 @@ extern "C" {
  *   dim 2: L in {4, 8, 16, 32, 64, 128};  dim 3: L in {2, 4, 6, 8, 10, 12, 16}. */
 
 /* One PA run.  beta_i = beta0 + (beta_max - beta0) * i / K, i = 0..K (Sec. 3
- * uses a constant step).  capacity = largest population the workspace holds;
+ * uses a constant step); beta_max is the final inverse temperature and may be
+ * below beta0 (heating).  capacity = largest population the workspace holds;
  * 0 selects R0 + 16 ceil(sqrt(R0)) + 1024.  instance_id < 2^28 separates the
- * random streams of runs that share a seed. */
+ * random streams of runs that share a seed.  init chooses the initial
+ * population (Sec. 2 describes both protocols): PA_INIT_RANDOM, uniform random
+ * states (cooling from beta0 = 0, ln Omega = N ln 2), or PA_INIT_GROUND, the
+ * ferromagnet's ground state with all spins +1 (heating from near T = 0,
+ * ln Omega = ln 2 + beta0 dim N for the two ground states). */
+#define PA_INIT_RANDOM 0
+#define PA_INIT_GROUND 1
 typedef struct {
     int32_t  dim;           /* 2 or 3                                  */
     int32_t  L;             /* linear size, even                        */
@@ -72,7 +79,7 @@ typedef struct {
     int32_t  K;             /* number of annealing steps, >= 1          */
     int32_t  theta;         /* Metropolis sweeps per step, >= 0         */
     int32_t  instance_id;   /* 0 .. 2^28-1                              */
-    int32_t  reserved;      /* must be 0                                */
+    int32_t  init;          /* PA_INIT_RANDOM | PA_INIT_GROUND          */
     int64_t  R0;            /* initial population, 1 .. 2^31            */
     int64_t  capacity;      /* 0 = default                              */
     double   beta0, beta_max;
@@ -177,9 +184,11 @@ typedef struct {
 
 /* Host-side tables the engine uploads, for bitwise comparison before any
  * kernel runs (no GPU needed): T[c] = floor(2^32 exp(-beta_i 4(c+1))), c=0..2,
- * the Metropolis acceptance thresholds at beta_i, and D[j] = exp(-(beta_i -
- * beta_{i-1}) 4 j), j = 0..bins-1, the Eq. 3 weights relative to the lowest
- * occupied energy level (levels are 4 apart).  D is not written for step 0. */
+ * the Metropolis acceptance thresholds at beta_i, and D[j] = exp(-|beta_i -
+ * beta_{i-1}| 4 j), j = 0..bins-1, the Eq. 3 weights of the level j steps
+ * away from the reference level (levels are 4 apart; the reference is the
+ * lowest occupied level when cooling, the highest when heating).  D is not
+ * written for step 0. */
 int pa_tables(const pa_config* cfg, int32_t step, uint64_t T[3], double* D, int64_t bins);
 
 /* Energy levels of (dim, L): dim L^dim / 2 + 1. */

@@ -41,7 +41,11 @@ class Config(C.Structure):
         ("R0", C.c_int64), ("capacity", C.c_int64),
         ("beta0", C.c_double), ("beta_max", C.c_double),
         ("seed", C.c_uint64), ("coupling_seed", C.c_uint64),
+        ("init", C.c_int32), ("pad", C.c_int32),
     ]
+
+
+INIT_RANDOM, INIT_GROUND = 0, 1
 
 
 class Obs(C.Structure):
@@ -84,7 +88,7 @@ def lib():
         L.or_sweep_replica.argtypes = [C.POINTER(Config), i8p, i8p, C.c_int64, C.c_int64,
                                        C.c_int32, u64p]
         L.or_sweep_replica.restype = C.c_int64
-        L.or_tau_table.argtypes = [u32p, C.c_int64, dp, C.c_int64, u32p, u32p, i64p]
+        L.or_tau_table.argtypes = [u32p, C.c_int64, dp, C.c_int64, C.c_int32, u32p, u32p, i64p]
         L.or_tau_table.restype = C.c_double
         L.or_copy_counts.argtypes = [C.POINTER(Config), C.c_int32, u32p, C.c_int64, u32p, u32p,
                                      u32p]
@@ -121,9 +125,10 @@ def _ptr(a: np.ndarray, ctype):
 
 
 def make_config(dim=2, L=16, model=MODEL_FERRO, K=100, theta=10, instance_id=0, R0=1000,
-                capacity=0, beta0=0.0, beta_max=1.0, seed=1, coupling_seed=0) -> Config:
+                capacity=0, beta0=0.0, beta_max=1.0, seed=1, coupling_seed=0,
+                init=INIT_RANDOM) -> Config:
     return Config(dim, L, model, K, theta, instance_id, R0, capacity, beta0, beta_max, seed,
-                  coupling_seed)
+                  coupling_seed, init, 0)
 
 
 # ---------------------------------------------------------------------------
@@ -192,7 +197,7 @@ def sweep_replica(cfg: Config, J: np.ndarray, spins: np.ndarray, slot: int, g0: 
                                       slot, g0, nsweeps, _ptr(Ta, C.c_uint64)))
 
 
-def tau_table(H: np.ndarray, Dtab: np.ndarray, R0: int):
+def tau_table(H: np.ndarray, Dtab: np.ndarray, R0: int, heating: bool = False):
     H = np.ascontiguousarray(H, dtype=np.uint32)
     Dtab = np.ascontiguousarray(Dtab, dtype=np.float64)
     bins = H.size
@@ -200,7 +205,8 @@ def tau_table(H: np.ndarray, Dtab: np.ndarray, R0: int):
     F = np.zeros(bins, dtype=np.uint32)
     kref = C.c_int64()
     S = lib().or_tau_table(_ptr(H, C.c_uint32), bins, _ptr(Dtab, C.c_double), R0,
-                           _ptr(n, C.c_uint32), _ptr(F, C.c_uint32), C.byref(kref))
+                           1 if heating else 0, _ptr(n, C.c_uint32), _ptr(F, C.c_uint32),
+                           C.byref(kref))
     return S, kref.value, n, F
 
 

@@ -52,8 +52,10 @@ static void draw(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t 
  * beta_i = beta0 + (beta_max - beta0) * i / K  (Sec. 3: constant step).
  * Metropolis threshold T(beta, dE) = floor(exp(-beta dE) * 2^32), so that a
  * uniform 32-bit u accepts with probability exp(-beta dE) when u < T.
- * Weight D[j] = exp(-dbeta * 4 j): the factor exp[-(beta_i - beta_{i-1}) E]
- * of Eq. 3 relative to the lowest occupied energy (energies are 4 apart).
+ * Weight D[j] = exp(-|dbeta| * 4 j): the factor exp[-(beta_i - beta_{i-1}) E]
+ * of Eq. 3 relative to the reference energy, j = |k - kref| levels away
+ * (energies are 4 apart): the lowest occupied level when cooling (dbeta >= 0),
+ * the highest when heating (dbeta < 0), so the exponent is never positive.
  * ---------------------------------------------------------------------- */
 double or_beta(const or_config* c, int32_t i)
 {
@@ -69,7 +71,7 @@ uint64_t or_threshold(double beta, int32_t dE)
 
 double or_weight(double dbeta, int64_t j)
 {
-    return exp(-(dbeta * (double)(4 * j)));
+    return exp(-(fabs(dbeta) * (double)(4 * j)));
 }
 
 /* Number of energy levels: U (unsatisfied bonds) runs over 0..dim*N in steps
@@ -154,10 +156,15 @@ void or_init_couplings(const or_config* c, int8_t* J)
 }
 
 /* Initial state at beta0 = 0: every state equally likely (Sec. 2), one
- * independent uniform bit per site.  The top bit of the draw set => -1. */
+ * independent uniform bit per site.  The top bit of the draw set => -1.
+ * Heating from near T = 0 starts from the ground state instead. */
 void or_init_replica(const or_config* c, int64_t slot, int8_t* spins)
 {
     int64_t N = site_count(c->dim, c->L);
+    if (c->init == OR_INIT_GROUND) {
+        for (int64_t s = 0; s < N; ++s) spins[s] = 1;
+        return;
+    }
     for (int64_t s = 0; s < N; ++s) {
         uint32_t out[4];
         draw(c->seed, (uint32_t)(s >> 2), 0u, (uint32_t)slot, OR_TAG_INIT,
@@ -243,20 +250,27 @@ int64_t or_sweep_replica(const or_config* c, const int8_t* J, int8_t* spins,
 
 /* ------------------------------------------------------------------------
  * Eq. 3 / Eq. 4 on the energy histogram H (levels 4 apart).
- *   kref = lowest occupied level, S = sum_k H_k D[k - kref]  (fixed order:
- *   256 contiguous chunks of ceil(bins/256) levels, each summed left to right
- *   from 0.0, then the 256 partial sums combined pairwise, level by level).
- *   tau_k = R0 D[k - kref] / S: Eq. 4 renormalised to the initial population
- *   R0, so that the expected population stays at R0 (Sec. 2 asks to keep it
- *   close to the original one).
+ *   kref = lowest occupied level when cooling, highest when heating; every
+ *   level on the far side of kref is empty.
+ *   S = sum_k H_k D[|k - kref|]  (fixed order: 256 contiguous chunks of
+ *   ceil(bins/256) levels, each summed left to right from 0.0, then the 256
+ *   partial sums combined pairwise, level by level).
+ *   tau_k = R0 D[|k - kref|] / S: Eq. 4 renormalised to the initial
+ *   population R0, so that the expected population stays at R0 (Sec. 2 asks
+ *   to keep it close to the original one).
  *   n_k = floor(tau_k), F_k = floor(frac(tau_k) * 2^32).
  * ---------------------------------------------------------------------- */
 double or_tau_table(const uint32_t* H, int64_t bins, const double* Dtab, int64_t R0,
-                    uint32_t* n, uint32_t* F, int64_t* kref_out)
+                    int32_t heating, uint32_t* n, uint32_t* F, int64_t* kref_out)
 {
     int64_t kref = -1;
-    for (int64_t k = 0; k < bins; ++k)
-        if (H[k] > 0) { kref = k; break; }
+    if (heating) {
+        for (int64_t k = bins - 1; k >= 0; --k)
+            if (H[k] > 0) { kref = k; break; }
+    } else {
+        for (int64_t k = 0; k < bins; ++k)
+            if (H[k] > 0) { kref = k; break; }
+    }
     *kref_out = kref;
     if (kref < 0) {
         for (int64_t k = 0; k < bins; ++k) n[k] = F[k] = 0;
@@ -266,16 +280,19 @@ double or_tau_table(const uint32_t* H, int64_t bins, const double* Dtab, int64_t
     int64_t ch = (bins + 255) / 256;
     for (int64_t ci = 0; ci < 256; ++ci) {
         double acc = 0.0;
-        for (int64_t k = ci * ch; k < (ci + 1) * ch && k < bins; ++k)
-            if (k >= kref) acc = acc + (double)H[k] * Dtab[k - kref];
+        for (int64_t k = ci * ch; k < (ci + 1) * ch && k < bins; ++k) {
+            int64_t j = heating ? kref - k : k - kref;
+            if (j >= 0) acc = acc + (double)H[k] * Dtab[j];
+        }
         part[ci] = acc;
     }
     for (int w = 256; w > 1; w /= 2)
         for (int j = 0; j < w / 2; ++j) part[j] = part[2 * j] + part[2 * j + 1];
     double S = part[0];
     for (int64_t k = 0; k < bins; ++k) {
-        if (k < kref) { n[k] = F[k] = 0; continue; }
-        double tau = ((double)R0 * Dtab[k - kref]) / S;
+        int64_t j = heating ? kref - k : k - kref;
+        if (j < 0) { n[k] = F[k] = 0; continue; }
+        double tau = ((double)R0 * Dtab[j]) / S;
         double nk = floor(tau);
         n[k] = (uint32_t)nk;
         F[k] = (uint32_t)floor((tau - nk) * 4294967296.0);
@@ -363,7 +380,8 @@ or_run* or_create(const or_config* c)
     if (c->L < 2 || (c->L & 1)) return NULL;
     if (c->K < 1 || c->theta < 0 || c->R0 < 1) return NULL;
     if (c->instance_id < 0 || c->instance_id >= (1 << 28)) return NULL;
-    if (c->beta_max < c->beta0) return NULL;
+    if (c->init != OR_INIT_RANDOM && c->init != OR_INIT_GROUND) return NULL;
+    if (c->init == OR_INIT_GROUND && c->model != OR_MODEL_FERRO) return NULL;
     or_run* r = (or_run*)calloc(1, sizeof(or_run));
     r->c = *c;
     r->N = site_count(c->dim, c->L);
@@ -406,7 +424,13 @@ or_run* or_create(const or_config* c)
         r->U[i] = U;
     }
     r->lnQ = 0.0;
-    r->lnZ = (double)r->N * log(2.0);
+    /* ln Z at beta0: N ln 2 states at infinite temperature; near T = 0 the two
+     * ground states (all up, all down) of energy -dim N (Sec. 2, Eq. 5's
+     * initial value ln Omega of each protocol). */
+    if (c->init == OR_INIT_GROUND)
+        r->lnZ = log(2.0) + c->beta0 * (double)((int64_t)c->dim * r->N);
+    else
+        r->lnZ = (double)r->N * log(2.0);
     measure(r);
     return r;
 }
@@ -432,7 +456,7 @@ int or_resample(or_run* r)
     int64_t hsum = 0;
     for (int64_t k = 0; k < r->bins; ++k) hsum += r->H[k];
     if (hsum != r->R) ++r->fails;                /* sum_k H_k = R */
-    r->S = or_tau_table(r->H, r->bins, Dtab, c->R0, r->tn, r->tF, &r->kref);
+    r->S = or_tau_table(r->H, r->bins, Dtab, c->R0, dbeta < 0.0, r->tn, r->tF, &r->kref);
     free(Dtab);
     int64_t Eref = 2 * (2 * r->kref + r->parity) - (int64_t)c->dim * r->N;
     r->lnQ = (log(r->S) - log((double)r->R)) - dbeta * (double)Eref;   /* Eq. 3 */

@@ -53,7 +53,15 @@ typedef struct {
     double   beta0, beta_max;
     uint64_t seed;          /* Philox key of init / sweep / resample     */
     uint64_t coupling_seed; /* Philox key of the +-J bonds               */
+    int32_t  init;          /* OR_INIT_RANDOM | OR_INIT_GROUND           */
+    int32_t  pad;
 } or_config;
+
+/* Initial population: uniform random states (cooling from beta0 = 0) or the
+ * ferromagnet's ground state, all spins +1 (heating from near T = 0; Sec. 2
+ * describes both protocols). */
+#define OR_INIT_RANDOM 0
+#define OR_INIT_GROUND 1
 
 /* Observables after the sweeps at beta_i (Sec. 2: population averages). */
 typedef struct {
@@ -82,7 +90,7 @@ int64_t  or_sweep_replica(const or_config* c, const int8_t* J, int8_t* spins,
 /* Eq. 3 / Eq. 4 on an energy histogram.  Writes n[], F[] (zero below kref),
  * returns S and the index of the lowest occupied bin. */
 double   or_tau_table(const uint32_t* H, int64_t bins, const double* Dtab, int64_t R0,
-                      uint32_t* n, uint32_t* F, int64_t* kref);
+                      int32_t heating, uint32_t* n, uint32_t* F, int64_t* kref);
 void     or_copy_counts(const or_config* c, int32_t step, const uint32_t* ebin, int64_t R,
                         const uint32_t* n, const uint32_t* F, uint32_t* r);
 void     or_derive_obs(or_obs* o, int64_t N);

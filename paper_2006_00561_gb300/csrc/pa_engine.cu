@@ -65,8 +65,9 @@ uint64_t threshold_of(double beta, int32_t dE) {
     return (uint64_t)std::floor(std::exp(x) * 4294967296.0);
 }
 
-// exp(-dbeta 4 j): Eq. 3 weight of level kref + j relative to level kref.
-double weight_of(double dbeta, int64_t j) { return std::exp(-(dbeta * (double)(4 * j))); }
+// exp(-|dbeta| 4 j): Eq. 3 weight of the level j steps away from the reference
+// level (lowest occupied when cooling, highest when heating).
+double weight_of(double dbeta, int64_t j) { return std::exp(-(std::fabs(dbeta) * (double)(4 * j))); }
 
 int64_t ipow(int64_t a, int b) {
     int64_t r = 1;
@@ -81,10 +82,13 @@ int validate(const pa_config* c) {
     if (c->L & 1) return PA_ERR_ODD_L;
     if (c->layout != PA_LAYOUT_INT8 && c->layout != PA_LAYOUT_PACKED) return PA_ERR_INVALID_ARG;
     if (c->model != PA_MODEL_FERRO && c->model != PA_MODEL_PMJ) return PA_ERR_INVALID_ARG;
-    if (c->K < 1 || c->theta < 0 || c->reserved != 0) return PA_ERR_INVALID_ARG;
+    if (c->K < 1 || c->theta < 0) return PA_ERR_INVALID_ARG;
+    if (c->init != PA_INIT_RANDOM && c->init != PA_INIT_GROUND) return PA_ERR_INVALID_ARG;
+    if (c->init == PA_INIT_GROUND && c->model != PA_MODEL_FERRO) return PA_ERR_INVALID_ARG;
     if (c->instance_id < 0 || c->instance_id >= (1 << 28)) return PA_ERR_INVALID_ARG;
     if (c->R0 < 1 || c->R0 > (int64_t(1) << 31)) return PA_ERR_INVALID_ARG;
-    if (!std::isfinite(c->beta0) || !std::isfinite(c->beta_max) || c->beta_max < c->beta0)
+    if (!std::isfinite(c->beta0) || !std::isfinite(c->beta_max) || c->beta0 < 0.0 ||
+        c->beta_max < 0.0)
         return PA_ERR_INVALID_ARG;
     if (c->capacity != 0 && (c->capacity < c->R0 || c->capacity > (int64_t(1) << 31)))
         return PA_ERR_INVALID_ARG;
@@ -103,9 +107,10 @@ void schedule(const pa_config* c, int64_t bins, std::vector<double>& beta,
     std::vector<double> uniq;
     for (int32_t i = 1; i <= c->K; ++i) {
         dbeta[i] = beta[i] - beta[i - 1];
+        const double mag = std::fabs(dbeta[i]);  // tables depend on |dbeta| only
         size_t j = 0;
-        while (j < uniq.size() && std::memcmp(&uniq[j], &dbeta[i], sizeof(double)) != 0) ++j;
-        if (j == uniq.size()) uniq.push_back(dbeta[i]);
+        while (j < uniq.size() && std::memcmp(&uniq[j], &mag, sizeof(double)) != 0) ++j;
+        if (j == uniq.size()) uniq.push_back(mag);
         dsel[i] = (uint32_t)j;
     }
     if (uniq.empty()) uniq.push_back(0.0);
@@ -333,6 +338,7 @@ int pa_init(const pa_config* cfg, void* ws, size_t bytes, void* stream, pa_run**
     d.coupling_seed = cfg->coupling_seed;
     d.one = 1u;
     d.theta = cfg->theta;
+    d.init = cfg->init;
     for (int k = 0; k < 10; ++k) {
         d.rk0[k] = (uint32_t)cfg->seed + (uint32_t)k * 0x9E3779B9u;
         d.rk1[k] = (uint32_t)(cfg->seed >> 32) + (uint32_t)k * 0xBB67AE85u;
@@ -361,7 +367,12 @@ int pa_init(const pa_config* cfg, void* ws, size_t bytes, void* stream, pa_run**
 
     std::memset(&r->init_state, 0, sizeof(DevState));
     r->init_state.R = (uint32_t)cfg->R0;
-    r->init_state.lnZ = (double)l.N * std::log(2.0);
+    // ln Omega of the protocol: N ln 2 states at beta0 = 0, or the two ground
+    // states of energy -dim N near T = 0
+    if (cfg->init == PA_INIT_GROUND)
+        r->init_state.lnZ = std::log(2.0) + cfg->beta0 * (double)((int64_t)cfg->dim * l.N);
+    else
+        r->init_state.lnZ = (double)l.N * std::log(2.0);
     cudaStream_t s = r->stream;
     const size_t K1 = (size_t)cfg->K + 1;
     bool ok = cudaMemcpyAsync(d.st, &r->init_state, sizeof(DevState), cudaMemcpyHostToDevice, s) ==

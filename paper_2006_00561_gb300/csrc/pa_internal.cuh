@@ -64,7 +64,7 @@ struct RunDev {
     const double* dtab;         // [ndist * bins] Eq. 3 weights
     const uint32_t* dsel;       // [K+1] weight table of step i
     const double* beta;         // [K+1]
-    const double* dbeta;        // [K+1] beta_i - beta_{i-1}
+    const double* dbeta;        // [K+1] beta_i - beta_{i-1} (negative when heating)
     unsigned long long* desc;   // [tiles] lookback descriptors
     pa_obs* obs;                // [K+1] per-step records
     uint32_t* jpk;              // packed couplings [dim][nwords] (bit set: J = -1), PMJ only
@@ -82,6 +82,7 @@ struct RunDev {
     uint32_t rk0[10], rk1[10];  // Philox round keys of `seed` (key + r * Weyl constant)
     uint32_t one;               // the value 1, opaque to the compiler (multiply-add tests)
     int32_t theta;              // sweeps per annealing step
+    int32_t init;               // PA_INIT_RANDOM | PA_INIT_GROUND
 };
 
 // A batch of runs stepped together (pa_batch_* in include/pa.h).  Arrays in

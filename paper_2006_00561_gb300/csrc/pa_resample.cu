@@ -2,11 +2,12 @@
 // Eq. 3 and Eq. 4) and the per-step observables (Sec. 2, Eq. 5).
 //
 //  k_tau       one CTA: the energy histogram H of the population at beta_{i-1}
-//              gives kref (lowest occupied level), S = sum_k H_k D[k - kref]
-//              with D[j] = exp(-(beta_i - beta_{i-1}) 4 j), Q = S exp(-dbeta
-//              E(kref)) / R (Eq. 3) and the per-level weights
-//              tau_k = R0 D[k - kref] / S (Eq. 4, renormalised to R0), kept as
-//              n_k = floor(tau_k), F_k = floor(frac(tau_k) 2^32).
+//              gives kref (lowest occupied level when cooling, highest when
+//              heating), S = sum_k H_k D[|k - kref|] with D[j] =
+//              exp(-|beta_i - beta_{i-1}| 4 j), Q = S exp(-dbeta E(kref)) / R
+//              (Eq. 3) and the per-level weights tau_k = R0 D[|k - kref|] / S
+//              (Eq. 4, renormalised to R0), kept as n_k = floor(tau_k),
+//              F_k = floor(frac(tau_k) 2^32).
 //  k_resample  one pass over the population, one tile of RS_TILE replicas per
 //              CTA: copy counts r_j = n_k + [u_j < F_k] (nearest-integer rule),
 //              a single-pass exclusive scan with decoupled lookback across
@@ -60,29 +61,41 @@ __device__ __forceinline__ void tau_run(const RunDev& d) {
         }
         return;
     }
+    // reference level: lowest occupied when cooling, highest when heating
+    const bool heating = d.dbeta[i] < 0.0;
     if (t == 0) {
-        s_kref = 0xffffffffu;
+        s_kref = heating ? 0u : 0xffffffffu;
         s_sum = 0;
     }
     __syncthreads();
-    uint32_t kmin = 0xffffffffu;
+    uint32_t kext = heating ? 0u : 0xffffffffu;
+    bool any = false;
     unsigned long long hs = 0;
     for (uint32_t k = t; k < bins; k += 256) {
         const uint32_t h = d.hist[k];
-        if (h && k < kmin) kmin = k;
+        if (h) {
+            any = true;
+            kext = heating ? (k > kext ? k : kext) : (k < kext ? k : kext);
+        }
         hs += h;
     }
-    atomicMin(&s_kref, kmin);
+    if (heating) {
+        if (any) atomicMax(&s_kref, kext);
+    } else {
+        atomicMin(&s_kref, kext);
+    }
     atomicAdd(&s_sum, hs);
     __syncthreads();
     const uint32_t kref = s_kref;
     const double* D = d.dtab + (size_t)d.dsel[i] * bins;
     // S in the fixed order: 256 contiguous chunks summed left to right, then a
-    // pairwise tree over the chunk sums.
+    // pairwise tree over the chunk sums; level k weighs D[|k - kref|].
     const uint32_t ch = (bins + 255) / 256;
     double acc = 0.0;
-    for (uint32_t k = t * ch; k < (t + 1) * ch && k < bins; ++k)
-        if (k >= kref) acc = __dadd_rn(acc, __dmul_rn((double)d.hist[k], D[k - kref]));
+    for (uint32_t k = t * ch; k < (t + 1) * ch && k < bins; ++k) {
+        const int64_t j = heating ? (int64_t)kref - (int64_t)k : (int64_t)k - (int64_t)kref;
+        if (j >= 0) acc = __dadd_rn(acc, __dmul_rn((double)d.hist[k], D[j]));
+    }
     part[t] = acc;
     __syncthreads();
     for (int w = 256; w > 1; w >>= 1) {
@@ -96,8 +109,9 @@ __device__ __forceinline__ void tau_run(const RunDev& d) {
     const double R0d = (double)d.R0;
     for (uint32_t k = t; k < bins; k += 256) {
         uint32_t n = 0, F = 0;
-        if (k >= kref) {
-            const double tau = __ddiv_rn(__dmul_rn(R0d, D[k - kref]), S);
+        const int64_t j = heating ? (int64_t)kref - (int64_t)k : (int64_t)k - (int64_t)kref;
+        if (j >= 0) {
+            const double tau = __ddiv_rn(__dmul_rn(R0d, D[j]), S);
             const double nk = floor(tau);
             n = (uint32_t)nk;
             F = (uint32_t)floor(__dmul_rn(__dsub_rn(tau, nk), 4294967296.0));

@@ -616,7 +616,8 @@ __global__ void __launch_bounds__(BW * 32) k_sweep_batched(BatchSweepArgs a) {
 }
 
 // --------------------------------------------------------------------------
-// Initial population (Sec. 2: uniform states at beta0 = 0) and couplings.
+// Initial population (Sec. 2: uniform states at beta0 = 0, or the ground
+// state for heating from near T = 0) and couplings.
 // Site s of replica `slot` takes the top bit of word s & 3 of the Philox
 // block (s >> 2, 0, slot, INIT | instance); set means spin -1.  Coupling of
 // bond (s, d): top bit of word s & 3 of (s >> 2, d, 0, COUPLING | instance)
@@ -628,6 +629,10 @@ __global__ void k_init_packed(RunDev d, int nrows, int NW) {
     if (gid >= total) return;
     const uint32_t slot = (uint32_t)(gid / d.nwords);
     const uint32_t w = (uint32_t)(gid % d.nwords);
+    if (d.init == PA_INIT_GROUND) {  // all spins +1
+        reinterpret_cast<uint32_t*>(d.spins[0] + (size_t)slot * d.stride)[w] = 0u;
+        return;
+    }
     const int r = (int)(w / NW), k = (int)(w % NW);
     const uint32_t ctr3 = (TAG_INIT << 28) | d.instance;
     const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
@@ -654,9 +659,16 @@ __global__ void k_init_i8(RunDev d) {
     if (gid >= (uint64_t)d.R0 * calls) return;
     const uint32_t slot = (uint32_t)(gid / calls);
     const uint32_t q = (uint32_t)(gid % calls);
+    int8_t* dst = reinterpret_cast<int8_t*>(d.spins[0] + (size_t)slot * d.stride);
+    if (d.init == PA_INIT_GROUND) {  // all spins +1
+        for (int j = 0; j < 4; ++j) {
+            const int64_t s = 4 * (int64_t)q + j;
+            if (s < d.N) dst[s] = 1;
+        }
+        return;
+    }
     const uint4 u = philox(q, 0u, slot, (TAG_INIT << 28) | d.instance, (uint32_t)d.seed,
                            (uint32_t)(d.seed >> 32));
-    int8_t* dst = reinterpret_cast<int8_t*>(d.spins[0] + (size_t)slot * d.stride);
     for (int j = 0; j < 4; ++j) {
         const int64_t s = 4 * (int64_t)q + j;
         if (s < d.N) dst[s] = (pick(u, (uint32_t)j) >> 31) ? (int8_t)-1 : (int8_t)1;

@@ -24,6 +24,7 @@ ERRORS = {
     -9: "PA_ERR_EMPTY", -10: "PA_ERR_INVARIANT",
 }
 MODEL_FERRO, MODEL_PMJ = 0, 1
+INIT_RANDOM, INIT_GROUND = 0, 1
 LAYOUT_INT8, LAYOUT_PACKED = 0, 1
 (DUMP_SPINS, DUMP_EBIN, DUMP_MAG, DUMP_HIST, DUMP_COUNTS, DUMP_OFFSETS, DUMP_TAB_N, DUMP_TAB_F,
  DUMP_COUPLINGS, DUMP_SPINS_RAW, DUMP_STATE) = range(11)
@@ -50,7 +51,7 @@ class Config(C.Structure):
     _fields_ = [
         ("dim", C.c_int32), ("L", C.c_int32), ("model", C.c_int32), ("layout", C.c_int32),
         ("K", C.c_int32), ("theta", C.c_int32), ("instance_id", C.c_int32),
-        ("reserved", C.c_int32), ("R0", C.c_int64), ("capacity", C.c_int64),
+        ("init", C.c_int32), ("R0", C.c_int64), ("capacity", C.c_int64),
         ("beta0", C.c_double), ("beta_max", C.c_double),
         ("seed", C.c_uint64), ("coupling_seed", C.c_uint64),
     ]
@@ -83,9 +84,9 @@ class State(C.Structure):
 
 def make_config(dim=2, L=16, model=MODEL_FERRO, layout=LAYOUT_PACKED, K=100, theta=10,
                 instance_id=0, R0=1000, capacity=0, beta0=0.0, beta_max=1.0, seed=1,
-                coupling_seed=0) -> Config:
-    return Config(dim, L, model, layout, K, theta, instance_id, 0, R0, capacity, beta0, beta_max,
-                  seed, coupling_seed)
+                coupling_seed=0, init=INIT_RANDOM) -> Config:
+    return Config(dim, L, model, layout, K, theta, instance_id, init, R0, capacity, beta0,
+                  beta_max, seed, coupling_seed)
 
 
 _lib = None

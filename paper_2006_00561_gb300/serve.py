@@ -79,7 +79,7 @@ class Server:
     # -- requests --------------------------------------------------------------
     def _cfg(self, spec: dict) -> P.Config:
         keys = ("dim", "L", "model", "K", "theta", "instance_id", "R0", "beta0", "beta_max",
-                "seed", "coupling_seed")
+                "seed", "coupling_seed", "init")
         return P.make_config(layout=self.layout, **{k: spec[k] for k in keys if k in spec})
 
     def footprint(self, spec: dict) -> int:

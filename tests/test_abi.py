@@ -50,7 +50,8 @@ def test_num_bins(P):
 
 @pytest.mark.parametrize("kw,code", [
     (dict(L=5), -2), (dict(L=6), -3), (dict(L=0), -1), (dict(dim=4), -1), (dict(K=0), -1),
-    (dict(R0=0), -1), (dict(theta=-1), -1), (dict(beta0=1.0, beta_max=0.5), -1),
+    (dict(R0=0), -1), (dict(theta=-1), -1), (dict(beta0=-1.0), -1), (dict(init=2), -1),
+    (dict(init=1, model=1), -1),
     (dict(instance_id=1 << 28), -1), (dict(layout=7), -1), (dict(model=3), -1),
     (dict(capacity=10, R0=100), -1), (dict(dim=3, L=14), -3), (dict(R0=(1 << 31) + 1), -1),
 ])
@@ -75,6 +76,7 @@ def test_workspace_size_grows_with_capacity(P):
     dict(dim=2, L=16, K=100, beta_max=1.0), dict(dim=2, L=64, K=400, beta_max=1.0),
     dict(dim=3, L=10, K=150, beta_max=3.0), dict(dim=2, L=128, K=300, beta_max=3.0),
     dict(dim=2, L=64, K=7, beta0=0.25, beta_max=0.9),
+    dict(dim=2, L=16, K=50, beta0=2.0, beta_max=0.0),
 ])
 def test_host_tables_bitwise_equal_to_oracle(P, spec):
     cfg = P.make_config(**spec)

@@ -71,6 +71,13 @@ def test_ferromagnet_3d(P):
                  beta_max=0.6, seed=12)
 
 
+@pytest.mark.parametrize("L,layout", [(16, 1), (64, 1), (16, 0), (128, 1)])
+def test_heating_from_the_ground_state(P, L, layout):
+    """Heating (Sec. 2): ground-state start at beta0 = 2, beta decreasing."""
+    run_lockstep(P, steps=8, dim=2, L=L, layout=layout, R0=1500 if L < 128 else 80, K=40,
+                 theta=2, beta0=2.0, beta_max=0.0, init=1, seed=60 + L)
+
+
 def test_several_tiles_with_ragged_tail(P):
     """R0 = 5001: three resample tiles, the last one nearly empty."""
     run_lockstep(P, steps=8, dim=2, L=8, layout=1, R0=5001, K=16, theta=2, beta_max=1.5, seed=13)

@@ -36,14 +36,17 @@ MUTANTS = [
      "boltzmann"),
     ("threshold_compare_reversed", "accept = u < T[dE / 4 - 1];",
      "accept = u >= T[dE / 4 - 1];", "beta_zero or boltzmann"),
-    ("weight_wrong_level_spacing", "return exp(-(dbeta * (double)(4 * j)));",
-     "return exp(-(dbeta * (double)(2 * j)));", "weights or tau_table or lnQ"),
+    ("weight_wrong_level_spacing", "return exp(-(fabs(dbeta) * (double)(4 * j)));",
+     "return exp(-(fabs(dbeta) * (double)(2 * j)));", "weights or tau_table or lnQ"),
+    ("weight_signed_dbeta", "return exp(-(fabs(dbeta) * (double)(4 * j)));",
+     "return exp(-(dbeta * (double)(4 * j)));", "weights"),
     ("lnQ_sign_of_reference_energy", "- dbeta * (double)Eref;", "+ dbeta * (double)Eref;",
      "lnQ"),
     ("tau_normalised_by_current_R", "r->S = or_tau_table(r->H, r->bins, Dtab, c->R0,",
      "r->S = or_tau_table(r->H, r->bins, Dtab, r->R,", "lnZ_and_energy_match_kaufman"),
-    ("tau_missing_reference_shift", "acc = acc + (double)H[k] * Dtab[k - kref];",
-     "acc = acc + (double)H[k] * Dtab[k];", "tau_table"),
+    ("tau_missing_reference_shift",
+     "            int64_t j = heating ? kref - k : k - kref;\n            if (j >= 0) acc",
+     "            int64_t j = heating ? kref - k : k;\n            if (j >= 0) acc", "tau_table"),
     ("counts_compare_reversed", "r[i] = n[k] + (u < F[k] ? 1u : 0u);",
      "r[i] = n[k] + (u > F[k] ? 1u : 0u);", "copy_counts"),
     ("offsets_inclusive", "        r->o[j] = (uint32_t)total;\n        total += r->r[j];",
@@ -51,6 +54,10 @@ MUTANTS = [
     ("init_one_word_per_block", "spins[s] = (out[s & 3] >> 31) ? -1 : 1;",
      "spins[s] = (out[0] >> 31) ? -1 : 1;", "fair_coins"),
     ("cv_sign", "(mE2 - mE * mE)", "(mE2 + mE * mE)", "observables"),
+    ("heating_uses_lowest_level", "for (int64_t k = bins - 1; k >= 0; --k)",
+     "for (int64_t k = 0; k < bins; ++k)", "tau_table"),
+    ("ground_state_lnZ_wrong_sign", "r->lnZ = log(2.0) + c->beta0 *",
+     "r->lnZ = log(2.0) - c->beta0 *", "heating_starts"),
 ]
 
 

@@ -36,6 +36,14 @@ def _run_seed(args):
     elif kind == "L4":
         cfg = O.make_config(dim=2, L=4, R0=3000, K=40, theta=4, beta_max=1.2, seed=seed)
         checks = (10, 20, 40)
+    elif kind == "L4_heat":
+        cfg = O.make_config(dim=2, L=4, R0=3000, K=40, theta=4, beta0=2.0, beta_max=0.0,
+                            init=O.INIT_GROUND, seed=seed)
+        checks = (10, 20, 30, 40)
+    elif kind == "L8_heat":
+        cfg = O.make_config(dim=2, L=8, R0=4000, K=100, theta=10, beta0=2.0, beta_max=0.0,
+                            init=O.INIT_GROUND, seed=seed)
+        checks = (40, 70, 100)
     else:
         cfg = O.make_config(dim=3, L=2, model=O.MODEL_PMJ, R0=3000, K=40, theta=4,
                             beta_max=2.0, seed=seed, coupling_seed=6)
@@ -83,6 +91,9 @@ def _pa_vs_dos(kind, dos):
         assert max(abs(r - 3000) for r in Rs) <= 2.5 * np.sqrt(3000)
     for i in res[0][0]:
         beta = res[0][0][i][0]
+        if beta == 0.0:
+            _assert_within([r[0][i][1] for r in res], 16 * np.log(2.0))
+            continue
         _assert_within([r[0][i][1] for r in res], float(exact.lnZ_from_dos(dos, beta)))
         _assert_within([r[0][i][2] for r in res], exact.mean_energy_from_dos(dos, beta))
 
@@ -93,6 +104,32 @@ def test_pa_lnZ_matches_bruteforce_2d_L4():
     J = np.ones(32, dtype=np.int8)
     dos = exact.density_of_states(2 * O.energy(2, 4, J, s)[0] - 32 for s in exact.all_states(16))
     _pa_vs_dos("L4", dos)
+
+
+@pytest.mark.slow
+def test_pa_heating_recovers_bruteforce_2d_L4():
+    """Heating (Sec. 2) from the ground state at beta0 = 2 down to beta = 0: ln Z
+    along the way matches brute force, and at beta = 0 it recovers N ln 2."""
+    from oracle import oracle as O
+    J = np.ones(32, dtype=np.int8)
+    dos = exact.density_of_states(2 * O.energy(2, 4, J, s)[0] - 32 for s in exact.all_states(16))
+    _pa_vs_dos("L4_heat", dos)
+
+
+@pytest.mark.slow
+def test_pa_heating_recovers_kaufman_L8():
+    """Heating the 8 x 8 torus from its ground state at beta0 = 2 through the
+    transition down to beta = 0 (R0 = 4000, 100 steps, theta = 10): ln Z within
+    3 SE of Kaufman on the way and of the exact N ln 2 at the end.  (PA's
+    finite-population bias shrinks like 1/R0 while the standard error shrinks
+    like 1/sqrt(R0); R0 = 4000 keeps the bias well inside 3 SE.)"""
+    res = _runs("L8_heat", list(range(300, 316)))
+    for out, fails, Rs in res:
+        assert fails == 0
+    for i in (40, 70, 100):
+        beta = res[0][0][i][0]
+        want = 64 * np.log(2.0) if beta == 0.0 else float(exact.kaufman_lnZ(8, beta))
+        _assert_within([r[0][i][1] for r in res], want)
 
 
 @pytest.mark.slow

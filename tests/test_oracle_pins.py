@@ -233,7 +233,9 @@ def test_thresholds_against_high_precision_exp():
 
 
 def test_weights_against_high_precision_exp():
+    """D[j] = exp(-|dbeta| 4 j): never above 1, for cooling and heating steps."""
     mp.mp.dps = 40
+    assert O.weight(-0.02, 7) == O.weight(0.02, 7)
     for dbeta in [0.0, 0.005, 0.0025, 0.02, 0.5]:
         for j in [0, 1, 2, 7, 100, 4096]:
             x = mp.mpf(dbeta) * 4 * j
@@ -334,16 +336,19 @@ def _random_hist(rng, bins, R, lo, width):
 
 @pytest.mark.parametrize("bins,R0,R,dbeta", [(257, 1000, 1013, 0.01), (4097, 2 ** 17, 131000, 0.005),
                                             (1501, 2 ** 14, 2 ** 14, 0.02), (9, 50, 47, 0.3),
-                                            (257, 1000, 990, 0.0)])
+                                            (257, 1000, 990, 0.0), (257, 1000, 1013, -0.01),
+                                            (4097, 2 ** 17, 131000, -0.005), (9, 50, 47, -0.3)])
 def test_tau_table_against_eq4_high_precision(bins, R0, R, dbeta):
     """tau_k = R0 exp(-dbeta E_k) / sum_j exp(-dbeta E_j) (Eq. 4 renormalised to
-    R0) in 40-digit arithmetic; n_k + F_k/2^32 reproduces it to < 2^-32."""
+    R0) in 40-digit arithmetic; n_k + F_k/2^32 reproduces it to < 2^-32.  A
+    negative dbeta is a heating step (reference level = highest occupied)."""
     mp.mp.dps = 40
     rng = np.random.default_rng(bins + R)
     H = _random_hist(rng, bins, R, lo=bins // 5, width=max(bins // 10, 3))
     Dtab = np.array([O.weight(dbeta, j) for j in range(bins)])
-    S, kref, n, F = O.tau_table(H, Dtab, R0)
-    assert kref == int(np.nonzero(H)[0][0])
+    S, kref, n, F = O.tau_table(H, Dtab, R0, heating=dbeta < 0)
+    occupied = np.nonzero(H)[0]
+    assert kref == int(occupied[-1] if dbeta < 0 else occupied[0])
     w = {k: mp.exp(-mp.mpf(dbeta) * 4 * k) for k in range(bins) if H[k]}
     Z = mp.fsum(H[k] * w[k] for k in w)
     S_exact = Z / w[kref]
@@ -355,7 +360,8 @@ def test_tau_table_against_eq4_high_precision(bins, R0, R, dbeta):
         assert abs(got - tau) <= mp.mpf(2) ** -32 + 1e-13 * tau, k
         total += H[k] * tau
     assert abs(total - R0) < 1e-9 * R0  # sum_k H_k tau_k = R0
-    assert (n[:kref] == 0).all() and (F[:kref] == 0).all()
+    far = slice(kref + 1, None) if dbeta < 0 else slice(0, kref)
+    assert (n[far] == 0).all() and (F[far] == 0).all()
 
 
 def test_copy_counts_are_nearest_integers_with_the_right_mean():
@@ -437,6 +443,22 @@ def test_resample_copies_are_exact_and_ordered():
         assert run.sweep(cfg.theta) == 0
 
 
+def test_heating_starts_from_the_ground_state():
+    """Heating (Sec. 2): all spins +1, ln Z(beta0) = ln 2 + beta0 dim N (the two
+    ground states of energy -dim N), and a heating step keeps the population."""
+    cfg = O.make_config(dim=2, L=8, R0=300, K=20, theta=2, beta0=2.0, beta_max=0.0,
+                        init=O.INIT_GROUND, seed=5)
+    run = O.Run(cfg)
+    assert (run.spins() == 1).all() and (run.ebin() == 0).all()
+    assert run.lnZ == np.log(2.0) + 2.0 * 128
+    o = run.observables()
+    assert o["sumE"] == -128 * 300 and o["m_abs"] == 1.0
+    for _ in range(5):
+        assert run.step() == 0
+    assert run.check_failures == 0
+    assert abs(run.R - 300) < 5 * np.sqrt(300)
+
+
 def test_capacity_overflow_is_an_error():
     cfg = O.make_config(dim=2, L=8, R0=200, capacity=200, K=50, theta=1, beta_max=3.0, seed=1)
     run = O.Run(cfg)
@@ -450,7 +472,8 @@ def test_capacity_overflow_is_an_error():
 
 def test_bad_configurations_are_rejected():
     for kw in [dict(L=5), dict(L=0), dict(dim=4), dict(K=0), dict(R0=0), dict(theta=-1),
-               dict(beta0=1.0, beta_max=0.5), dict(instance_id=1 << 28)]:
+               dict(init=2), dict(init=O.INIT_GROUND, model=O.MODEL_PMJ),
+               dict(instance_id=1 << 28)]:
         with pytest.raises(ValueError):
             O.Run(O.make_config(**kw))
 
