@@ -205,15 +205,38 @@ int64_t pa_num_bins(int32_t dim, int32_t L);
  * caller keeps host_src alive until the stream reaches it. */
 int pa_load(pa_run* run, int32_t what, const void* host_src, int64_t count, size_t bytes);
 
+/* Adaptive temperature step (Sec. 3 points to the adaptive step of its
+ * reference).  pa_adaptive_beta synchronises, reads the energy histogram of the
+ * measured population at the current beta, and returns in *beta_next the
+ * largest step towards beta_end (smaller than beta for heating) whose
+ * reweighted histogram still overlaps the current one by at least
+ * overlap_target, where overlap = sum_k min(H_k / R, H_k w_k / sum_j H_j w_j)
+ * and w_k = exp(-|dbeta| 4 |k - kref|) (60 bisection steps on |dbeta|; beta_end
+ * itself when its overlap suffices).  The decision is taken on the host in
+ * IEEE double with libm exp, in a fixed order.
+ * Call it between steps (after the sweeps of the current step), when the
+ * histogram describes the current population.
+ * pa_resample_to is pa_resample towards an arbitrary beta_next >= 0: the step
+ * index i advances by one, and step i's beta, thresholds and weight table are
+ * replaced (weight tables of such steps go to two slots reserved in the
+ * workspace).  Later pa_step / pa_resample calls keep the fixed schedule's
+ * betas, the first of them with its temperature step taken from beta_next, so
+ * adaptive and scheduled steps can be mixed.  Synchronises; PA_ERR_DONE once
+ * the step index would pass K. */
+int pa_adaptive_beta(pa_run* run, double overlap_target, double beta_end, double* beta_next);
+int pa_resample_to(pa_run* run, double beta_next);
+
 /* Checkpoint / resume.  Random numbers are keyed by step, sweep index, slot
  * and site, so the complete state of a run at a step boundary is its
  * population (spins, energy levels, magnetisations), its energy histogram,
  * the per-step records and a few scalars (step, population sizes, sweep
  * counter, ln Z, ln Q, S).  pa_checkpoint writes them to host memory
  * (pa_checkpoint_size bytes; synchronises; refuses a run with a sticky error).
- * pa_restore loads such a checkpoint into a run created with the same
- * pa_config (compared byte for byte; PA_ERR_INVALID_ARG otherwise), after
- * which the run continues exactly as the checkpointed one would have. */
+ * The current step's beta is stored too, so a run on adaptive steps resumes
+ * from where it stood.  pa_restore loads such a checkpoint into a run created
+ * with the same pa_config (compared byte for byte; PA_ERR_INVALID_ARG
+ * otherwise), after which the run continues exactly as the checkpointed one
+ * would have. */
 int64_t pa_checkpoint_size(pa_run* run);
 int pa_checkpoint(pa_run* run, void* host_dst, size_t bytes);
 int pa_restore(pa_run* run, const void* host_src, size_t bytes);

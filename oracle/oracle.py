@@ -93,6 +93,15 @@ def lib():
         L.or_copy_counts.argtypes = [C.POINTER(Config), C.c_int32, u32p, C.c_int64, u32p, u32p,
                                      u32p]
         L.or_derive_obs.argtypes = [C.POINTER(Obs), C.c_int64]
+        L.or_overlap.argtypes = [u32p, C.c_int64, C.c_int64, C.c_double]
+        L.or_overlap.restype = C.c_double
+        L.or_adaptive_next.argtypes = [u32p, C.c_int64, C.c_int64, C.c_double, C.c_double,
+                                       C.c_double]
+        L.or_adaptive_next.restype = C.c_double
+        L.or_resample_to.argtypes = [C.c_void_p, C.c_double]
+        L.or_resample_to.restype = C.c_int
+        L.or_current_beta.argtypes = [C.c_void_p]
+        L.or_current_beta.restype = C.c_double
         L.or_create.argtypes = [C.POINTER(Config)]
         L.or_create.restype = C.c_void_p
         L.or_destroy.argtypes = [C.c_void_p]
@@ -220,6 +229,16 @@ def copy_counts(cfg: Config, step: int, ebin: np.ndarray, n: np.ndarray, F: np.n
     return r
 
 
+def overlap(H: np.ndarray, R: int, dbeta: float) -> float:
+    H = np.ascontiguousarray(H, dtype=np.uint32)
+    return float(lib().or_overlap(_ptr(H, C.c_uint32), H.size, R, dbeta))
+
+
+def adaptive_next(H: np.ndarray, R: int, beta: float, beta_end: float, target: float) -> float:
+    H = np.ascontiguousarray(H, dtype=np.uint32)
+    return float(lib().or_adaptive_next(_ptr(H, C.c_uint32), H.size, R, beta, beta_end, target))
+
+
 def derive_obs(sums: dict, N: int) -> dict:
     o = Obs()
     for k in ("step", "R", "sumE", "sumE2", "sumAbsM", "sumM2", "beta", "lnQ", "lnZ"):
@@ -257,6 +276,13 @@ class Run:
 
     def sweep(self, n: int) -> int:
         return lib().or_sweep(self._h, n)
+
+    def resample_to(self, beta_next: float) -> int:
+        return lib().or_resample_to(self._h, beta_next)
+
+    @property
+    def beta(self) -> float:
+        return float(lib().or_current_beta(self._h))
 
     def step(self) -> int:
         return lib().or_step(self._h)

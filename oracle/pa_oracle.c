@@ -300,6 +300,54 @@ double or_tau_table(const uint32_t* H, int64_t bins, const double* Dtab, int64_t
     return S;
 }
 
+/* ------------------------------------------------------------------------
+ * Adaptive temperature step (Sec. 3 points to the adaptive step of its
+ * reference): keep the energy histograms of successive temperatures
+ * overlapping by a target fraction.
+ * ---------------------------------------------------------------------- */
+double or_overlap(const uint32_t* H, int64_t bins, int64_t R, double dbeta)
+{
+    int heating = dbeta < 0.0;
+    int64_t kref = -1;
+    if (heating) {
+        for (int64_t k = bins - 1; k >= 0; --k)
+            if (H[k] > 0) { kref = k; break; }
+    } else {
+        for (int64_t k = 0; k < bins; ++k)
+            if (H[k] > 0) { kref = k; break; }
+    }
+    if (kref < 0 || R < 1) return 0.0;
+    double sw = 0.0;
+    for (int64_t k = 0; k < bins; ++k) {
+        int64_t j = heating ? kref - k : k - kref;
+        if (j >= 0 && H[k]) sw = sw + (double)H[k] * or_weight(dbeta, j);
+    }
+    double a = 0.0;
+    for (int64_t k = 0; k < bins; ++k) {
+        int64_t j = heating ? kref - k : k - kref;
+        if (j < 0 || !H[k]) continue;
+        double p = (double)H[k] / (double)R;
+        double q = ((double)H[k] * or_weight(dbeta, j)) / sw;
+        a = a + (p < q ? p : q);
+    }
+    return a;
+}
+
+double or_adaptive_next(const uint32_t* H, int64_t bins, int64_t R, double beta,
+                        double beta_end, double target)
+{
+    double span = beta_end - beta;
+    if (span == 0.0) return beta;
+    if (or_overlap(H, bins, R, span) >= target) return beta_end;
+    double lo = 0.0, hi = fabs(span), sgn = span < 0.0 ? -1.0 : 1.0;
+    for (int it = 0; it < 60; ++it) {
+        double mid = lo + (hi - lo) * 0.5;
+        if (or_overlap(H, bins, R, sgn * mid) >= target) lo = mid;
+        else hi = mid;
+    }
+    return beta + sgn * lo;
+}
+
 /* Nearest-integer resampling (the Poisson draw of Sec. 2 replaced by one of
  * its variants): r_i = n_k + [u_i < F_k], u_i = word (i & 3) of the Philox
  * block (i >> 2, step, 0, RESAMPLE|id).  E[r_i] = tau_k. */
@@ -342,6 +390,7 @@ struct or_run {
     int32_t *M, *M2;
     int64_t *U, *U2;       /* energies tracked through the sweeps */
     uint64_t *T;           /* [(K+1) * 3] */
+    double *betas;         /* [K+1] inverse temperature of every step */
     double S, lnQ, lnZ;
     or_obs obs;
 };
@@ -368,7 +417,7 @@ static void measure(or_run* r)
         o->sumAbsM += M < 0 ? -M : M;
         o->sumM2 += M * M;
     }
-    o->beta = or_beta(&r->c, r->step);
+    o->beta = r->betas[r->step];
     o->lnQ = r->lnQ;
     o->lnZ = r->lnZ;
     or_derive_obs(o, r->N);
@@ -405,9 +454,12 @@ or_run* or_create(const or_config* c)
     r->tn = (uint32_t*)calloc(bins, 4);
     r->tF = (uint32_t*)calloc(bins, 4);
     r->T = (uint64_t*)calloc((size_t)(c->K + 1) * 3, 8);
-    for (int32_t i = 0; i <= c->K; ++i)
+    r->betas = (double*)calloc((size_t)(c->K + 1), 8);
+    for (int32_t i = 0; i <= c->K; ++i) {
+        r->betas[i] = or_beta(c, i);
         for (int cl = 0; cl < 3; ++cl)
-            r->T[i * 3 + cl] = or_threshold(or_beta(c, i), 4 * (cl + 1));
+            r->T[i * 3 + cl] = or_threshold(r->betas[i], 4 * (cl + 1));
+    }
     or_init_couplings(c, r->J);
     r->R = c->R0;
     r->kref = -1;
@@ -440,9 +492,20 @@ void or_destroy(or_run* r)
     if (!r) return;
     free(r->J); free(r->spins); free(r->spins2); free(r->ebin); free(r->ebin2);
     free(r->M); free(r->M2); free(r->U); free(r->U2); free(r->r); free(r->o);
-    free(r->H); free(r->tn); free(r->tF); free(r->T);
+    free(r->H); free(r->tn); free(r->tF); free(r->T); free(r->betas);
     free(r);
 }
+
+int or_resample_to(or_run* r, double beta_next)
+{
+    int32_t i = r->step + 1;
+    if (i > r->c.K) return -2;
+    r->betas[i] = beta_next;
+    for (int cl = 0; cl < 3; ++cl) r->T[i * 3 + cl] = or_threshold(beta_next, 4 * (cl + 1));
+    return or_resample(r);
+}
+
+double or_current_beta(const or_run* r) { return r->betas[r->step]; }
 
 int or_resample(or_run* r)
 {
@@ -450,7 +513,7 @@ int or_resample(or_run* r)
     int32_t i = r->step + 1;
     if (i > c->K) return -2;
     if (r->R < 1) return -4;
-    double dbeta = or_beta(c, i) - or_beta(c, i - 1);
+    double dbeta = r->betas[i] - r->betas[i - 1];
     double* Dtab = (double*)malloc(sizeof(double) * (size_t)r->bins);
     for (int64_t j = 0; j < r->bins; ++j) Dtab[j] = or_weight(dbeta, j);
     int64_t hsum = 0;

@@ -95,11 +95,26 @@ void     or_copy_counts(const or_config* c, int32_t step, const uint32_t* ebin, 
                         const uint32_t* n, const uint32_t* F, uint32_t* r);
 void     or_derive_obs(or_obs* o, int64_t N);
 
+/* Histogram overlap between the population at the current beta (levels H,
+ * R replicas) and its reweighting to beta + dbeta:
+ *   alpha = sum_k min(H_k / R, H_k w_k / sum_j H_j w_j),
+ *   w_k = D[|k - kref|] of or_weight.  Sums run over k ascending from 0.0. */
+double   or_overlap(const uint32_t* H, int64_t bins, int64_t R, double dbeta);
+/* Adaptive step: the largest beta_next in [beta, beta_end] (or (beta_end,
+ * beta] when heating) whose overlap is >= target, by 60 bisection steps on
+ * |dbeta| (beta_end itself when its overlap suffices). */
+double   or_adaptive_next(const uint32_t* H, int64_t bins, int64_t R, double beta,
+                          double beta_end, double target);
+
 /* ---- a whole run ------------------------------------------------------- */
 typedef struct or_run or_run;
 or_run*  or_create(const or_config* c);      /* NULL on bad config */
 void     or_destroy(or_run* r);
 int      or_resample(or_run* r);              /* beta_{i-1} -> beta_i; 0 ok, <0 error */
+/* Resample to an arbitrary next inverse temperature (the step index still
+ * advances by one; the thresholds of that step follow beta_next). */
+int      or_resample_to(or_run* r, double beta_next);
+double   or_current_beta(const or_run* r);
 int      or_sweep(or_run* r, int32_t nsweeps);/* at beta_i, then measure           */
 int      or_step(or_run* r);                  /* or_resample + or_sweep(theta)      */
 void     or_observables(const or_run* r, or_obs* out);

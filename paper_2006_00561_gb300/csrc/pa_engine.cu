@@ -25,6 +25,11 @@ struct pa_run {
     std::vector<uint32_t> thr;
     std::vector<double> beta, dbeta, dtab;
     std::vector<uint32_t> dsel;
+    uint32_t ndist;  // weight tables of the fixed schedule
+    // the fixed schedule, kept to undo the per-step overrides of pa_resample_to
+    std::vector<uint32_t> thr_fixed, dsel_fixed;
+    std::vector<double> beta_fixed, dbeta_fixed;
+    std::vector<double> dyn_table[2];  // host copies of the two dynamic weight slots
     DevState init_state;
     cudaStream_t cap_stream;
     cudaGraphExec_t graph;
@@ -153,7 +158,7 @@ int make_layout(const pa_config* c, Layout* Lo, std::vector<double>* beta, std::
     l.beta = take(K1 * 8);
     l.dbeta = take(K1 * 8);
     l.dsel = take(K1 * 4);
-    l.dtab = take((size_t)(l.ndist * l.bins * 8));
+    l.dtab = take((size_t)((l.ndist + 2) * l.bins * 8));  // + two dynamic slots
     l.accum = take(16 + (size_t)l.bins * 4);
     l.tabn = take((size_t)l.bins * 4);
     l.tabF = take((size_t)l.bins * 4);
@@ -233,6 +238,59 @@ int enqueue_resample(pa_run* r, cudaStream_t s) {
     return timed(r, s, 1, [&] { return pa::launch_resample(r->d, s); });
 }
 
+// Metropolis thresholds of the three dE classes at beta, and the mask of the
+// classes that always accept.
+void thresholds_into(double beta, uint32_t* t4) {
+    uint32_t full = 0;
+    for (int c = 0; c < 3; ++c) {
+        const uint64_t T = threshold_of(beta, 4 * (c + 1));
+        if (T >= 4294967296ull) {
+            full |= 1u << c;
+            t4[c] = 0xffffffffu;
+        } else {
+            t4[c] = (uint32_t)T;
+        }
+    }
+    t4[3] = full;
+}
+
+// Moves step i of the schedule to inverse temperature b, with temperature step
+// b - beta[i-1]: the thresholds, beta and dbeta of step i are replaced, and its
+// weight table goes to dynamic slot i & 1 unless the fixed schedule already
+// has this exact step.  Host copies first, then stream-ordered uploads.
+int set_step(pa_run* r, uint32_t i, double b, cudaStream_t s) {
+    RunDev& d = r->d;
+    r->beta[i] = b;
+    thresholds_into(b, &r->thr[(size_t)i * 4]);
+    if (i >= 1) {
+        r->dbeta[i] = b - r->beta[i - 1];
+        if (r->dbeta[i] == r->dbeta_fixed[i]) {
+            r->dsel[i] = r->dsel_fixed[i];
+        } else {
+            std::vector<double>& t = r->dyn_table[i & 1];
+            t.resize((size_t)d.bins);
+            for (int64_t j = 0; j < d.bins; ++j) t[j] = weight_of(r->dbeta[i], j);
+            r->dsel[i] = r->ndist + (i & 1);
+            CK(cudaMemcpyAsync((void*)(d.dtab + (size_t)r->dsel[i] * d.bins), t.data(),
+                               (size_t)d.bins * 8, cudaMemcpyHostToDevice, s));
+        }
+        CK(cudaMemcpyAsync((void*)(d.dbeta + i), &r->dbeta[i], 8, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync((void*)(d.dsel + i), &r->dsel[i], 4, cudaMemcpyHostToDevice, s));
+    }
+    CK(cudaMemcpyAsync((void*)(d.beta + i), &r->beta[i], 8, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync((void*)(d.thr + (size_t)i * 4), &r->thr[(size_t)i * 4], 16,
+                       cudaMemcpyHostToDevice, s));
+    return PA_OK;
+}
+
+// Step i at beta_i; step i + 1 keeps its fixed beta, with its temperature step
+// taken from beta_i.
+int move_step(pa_run* r, uint32_t i, double b, cudaStream_t s) {
+    int rc = set_step(r, i, b, s);
+    if (rc == PA_OK && i + 1 <= (uint32_t)r->cfg.K) rc = set_step(r, i + 1, r->beta_fixed[i + 1], s);
+    return rc;
+}
+
 int enqueue_step(pa_run* r, cudaStream_t s) {
     int rc = enqueue_resample(r, s);
     if (rc) return rc;
@@ -285,6 +343,7 @@ int pa_init(const pa_config* cfg, void* ws, size_t bytes, void* stream, pa_run**
     r->dbeta = dbeta;
     r->dsel = dsel;
     r->dtab = dtab;
+    r->ndist = (uint32_t)l.ndist;
     r->cap_stream = nullptr;
     r->graph = nullptr;
     r->prof = false;
@@ -294,19 +353,11 @@ int pa_init(const pa_config* cfg, void* ws, size_t bytes, void* stream, pa_run**
     }
     r->load_R = 0;
     r->thr.assign((size_t)(cfg->K + 1) * 4, 0u);
-    for (int32_t i = 0; i <= cfg->K; ++i) {
-        uint32_t full = 0;
-        for (int c = 0; c < 3; ++c) {
-            const uint64_t T = threshold_of(beta[i], 4 * (c + 1));
-            if (T >= 4294967296ull) {
-                full |= 1u << c;
-                r->thr[i * 4 + c] = 0xffffffffu;
-            } else {
-                r->thr[i * 4 + c] = (uint32_t)T;
-            }
-        }
-        r->thr[i * 4 + 3] = full;
-    }
+    for (int32_t i = 0; i <= cfg->K; ++i) thresholds_into(beta[i], &r->thr[(size_t)i * 4]);
+    r->thr_fixed = r->thr;
+    r->dsel_fixed = r->dsel;
+    r->beta_fixed = r->beta;
+    r->dbeta_fixed = r->dbeta;
 
     uint8_t* base = (uint8_t*)ws;
     RunDev& d = r->d;
@@ -675,9 +726,10 @@ struct CkptHeader {
     pa_config cfg;
     DevState st;
     uint64_t R, bins, stride, nrec;
+    double beta_step;  // beta of the current step (differs from the schedule after pa_resample_to)
 };
 
-static const char kCkptMagic[8] = {'P', 'A', 'G', 'B', '3', '0', '0', '1'};
+static const char kCkptMagic[8] = {'P', 'A', 'G', 'B', '3', '0', '0', '2'};
 
 int64_t pa_checkpoint_size(pa_run* r) {
     if (!r) return -1;
@@ -700,13 +752,14 @@ int pa_checkpoint(pa_run* r, void* dst, size_t bytes) {
     CkptHeader h;
     std::memset(&h, 0, sizeof(h));
     std::memcpy(h.magic, kCkptMagic, 8);
-    h.version = 1;
+    h.version = 2;
     h.cfg = r->cfg;
     h.st = st;
     h.R = st.R;
     h.bins = (uint64_t)d.bins;
     h.stride = d.stride;
     h.nrec = (uint64_t)st.step + 1;
+    h.beta_step = r->beta[st.step];
     uint8_t* o = (uint8_t*)dst;
     std::memcpy(o, &h, sizeof(h));
     o += sizeof(h);
@@ -729,7 +782,7 @@ int pa_restore(pa_run* r, const void* src, size_t bytes) {
     CkptHeader h;
     std::memcpy(&h, src, sizeof(h));
     const RunDev& d = r->d;
-    if (std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 1) return PA_ERR_INVALID_ARG;
+    if (std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 2) return PA_ERR_INVALID_ARG;
     if (std::memcmp(&h.cfg, &r->cfg, sizeof(pa_config)) != 0) return PA_ERR_INVALID_ARG;
     if (h.bins != (uint64_t)d.bins || h.stride != d.stride || h.R > d.cap ||
         h.nrec != (uint64_t)h.st.step + 1 || h.st.step > (uint32_t)r->cfg.K)
@@ -761,7 +814,95 @@ int pa_restore(pa_run* r, const void* src, size_t bytes) {
     }
     CK(cudaMemcpy(d.hist, in, h.bins * 4, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d.st, &r->init_state, sizeof(DevState), cudaMemcpyHostToDevice));
+    // back to the fixed schedule, then the checkpointed step's own beta
+    const size_t K1 = (size_t)r->cfg.K + 1;
+    r->thr = r->thr_fixed;
+    r->dsel = r->dsel_fixed;
+    r->beta = r->beta_fixed;
+    r->dbeta = r->dbeta_fixed;
+    CK(cudaMemcpy((void*)d.thr, r->thr.data(), K1 * 16, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy((void*)d.beta, r->beta.data(), K1 * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy((void*)d.dbeta, r->dbeta.data(), K1 * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy((void*)d.dsel, r->dsel.data(), K1 * 4, cudaMemcpyHostToDevice));
+    if (h.beta_step != r->beta_fixed[h.st.step]) {
+        rc = move_step(r, h.st.step, h.beta_step, r->stream);
+        if (rc) return rc;
+        CK(cudaStreamSynchronize(r->stream));
+    }
     return PA_OK;
+}
+
+// Histogram overlap of the population with its reweighting to beta + dbeta:
+// sum_k min(H_k / R, H_k w_k / sum_j H_j w_j), sums over k ascending.
+static double overlap_of(const std::vector<uint32_t>& H, int64_t R, double dbeta) {
+    const bool heating = dbeta < 0.0;
+    const int64_t bins = (int64_t)H.size();
+    int64_t kref = -1;
+    if (heating) {
+        for (int64_t k = bins - 1; k >= 0; --k)
+            if (H[k]) {
+                kref = k;
+                break;
+            }
+    } else {
+        for (int64_t k = 0; k < bins; ++k)
+            if (H[k]) {
+                kref = k;
+                break;
+            }
+    }
+    if (kref < 0 || R < 1) return 0.0;
+    double sw = 0.0;
+    for (int64_t k = 0; k < bins; ++k) {
+        const int64_t j = heating ? kref - k : k - kref;
+        if (j >= 0 && H[k]) sw = sw + (double)H[k] * weight_of(dbeta, j);
+    }
+    double a = 0.0;
+    for (int64_t k = 0; k < bins; ++k) {
+        const int64_t j = heating ? kref - k : k - kref;
+        if (j < 0 || !H[k]) continue;
+        const double p = (double)H[k] / (double)R;
+        const double q = ((double)H[k] * weight_of(dbeta, j)) / sw;
+        a = a + (p < q ? p : q);
+    }
+    return a;
+}
+
+int pa_adaptive_beta(pa_run* r, double target, double beta_end, double* beta_next) {
+    if (!r || !beta_next || !std::isfinite(target) || !std::isfinite(beta_end) || beta_end < 0.0)
+        return PA_ERR_INVALID_ARG;
+    DevState st;
+    int rc = read_state(r, &st);
+    if (rc) return rc;
+    if (st.status) return sticky_to_code(st.status);
+    std::vector<uint32_t> H((size_t)r->d.bins);
+    CK(cudaMemcpy(H.data(), r->d.hist, H.size() * 4, cudaMemcpyDeviceToHost));
+    const double beta = r->beta[st.step];
+    const double span = beta_end - beta;
+    if (span == 0.0 || overlap_of(H, st.R, span) >= target) {
+        *beta_next = span == 0.0 ? beta : beta_end;
+        return PA_OK;
+    }
+    double lo = 0.0, hi = std::fabs(span);
+    const double sgn = span < 0.0 ? -1.0 : 1.0;
+    for (int it = 0; it < 60; ++it) {
+        const double mid = lo + (hi - lo) * 0.5;
+        if (overlap_of(H, st.R, sgn * mid) >= target) lo = mid;
+        else hi = mid;
+    }
+    *beta_next = beta + sgn * lo;
+    return PA_OK;
+}
+
+int pa_resample_to(pa_run* r, double beta_next) {
+    if (!r || !std::isfinite(beta_next) || beta_next < 0.0) return PA_ERR_INVALID_ARG;
+    DevState st;
+    int rc = read_state(r, &st);
+    if (rc) return rc;
+    if (st.step + 1 > (uint32_t)r->cfg.K) return PA_ERR_DONE;
+    rc = move_step(r, st.step + 1, beta_next, r->stream);
+    if (rc) return rc;
+    return enqueue_resample(r, r->stream);
 }
 
 int pa_profile(pa_run* r, int32_t enable) {

@@ -37,6 +37,7 @@ EXPORTS = [
     "pa_batch_workspace_size", "pa_batch_init", "pa_batch_step", "pa_batch_run_steps",
     "pa_batch_sync", "pa_batch_num_classes", "pa_batch_class_info", "pa_batch_set_shape",
     "pa_batch_free", "pa_checkpoint_size", "pa_checkpoint", "pa_restore",
+    "pa_adaptive_beta", "pa_resample_to",
 ]
 NOALLOC_MAX_REPLICAS = 8388608
 
@@ -135,6 +136,8 @@ def lib():
         L.pa_batch_set_shape.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32]
         L.pa_batch_free.argtypes = [vp]
         L.pa_batch_free.restype = None
+        L.pa_adaptive_beta.argtypes = [vp, C.c_double, C.c_double, C.POINTER(C.c_double)]
+        L.pa_resample_to.argtypes = [vp, C.c_double]
         L.pa_checkpoint_size.argtypes = [vp]
         L.pa_checkpoint_size.restype = C.c_int64
         L.pa_checkpoint.argtypes = [vp, vp, C.c_size_t]
@@ -352,6 +355,15 @@ class Run:
 
     def dump(self, what: int) -> np.ndarray:
         return pa_dump(self.h, what)
+
+    def adaptive_beta(self, overlap_target: float, beta_end: float) -> float:
+        out = C.c_double()
+        _check(lib().pa_adaptive_beta(C.c_void_p(self.h), overlap_target, beta_end,
+                                      C.byref(out)), "pa_adaptive_beta")
+        return out.value
+
+    def resample_to(self, beta_next: float):
+        _check(lib().pa_resample_to(C.c_void_p(self.h), beta_next), "pa_resample_to")
 
     def checkpoint(self) -> bytes:
         n = int(lib().pa_checkpoint_size(C.c_void_p(self.h)))

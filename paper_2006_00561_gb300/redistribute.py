@@ -22,10 +22,12 @@ Policies:
   * naive       -- per-replica exchange in proportion to the offspring
     surplus: every shard above the desired load gives a fraction `alpha` of
     its surplus, shards below it take in proportion to their shortage.
-Readings (the paper leaves them open): the main algorithm moves one block at a
-time from the shard with the largest excess to the shard with the largest
-shortage (lowest index on ties) until no pair qualifies; the naive rule is the
-proportional partial exchange above with alpha = 1/2.
+Readings (the paper leaves them open): the main algorithm matches surplus
+blocks to deficit blocks greedily in shard order (the lowest-indexed shard with
+a qualifying excess gives to the lowest-indexed shard with a qualifying
+shortage, a block at a time); `main_largest` is the alternative reading that
+always moves from the largest excess to the largest shortage.  The naive rule
+is the proportional partial exchange above with alpha = 1/2.
 """
 from __future__ import annotations
 
@@ -75,12 +77,31 @@ def desired_loads(R: int, N: int) -> list:
     return [base + (1 if n < rem else 0) for n in range(N)]
 
 
-def plan_main(loads: list, block: int = 1024, maxexc: int = 1) -> list:
-    """Block moves (src, dst) of the main algorithm for the given loads."""
+def plan_main(loads: list, block: int = 1024, maxexc: int = 1, match: str = "order") -> list:
+    """Block moves (src, dst) of the main algorithm for the given loads.  A shard
+    gives while its excess maxg_n is at least `maxexc` blocks (and it holds a
+    block), and takes while its shortage minl_n is at least `maxexc` blocks.
+    match = "order": surplus and deficit shards are paired in shard order;
+    match = "largest": each block goes from the largest excess to the largest
+    shortage."""
     N = len(loads)
     cur = list(loads)
     want = desired_loads(sum(loads), N)
     moves = []
+    if match == "order":
+        src, dst = 0, 0
+        while src < N and dst < N:
+            if cur[src] - want[src] < maxexc * block or cur[src] < block:
+                src += 1
+            elif want[dst] - cur[dst] < maxexc * block:
+                dst += 1
+            else:
+                cur[src] -= block
+                cur[dst] += block
+                moves.append((src, dst))
+        return moves
+    if match != "largest":
+        raise ValueError(match)
     while True:
         exc = [cur[n] - want[n] for n in range(N)]
         src = max(range(N), key=lambda n: (exc[n], -n))
@@ -152,8 +173,9 @@ class Shards:
                      alpha: float = 0.5) -> int:
         """Applies a policy; returns the replicas moved."""
         moved = 0
-        if policy == "main":
-            for s, d in plan_main(self.loads(), block, maxexc):
+        if policy in ("main", "main_largest"):
+            match = "order" if policy == "main" else "largest"
+            for s, d in plan_main(self.loads(), block, maxexc, match):
                 self.move(s, d, block)
                 moved += block
         elif policy == "naive":
@@ -165,7 +187,8 @@ class Shards:
         return moved
 
 
-def run_sharded(run, K: int, N: int, policies=("independent", "naive", "main"), block=1024,
+def run_sharded(run, K: int, N: int, policies=("independent", "naive", "main", "main_largest"),
+                block=1024,
                 maxexc=1, alpha=0.5, theta=None) -> dict:
     """Anneals `run` for K steps and follows every policy on the same sequence
     of resamples (the redistribution does not change the physics).  Returns

@@ -221,3 +221,37 @@ class Server:
         if attempts is not None and wall > 0:
             out["served_attempts_per_ns"] = attempts / (wall * 1e9)
         return out
+
+
+def main(argv=None):
+    """python -m paper_2006_00561_gb300.serve --requests 256 --rate 50
+    Serves the seeded request trace in real time and prints latency /
+    throughput statistics (offered vs served load) as one JSON line."""
+    import argparse
+    import json
+
+    from . import workloads
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--requests", type=int, default=256)
+    ap.add_argument("--rate", type=float, default=50.0)
+    ap.add_argument("--seed", type=int, default=5)
+    ap.add_argument("--budget-gb", type=float, default=64.0)
+    ap.add_argument("--quantum", type=int, default=8)
+    ap.add_argument("--r0-exp", type=int, nargs=2, default=(12, 18))
+    ap.add_argument("--k-range", type=int, nargs=2, default=(100, 300))
+    a = ap.parse_args(argv)
+    trace = workloads.serving_trace(a.requests, rate=a.rate, seed=a.seed, R0_exp=tuple(a.r0_exp),
+                                    K_range=tuple(a.k_range))
+    offered = sum(t["R0"] * t["L"] ** t["dim"] * t["theta"] * t["K"] for t in trace)
+    span = trace[-1]["arrival"]
+    srv = Server(hbm_budget=int(a.budget_gb * (1 << 30)), quantum=a.quantum)
+    st = srv.run_trace(trace)
+    st.update({"requests": a.requests, "rate_per_s": a.rate, "seed": a.seed,
+               "offered_attempts": offered, "offered_attempts_per_ns": offered / (span * 1e9),
+               "trace_span_s": span, "R0_exp": list(a.r0_exp), "K_range": list(a.k_range)})
+    print(json.dumps(st))
+    return st
+
+
+if __name__ == "__main__":
+    main()

@@ -65,3 +65,31 @@ def test_checkpoint_refused_by_another_configuration(P):
         a.restore(bytes(bad))
     with pytest.raises(P.PaError):
         a.restore(blob[:100])
+
+
+def test_restored_adaptive_run_continues_identically(P):
+    """A run on adaptive temperature steps resumes at its own beta: the step
+    after the restore takes its temperature step from there."""
+    spec = dict(dim=2, L=16, layout=1, R0=2000, K=30, theta=2, beta_max=1.0, seed=45)
+    a = P.Run(P.make_config(**spec))
+    for _ in range(4):
+        a.resample_to(a.adaptive_beta(0.7, 1.0))
+        a.sweep(2)
+    blob = a.checkpoint()
+    a.step()
+    a.resample_to(a.adaptive_beta(0.7, 1.0))
+    a.sweep(2)
+    b = P.Run(P.make_config(**spec))
+    for _ in range(6):
+        b.resample_to(b.adaptive_beta(0.5, 1.0))  # another trajectory, to be replaced
+        b.sweep(2)
+    b.restore(blob)
+    assert b.observables()["beta"] == a.history(4, 1)[0]["beta"]
+    b.step()
+    b.resample_to(b.adaptive_beta(0.7, 1.0))
+    b.sweep(2)
+    for what in (P.DUMP_SPINS_RAW, P.DUMP_HIST, P.DUMP_COUNTS, P.DUMP_OFFSETS):
+        assert np.array_equal(a.dump(what), b.dump(what)), what
+    assert a.history(0, 7) == b.history(0, 7)
+    a.close()
+    b.close()

@@ -78,6 +78,70 @@ def test_heating_from_the_ground_state(P, L, layout):
                  theta=2, beta0=2.0, beta_max=0.0, init=1, seed=60 + L)
 
 
+@pytest.mark.parametrize("L,layout,beta0,beta_end", [(16, 1, 0.0, 1.0), (64, 1, 0.0, 1.0),
+                                                     (16, 0, 0.0, 1.0), (16, 1, 2.0, 0.0)])
+def test_adaptive_schedule(P, L, layout, beta0, beta_end):
+    """Adaptive temperature steps: the engine picks the same next beta as the
+    oracle (bit for bit) and the resample / sweep at it match."""
+    init = 1 if beta0 > beta_end else 0
+    from lockstep import compare_state
+    ocfg, gcfg = configs(P, dim=2, L=L, layout=layout, R0=1200, K=40, theta=2, beta0=beta0,
+                         beta_max=beta_end, seed=70 + L, init=init)
+    orun, grun = O.Run(ocfg), P.Run(gcfg)
+    for i in range(1, 9):
+        H = orun.hist()
+        b_o = O.adaptive_next(H, orun.R, orun.beta, beta_end, 0.8)
+        b_g = grun.adaptive_beta(0.8, beta_end)
+        assert b_g == b_o, (i, b_g, b_o)
+        assert orun.resample_to(b_o) == 0 and orun.sweep(2) == 0
+        grun.resample_to(b_g)
+        grun.sweep(2)
+        compare_state(P, grun, orun, i)
+        assert grun.observables()["beta"] == b_o
+    # back on the fixed schedule: the next step's dbeta starts from the adaptive
+    # beta (and may change sign), the one after is the schedule's own
+    for i in range(9, 12):
+        assert orun.step() == 0
+        grun.step()
+        compare_state(P, grun, orun, i)
+    # and adaptive again, once more, through a CUDA graph in between
+    b_o = O.adaptive_next(orun.hist(), orun.R, orun.beta, beta_end, 0.9)
+    assert grun.adaptive_beta(0.9, beta_end) == b_o
+    assert orun.resample_to(b_o) == 0 and orun.sweep(2) == 0
+    grun.resample_to(b_o)
+    grun.sweep(2)
+    compare_state(P, grun, orun, 12)
+    for i in range(13, 15):
+        assert orun.step() == 0
+    grun.run_steps(2)
+    compare_state(P, grun, orun, 14)
+    grun.close()
+    orun.close()
+
+
+def test_adaptive_step_reaches_the_end_and_stops(P):
+    """A run driven by adaptive steps reaches beta_end exactly; past K it reports
+    PA_ERR_DONE; an invalid target beta is rejected."""
+    _, gcfg = configs(P, dim=2, L=8, layout=1, R0=2000, K=30, theta=2, beta_max=0.3, seed=88)
+    run = P.Run(gcfg)
+    with pytest.raises(P.PaError) as e:
+        run.resample_to(-0.5)
+    assert e.value.code == -1
+    n = 0
+    while run.observables()["beta"] < 0.3:
+        run.resample_to(run.adaptive_beta(0.5, 0.3))
+        run.sweep(2)
+        n += 1
+        assert n <= 30
+    assert run.observables()["beta"] == 0.3
+    while run.state()["step"] < 30:
+        run.resample_to(0.3)
+    with pytest.raises(P.PaError) as e:
+        run.resample_to(0.3)
+    assert e.value.code == -8
+    run.close()
+
+
 def test_several_tiles_with_ragged_tail(P):
     """R0 = 5001: three resample tiles, the last one nearly empty."""
     run_lockstep(P, steps=8, dim=2, L=8, layout=1, R0=5001, K=16, theta=2, beta_max=1.5, seed=13)

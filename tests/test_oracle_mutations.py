@@ -54,8 +54,16 @@ MUTANTS = [
     ("init_one_word_per_block", "spins[s] = (out[s & 3] >> 31) ? -1 : 1;",
      "spins[s] = (out[0] >> 31) ? -1 : 1;", "fair_coins"),
     ("cv_sign", "(mE2 - mE * mE)", "(mE2 + mE * mE)", "observables"),
-    ("heating_uses_lowest_level", "for (int64_t k = bins - 1; k >= 0; --k)",
-     "for (int64_t k = 0; k < bins; ++k)", "tau_table"),
+    ("heating_uses_lowest_level",
+     "{\n    int64_t kref = -1;\n    if (heating) {\n        for (int64_t k = bins - 1; k >= 0; --k)",
+     "{\n    int64_t kref = -1;\n    if (heating) {\n        for (int64_t k = 0; k < bins; ++k)",
+     "tau_table"),
+    ("overlap_heating_uses_lowest_level",
+     "dbeta < 0.0;\n    int64_t kref = -1;\n    if (heating) {\n        for (int64_t k = bins - 1;"
+     " k >= 0; --k)",
+     "dbeta < 0.0;\n    int64_t kref = -1;\n    if (heating) {\n        for (int64_t k = 0; k < bins;"
+     " ++k)", "overlap"),
+    ("overlap_uses_max", "a = a + (p < q ? p : q);", "a = a + (p > q ? p : q);", "overlap"),
     ("ground_state_lnZ_wrong_sign", "r->lnZ = log(2.0) + c->beta0 *",
      "r->lnZ = log(2.0) - c->beta0 *", "heating_starts"),
 ]

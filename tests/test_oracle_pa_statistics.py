@@ -48,6 +48,18 @@ def _run_seed(args):
         cfg = O.make_config(dim=3, L=2, model=O.MODEL_PMJ, R0=3000, K=40, theta=4,
                             beta_max=2.0, seed=seed, coupling_seed=6)
         checks = (10, 20, 40)
+    if kind == "L16_adaptive":
+        cfg = O.make_config(dim=2, L=16, R0=1000, K=400, theta=10, seed=seed)
+        run = O.Run(cfg)
+        betas = [0.0]
+        while run.beta < 1.0:
+            b = O.adaptive_next(run.hist(), run.R, run.beta, 1.0, 0.85)
+            assert b > run.beta
+            assert run.resample_to(b) == 0
+            assert run.sweep(cfg.theta) == 0
+            betas.append(run.beta)
+        o = run.observables()
+        return {"betas": betas, "lnZ": o["lnZ"], "e": o["sumE"] / o["R"]}, run.check_failures, []
     run = O.Run(cfg)
     out, Rs = {}, []
     for i in range(1, cfg.K + 1):
@@ -130,6 +142,23 @@ def test_pa_heating_recovers_kaufman_L8():
         beta = res[0][0][i][0]
         want = 64 * np.log(2.0) if beta == 0.0 else float(exact.kaufman_lnZ(8, beta))
         _assert_within([r[0][i][1] for r in res], want)
+
+
+@pytest.mark.slow
+def test_pa_adaptive_schedule_matches_kaufman_L16():
+    """Adaptive temperature steps (overlap target 0.85) from beta 0 to 1 on the
+    16 x 16 torus: ln Z(1) and <E>/N within 3 SE of Kaufman; the steps shrink
+    where the energy distribution narrows less than it shifts (near beta_c)."""
+    res = _runs("L16_adaptive", list(range(500, 516)))
+    for out, fails, _ in res:
+        assert fails == 0
+        b = np.array(out["betas"])
+        assert b[-1] == 1.0 and (np.diff(b) > 0).all()
+    _assert_within([r[0]["lnZ"] for r in res], float(exact.kaufman_lnZ(16, 1.0)))
+    _assert_within([r[0]["e"] / 256 for r in res], exact.kaufman_energy_per_site(16, 1.0))
+    steps = np.diff(res[0][0]["betas"])
+    mids = 0.5 * (np.array(res[0][0]["betas"][1:]) + np.array(res[0][0]["betas"][:-1]))
+    assert steps[(mids > 0.4) & (mids < 0.5)].mean() < steps[mids < 0.1].mean()
 
 
 @pytest.mark.slow

@@ -443,6 +443,44 @@ def test_resample_copies_are_exact_and_ordered():
         assert run.sweep(cfg.theta) == 0
 
 
+@pytest.mark.parametrize("dbeta", [0.0, 0.004, 0.02, 0.1, -0.01, -0.05])
+def test_overlap_against_high_precision(dbeta):
+    """Overlap of the current energy histogram and its reweighting to
+    beta + dbeta, sum_k min(H_k/R, H_k w_k / sum_j H_j w_j), in 40 digits."""
+    mp.mp.dps = 40
+    rng = np.random.default_rng(int(abs(dbeta) * 1e4) + (dbeta < 0))
+    H = _random_hist(rng, 257, 5000, lo=60, width=40)
+    R = int(H.sum())
+    E = {k: 4 * k for k in range(257) if H[k]}
+    w = {k: mp.exp(-mp.mpf(dbeta) * E[k]) for k in E}
+    Z = mp.fsum(H[k] * w[k] for k in E)
+    want = mp.fsum(min(mp.mpf(int(H[k])) / R, H[k] * w[k] / Z) for k in E)
+    got = O.overlap(H, R, dbeta)
+    assert abs(got - want) < 1e-13
+    assert 0.0 < got <= 1.0 + 1e-15
+
+
+def test_adaptive_step_brackets_the_target():
+    """The adaptive next beta keeps the overlap at or above the target, and a
+    slightly larger step would fall below it (monotone bisection)."""
+    rng = np.random.default_rng(3)
+    for target in (0.5, 0.8, 0.95):
+        H = _random_hist(rng, 4097, 131072, lo=1500, width=200)
+        R = int(H.sum())
+        b = O.adaptive_next(H, R, 0.3, 1.0, target)
+        assert 0.3 < b < 1.0
+        # b - 0.3 re-rounds the kept step, hence the 1e-12 slack
+        assert O.overlap(H, R, b - 0.3) >= target - 1e-12
+        assert O.overlap(H, R, (b - 0.3) * (1 + 1e-6)) < target
+        assert O.overlap(H, R, (b - 0.3) * 0.5) > O.overlap(H, R, b - 0.3)
+    # the end of the schedule is taken when its overlap suffices
+    H = _random_hist(rng, 257, 1000, lo=60, width=40)
+    assert O.adaptive_next(H, 1000, 0.99, 1.0, 0.5) == 1.0
+    # heating goes down
+    b = O.adaptive_next(H, 1000, 1.0, 0.0, 0.9)
+    assert 0.0 < b < 1.0
+
+
 def test_heating_starts_from_the_ground_state():
     """Heating (Sec. 2): all spins +1, ln Z(beta0) = ln 2 + beta0 dim N (the two
     ground states of energy -dim N), and a heating step keeps the population."""

@@ -26,13 +26,17 @@ def test_take_from_end_and_loads():
     assert RD.load(kept) + RD.load(taken) == 8
 
 
+@pytest.mark.parametrize("match", ["order", "largest"])
 @pytest.mark.parametrize("maxexc", [1, 2])
-def test_main_plan_conserves_and_balances(maxexc):
+def test_main_plan_conserves_and_balances(maxexc, match):
     rng = np.random.default_rng(maxexc)
     B = 1024
     for _ in range(200):
         loads = [int(x) for x in rng.integers(5_000, 60_000, size=8)]
-        moves = RD.plan_main(loads, block=B, maxexc=maxexc)
+        moves = RD.plan_main(loads, block=B, maxexc=maxexc, match=match)
+        if match == "order":
+            # surplus and deficit shards are paired in shard order
+            assert moves == sorted(moves)
         cur = list(loads)
         for s, d in moves:
             assert s != d
@@ -47,6 +51,16 @@ def test_main_plan_conserves_and_balances(maxexc):
         # blocks only leave shards that were above the desired load
         for s, _ in moves:
             assert loads[s] > want[s]
+
+
+def test_main_order_matching_small_case():
+    """Four shards at desired load 10 (block 2, maxexc 1): shard 0 (+4) fills
+    shard 1 (-4) before shard 2 (+2) gives to shard 3 (-2)."""
+    loads = [14, 6, 12, 8]
+    assert RD.plan_main(loads, block=2, maxexc=1) == [(0, 1), (0, 1), (2, 3)]
+    assert RD.plan_main(loads, block=2, maxexc=2) == [(0, 1)]
+    with pytest.raises(ValueError):
+        RD.plan_main(loads, block=2, match="nearest")
 
 
 def test_naive_plan_moves_half_the_surplus():
