@@ -41,11 +41,12 @@ class Config(C.Structure):
         ("R0", C.c_int64), ("capacity", C.c_int64),
         ("beta0", C.c_double), ("beta_max", C.c_double),
         ("seed", C.c_uint64), ("coupling_seed", C.c_uint64),
-        ("init", C.c_int32), ("pad", C.c_int32),
+        ("init", C.c_int32), ("resample", C.c_int32),
     ]
 
 
 INIT_RANDOM, INIT_GROUND = 0, 1
+RESAMPLE_NEAREST, RESAMPLE_POISSON = 0, 1
 
 
 class Obs(C.Structure):
@@ -92,6 +93,10 @@ def lib():
         L.or_tau_table.restype = C.c_double
         L.or_copy_counts.argtypes = [C.POINTER(Config), C.c_int32, u32p, C.c_int64, u32p, u32p,
                                      u32p]
+        L.or_copy_counts_poisson.argtypes = [C.POINTER(Config), C.c_int32, u32p, C.c_int64,
+                                             u32p, u32p, u32p]
+        L.or_poisson1_thresholds.argtypes = [u32p, C.c_int32]
+        L.or_poisson1_thresholds.restype = C.c_int32
         L.or_derive_obs.argtypes = [C.POINTER(Obs), C.c_int64]
         L.or_overlap.argtypes = [u32p, C.c_int64, C.c_int64, C.c_double]
         L.or_overlap.restype = C.c_double
@@ -135,9 +140,9 @@ def _ptr(a: np.ndarray, ctype):
 
 def make_config(dim=2, L=16, model=MODEL_FERRO, K=100, theta=10, instance_id=0, R0=1000,
                 capacity=0, beta0=0.0, beta_max=1.0, seed=1, coupling_seed=0,
-                init=INIT_RANDOM) -> Config:
+                init=INIT_RANDOM, resample=RESAMPLE_NEAREST) -> Config:
     return Config(dim, L, model, K, theta, instance_id, R0, capacity, beta0, beta_max, seed,
-                  coupling_seed, init, 0)
+                  coupling_seed, init, resample)
 
 
 # ---------------------------------------------------------------------------
@@ -227,6 +232,23 @@ def copy_counts(cfg: Config, step: int, ebin: np.ndarray, n: np.ndarray, F: np.n
     lib().or_copy_counts(C.byref(cfg), step, _ptr(ebin, C.c_uint32), ebin.size,
                          _ptr(n, C.c_uint32), _ptr(F, C.c_uint32), _ptr(r, C.c_uint32))
     return r
+
+
+def copy_counts_poisson(cfg: Config, step: int, ebin: np.ndarray, n: np.ndarray,
+                        F: np.ndarray):
+    ebin = np.ascontiguousarray(ebin, dtype=np.uint32)
+    n = np.ascontiguousarray(n, dtype=np.uint32)
+    F = np.ascontiguousarray(F, dtype=np.uint32)
+    r = np.zeros(ebin.size, dtype=np.uint32)
+    lib().or_copy_counts_poisson(C.byref(cfg), step, _ptr(ebin, C.c_uint32), ebin.size,
+                                 _ptr(n, C.c_uint32), _ptr(F, C.c_uint32), _ptr(r, C.c_uint32))
+    return r
+
+
+def poisson1_thresholds() -> np.ndarray:
+    T = np.zeros(64, dtype=np.uint32)
+    m = lib().or_poisson1_thresholds(_ptr(T, C.c_uint32), 64)
+    return T[:m].copy()
 
 
 def overlap(H: np.ndarray, R: int, dbeta: float) -> float:

@@ -364,6 +364,73 @@ void or_copy_counts(const or_config* c, int32_t step, const uint32_t* ebin, int6
     }
 }
 
+/* Poisson(1) distribution function, term by term: P(X <= m) = sum_{j<=m}
+ * e^-1 / j!, each term the previous one divided by j, the sum in the order
+ * of m.  Entries are scaled to 32-bit thresholds and truncated. */
+int32_t or_poisson1_thresholds(uint32_t* T, int32_t cap)
+{
+    double term = exp(-1.0), cdf = 0.0;
+    for (int32_t m = 0; m < cap; ++m) {
+        if (m > 0) term = term / (double)m;
+        cdf = cdf + term;
+        double scaled = floor(ldexp(cdf, 32));
+        T[m] = scaled >= 4294967295.0 ? 0xffffffffu : (uint32_t)scaled;
+        if (T[m] == 0xffffffffu) return m + 1;
+    }
+    return cap;
+}
+
+/* Poisson resampling, the draw Sec. 2 prescribes: r_i ~ Poisson(tau_k) with
+ * tau_k = n_k + f_k, f_k = F_k / 2^32.  A Poisson(tau) count is the number of
+ * events of a unit-rate Poisson process on [0, tau]: every unit interval adds
+ * an independent Poisson(1) count, drawn by inversion (the smallest m with
+ * u < T[m]), and the last interval of length f_k adds a Poisson(f_k) count,
+ * drawn as a Poisson(1) count whose events are kept with probability f_k
+ * (thinning: keep when u < F_k).  The uniforms u_0, u_1, ... of replica i are
+ * the words of the Philox blocks (i, step, b, POISSON|id), b = 0, 1, ...,
+ * taken in order: first the fractional interval's count, then its thinning
+ * draws, then the n_k unit-interval counts. */
+typedef struct {
+    const or_config* c;
+    uint32_t i, step, b, w;
+    uint32_t out[4];
+} or_ustream;
+
+static uint32_t next_u(or_ustream* s)
+{
+    if (s->w == 4) {
+        draw(s->c->seed, s->i, s->step, s->b, OR_TAG_POISSON, s->c->instance_id, s->out);
+        s->b++;
+        s->w = 0;
+    }
+    return s->out[s->w++];
+}
+
+static uint32_t poisson1(or_ustream* s, const uint32_t* T, int32_t len)
+{
+    uint32_t u = next_u(s);
+    uint32_t m = 0;
+    while ((int32_t)m < len && u >= T[m]) ++m;
+    return m;
+}
+
+void or_copy_counts_poisson(const or_config* c, int32_t step, const uint32_t* ebin, int64_t R,
+                            const uint32_t* n, const uint32_t* F, uint32_t* r)
+{
+    uint32_t T[64];
+    int32_t len = or_poisson1_thresholds(T, 64);
+    for (int64_t i = 0; i < R; ++i) {
+        or_ustream s = { c, (uint32_t)i, (uint32_t)step, 0u, 4u, { 0, 0, 0, 0 } };
+        uint32_t k = ebin[i];
+        uint32_t count = 0;
+        uint32_t events = poisson1(&s, T, len);          /* interval of length 1 ... */
+        for (uint32_t e = 0; e < events; ++e)           /* ... thinned to f_k       */
+            if (next_u(&s) < F[k]) ++count;
+        for (uint32_t j = 0; j < n[k]; ++j) count += poisson1(&s, T, len);
+        r[i] = count;
+    }
+}
+
 /* Population averages (Sec. 2) from exact integer sums. */
 void or_derive_obs(or_obs* o, int64_t N)
 {
@@ -431,6 +498,7 @@ or_run* or_create(const or_config* c)
     if (c->instance_id < 0 || c->instance_id >= (1 << 28)) return NULL;
     if (c->init != OR_INIT_RANDOM && c->init != OR_INIT_GROUND) return NULL;
     if (c->init == OR_INIT_GROUND && c->model != OR_MODEL_FERRO) return NULL;
+    if (c->resample != OR_RESAMPLE_NEAREST && c->resample != OR_RESAMPLE_POISSON) return NULL;
     or_run* r = (or_run*)calloc(1, sizeof(or_run));
     r->c = *c;
     r->N = site_count(c->dim, c->L);
@@ -524,7 +592,10 @@ int or_resample(or_run* r)
     int64_t Eref = 2 * (2 * r->kref + r->parity) - (int64_t)c->dim * r->N;
     r->lnQ = (log(r->S) - log((double)r->R)) - dbeta * (double)Eref;   /* Eq. 3 */
     r->lnZ = r->lnZ + r->lnQ;                                          /* Eq. 5 */
-    or_copy_counts(c, i, r->ebin, r->R, r->tn, r->tF, r->r);
+    if (c->resample == OR_RESAMPLE_POISSON)
+        or_copy_counts_poisson(c, i, r->ebin, r->R, r->tn, r->tF, r->r);
+    else
+        or_copy_counts(c, i, r->ebin, r->R, r->tn, r->tF, r->r);
     int64_t total = 0;
     for (int64_t j = 0; j < r->R; ++j) {
         r->o[j] = (uint32_t)total;

@@ -12,8 +12,8 @@
  *     +-J Edwards-Anderson variant with one coupling per bond),
  *   - an initial population of R0 uniformly random states at beta0 (Sec. 2),
  *   - per annealing step i: the partition-function ratio Q (Eq. 3), the
- *     normalised weights tau (Eq. 4), resampling into exact copies (Sec. 2,
- *     with the nearest-integer rule in place of the Poisson draw), theta
+ *     normalised weights tau (Eq. 4), resampling into exact copies (Sec. 2:
+ *     the Poisson draw, or its nearest-integer variant), theta
  *     checkerboard Metropolis sweeps at beta_i, then observables and the
  *     free-energy recursion (Eq. 5, read as ln Z_i = N ln 2 + sum ln Q).
  *
@@ -37,6 +37,11 @@ extern "C" {
 #define OR_TAG_SWEEP    2u
 #define OR_TAG_RESAMPLE 3u
 #define OR_TAG_COUPLING 4u
+#define OR_TAG_POISSON  5u
+
+/* Copy-count rules of the resampling step (Sec. 2). */
+#define OR_RESAMPLE_NEAREST 0  /* r = floor(tau) + [u < frac(tau)]        */
+#define OR_RESAMPLE_POISSON 1  /* r ~ Poisson(tau)                         */
 
 #define OR_MODEL_FERRO 0   /* J_ij = +1 on every bond (Eq. 6)            */
 #define OR_MODEL_PMJ   1   /* J_ij = +-1 with p = 1/2, one draw per bond */
@@ -54,7 +59,7 @@ typedef struct {
     uint64_t seed;          /* Philox key of init / sweep / resample     */
     uint64_t coupling_seed; /* Philox key of the +-J bonds               */
     int32_t  init;          /* OR_INIT_RANDOM | OR_INIT_GROUND           */
-    int32_t  pad;
+    int32_t  resample;      /* OR_RESAMPLE_NEAREST | OR_RESAMPLE_POISSON */
 } or_config;
 
 /* Initial population: uniform random states (cooling from beta0 = 0) or the
@@ -93,6 +98,13 @@ double   or_tau_table(const uint32_t* H, int64_t bins, const double* Dtab, int64
                       int32_t heating, uint32_t* n, uint32_t* F, int64_t* kref);
 void     or_copy_counts(const or_config* c, int32_t step, const uint32_t* ebin, int64_t R,
                         const uint32_t* n, const uint32_t* F, uint32_t* r);
+/* Poisson(1) inversion table: T[m] = floor(2^32 P(X <= m)), X ~ Poisson(1),
+ * for m = 0, 1, ... up to and including the first entry that reaches
+ * 2^32 - 1 (at most cap entries).  Returns the number of entries. */
+int32_t  or_poisson1_thresholds(uint32_t* T, int32_t cap);
+/* Poisson copy counts r_i ~ Poisson(tau_k), tau_k = n_k + F_k / 2^32. */
+void     or_copy_counts_poisson(const or_config* c, int32_t step, const uint32_t* ebin,
+                                int64_t R, const uint32_t* n, const uint32_t* F, uint32_t* r);
 void     or_derive_obs(or_obs* o, int64_t N);
 
 /* Histogram overlap between the population at the current beta (levels H,

@@ -64,6 +64,16 @@ MUTANTS = [
      "dbeta < 0.0;\n    int64_t kref = -1;\n    if (heating) {\n        for (int64_t k = 0; k < bins;"
      " ++k)", "overlap"),
     ("overlap_uses_max", "a = a + (p < q ? p : q);", "a = a + (p > q ? p : q);", "overlap"),
+    ("poisson_thinning_reversed", "if (next_u(&s) < F[k]) ++count;",
+     "if (next_u(&s) >= F[k]) ++count;", "poisson_counts"),
+    ("poisson_fraction_dropped", "uint32_t events = poisson1(&s, T, len);",
+     "uint32_t events = 0;", "poisson_counts"),
+    ("poisson1_wrong_factorial", "if (m > 0) term = term / (double)m;",
+     "if (m > 0) term = term / (double)(m + 1);", "poisson1_thresholds or poisson_counts"),
+    ("poisson_one_unit_draw_short", "for (uint32_t j = 0; j < n[k]; ++j)",
+     "for (uint32_t j = 1; j < n[k]; ++j)", "poisson_counts"),
+    ("poisson_one_stream_for_all", "or_ustream s = { c, (uint32_t)i,", "or_ustream s = { c, 0u,",
+     "poisson_counts_are_independent"),
     ("ground_state_lnZ_wrong_sign", "r->lnZ = log(2.0) + c->beta0 *",
      "r->lnZ = log(2.0) - c->beta0 *", "heating_starts"),
 ]

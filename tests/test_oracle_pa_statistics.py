@@ -36,6 +36,14 @@ def _run_seed(args):
     elif kind == "L4":
         cfg = O.make_config(dim=2, L=4, R0=3000, K=40, theta=4, beta_max=1.2, seed=seed)
         checks = (10, 20, 40)
+    elif kind == "L4_poisson":
+        cfg = O.make_config(dim=2, L=4, R0=3000, K=40, theta=4, beta_max=1.2, seed=seed,
+                            resample=O.RESAMPLE_POISSON)
+        checks = (10, 20, 40)
+    elif kind == "L16_poisson":
+        cfg = O.make_config(dim=2, L=16, R0=1000, K=100, theta=10, seed=seed,
+                            resample=O.RESAMPLE_POISSON)
+        checks = CHECK_STEPS_L16
     elif kind == "L4_heat":
         cfg = O.make_config(dim=2, L=4, R0=3000, K=40, theta=4, beta0=2.0, beta_max=0.0,
                             init=O.INIT_GROUND, seed=seed)
@@ -96,11 +104,11 @@ def test_pa_lnZ_and_energy_match_kaufman_L16():
         _assert_within([r[0][i][2] / 256 for r in res], exact.kaufman_energy_per_site(16, beta))
 
 
-def _pa_vs_dos(kind, dos):
+def _pa_vs_dos(kind, dos, pop_sigmas=2.5):
     res = _runs(kind, list(range(40, 56)))
     for out, fails, Rs in res:
         assert fails == 0
-        assert max(abs(r - 3000) for r in Rs) <= 2.5 * np.sqrt(3000)
+        assert max(abs(r - 3000) for r in Rs) <= pop_sigmas * np.sqrt(3000)
     for i in res[0][0]:
         beta = res[0][0][i][0]
         if beta == 0.0:
@@ -116,6 +124,33 @@ def test_pa_lnZ_matches_bruteforce_2d_L4():
     J = np.ones(32, dtype=np.int8)
     dos = exact.density_of_states(2 * O.energy(2, 4, J, s)[0] - 32 for s in exact.all_states(16))
     _pa_vs_dos("L4", dos)
+
+
+@pytest.mark.slow
+def test_pa_poisson_resampling_matches_bruteforce_2d_L4():
+    """Poisson resampling (the draw Sec. 2 prescribes): ln Z and <E> within 3 SE
+    of brute force; the population is then Poisson(R0) at every step, so it
+    stays within 5 sqrt(R0) of R0 over 16 x 40 steps."""
+    from oracle import oracle as O
+    J = np.ones(32, dtype=np.int8)
+    dos = exact.density_of_states(2 * O.energy(2, 4, J, s)[0] - 32 for s in exact.all_states(16))
+    _pa_vs_dos("L4_poisson", dos, pop_sigmas=5.0)
+
+
+@pytest.mark.slow
+def test_pa_poisson_resampling_matches_kaufman_L16():
+    """The config-1 workload with Poisson resampling: ln Z and <E>/N within 3 SE
+    of Kaufman at four temperatures; the population's spread across steps and
+    seeds is that of Poisson(R0) (variance R0 within 20 %)."""
+    res = _runs("L16_poisson", list(range(700, 716)))
+    allR = np.concatenate([np.array(Rs, dtype=np.float64) for _, _, Rs in res])
+    assert abs(allR.var() / 1000 - 1.0) < 0.2
+    for out, fails, _ in res:
+        assert fails == 0
+    for i in CHECK_STEPS_L16:
+        beta = res[0][0][i][0]
+        _assert_within([r[0][i][1] for r in res], float(exact.kaufman_lnZ(16, beta)))
+        _assert_within([r[0][i][2] / 256 for r in res], exact.kaufman_energy_per_site(16, beta))
 
 
 @pytest.mark.slow

@@ -385,6 +385,75 @@ def test_copy_counts_are_nearest_integers_with_the_right_mean():
     assert not np.array_equal(r, r2)
 
 
+def test_poisson1_thresholds_against_high_precision():
+    """T[m] = floor(2^32 P(X <= m)) for X ~ Poisson(1), in 40 digits, up to the
+    first entry that reaches 2^32 - 1."""
+    mp.mp.dps = 40
+    T = O.poisson1_thresholds()
+    cdf, want = mp.mpf(0), []
+    for m in range(64):
+        cdf += mp.e ** -1 / mp.factorial(m)
+        v = min(int(mp.floor(cdf * 2 ** 32)), 2 ** 32 - 1)
+        want.append(v)
+        if v == 2 ** 32 - 1:
+            break
+    assert [int(t) for t in T] == want
+    assert len(T) == 13
+
+
+def _poisson_pmf(tau, m):
+    return float(mp.e ** -mp.mpf(tau) * mp.mpf(tau) ** m / mp.factorial(m))
+
+
+@pytest.mark.parametrize("n,frac", [(0, 0.3), (1, 0.0), (0, 0.5), (2, 0.7), (7, 0.25),
+                                    (0, 0.0)])
+def test_poisson_counts_follow_the_poisson_law(n, frac):
+    """Sec. 2 draws the number of copies of a replica from the Poisson law with
+    mean tau: the counts of 120 000 replicas at one level pass a chi-square
+    test against the exact Poisson(tau) probabilities (p > 1e-4), and their mean
+    and variance both sit within 5 standard errors of tau."""
+    from scipy import stats
+    F = int(np.floor(frac * 2 ** 32))
+    tau = n + F / 2 ** 32
+    cfg = O.make_config(seed=1000 + n, resample=O.RESAMPLE_POISSON)
+    R = 120000
+    r = O.copy_counts_poisson(cfg, 5, np.zeros(R, np.uint32), np.array([n], np.uint32),
+                              np.array([F], np.uint32)).astype(np.int64)
+    if tau == 0.0:
+        assert (r == 0).all()
+        return
+    mean_se = np.sqrt(tau / R)
+    assert abs(r.mean() - tau) < 5 * mean_se
+    # Var of the sample variance of a Poisson law: (mu4 - s^4)/R, mu4 = tau + 3 tau^2
+    var_se = np.sqrt((tau + 2 * tau ** 2) / R)
+    assert abs(r.var(ddof=1) - tau) < 5 * var_se
+    # chi-square on the cells with expectation >= 20, the tail pooled
+    hi = 0
+    while R * _poisson_pmf(tau, hi + 1) >= 20:
+        hi += 1
+    p = np.array([_poisson_pmf(tau, m) for m in range(hi + 1)])
+    obs = np.array([(r == m).sum() for m in range(hi + 1)] + [(r > hi).sum()])
+    exp = np.append(p, max(0.0, 1.0 - p.sum())) * R
+    keep = exp > 0
+    if keep.sum() < 2:
+        return
+    chi2 = (((obs - exp) ** 2)[keep] / exp[keep]).sum()
+    assert stats.chi2.sf(chi2, keep.sum() - 1) > 1e-4, (chi2, obs, exp)
+
+
+def test_poisson_counts_are_independent_across_replicas_and_steps():
+    """Counts of neighbouring replicas (which share no Philox block) and of the
+    same replica at two steps are uncorrelated."""
+    cfg = O.make_config(seed=77, resample=O.RESAMPLE_POISSON)
+    R = 100000
+    args = (np.zeros(R, np.uint32), np.array([1], np.uint32),
+            np.array([int(0.4 * 2 ** 32)], np.uint32))
+    a = O.copy_counts_poisson(cfg, 3, *args).astype(np.float64)
+    b = O.copy_counts_poisson(cfg, 4, *args).astype(np.float64)
+    assert abs(np.corrcoef(a[:-1], a[1:])[0, 1]) < 5 / np.sqrt(R)
+    assert abs(np.corrcoef(a, b)[0, 1]) < 5 / np.sqrt(R)
+
+
 def test_zero_temperature_step_resample_is_identity():
     """beta_i = beta_{i-1} and R = R0: tau = 1 everywhere, every replica is
     copied once into its own slot (Eq. 4 with a zero temperature step)."""
