@@ -71,6 +71,17 @@ extern "C" {
  * ln Omega = ln 2 + beta0 dim N for the two ground states). */
 #define PA_INIT_RANDOM 0
 #define PA_INIT_GROUND 1
+/* Copy counts of the resampling step (Sec. 2), from the normalised weight
+ * tau_k = n_k + F_k / 2^32 of the replica's level (Eq. 4):
+ *   PA_RESAMPLE_NEAREST  r = n_k + [u < F_k], one 32-bit uniform per replica;
+ *   PA_RESAMPLE_POISSON  r ~ Poisson(tau_k), the draw Sec. 2 prescribes: the
+ *     event count of a unit-rate Poisson process on [0, tau_k], i.e. n_k
+ *     Poisson(1) counts (inversion against pa_poisson1_table) plus one
+ *     Poisson(1) count thinned with keep probability F_k / 2^32; uniforms from
+ *     Philox blocks (i, step, b, POISSON|id), b = 0, 1, ..., fractional count
+ *     and its thinning draws first.  The population is then Poisson(R0). */
+#define PA_RESAMPLE_NEAREST 0
+#define PA_RESAMPLE_POISSON 1
 typedef struct {
     int32_t  dim;           /* 2 or 3                                  */
     int32_t  L;             /* linear size, even                        */
@@ -85,6 +96,8 @@ typedef struct {
     double   beta0, beta_max;
     uint64_t seed;          /* Philox key: init, sweeps, resampling     */
     uint64_t coupling_seed; /* Philox key of the +-J couplings          */
+    int32_t  resample;      /* PA_RESAMPLE_NEAREST | PA_RESAMPLE_POISSON */
+    int32_t  reserved;      /* must be 0                                */
 } pa_config;
 
 /* Population averages after the sweeps at beta_i (Sec. 2), from exact
@@ -190,6 +203,12 @@ typedef struct {
  * lowest occupied level when cooling, the highest when heating).  D is not
  * written for step 0. */
 int pa_tables(const pa_config* cfg, int32_t step, uint64_t T[3], double* D, int64_t bins);
+
+/* The Poisson(1) inversion table of PA_RESAMPLE_POISSON, host side:
+ * T[m] = floor(2^32 P(X <= m)), X ~ Poisson(1), m = 0, 1, ... up to and
+ * including the first entry that reaches 2^32 - 1.  Writes at most cap entries
+ * and returns how many the table has (13), or PA_ERR_INVALID_ARG. */
+int pa_poisson1_table(uint32_t* T, int32_t cap);
 
 /* Energy levels of (dim, L): dim L^dim / 2 + 1. */
 int64_t pa_num_bins(int32_t dim, int32_t L);

@@ -90,6 +90,9 @@ int validate(const pa_config* c) {
     if (c->K < 1 || c->theta < 0) return PA_ERR_INVALID_ARG;
     if (c->init != PA_INIT_RANDOM && c->init != PA_INIT_GROUND) return PA_ERR_INVALID_ARG;
     if (c->init == PA_INIT_GROUND && c->model != PA_MODEL_FERRO) return PA_ERR_INVALID_ARG;
+    if (c->resample != PA_RESAMPLE_NEAREST && c->resample != PA_RESAMPLE_POISSON)
+        return PA_ERR_INVALID_ARG;
+    if (c->reserved != 0) return PA_ERR_INVALID_ARG;
     if (c->instance_id < 0 || c->instance_id >= (1 << 28)) return PA_ERR_INVALID_ARG;
     if (c->R0 < 1 || c->R0 > (int64_t(1) << 31)) return PA_ERR_INVALID_ARG;
     if (!std::isfinite(c->beta0) || !std::isfinite(c->beta_max) || c->beta0 < 0.0 ||
@@ -99,6 +102,26 @@ int validate(const pa_config* c) {
         return PA_ERR_INVALID_ARG;
     if (!pa::sweep_supported(c->layout, c->dim, c->L)) return PA_ERR_UNSUPPORTED;
     return PA_OK;
+}
+
+// Poisson(1) distribution function scaled to 32 bits: the probabilities
+// e^-1 / m! by the recurrence p_m = p_{m-1} / m, accumulated in order of m,
+// each partial sum truncated to floor(2^32 P); the table ends at the first
+// entry that saturates at 2^32 - 1.
+int poisson1_table(uint32_t* T, int cap) {
+    double p = std::exp(-1.0);
+    double acc = 0.0;
+    int m = 0;
+    while (m < cap) {
+        acc = acc + p;
+        const double scaled = std::floor(std::ldexp(acc, 32));
+        const bool top = !(scaled < 4294967295.0);
+        T[m] = top ? 0xffffffffu : (uint32_t)scaled;
+        ++m;
+        if (top) break;
+        p = p / (double)m;
+    }
+    return m;
 }
 
 // Schedule and deduplicated weight tables (one per distinct dbeta bit pattern).
@@ -301,6 +324,14 @@ int enqueue_step(pa_run* r, cudaStream_t s) {
 
 extern "C" {
 
+int pa_poisson1_table(uint32_t* T, int32_t cap) {
+    if (!T || cap < 1) return PA_ERR_INVALID_ARG;
+    uint32_t full[pa::P1_MAX];
+    const int n = poisson1_table(full, pa::P1_MAX);
+    for (int m = 0; m < n && m < cap; ++m) T[m] = full[m];
+    return n;
+}
+
 int64_t pa_num_bins(int32_t dim, int32_t L) {
     if ((dim != 2 && dim != 3) || L < 1) return 0;
     return (int64_t)dim * ipow(L, dim) / 2 + 1;
@@ -390,6 +421,8 @@ int pa_init(const pa_config* cfg, void* ws, size_t bytes, void* stream, pa_run**
     d.one = 1u;
     d.theta = cfg->theta;
     d.init = cfg->init;
+    d.resample = cfg->resample;
+    d.p1_len = (uint32_t)poisson1_table(d.p1, pa::P1_MAX);
     for (int k = 0; k < 10; ++k) {
         d.rk0[k] = (uint32_t)cfg->seed + (uint32_t)k * 0x9E3779B9u;
         d.rk1[k] = (uint32_t)(cfg->seed >> 32) + (uint32_t)k * 0xBB67AE85u;
@@ -1154,6 +1187,9 @@ int pa_batch_init(pa_run* const* runs, int32_t nruns, void* ws, size_t bytes, vo
     b->bd.nruns = (uint32_t)nruns;
     b->bd.tile_base = d_tile_base;
     b->bd.total_tiles = tile_base.back();
+    b->bd.any_poisson = 0;
+    for (const auto& h : h_runs)
+        if (h.resample == PA_RESAMPLE_POISSON) b->bd.any_poisson = 1;
     b->bd.counters = d_counters;
     b->bd.ncounters = (uint32_t)(1 + b->cls.size());
     cudaStream_t s = b->stream;

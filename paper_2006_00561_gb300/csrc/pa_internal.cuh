@@ -17,6 +17,8 @@ constexpr uint32_t TAG_INIT = 1u;
 constexpr uint32_t TAG_SWEEP = 2u;
 constexpr uint32_t TAG_RESAMPLE = 3u;
 constexpr uint32_t TAG_COUPLING = 4u;
+constexpr uint32_t TAG_POISSON = 5u;
+constexpr int P1_MAX = 16;  // entries of the Poisson(1) inversion table
 
 // Sticky status bits of DevState::status.
 constexpr uint32_t ST_CAPACITY = 1u;
@@ -83,6 +85,9 @@ struct RunDev {
     uint32_t one;               // the value 1, opaque to the compiler (multiply-add tests)
     int32_t theta;              // sweeps per annealing step
     int32_t init;               // PA_INIT_RANDOM | PA_INIT_GROUND
+    int32_t resample;           // PA_RESAMPLE_NEAREST | PA_RESAMPLE_POISSON
+    uint32_t p1_len;            // entries of p1
+    uint32_t p1[P1_MAX];        // Poisson(1) thresholds floor(2^32 P(X <= m))
 };
 
 // A batch of runs stepped together (pa_batch_* in include/pa.h).  Arrays in
@@ -93,6 +98,7 @@ struct BatchDev {
     uint32_t nruns;
     const uint32_t* tile_base;   // [nruns + 1] prefix sums of each run's resample tiles
     uint32_t total_tiles;
+    uint32_t any_poisson;        // some run resamples by the Poisson rule
     uint32_t* counters;          // [0]: resample tiles, [1 + c]: sweep chunks of class c
     uint32_t ncounters;
 };

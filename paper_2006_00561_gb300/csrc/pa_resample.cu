@@ -161,6 +161,45 @@ struct ResampleSmem {
 };
 
 // Counts, scan and gather of tile `tile` of one run (all threads of the CTA).
+// Poisson(tau_k) copy count of replica i (Sec. 2), tau_k = n + F / 2^32: the
+// event count of a unit-rate Poisson process on [0, tau_k].  The fractional
+// interval contributes a Poisson(1) count thinned with keep probability
+// F / 2^32, each unit interval a Poisson(1) count, every one drawn by
+// inversion against the 32-bit thresholds p1.  Uniforms: words of the Philox
+// blocks (i, step, b, POISSON|id), b = 0, 1, ..., consumed in that order.
+// A level with n above the capacity overflows whatever the draw: its count is
+// then n itself, which the capacity check rejects, instead of n draws.
+__device__ __noinline__ uint32_t poisson_count(const RunDev& d, uint32_t i, uint32_t step,
+                                               uint32_t n, uint32_t F) {
+    if (n > d.cap) return n;
+    const uint32_t ctr3 = (TAG_POISSON << 28) | d.instance;
+    const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
+    uint4 blk = philox(i, step, 0u, ctr3, k0, k1);
+    uint32_t b = 1, w = 0;
+    auto next = [&]() -> uint32_t {
+        if (w == 4) {
+            blk = philox(i, step, b, ctr3, k0, k1);
+            ++b;
+            w = 0;
+        }
+        return pick(blk, w++);
+    };
+    auto unit = [&]() -> uint32_t {
+        const uint32_t u = next();
+        uint32_t m = 0;
+        while (m < d.p1_len && u >= d.p1[m]) ++m;
+        return m;
+    };
+    uint32_t count = 0;
+    const uint32_t events = unit();
+    for (uint32_t e = 0; e < events; ++e) count += next() < F ? 1u : 0u;
+    for (uint32_t j = 0; j < n; ++j) count += unit();
+    return count;
+}
+
+// POISSON = false compiles the nearest-integer rule alone (the register
+// budget of the HBM-bound default path); true adds the per-run Poisson branch.
+template <bool POISSON>
 __device__ __forceinline__ void resample_tile(const RunDev& d, uint32_t tile, ResampleSmem& sm) {
     DevState* st = d.st;
     uint32_t* s_r = sm.r;
@@ -179,6 +218,19 @@ __device__ __forceinline__ void resample_tile(const RunDev& d, uint32_t tile, Re
     const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
     uint32_t r[RS_ITEMS];
     uint32_t sum = 0;
+    if (POISSON && d.resample == PA_RESAMPLE_POISSON) {
+#pragma unroll
+        for (int j = 0; j < RS_ITEMS; ++j) {
+            const uint32_t i = base + (uint32_t)t * RS_ITEMS + j;
+            uint32_t v = 0;
+            if (i < R) {
+                const uint32_t k = eb[i];
+                v = poisson_count(d, i, step, d.tab_n[k], d.tab_F[k]);
+            }
+            r[j] = v;
+            sum += v;
+        }
+    } else
 #pragma unroll
     for (int j0 = 0; j0 < RS_ITEMS; j0 += 4) {
         const uint32_t i0 = base + (uint32_t)t * RS_ITEMS + j0;
@@ -325,6 +377,7 @@ __device__ __forceinline__ void resample_tile(const RunDev& d, uint32_t tile, Re
 // Persistent: one wave of CTAs, each claiming tiles until none is left.
 // Claims come in increasing order, so a tile's lookback only waits on tiles
 // already claimed by running CTAs.
+template <bool POISSON>
 __global__ void __launch_bounds__(RS_THREADS) k_resample(RunDev d) {
     __shared__ ResampleSmem sm;
     if (!d.st->active) return;
@@ -334,7 +387,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_resample(RunDev d) {
         __syncthreads();
         const uint32_t tile = sm.tile;
         if (tile * (uint32_t)RS_TILE >= R) break;
-        resample_tile(d, tile, sm);
+        resample_tile<POISSON>(d, tile, sm);
         __syncthreads();  // sm is reused by the next tile
     }
 }
@@ -342,6 +395,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_resample(RunDev d) {
 // Batched: global tile ids are claimed in increasing order; run r owns ids
 // tile_base[r] .. tile_base[r+1]-1, so within a run tiles are claimed in order
 // and the lookback only ever waits on tiles already running.
+template <bool POISSON>
 __global__ void __launch_bounds__(RS_THREADS) k_resample_batched(BatchDev b) {
     __shared__ ResampleSmem sm;
     __shared__ uint32_t s_run;
@@ -364,7 +418,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_resample_batched(BatchDev b) {
         __syncthreads();
         if (s_run == 0xffffffffu) break;
         const RunDev& d = b.runs[s_run];
-        if (d.st->active) resample_tile(d, sm.tile, sm);
+        if (d.st->active) resample_tile<POISSON>(d, sm.tile, sm);
         __syncthreads();
     }
 }
@@ -450,7 +504,7 @@ cudaError_t launch_tau(const RunDev& d, cudaStream_t s) {
 // One wave of resident CTAs (capped by the number of tiles), looked up once
 // per device and kernel.
 static int resample_wave(const void* fn, int which, uint32_t tiles) {
-    static int cache[64][2];
+    static int cache[64][4];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
     int wave = cache[dev][which];
@@ -466,9 +520,15 @@ static int resample_wave(const void* fn, int which, uint32_t tiles) {
 }
 
 cudaError_t launch_resample(const RunDev& d, cudaStream_t s) {
-    const int grid = resample_wave((const void*)k_resample, 0, d.tiles);
-    if (grid <= 0) return cudaErrorInvalidValue;
-    k_resample<<<grid, RS_THREADS, 0, s>>>(d);
+    if (d.resample == PA_RESAMPLE_POISSON) {
+        const int grid = resample_wave((const void*)k_resample<true>, 2, d.tiles);
+        if (grid <= 0) return cudaErrorInvalidValue;
+        k_resample<true><<<grid, RS_THREADS, 0, s>>>(d);
+    } else {
+        const int grid = resample_wave((const void*)k_resample<false>, 0, d.tiles);
+        if (grid <= 0) return cudaErrorInvalidValue;
+        k_resample<false><<<grid, RS_THREADS, 0, s>>>(d);
+    }
     return cudaGetLastError();
 }
 
@@ -483,9 +543,15 @@ cudaError_t launch_tau_batched(const BatchDev& b, cudaStream_t s) {
 }
 
 cudaError_t launch_resample_batched(const BatchDev& b, cudaStream_t s) {
-    const int grid = resample_wave((const void*)k_resample_batched, 1, b.total_tiles);
-    if (grid <= 0) return cudaErrorInvalidValue;
-    k_resample_batched<<<grid, RS_THREADS, 0, s>>>(b);
+    if (b.any_poisson) {
+        const int grid = resample_wave((const void*)k_resample_batched<true>, 3, b.total_tiles);
+        if (grid <= 0) return cudaErrorInvalidValue;
+        k_resample_batched<true><<<grid, RS_THREADS, 0, s>>>(b);
+    } else {
+        const int grid = resample_wave((const void*)k_resample_batched<false>, 1, b.total_tiles);
+        if (grid <= 0) return cudaErrorInvalidValue;
+        k_resample_batched<false><<<grid, RS_THREADS, 0, s>>>(b);
+    }
     return cudaGetLastError();
 }
 

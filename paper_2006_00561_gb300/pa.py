@@ -25,6 +25,7 @@ ERRORS = {
 }
 MODEL_FERRO, MODEL_PMJ = 0, 1
 INIT_RANDOM, INIT_GROUND = 0, 1
+RESAMPLE_NEAREST, RESAMPLE_POISSON = 0, 1
 LAYOUT_INT8, LAYOUT_PACKED = 0, 1
 (DUMP_SPINS, DUMP_EBIN, DUMP_MAG, DUMP_HIST, DUMP_COUNTS, DUMP_OFFSETS, DUMP_TAB_N, DUMP_TAB_F,
  DUMP_COUPLINGS, DUMP_SPINS_RAW, DUMP_STATE) = range(11)
@@ -37,7 +38,7 @@ EXPORTS = [
     "pa_batch_workspace_size", "pa_batch_init", "pa_batch_step", "pa_batch_run_steps",
     "pa_batch_sync", "pa_batch_num_classes", "pa_batch_class_info", "pa_batch_set_shape",
     "pa_batch_free", "pa_checkpoint_size", "pa_checkpoint", "pa_restore",
-    "pa_adaptive_beta", "pa_resample_to",
+    "pa_adaptive_beta", "pa_resample_to", "pa_poisson1_table",
 ]
 NOALLOC_MAX_REPLICAS = 8388608
 
@@ -55,6 +56,7 @@ class Config(C.Structure):
         ("init", C.c_int32), ("R0", C.c_int64), ("capacity", C.c_int64),
         ("beta0", C.c_double), ("beta_max", C.c_double),
         ("seed", C.c_uint64), ("coupling_seed", C.c_uint64),
+        ("resample", C.c_int32), ("reserved", C.c_int32),
     ]
 
 
@@ -85,9 +87,9 @@ class State(C.Structure):
 
 def make_config(dim=2, L=16, model=MODEL_FERRO, layout=LAYOUT_PACKED, K=100, theta=10,
                 instance_id=0, R0=1000, capacity=0, beta0=0.0, beta_max=1.0, seed=1,
-                coupling_seed=0, init=INIT_RANDOM) -> Config:
+                coupling_seed=0, init=INIT_RANDOM, resample=RESAMPLE_NEAREST) -> Config:
     return Config(dim, L, model, layout, K, theta, instance_id, init, R0, capacity, beta0,
-                  beta_max, seed, coupling_seed)
+                  beta_max, seed, coupling_seed, resample, 0)
 
 
 _lib = None
@@ -120,6 +122,7 @@ def lib():
         L.pa_profile_read.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_double), C.c_int32]
         L.pa_tables.argtypes = [cfgp, C.c_int32, C.POINTER(C.c_uint64), C.POINTER(C.c_double),
                                 C.c_int64]
+        L.pa_poisson1_table.argtypes = [C.POINTER(C.c_uint32), C.c_int32]
         L.pa_num_bins.argtypes = [C.c_int32, C.c_int32]
         L.pa_num_bins.restype = C.c_int64
         L.pa_free.argtypes = [vp]
@@ -163,6 +166,14 @@ def _check(rc: int, what: str):
 # ---- the C ABI, name for name ------------------------------------------------
 def pa_workspace_size(cfg: Config) -> int:
     return int(lib().pa_workspace_size(C.byref(cfg)))
+
+
+def pa_poisson1_table() -> np.ndarray:
+    T = np.zeros(32, dtype=np.uint32)
+    n = lib().pa_poisson1_table(T.ctypes.data_as(C.POINTER(C.c_uint32)), 32)
+    if n < 0:
+        raise PaError(n, "pa_poisson1_table")
+    return T[:n].copy()
 
 
 def pa_num_bins(dim: int, L: int) -> int:

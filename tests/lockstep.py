@@ -12,13 +12,15 @@ FP_RTOL = 1e-12  # FP64 observables: ln() may differ in the last ulp, the rest i
 
 
 def configs(P, dim=2, L=16, model=0, layout=1, R0=1000, K=100, theta=10, beta0=0.0,
-            beta_max=1.0, seed=1, coupling_seed=0, instance_id=0, capacity=0, init=0):
+            beta_max=1.0, seed=1, coupling_seed=0, instance_id=0, capacity=0, init=0,
+            resample=0):
     o = O.make_config(dim=dim, L=L, model=model, K=K, theta=theta, instance_id=instance_id,
                       R0=R0, capacity=capacity, beta0=beta0, beta_max=beta_max, seed=seed,
-                      coupling_seed=coupling_seed, init=init)
+                      coupling_seed=coupling_seed, init=init, resample=resample)
     g = P.make_config(dim=dim, L=L, model=model, layout=layout, K=K, theta=theta,
                       instance_id=instance_id, R0=R0, capacity=capacity, beta0=beta0,
-                      beta_max=beta_max, seed=seed, coupling_seed=coupling_seed, init=init)
+                      beta_max=beta_max, seed=seed, coupling_seed=coupling_seed, init=init,
+                      resample=resample)
     return o, g
 
 

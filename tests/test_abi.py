@@ -27,7 +27,7 @@ def P():
 def declared_symbols():
     src = open(os.path.join(ROOT, "include", "pa.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(pa_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(pa_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_library_exports_every_declared_symbol(P):
@@ -91,3 +91,20 @@ def test_host_tables_bitwise_equal_to_oracle(P, spec):
             db = O.beta(ocfg, step) - O.beta(ocfg, step - 1)
             want = np.array([O.weight(db, j) for j in range(bins)])
             assert np.array_equal(D.view(np.uint64), want.view(np.uint64))
+
+
+def test_poisson1_table_equals_oracle_and_exact(P):
+    """The engine's host-built Poisson(1) inversion table equals the oracle's
+    (which is pinned to 40-digit sums) entry for entry."""
+    T = P.pa_poisson1_table()
+    assert T.dtype == np.uint32 and len(T) == 13 and T[-1] == 2 ** 32 - 1
+    assert np.array_equal(T, O.poisson1_thresholds())
+
+
+def test_resample_rule_is_validated(P):
+    assert P.pa_workspace_size(P.make_config(resample=1)) > 0
+    for bad in (dict(resample=2), dict(resample=-1)):
+        assert P.pa_workspace_size(P.make_config(**bad)) == 0
+    cfg = P.make_config()
+    cfg.reserved = 1
+    assert P.pa_workspace_size(cfg) == 0

@@ -105,6 +105,27 @@ def test_batched_run_matches_oracle(P):
     batch.close()
 
 
+def test_batch_mixing_resampling_rules(P):
+    """Runs on the Poisson rule and on the nearest-integer rule in one batch:
+    each run equals its plain twin, and a Poisson run equals the oracle."""
+    specs = [dict(MIX[i], resample=i % 2) for i in (1, 4, 5, 6)]
+    plain = _runs(P, specs)
+    batched = _runs(P, specs)
+    spec = dict(COMMON, **specs[1])
+    orun = O.Run(O.make_config(**{k: v for k, v in spec.items() if k != "layout"}))
+    batch = P.Batch(batched)
+    for step in range(1, 6):
+        for r in plain:
+            r.step()
+        assert orun.step() == 0
+        batch.run_steps(1)
+        assert batch.sync() == 0
+        for i, (a, b) in enumerate(zip(plain, batched)):
+            _same(P, a, b, f"step {step} run {i}")
+        compare_state(P, batched[1], orun, step)
+    batch.close()
+
+
 def test_batch_refuses_to_pass_K(P):
     runs = _runs(P, [dict(dict(COMMON, K=2), **MIX[0])])
     batch = P.Batch(runs)

@@ -142,6 +142,43 @@ def test_adaptive_step_reaches_the_end_and_stops(P):
     run.close()
 
 
+@pytest.mark.parametrize("spec", [
+    dict(dim=2, L=16, layout=1, R0=1000, K=100, theta=10, seed=21),
+    dict(dim=2, L=16, layout=0, R0=1000, K=100, theta=10, seed=22),
+    dict(dim=2, L=64, layout=1, R0=2300, K=20, theta=2, seed=23),
+    dict(dim=2, L=8, layout=1, R0=5001, K=16, theta=2, beta_max=1.5, seed=24),
+    dict(dim=3, L=8, model=1, layout=1, R0=900, K=10, theta=3, beta_max=3.0, seed=25,
+         coupling_seed=26, instance_id=3),
+    dict(dim=2, L=16, layout=1, R0=1500, K=40, theta=2, beta0=2.0, beta_max=0.0, init=1,
+         seed=27),
+], ids=["2d_L16_packed", "2d_L16_int8", "2d_L64", "ragged_tiles", "3d_L8_pmj", "heating"])
+def test_poisson_resampling(P, spec):
+    """The Poisson draw of Sec. 2: copy counts, offsets and the population
+    (whose size now fluctuates as Poisson(R0)) bit for bit with the oracle."""
+    run_lockstep(P, steps=8, resample=1, **spec)
+
+
+def test_poisson_resampling_graph_replay(P):
+    run_lockstep(P, steps=8, use_graph=True, resample=1, dim=2, L=64, layout=1, R0=3000, K=20,
+                 theta=2, beta_max=1.0, seed=28)
+
+
+def test_poisson_capacity_overflow_is_reported(P):
+    ocfg, gcfg = configs(P, dim=2, L=8, R0=200, capacity=200, K=50, theta=1, beta_max=3.0,
+                         seed=1, resample=1)
+    orun, grun = O.Run(ocfg), P.Run(gcfg)
+    code = 0
+    for _ in range(50):
+        orc = orun.step()
+        grun.step()
+        code = grun.status()
+        if orc:
+            assert orc == -3
+            break
+    assert code == -4  # PA_ERR_CAPACITY
+    grun.close()
+
+
 def test_several_tiles_with_ragged_tail(P):
     """R0 = 5001: three resample tiles, the last one nearly empty."""
     run_lockstep(P, steps=8, dim=2, L=8, layout=1, R0=5001, K=16, theta=2, beta_max=1.5, seed=13)
