@@ -15,6 +15,8 @@ e2e       = the same metric through the C ABI with host buffers: every step
             and downloads it again (pa_dump_range) with the observables.
 roofline  = the sweep kernel (dominant), integer-ALU bound.
 cpu_baseline = the CPU oracle (single thread) on a bounded slice.
+next_items = Poisson resampling, adaptive temperature steps and checkpoints
+            measured on the same workload (outside the headline timed region).
 --impl reference: the CPU oracle alone, as the reference arm.
 """
 from __future__ import annotations
@@ -245,6 +247,83 @@ def serving_measure(P, n: int = 48, rates=(400.0, 40.0)) -> dict:
     return out
 
 
+def next_items_measure(P, steps: int = 5, R0: int = WORKLOAD["R0"]) -> dict:
+    """The extensions of the fixed-schedule path, each on the headline workload
+    (2D Ising L = 64 packed, theta = 10, beta 0 -> 1 in 400 steps):
+      poisson    -- Poisson copy counts (Sec. 2's draw): graph-replayed step rate
+                    and k_resample time per launch (kernel events);
+      adaptive   -- adaptive temperature steps (overlap target 0.9): host time of
+                    the decision (histogram read + bisection) and wall time of a
+                    whole adaptive step (decision, resample, sweeps, synchronise);
+      checkpoint -- pa_checkpoint / pa_restore of the whole run to and from
+                    pageable host memory."""
+    import torch
+    wl = dict(WORKLOAD, R0=R0)
+    N, theta = wl["L"] ** 2, wl["theta"]
+    stream = torch.cuda.Stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"workload": f"2D Ising L=64 packed, R0={R0}, theta=10, beta 0->1 in K=400"}
+
+    run = P.Run(P.make_config(layout=P.LAYOUT_PACKED, resample=P.RESAMPLE_POISSON, **wl),
+                stream=stream)
+    run.run_steps(3)
+    run.observables()
+    first = run.state()["step"] + 1
+    torch.cuda.synchronize()
+    e0.record(stream)
+    run.run_steps(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    h = run.history(first - 1, steps + 1)
+    att = sum(x["R"] for x in h[1:]) * N * theta
+    P.pa_profile(run.h, True)
+    P.pa_profile_read(run.h, reset=True)
+    for _ in range(steps):
+        run.step()
+    prof = P.pa_profile_read(run.h, reset=True)
+    P.pa_profile(run.h, False)
+    run.observables()
+    out["poisson"] = {
+        "attempts_per_ns": att / (ms * 1e6), "ms_per_step": ms / steps,
+        "k_resample_ms": prof["resample"][1] / max(prof["resample"][0], 1),
+        "k_tau_ms": prof["tau"][1] / max(prof["tau"][0], 1),
+        "R_per_step": [x["R"] for x in h[1:]]}
+
+    t0 = time.perf_counter()
+    blob = run.checkpoint()
+    t1 = time.perf_counter()
+    run.restore(blob)
+    t2 = time.perf_counter()
+    out["checkpoint"] = {"bytes": len(blob), "checkpoint_s": t1 - t0, "restore_s": t2 - t1,
+                         "checkpoint_gbs": len(blob) / (t1 - t0) / 1e9,
+                         "restore_gbs": len(blob) / (t2 - t1) / 1e9}
+    del blob
+    run.close()
+
+    run = P.Run(P.make_config(layout=P.LAYOUT_PACKED, **wl), stream=stream)
+    run.run_steps(3)
+    run.observables()
+    dec, wall, betas = [], [], []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        b = run.adaptive_beta(0.9, 1.0)
+        t1 = time.perf_counter()
+        run.resample_to(b)
+        run.sweep(theta)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        dec.append((t1 - t0) * 1e3)
+        wall.append((t2 - t0) * 1e3)
+        betas.append(b)
+    run.observables()
+    out["adaptive"] = {"target": 0.9, "decision_ms": statistics.median(dec),
+                       "step_wall_ms": statistics.median(wall), "betas": betas,
+                       "bins": P.pa_num_bins(2, 64)}
+    run.close()
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -286,6 +365,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-next", action="store_true",
+                    help="skip the Poisson / adaptive / checkpoint measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -408,15 +489,16 @@ def main():
                "path": "pa_load(pinned host population) + pa_step + pa_observables + "
                        "pa_dump_range(pinned host) every step"}
 
-    ens = None
+    run.close()
+    del run
+    torch.cuda.empty_cache()
+    ens = srv = nxt = None
     if not args.no_ensemble and world == 1:
-        run.close()
-        del run
-        torch.cuda.empty_cache()
         ens = ensemble_compare(P, steps=3)
-    srv = None
     if not args.no_serving and world == 1:
         srv = serving_measure(P)
+    if not args.no_next and world == 1:
+        nxt = next_items_measure(P, R0=args.R0)
 
     if rank != 0:
         if dist is not None:
@@ -470,6 +552,8 @@ def main():
         line["batched_ensemble"] = ens
     if srv:
         line["serving"] = srv
+    if nxt:
+        line["next_items"] = nxt
     if cpu:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
