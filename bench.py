@@ -129,15 +129,24 @@ class Clocks:
                            "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_rate(seconds: float, L=64, R0=512, theta=10):
-    """Single-threaded oracle on a slice of the workload: attempts/ns and
-    resampled replicas/s (one thread)."""
+def _oracle_worker(job):
+    """One oracle process: full PA steps of the L = 64 workload at a small R0,
+    for `seconds` or for warmup + steps steps.  Returns its counts and times."""
+    seconds, warmup, steps, R0, seed = job
+    sys.path.insert(0, ROOT)
     from oracle import oracle as O
-    cfg = O.make_config(dim=2, L=L, R0=R0, K=WORKLOAD["K"], theta=theta, seed=WORKLOAD["seed"])
+    L, theta = WORKLOAD["L"], WORKLOAD["theta"]
+    cfg = O.make_config(dim=2, L=L, R0=R0, K=WORKLOAD["K"], theta=theta, seed=seed)
     run = O.Run(cfg)
-    attempts, t_sweep, t_res, resampled, steps = 0, 0.0, 0.0, 0, 0
-    t_end = time.perf_counter() + seconds
-    while time.perf_counter() < t_end and steps < cfg.K:
+    for _ in range(warmup):
+        assert run.step() == 0
+    attempts, t_sweep, t_res, resampled, n = 0, 0.0, 0.0, 0, 0
+    t_start = time.perf_counter()
+    while n < cfg.K - warmup:
+        if steps is not None and n >= steps:
+            break
+        if seconds is not None and time.perf_counter() - t_start >= seconds:
+            break
         R_prev = run.R
         t0 = time.perf_counter()
         assert run.resample() == 0
@@ -148,10 +157,46 @@ def oracle_rate(seconds: float, L=64, R0=512, theta=10):
         resampled += R_prev
         t_res += t1 - t0
         t_sweep += t2 - t1
-        steps += 1
-    total = t_res + t_sweep
-    return {"attempts_per_ns": attempts / total / 1e9, "steps": steps, "R0": R0,
-            "seconds": total, "resampled_replicas_per_s": resampled / t_res if t_res else None}
+        n += 1
+    return {"attempts": attempts, "resampled": resampled, "t_res": t_res, "t_sweep": t_sweep,
+            "steps": n, "wall": time.perf_counter() - t_start}
+
+
+def oracle_rate(seconds: float = None, R0=512, procs: int = 1, warmup: int = 0, steps=None):
+    """The oracle on a slice of the workload (L = 64, R0 small, theta = 10):
+    `procs` independent single-threaded processes (spawned, different seeds),
+    each for `seconds` or `steps` steps.  Returns attempts/ns and resampled
+    replicas/s over the slowest process's wall time."""
+    jobs = [(seconds, warmup, steps, R0, WORKLOAD["seed"] + 1000 * p) for p in range(procs)]
+    if procs == 1:
+        res = [_oracle_worker(jobs[0])]
+        wall = res[0]["t_res"] + res[0]["t_sweep"]
+    else:
+        import multiprocessing as mp
+        t0 = time.perf_counter()
+        with mp.get_context("spawn").Pool(procs) as pool:
+            res = pool.map(_oracle_worker, jobs)
+        wall = max(r["wall"] for r in res)
+        del t0
+    att = sum(r["attempts"] for r in res)
+    rs = sum(r["resampled"] for r in res)
+    t_res = max(r["t_res"] for r in res)
+    return {"attempts_per_ns": att / wall / 1e9, "steps": sum(r["steps"] for r in res),
+            "R0": R0, "seconds": wall, "procs": procs,
+            "resampled_replicas_per_s": rs / t_res if t_res else None}
+
+
+def host_info() -> dict:
+    import platform
+    info = {"nproc": os.cpu_count(), "machine": platform.machine()}
+    try:
+        for line in open("/proc/cpuinfo"):
+            k = line.split(":")[0].strip().lower()
+            if k in ("model name", "cpu part", "cpu implementer"):
+                info.setdefault(k.replace(" ", "_"), line.split(":", 1)[1].strip())
+    except OSError:
+        pass
+    return info
 
 
 def ensemble_compare(P, steps: int, tune_cache=None) -> dict:
@@ -325,31 +370,28 @@ def next_items_measure(P, steps: int = 5, R0: int = WORKLOAD["R0"]) -> dict:
 
 
 def run_reference(args):
+    """The reference arm: the oracle as it stands, one single-threaded process
+    per host core, each running W + K full PA steps of the L = 64 workload at
+    R0 = 256 (a bounded slice of the 2^21-replica run, different seeds)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     from oracle import oracle as O
     O.build()
-    L, R0, theta = WORKLOAD["L"], 256, WORKLOAD["theta"]
-    cfg = O.make_config(dim=2, L=L, R0=R0, K=WORKLOAD["K"], theta=theta, seed=WORKLOAD["seed"])
-    run = O.Run(cfg)
-    for _ in range(args.warmup):
-        assert run.step() == 0
-    attempts = 0
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        assert run.step() == 0
-        attempts += run.R * L * L * theta
-    dt = time.perf_counter() - t0
-    v = attempts / dt / 1e9
-    sample = (f"oracle PA steps of L=64, R0={R0} (the 2^21-replica workload scaled down), "
-              f"theta={theta}, steps {args.warmup + 1}..{args.warmup + args.steps} of K=400")
+    R0 = 256
+    procs = os.cpu_count() or 1
+    r = oracle_rate(R0=R0, procs=procs, warmup=args.warmup, steps=args.steps)
+    v = r["attempts_per_ns"]
+    sample = (f"{procs} oracle processes, each PA steps {args.warmup + 1}..{args.warmup + args.steps}"
+              f" of the L=64 workload at R0={R0} (the 2^21-replica run scaled down), theta=10, "
+              f"K=400, seeds 3 + 1000 p")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": r["seconds"] * 1e3 / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8",
             "data": "synthetic", "config": {"workload": sample},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": procs, "kind": "oracle",
+                             "sample": sample, "host": host_info()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -507,11 +549,18 @@ def main():
 
     cpu = None
     if world == 1 and args.cpu_seconds > 0:
-        r = oracle_rate(args.cpu_seconds)
-        cpu = {"value": r["attempts_per_ns"], "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{r['steps']} full PA steps of the oracle at L=64, R0={r['R0']} "
-                         f"(theta=10), {r['seconds']:.1f} s, one thread",
-               "resampled_replicas_per_s": r["resampled_replicas_per_s"]}
+        procs = os.cpu_count() or 1
+        r1 = oracle_rate(args.cpu_seconds / 2)
+        rp = oracle_rate(args.cpu_seconds / 2, procs=procs)
+        cpu = {"value": rp["attempts_per_ns"], "unit": UNIT, "cores": procs, "kind": "oracle",
+               "sample": f"{procs} independent oracle processes (different seeds), "
+                         f"{rp['steps']} full PA steps in all of the L=64 workload at "
+                         f"R0={rp['R0']} (theta=10), {rp['seconds']:.1f} s",
+               "resampled_replicas_per_s": rp["resampled_replicas_per_s"],
+               "single_thread": {"value": r1["attempts_per_ns"], "cores": 1,
+                                 "steps": r1["steps"], "seconds": r1["seconds"],
+                                 "resampled_replicas_per_s": r1["resampled_replicas_per_s"]},
+               "host": host_info()}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

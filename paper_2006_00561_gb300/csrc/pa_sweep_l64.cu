@@ -28,7 +28,11 @@ namespace {
 //   PA_L64_CMP_MODE 0: both tests as compare + predicated OR (ALU pipe);
 //                   1: the dE = 4 test on the FMA pipe, dE = 8 on the ALU;
 //                   2: both on the FMA pipe;
-//                   3: the dE = 4 test of half of the blocks on the FMA pipe.
+//                   3: the dE = 4 test of half of the blocks on the FMA pipe;
+//                   4: as 3, as a carry chain (mad.lo.cc + madc: the carry of
+//                      u + (2^32 - T) is [u >= T], shifted into an accumulator);
+//                   5: every dE = 4 test as a carry chain;
+//                   7: the dE = 4 test of a quarter of the blocks as a carry chain.
 // On the FMA pipe, u < T is the high word of the 32x32+64 multiply-add
 // u * 1 + (2^64 - T) (all ones iff no carry out, i.e. u < T), and the site's
 // bit is added to the mask by a second multiply-add with -(1 << bit).  The
@@ -39,6 +43,12 @@ namespace {
 #endif
 #ifndef PA_L64_CMP_MODE
 #define PA_L64_CMP_MODE 3
+#endif
+
+// How the Philox products are formed: 0 = high and low halves from C++
+// (__umulhi, *), 1 = one mul.wide.u32, 2 = separate mul.hi.u32 / mul.lo.u32.
+#ifndef PA_L64_MUL_MODE
+#define PA_L64_MUL_MODE 0
 #endif
 
 #ifndef PA_L64_WARPS
@@ -119,25 +129,54 @@ __device__ __forceinline__ HalfSweepGen half_sweep_gen(const Keys& d, uint32_t c
     return g;
 }
 
+__device__ __forceinline__ void mul_hilo(uint32_t m, uint32_t a, uint32_t& hi, uint32_t& lo) {
+#if PA_L64_MUL_MODE == 1
+    uint64_t p;
+    asm("mul.wide.u32 %0, %1, %2;" : "=l"(p) : "r"(a), "r"(m));
+    hi = (uint32_t)(p >> 32);
+    lo = (uint32_t)p;
+#elif PA_L64_MUL_MODE == 2
+    asm("mul.hi.u32 %0, %1, %2;" : "=r"(hi) : "r"(a), "r"(m));
+    asm("mul.lo.u32 %0, %1, %2;" : "=r"(lo) : "r"(a), "r"(m));
+#else
+    hi = __umulhi(m, a);
+    lo = m * a;
+#endif
+}
+
 // pA = M0 * c0 (64-bit) of the block.
 __device__ __forceinline__ uint4 philox_block(const Keys& d, const HalfSweepGen& g, uint64_t pA) {
     const uint32_t x2 = (uint32_t)(pA >> 32) ^ g.c3k;
     const uint32_t x3 = (uint32_t)pA;
-    uint32_t c0 = __umulhi(PM1, x2) ^ g.x1k;
-    uint32_t c1 = PM1 * x2;
+    uint32_t h1, l1;
+    mul_hilo(PM1, x2, h1, l1);
+    uint32_t c0 = h1 ^ g.x1k;
+    uint32_t c1 = l1;
     uint32_t c2 = g.hiA2k ^ x3;
     uint32_t c3 = g.loA2;
 #pragma unroll
     for (int r = 2; r < 10; ++r) {
         const uint32_t a = c0, b = c2;
-        const uint32_t hiA = __umulhi(PM0, a), loA = PM0 * a;
-        const uint32_t hiB = __umulhi(PM1, b), loB = PM1 * b;
+        uint32_t hiA, loA, hiB, loB;
+        mul_hilo(PM0, a, hiA, loA);
+        mul_hilo(PM1, b, hiB, loB);
         c0 = hiB ^ c1 ^ d.rk0[r];
         c1 = loB;
         c2 = hiA ^ c3 ^ d.rk1[r];
         c3 = loA;
     }
     return make_uint4(c0, c1, c2, c3);
+}
+
+// acc * 4 + [u >= T] on the FMA pipe: the carry out of u * 1 + (2^32 - T)
+// feeds the multiply-add that shifts the accumulator (T > 0).
+__device__ __forceinline__ uint32_t carry_ge(uint32_t acc, uint32_t u, uint32_t one,
+                                             uint32_t negT, uint32_t four) {
+    uint32_t out;
+    asm("{\n\t.reg .u32 t;\n\tmad.lo.cc.u32 t, %1, %2, %3;\n\tmadc.lo.u32 %0, %4, %5, 0;\n\t}"
+        : "=r"(out)
+        : "r"(u), "r"(one), "r"(negT), "r"(acc), "r"(four));
+    return out;
 }
 
 // Acceptance masks of the 32 colour-c sites of row y, P = (y + c) & 1: sites
@@ -149,26 +188,40 @@ __device__ __forceinline__ void row_accepts(const Keys& d, const HalfSweepGen& g
                                             const Thr& t4, const Thr& t8, uint64_t& a4,
                                             uint64_t& a8) {
     const uint32_t one = d.one;
+    constexpr int M = PA_L64_CMP_MODE;
+    // blocks h < HC take the dE = 4 test as a carry chain
+    constexpr int HC = M == 4 ? 2 : M == 5 ? 4 : M == 7 ? 1 : 0;
+    const uint32_t negT4 = 0u - t4.T, four = one << 2;
     uint32_t h4[2], h8[2];
 #pragma unroll 1
     for (uint32_t q = 0; q < 2; ++q) {
-        uint32_t k4 = 0, k8 = 0;
+        uint32_t k4 = 0, k8 = 0, kc = 0;
         const uint64_t base = (uint64_t)PM0 * (8u * y + 4u * q);
+        // blocks in decreasing h so that the carry chain sees its sites in
+        // decreasing order: site j = 4h + m ends at bit 2j
 #pragma unroll
-        for (int h = 0; h < 4; ++h) {
+        for (int h = 3; h >= 0; --h) {
             const uint4 u = philox_block(d, gen, base + (uint64_t)PM0 * (uint64_t)h);
             const uint32_t w[4] = {u.x, u.y, u.z, u.w};
-            constexpr int M = PA_L64_CMP_MODE;
             const bool f4 = M == 1 || M == 2 || (M == 3 && h < 2);
             const bool f8 = M == 2;
+            const bool c4 = h < HC;
 #pragma unroll
-            for (int m = 0; m < 4; ++m) {
+            for (int m = 3; m >= 0; --m) {
                 const int bit = 8 * h + 2 * m + P;
-                k4 = f4 ? add_if_below<true>(k4, w[m], t4, one, bit)
-                        : add_if_below<false>(k4, w[m], t4, one, bit);
+                if (c4)
+                    kc = carry_ge(kc, w[m], one, negT4, four);
+                else
+                    k4 = f4 ? add_if_below<true>(k4, w[m], t4, one, bit)
+                            : add_if_below<false>(k4, w[m], t4, one, bit);
                 k8 = f8 ? add_if_below<true>(k8, w[m], t8, one, bit)
                         : add_if_below<false>(k8, w[m], t8, one, bit);
             }
+        }
+        if (HC > 0) {
+            constexpr uint32_t even = HC >= 4 ? 0x55555555u : ((1u << (8 * HC)) - 1u) & 0x55555555u;
+            const uint32_t below = t4.T ? (~kc & even) : 0u;  // T = 0: nothing is below
+            k4 |= below << P;
         }
         if (q == 0) {
             h4[0] = k4;

@@ -5,7 +5,8 @@
   * reweight, on the whole population: tau tables (n, F), kref and S of
     Eq. 3 / 4 recomputed by the oracle from the dumped histogram;
   * copy counts and offsets of every replica, recomputed by the oracle from
-    the dumped energy levels (bit for bit), and the new population size;
+    the dumped energy levels (bit for bit), and the new population size, for
+    the nearest-integer rule and for the Poisson draw;
   * gather: sampled output slots hold exact copies of their source replica;
   * sweep: theta = 10 Metropolis sweeps of sampled replicas recomputed by the
     oracle from their dumped pre-sweep state (each replica's sweep is a pure
@@ -59,7 +60,8 @@ def check_step(P, run, ocfg, rng, nsample=48):
     assert np.array_equal(run.dump(P.DUMP_TAB_N), n)
     assert np.array_equal(run.dump(P.DUMP_TAB_F), F)
     counts = run.dump(P.DUMP_COUNTS)
-    assert np.array_equal(counts, O.copy_counts(ocfg, step, ebin, n, F))
+    draw = O.copy_counts_poisson if ocfg.resample == O.RESAMPLE_POISSON else O.copy_counts
+    assert np.array_equal(counts, draw(ocfg, step, ebin, n, F))
     offsets = run.dump(P.DUMP_OFFSETS)
     csum = np.cumsum(counts.astype(np.int64))
     assert np.array_equal(offsets.astype(np.int64), csum - counts)
@@ -84,12 +86,14 @@ def check_step(P, run, ocfg, rng, nsample=48):
     assert run.status() == 0
 
 
-@pytest.mark.parametrize("R0,seed,checks", [(1 << 21, 3, 3), (1 << 17, 2, 4)])
-def test_fullsize_parity(P, R0, seed, checks):
+@pytest.mark.parametrize("R0,seed,checks,resample", [(1 << 21, 3, 3, 0), (1 << 17, 2, 4, 0),
+                                                     (1 << 21, 3, 3, 1)],
+                         ids=["2p21", "2p17", "2p21_poisson"])
+def test_fullsize_parity(P, R0, seed, checks, resample):
     K = 400 if R0 == 1 << 21 else 200
-    ocfg = O.make_config(dim=2, L=64, R0=R0, K=K, theta=10, seed=seed)
+    ocfg = O.make_config(dim=2, L=64, R0=R0, K=K, theta=10, seed=seed, resample=resample)
     run = P.Run(P.make_config(dim=2, L=64, layout=P.LAYOUT_PACKED, R0=R0, K=K, theta=10,
-                              seed=seed))
+                              seed=seed, resample=resample))
     rng = np.random.default_rng(R0)
     # initial population: sampled replicas equal the oracle's uniform init
     for s in rng.choice(R0, size=16, replace=False):
