@@ -48,9 +48,10 @@ OPS_PER_ATTEMPT = 19.5
 # the FMA-heavy pipe (integer multiply-add), 152 SMs, 2070 MHz maximum clock.
 ALU_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12
 # DRAM bytes of one sweep launch, from the ncu capture of the same kernel at
-# 2^18 replicas (profiles/k_sweep_l64_ising2d_L64_R2p18.md: 210.2 MB), scaled
-# by the replica count to 2^21.  None whenever the kernel changes.
-SWEEP_TRAFFIC_BYTES_2P21 = 210.2e6 * 8
+# 2^18 replicas (profiles/k_sweep_l64_ising2d_L64_R2p18.md), scaled by the
+# replica count to 2^21.  None whenever the kernel changes, until the next
+# capture.
+SWEEP_TRAFFIC_BYTES_2P21 = None
 
 
 def rank_workload(rank: int, R0: int) -> dict:
@@ -579,7 +580,8 @@ def main():
         "sweep_attempts_per_ns_kernel": sweep_attempts_per_launch / (sweep_ms * 1e6),
         "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": ALU_PEAK_TOPS,
                      "unit": "Tops/s (32-bit int)", "frac": achieved_tops / ALU_PEAK_TOPS,
-                     "traffic": SWEEP_TRAFFIC_BYTES_2P21 if wl["R0"] == 1 << 21 else None,
+                     "traffic": (SWEEP_TRAFFIC_BYTES_2P21
+                                 if wl["R0"] == 1 << 21 and SWEEP_TRAFFIC_BYTES_2P21 else None),
                      "traffic_note": "ncu dram bytes at 2^18 replicas x 8 (profiles/)",
                      "kernel": "k_sweep_l64 (theta=10 sweeps + measurement)",
                      "ops_per_attempt": OPS_PER_ATTEMPT,

@@ -118,7 +118,30 @@ __device__ __forceinline__ void count_add(uint32_t& b0, uint32_t& b1, uint32_t& 
 // Per-run scalars of one sweep launch, read from the run's device state.
 struct SweepCtx {
     uint32_t R, cur, step, g0, parity, T0, T1, T2, full, ctr3, k0, k1;
+    uint32_t nT0, nT1, nT2, one, four;  // 2^32 - T_c, and opaque 1 and 4 (carry-chain tests)
 };
+
+// Which thresholds of the row kernel run their test as a carry chain (bit c
+// for class c), in 2D and in 3D.  Measured on GB300: 2D L = 32 gains 10 %
+// with both classes on the chain; 3D (L = 8, 10) is not bound by the tests
+// and keeps the dE = 4 class on the chain only.
+#ifndef PA_ROWS_CARRY2
+#define PA_ROWS_CARRY2 3
+#endif
+#ifndef PA_ROWS_CARRY3
+#define PA_ROWS_CARRY3 1
+#endif
+
+// acc * 4 + [u >= T] on the FMA pipe: the carry out of u * 1 + (2^32 - T)
+// feeds the multiply-add that shifts the accumulator (valid for T > 0).
+__device__ __forceinline__ uint32_t carry_ge4(uint32_t acc, uint32_t u, uint32_t one,
+                                              uint32_t negT, uint32_t four) {
+    uint32_t out;
+    asm("{\n\t.reg .u32 t;\n\tmad.lo.cc.u32 t, %1, %2, %3;\n\tmadc.lo.u32 %0, %4, %5, 0;\n\t}"
+        : "=r"(out)
+        : "r"(u), "r"(one), "r"(negT), "r"(acc), "r"(four));
+    return out;
+}
 
 __device__ __forceinline__ SweepCtx sweep_ctx(const RunDev& d) {
     SweepCtx x;
@@ -135,6 +158,11 @@ __device__ __forceinline__ SweepCtx sweep_ctx(const RunDev& d) {
     x.ctr3 = (TAG_SWEEP << 28) | d.instance;
     x.k0 = (uint32_t)d.seed;
     x.k1 = (uint32_t)(d.seed >> 32);
+    x.nT0 = 0u - x.T0;
+    x.nT1 = 0u - x.T1;
+    x.nT2 = 0u - x.T2;
+    x.one = d.one;
+    x.four = d.one << 2;
     return x;
 }
 
@@ -487,19 +515,31 @@ __device__ __forceinline__ uint32_t rows_replica(const RunDev& d, const SweepCtx
                 const int p = (c + par[k]) & 1;
                 const uint32_t* ur = U + HR * r;
                 uint32_t a0 = 0, a1 = 0, a2 = 0;
+                constexpr uint32_t EVEN = 0x55555555u;
+                constexpr uint32_t SITES = (HR >= 16 ? 0xffffffffu : ((1u << (2 * HR)) - 1u)) & EVEN;
+                // thresholds whose test runs as a carry chain on the FMA pipe
+                // (acc * 4 + [u >= T], sites in decreasing j so site j ends at
+                // bit 2j), the others as compare and select on the ALU
+                constexpr int CM = DIM == 2 ? PA_ROWS_CARRY2 : PA_ROWS_CARRY3;
 #pragma unroll
-                for (int j = 0; j < HR; ++j) {
+                for (int j = HR - 1; j >= 0; --j) {
                     const uint32_t u = ur[j];
                     const uint32_t bit = 1u << (2 * j);
-                    if (u < x.T0) a0 |= bit;
-                    if (u < x.T1) a1 |= bit;
-                    if constexpr (DIM == 3)
-                        if (u < x.T2) a2 |= bit;
+                    if constexpr (CM & 1) a0 = carry_ge4(a0, u, x.one, x.nT0, x.four);
+                    else if (u < x.T0) a0 |= bit;
+                    if constexpr (CM & 2) a1 = carry_ge4(a1, u, x.one, x.nT1, x.four);
+                    else if (u < x.T1) a1 |= bit;
+                    if constexpr (DIM == 3) {
+                        if constexpr (CM & 4) a2 = carry_ge4(a2, u, x.one, x.nT2, x.four);
+                        else if (u < x.T2) a2 |= bit;
+                    }
                 }
+                if constexpr (CM & 1) a0 = x.T0 ? (~a0 & SITES) : 0u;
+                if constexpr (CM & 2) a1 = x.T1 ? (~a1 & SITES) : 0u;
+                if constexpr (DIM == 3 && (CM & 4)) a2 = x.T2 ? (~a2 & SITES) : 0u;
                 if (x.full & 1u) a0 = ~0u;
                 if (x.full & 2u) a1 = ~0u;
                 if (x.full & 4u) a2 = ~0u;
-                constexpr uint32_t EVEN = 0x55555555u;
                 const uint32_t acc = ((alw >> p) | ((m0 >> p) & a0) | ((m1 >> p) & a1) |
                                       ((m2 >> p) & a2)) & EVEN;
                 flip[k] = (acc << p) & RG::MASK;

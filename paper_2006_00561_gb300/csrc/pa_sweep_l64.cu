@@ -14,6 +14,10 @@
 //   * a row holds 32 sites of each colour = 8 Philox blocks, each block
 //     covering 4 sites of that row, and both acceptance tests (dE = 4 and 8)
 //     are folded into two bit masks, so no shared memory and no atomics;
+//   * each test is a carry chain: the carry out of u - T is [u >= T], and an
+//     add with carry-in shifts it into an accumulator that holds both tests
+//     of 16 sites (two instructions per test, no predicates or selects; the
+//     FMA pipe is left to the Philox multiplies);
 //   * the Philox round keys come from the kernel parameters, and the products
 //     shared by all blocks of a half-sweep are formed once.
 // Grid-stride (persistent) over replicas; the population size is read from
@@ -24,31 +28,39 @@ namespace pa {
 namespace {
 
 // Tuning knobs (compile time): warps per block, resident blocks per SM the
-// register budget is sized for, and which pipe evaluates the threshold tests u < T:
-//   PA_L64_CMP_MODE 0: both tests as compare + predicated OR (ALU pipe);
+// register budget is sized for, and how the threshold tests u < T run:
+//   PA_L64_CARRY4 / PA_L64_CARRY8 (0..4): the dE = 4 / dE = 8 tests of the
+//                   first that many of the four blocks of a group run as a
+//                   carry chain on the FMA pipe (mad.lo.cc + madc: the carry
+//                   of u + (2^32 - T) is [u >= T], shifted into an accumulator
+//                   two bits at a time).  Default: all of them (+9 % over the
+//                   compare-and-select forms below on GB300).
+//   PA_L64_CMP_MODE, for the remaining tests:
+//                   0: both tests as compare + predicated OR (ALU pipe);
 //                   1: the dE = 4 test on the FMA pipe, dE = 8 on the ALU;
 //                   2: both on the FMA pipe;
-//                   3: the dE = 4 test of half of the blocks on the FMA pipe;
-//                   4: as 3, as a carry chain (mad.lo.cc + madc: the carry of
-//                      u + (2^32 - T) is [u >= T], shifted into an accumulator);
-//                   5: every dE = 4 test as a carry chain;
-//                   7: the dE = 4 test of a quarter of the blocks as a carry chain.
-// On the FMA pipe, u < T is the high word of the 32x32+64 multiply-add
-// u * 1 + (2^64 - T) (all ones iff no carry out, i.e. u < T), and the site's
-// bit is added to the mask by a second multiply-add with -(1 << bit).  The
-// Philox multiplies already load the FMA pipe and its xors the ALU pipe, so
-// moving the tests balances the two.
+//                   3: the dE = 4 test of half of the blocks on the FMA pipe.
+//   On the FMA pipe (modes 1-3), u < T is the high word of the 32x32+64
+//   multiply-add u * 1 + (2^64 - T) (all ones iff no carry out, i.e. u < T),
+//   and the site's bit is added to the mask by a second multiply-add with
+//   -(1 << bit).
 #ifndef PA_L64_MIN_BLOCKS
 #define PA_L64_MIN_BLOCKS 1
 #endif
 #ifndef PA_L64_CMP_MODE
 #define PA_L64_CMP_MODE 3
 #endif
+#ifndef PA_L64_CARRY4
+#define PA_L64_CARRY4 4
+#endif
+#ifndef PA_L64_CARRY8
+#define PA_L64_CARRY8 4
+#endif
 
 // How the Philox products are formed: 0 = high and low halves from C++
 // (__umulhi, *), 1 = one mul.wide.u32, 2 = separate mul.hi.u32 / mul.lo.u32.
 #ifndef PA_L64_MUL_MODE
-#define PA_L64_MUL_MODE 0
+#define PA_L64_MUL_MODE 1
 #endif
 
 #ifndef PA_L64_WARPS
@@ -179,6 +191,42 @@ __device__ __forceinline__ uint32_t carry_ge(uint32_t acc, uint32_t u, uint32_t 
     return out;
 }
 
+// Both tests of one site into a shared accumulator, two bits per site:
+// acc = 4 acc + 2 c4 + c8, where c is the carry of the compare, written by
+// mad.lo.cc (FMA pipe: u * 1 + (2^32 - T) carries iff u >= T, for T > 0) or
+// by sub.cc (ALU pipe: u + ~T + 1 carries iff u >= T, for every T), and
+// shifted in by addc (ALU pipe).
+template <bool F4, bool F8>
+__device__ __forceinline__ uint32_t site_chain(uint32_t acc, uint32_t u, uint32_t one,
+                                               uint32_t c4, uint32_t c8) {
+    uint32_t out;
+    if constexpr (F4 && F8)
+        asm("{\n\t.reg .u32 t, a;\n\tmad.lo.cc.u32 t, %1, %2, %3;\n\taddc.u32 a, %4, %4;"
+            "\n\tmad.lo.cc.u32 t, %1, %2, %5;\n\taddc.u32 %0, a, a;\n\t}"
+            : "=r"(out) : "r"(u), "r"(one), "r"(c4), "r"(acc), "r"(c8));
+    else if constexpr (F4)
+        asm("{\n\t.reg .u32 t, a;\n\tmad.lo.cc.u32 t, %1, %2, %3;\n\taddc.u32 a, %4, %4;"
+            "\n\tsub.cc.u32 t, %1, %5;\n\taddc.u32 %0, a, a;\n\t}"
+            : "=r"(out) : "r"(u), "r"(one), "r"(c4), "r"(acc), "r"(c8));
+    else if constexpr (F8)
+        asm("{\n\t.reg .u32 t, a;\n\tsub.cc.u32 t, %1, %3;\n\taddc.u32 a, %4, %4;"
+            "\n\tmad.lo.cc.u32 t, %1, %2, %5;\n\taddc.u32 %0, a, a;\n\t}"
+            : "=r"(out) : "r"(u), "r"(one), "r"(c4), "r"(acc), "r"(c8));
+    else
+        asm("{\n\t.reg .u32 t, a;\n\tsub.cc.u32 t, %1, %3;\n\taddc.u32 a, %4, %4;"
+            "\n\tsub.cc.u32 t, %1, %5;\n\taddc.u32 %0, a, a;\n\t}"
+            : "=r"(out) : "r"(u), "r"(one), "r"(c4), "r"(acc), "r"(c8));
+    return out;
+}
+
+// PA_L64_CHAIN > 0: both tests of a site into one accumulator (site_chain);
+// 3 (compares on the ALU, default) runs 7.5 % faster on GB300 than the
+// separate FMA chains of PA_L64_CARRY4/8 and 17 % faster than compare and
+// select.  0 selects the PA_L64_CARRY4/8 and PA_L64_CMP_MODE forms.
+#ifndef PA_L64_CHAIN
+#define PA_L64_CHAIN 3
+#endif
+
 // Acceptance masks of the 32 colour-c sites of row y, P = (y + c) & 1: sites
 // x = 8j + 2m + P take word m of Philox block 8y + j; bit x of a4 / a8 is set
 // when that uniform is below T4 / T8.  Four blocks per iteration fill one
@@ -189,13 +237,49 @@ __device__ __forceinline__ void row_accepts(const Keys& d, const HalfSweepGen& g
                                             uint64_t& a8) {
     const uint32_t one = d.one;
     constexpr int M = PA_L64_CMP_MODE;
-    // blocks h < HC take the dE = 4 test as a carry chain
-    constexpr int HC = M == 4 ? 2 : M == 5 ? 4 : M == 7 ? 1 : 0;
-    const uint32_t negT4 = 0u - t4.T, four = one << 2;
+    // blocks h < HC4 (HC8) take the dE = 4 (dE = 8) test as a carry chain
+    constexpr int HC4 = PA_L64_CARRY4, HC8 = PA_L64_CARRY8;
+    const uint32_t negT4 = 0u - t4.T, negT8 = 0u - t8.T, four = one << 2;
     uint32_t h4[2], h8[2];
+    if constexpr (PA_L64_CHAIN > 0) {
+        // PA_L64_CHAIN: 1 both compares on the FMA pipe, 2 dE = 4 on the FMA
+        // pipe and dE = 8 on the ALU, 3 both on the ALU, 4 the reverse of 2
+        constexpr bool F4 = PA_L64_CHAIN == 1 || PA_L64_CHAIN == 2;
+        constexpr bool F8 = PA_L64_CHAIN == 1 || PA_L64_CHAIN == 4;
+        const uint32_t c4 = F4 ? negT4 : t4.T, c8 = F8 ? negT8 : t8.T;
+#pragma unroll 1
+        for (uint32_t q = 0; q < 2; ++q) {
+            uint32_t kc = 0;
+            const uint64_t base = (uint64_t)PM0 * (8u * y + 4u * q);
+#pragma unroll
+            for (int h = 3; h >= 0; --h) {
+                const uint4 u = philox_block(d, gen, base + (uint64_t)PM0 * (uint64_t)h);
+                const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                for (int m = 3; m >= 0; --m) kc = site_chain<F4, F8>(kc, w[m], one, c4, c8);
+            }
+            // site j = 4h + m: dE = 4 carry at bit 2j + 1, dE = 8 carry at bit 2j
+            constexpr uint32_t EV = 0x55555555u;
+            const uint32_t r4 = (kc >> 1) & EV, r8 = kc & EV;
+            // a carry is [u >= T]; below is its complement (T = 0 on the FMA
+            // form carries never, and nothing is below it)
+            const uint32_t b4 = (F4 && !t4.T) ? 0u : (~r4 & EV);
+            const uint32_t b8 = (F8 && !t8.T) ? 0u : (~r8 & EV);
+            if (q == 0) {
+                h4[0] = b4 << P;
+                h8[0] = b8 << P;
+            } else {
+                h4[1] = b4 << P;
+                h8[1] = b8 << P;
+            }
+        }
+        a4 = ((uint64_t)h4[1] << 32) | h4[0];
+        a8 = ((uint64_t)h8[1] << 32) | h8[0];
+        return;
+    }
 #pragma unroll 1
     for (uint32_t q = 0; q < 2; ++q) {
-        uint32_t k4 = 0, k8 = 0, kc = 0;
+        uint32_t k4 = 0, k8 = 0, kc4 = 0, kc8 = 0;
         const uint64_t base = (uint64_t)PM0 * (8u * y + 4u * q);
         // blocks in decreasing h so that the carry chain sees its sites in
         // decreasing order: site j = 4h + m ends at bit 2j
@@ -205,23 +289,30 @@ __device__ __forceinline__ void row_accepts(const Keys& d, const HalfSweepGen& g
             const uint32_t w[4] = {u.x, u.y, u.z, u.w};
             const bool f4 = M == 1 || M == 2 || (M == 3 && h < 2);
             const bool f8 = M == 2;
-            const bool c4 = h < HC;
 #pragma unroll
             for (int m = 3; m >= 0; --m) {
                 const int bit = 8 * h + 2 * m + P;
-                if (c4)
-                    kc = carry_ge(kc, w[m], one, negT4, four);
+                if (h < HC4)
+                    kc4 = carry_ge(kc4, w[m], one, negT4, four);
                 else
                     k4 = f4 ? add_if_below<true>(k4, w[m], t4, one, bit)
                             : add_if_below<false>(k4, w[m], t4, one, bit);
-                k8 = f8 ? add_if_below<true>(k8, w[m], t8, one, bit)
-                        : add_if_below<false>(k8, w[m], t8, one, bit);
+                if (h < HC8)
+                    kc8 = carry_ge(kc8, w[m], one, negT8, four);
+                else
+                    k8 = f8 ? add_if_below<true>(k8, w[m], t8, one, bit)
+                            : add_if_below<false>(k8, w[m], t8, one, bit);
             }
         }
-        if (HC > 0) {
-            constexpr uint32_t even = HC >= 4 ? 0x55555555u : ((1u << (8 * HC)) - 1u) & 0x55555555u;
-            const uint32_t below = t4.T ? (~kc & even) : 0u;  // T = 0: nothing is below
-            k4 |= below << P;
+        // carry-chain site j = 4h + m sits at bit 2j; [u >= T] inverts to
+        // [u < T], and T = 0 has nothing below it
+        if (HC4 > 0) {
+            constexpr uint32_t even = HC4 >= 4 ? 0x55555555u : ((1u << (8 * HC4)) - 1u) & 0x55555555u;
+            k4 |= (t4.T ? (~kc4 & even) : 0u) << P;
+        }
+        if (HC8 > 0) {
+            constexpr uint32_t even = HC8 >= 4 ? 0x55555555u : ((1u << (8 * HC8)) - 1u) & 0x55555555u;
+            k8 |= (t8.T ? (~kc8 & even) : 0u) << P;
         }
         if (q == 0) {
             h4[0] = k4;
