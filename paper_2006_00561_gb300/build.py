@@ -25,6 +25,7 @@ HEADERS = ["pa_internal.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + [
     "-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-prec-div=true", "-prec-sqrt=true",
+    "-diag-suppress", "177",  # members of the geometry templates that some sizes leave unused
     "-Xcompiler", "-fPIC,-ffp-contract=off,-fno-fast-math",
     "-I", os.path.join(ROOT, "include"),
 ]

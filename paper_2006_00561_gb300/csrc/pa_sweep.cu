@@ -656,6 +656,390 @@ __global__ void __launch_bounds__(BW * 32) k_sweep_batched(BatchSweepArgs a) {
 }
 
 // --------------------------------------------------------------------------
+// Replica-sliced sweeps (packed layout, L <= 32): a warp takes 32 replicas of
+// one run, slots b0 .. b0 + 31, and keeps in shared memory one 32-bit word
+// per lattice site whose bit r is the spin of replica b0 + r (set = -1).
+// All bit logic (bond states, the bit-sliced count of unsatisfied bonds, the
+// energy classes, the flips) then runs on 32 replicas at once, whatever L and
+// the dimension, and no lane idles on a short row.
+//
+// Random numbers and update rule are those of the other kernels: in a
+// half-sweep of colour c, lane k of the work takes the group of the four
+// colour-c sites with h = s >> 1 in 4k .. 4k + 3 (Philox counter
+// (k, 2g + c, slot, SWEEP | instance), word h & 3), draws the 32 replicas'
+// blocks and folds every uniform into carry chains, one per (site, class):
+// acc = 2 acc + [u >= T_class], replica r ending at bit r.  A site flips in
+// replica r if its class has dE <= 0, or if bit r of the chain of its class
+// is clear (u < T).
+// --------------------------------------------------------------------------
+template <int DIM, int L, bool PMJ>
+struct RSGeo {
+    static constexpr int N = DIM == 2 ? L * L : L * L * L;
+    static constexpr int HALF = N / 2;
+    static constexpr int NGROUPS = HALF / 4;
+    static constexpr int NROWS = DIM == 2 ? L : L * L;
+    static constexpr int NCLS = DIM == 2 ? 2 : 3;
+    static constexpr int JWORDS = PMJ ? (N + 3) / 4 : 0;  // coupling pattern, one byte per site
+    static constexpr int WORDS = N + JWORDS + 20;         // + round keys (batched form)
+    static constexpr int SPL = (N + 31) / 32;             // sites per lane in the measurement
+    static constexpr int bits(int v) { return v <= 1 ? 1 : 1 + bits(v >> 1); }
+    static constexpr int KU = bits(DIM * SPL);
+    static constexpr int KM = bits(SPL);
+    static constexpr bool OK = L <= 32 && (HALF % 4) == 0 && N >= 8;
+};
+
+template <int DIM, int L, int RSW>
+__host__ __device__ constexpr int rs_words(bool pmj) {
+    return pmj ? RSGeo<DIM, L, true>::WORDS : RSGeo<DIM, L, false>::WORDS;
+}
+
+// Neighbours of site s in the order +x, -x, +y, -y (, +z, -z), periodic.
+template <int DIM, int L>
+__device__ __forceinline__ void rs_nbrs(int s, int (&nb)[2 * DIM]) {
+    const int x = s % L, row = s / L, y = row % L;
+    nb[0] = x == L - 1 ? s - (L - 1) : s + 1;
+    nb[1] = x == 0 ? s + (L - 1) : s - 1;
+    nb[2] = y == L - 1 ? s - (L - 1) * L : s + L;
+    nb[3] = y == 0 ? s + (L - 1) * L : s - L;
+    if constexpr (DIM == 3) {
+        const int z = row / L;
+        nb[4] = z == L - 1 ? s - (L - 1) * L * L : s + L * L;
+        nb[5] = z == 0 ? s + (L - 1) * L * L : s - L * L;
+    }
+}
+
+// Colour-c site of pair h = s >> 1.
+template <int DIM, int L>
+__device__ __forceinline__ int rs_site(int h, int c) {
+    const int row = h / (L / 2), m = h % (L / 2);
+    const int par = DIM == 2 ? (row & 1) : ((row % L + row / L) & 1);
+    return row * L + 2 * m + ((c + par) & 1);
+}
+
+// acc = 2 acc + [u >= T]: the carry of u - T, shifted in with the add.
+__device__ __forceinline__ uint32_t rs_chain(uint32_t acc, uint32_t u, uint32_t T) {
+    uint32_t out;
+    asm("{\n\t.reg .u32 t;\n\tsub.cc.u32 t, %1, %2;\n\taddc.u32 %0, %3, %3;\n\t}"
+        : "=r"(out) : "r"(u), "r"(T), "r"(acc));
+    return out;
+}
+
+// Bit-sliced counter of 32 lanes' worth of bits: adds word v into C[0..K-1].
+template <int K>
+__device__ __forceinline__ void rs_count(uint32_t (&C)[K], uint32_t v) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const uint32_t t = C[k] & v;
+        C[k] ^= v;
+        v = t;
+    }
+}
+
+// Sum over the warp of the bit-sliced counters, for replica r = lane: bit r
+// of plane k over all lanes, weighted 2^k (a transpose by ballots).
+template <int K>
+__device__ __forceinline__ uint32_t rs_total(const uint32_t (&C)[K], int lane) {
+    uint32_t tot = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+#pragma unroll 8
+        for (int r = 0; r < 32; ++r) {
+            const uint32_t b = __ballot_sync(0xffffffffu, (C[k] >> r) & 1u);
+            if (lane == r) tot += (uint32_t)__popc(b) << k;
+        }
+    }
+    return tot;
+}
+
+struct RSKeys {
+    const uint32_t* rk0;
+    const uint32_t* rk1;
+};
+
+// One half-sweep group: sites of pairs 4k .. 4k + 3, colour c, 32 replicas.
+template <int DIM, int L, bool PMJ>
+__device__ __forceinline__ void rs_group(uint32_t* S, const uint8_t* JS, int k, int c, uint32_t g,
+                                         uint32_t b0, uint32_t ctr3, const RSKeys& K,
+                                         const SweepCtx& x) {
+    using G = RSGeo<DIM, L, PMJ>;
+    constexpr int NC = G::NCLS;
+    constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t T[3] = {x.T0, x.T1, x.T2};
+    uint32_t acc[4][NC];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int cl = 0; cl < NC; ++cl) acc[i][cl] = 0u;
+    // rounds 1 and 2 of Philox: the products of the counter words shared by
+    // the 32 replicas (c0 = k, c1, c3) are formed once; M1 * slot steps down
+    // by M1 from slot b0 + 31
+    const uint32_t c1 = 2u * g + (uint32_t)c;
+    const uint32_t x2 = __umulhi(M0, (uint32_t)k) ^ ctr3 ^ K.rk1[0];
+    const uint32_t x3 = M0 * (uint32_t)k;
+    const uint32_t y0k = __umulhi(M1, x2) ^ K.rk0[1];
+    const uint32_t y1 = M1 * x2;
+    uint64_t P = (uint64_t)M1 * (uint64_t)(b0 + 31u);
+#pragma unroll 2
+    for (int r = 31; r >= 0; --r) {
+        const uint32_t x0 = (uint32_t)(P >> 32) ^ c1 ^ K.rk0[0];
+        const uint32_t x1 = (uint32_t)P;
+        P -= M1;
+        uint32_t c0w = y0k ^ x1;
+        uint32_t c1w = y1;
+        uint32_t c2w = __umulhi(M0, x0) ^ x3 ^ K.rk1[1];
+        uint32_t c3w = M0 * x0;
+#pragma unroll
+        for (int rr = 2; rr < 10; ++rr) {
+            const uint32_t a = c0w, b = c2w;
+            const uint32_t hiA = __umulhi(M0, a), loA = M0 * a;
+            const uint32_t hiB = __umulhi(M1, b), loB = M1 * b;
+            c0w = hiB ^ c1w ^ K.rk0[rr];
+            c1w = loB;
+            c2w = hiA ^ c3w ^ K.rk1[rr];
+            c3w = loA;
+        }
+        const uint32_t w[4] = {c0w, c1w, c2w, c3w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int cl = 0; cl < NC; ++cl) acc[i][cl] = rs_chain(acc[i][cl], w[i], T[cl]);
+    }
+    // flips: count the unsatisfied bonds of every replica bit-sliced
+    uint32_t full[3];
+#pragma unroll
+    for (int cl = 0; cl < 3; ++cl) full[cl] = (x.full >> cl) & 1u ? 0xffffffffu : 0u;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int s = rs_site<DIM, L>(4 * k + i, c);
+        int nb[2 * DIM];
+        rs_nbrs<DIM, L>(s, nb);
+        const uint32_t W = S[s];
+        uint32_t v[2 * DIM];
+        const uint32_t jp = PMJ ? (uint32_t)JS[s] : 0u;
+#pragma unroll
+        for (int d = 0; d < 2 * DIM; ++d) {
+            const uint32_t jm = PMJ ? (0u - ((jp >> d) & 1u)) : 0u;
+            v[d] = W ^ S[nb[d]] ^ jm;
+        }
+        uint32_t b0c, b1c, b2c;
+        if constexpr (DIM == 2) {
+            const uint32_t s1 = v[0] ^ v[1] ^ v[2], k1 = (v[0] & v[1]) | (v[2] & (v[0] ^ v[1]));
+            b0c = s1 ^ v[3];
+            const uint32_t k2 = s1 & v[3];
+            b1c = k1 ^ k2;
+            b2c = k1 & k2;
+        } else {
+            const uint32_t s1 = v[0] ^ v[1] ^ v[2], k1 = (v[0] & v[1]) | (v[2] & (v[0] ^ v[1]));
+            const uint32_t s2 = v[3] ^ v[4] ^ v[5], k2 = (v[3] & v[4]) | (v[5] & (v[3] ^ v[4]));
+            b0c = s1 ^ s2;
+            const uint32_t k3 = s1 & s2;
+            b1c = k1 ^ k2 ^ k3;
+            b2c = (k1 & k2) | (k3 & (k1 ^ k2));
+        }
+        uint32_t flip;
+        if constexpr (DIM == 2) {
+            const uint32_t alw = b1c | b2c;              // c_u >= 2: dE <= 0
+            const uint32_t m0 = b0c & ~b1c & ~b2c;       // c_u = 1: dE = 4
+            const uint32_t m1 = ~(b0c | b1c | b2c);      // c_u = 0: dE = 8
+            flip = alw | (m0 & (~acc[i][0] | full[0])) | (m1 & (~acc[i][1] | full[1]));
+        } else {
+            const uint32_t alw = b2c | (b1c & b0c);      // c_u >= 3
+            const uint32_t m0 = b1c & ~b0c & ~b2c;       // c_u = 2: dE = 4
+            const uint32_t m1 = b0c & ~b1c & ~b2c;       // c_u = 1: dE = 8
+            const uint32_t m2 = ~(b0c | b1c | b2c);      // c_u = 0: dE = 12
+            flip = alw | (m0 & (~acc[i][0] | full[0])) | (m1 & (~acc[i][1] | full[1])) |
+                   (m2 & (~acc[i][NC - 1] | full[2]));
+        }
+        S[s] = W ^ flip;
+    }
+}
+
+// One chunk of 32 replicas (slots b0 .. b0 + 31, those below R valid): load
+// and transpose, theta sweeps, measurement, transpose back and store.
+template <int DIM, int L, bool PMJ>
+__device__ __forceinline__ void rs_chunk(const RunDev& d, const SweepCtx& x, uint32_t b0,
+                                         int nsweeps, uint32_t* S, const uint8_t* JS,
+                                         const RSKeys& K, int lane, long long& sAbsM,
+                                         long long& sM2) {
+    using G = RSGeo<DIM, L, PMJ>;
+    constexpr int N = G::N;
+    const uint32_t slot = b0 + (uint32_t)lane;
+    const bool valid = slot < x.R;
+    const int nvalid = (int)min(32u, x.R - b0);
+    uint8_t* spins = d.spins[x.cur];
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(spins + (size_t)slot * d.stride);
+    // load: row words of each lane's replica, one ballot per site
+    uint32_t keep = 0;
+    for (int row = 0; row < G::NROWS; ++row) {
+        const uint32_t word = valid ? __ldg(src + row) : 0u;
+#pragma unroll
+        for (int xx = 0; xx < L; ++xx) {
+            const int s = row * L + xx;
+            const uint32_t bits = __ballot_sync(0xffffffffu, (word >> xx) & 1u);
+            if ((s & 31) == lane) keep = bits;
+            if ((s & 31) == 31) S[s - 31 + lane] = keep;
+        }
+    }
+    if (N & 31) {
+        if (lane < (N & 31)) S[(N & ~31) + lane] = keep;
+    }
+    __syncwarp();
+    const uint32_t ctr3 = x.ctr3;
+    for (int t = 0; t < nsweeps; ++t) {
+        const uint32_t g = x.g0 + (uint32_t)t;
+#pragma unroll 1
+        for (int c = 0; c < 2; ++c) {
+            for (int k = lane; k < G::NGROUPS; k += 32)
+                rs_group<DIM, L, PMJ>(S, JS, k, c, g, b0, ctr3, K, x);
+            __syncwarp();
+        }
+    }
+    // measurement: unsatisfied bonds (s, +d) and spins down, bit-sliced per
+    // lane over its sites, then summed per replica
+    uint32_t CU[G::KU], CM[G::KM];
+#pragma unroll
+    for (int k = 0; k < G::KU; ++k) CU[k] = 0u;
+#pragma unroll
+    for (int k = 0; k < G::KM; ++k) CM[k] = 0u;
+    for (int s = lane; s < N; s += 32) {
+        int nb[2 * DIM];
+        rs_nbrs<DIM, L>(s, nb);
+        const uint32_t W = S[s];
+        const uint32_t jp = PMJ ? (uint32_t)JS[s] : 0u;
+        rs_count<G::KM>(CM, W);
+#pragma unroll
+        for (int dd = 0; dd < DIM; ++dd) {
+            const uint32_t jm = PMJ ? (0u - ((jp >> (2 * dd)) & 1u)) : 0u;
+            rs_count<G::KU>(CU, W ^ S[nb[2 * dd]] ^ jm);
+        }
+    }
+    const uint32_t U = rs_total<G::KU>(CU, lane);
+    const uint32_t down = rs_total<G::KM>(CM, lane);
+    const int M = N - 2 * (int)down;
+    // store: each lane gathers its replica's bits back into row words
+    if (nsweeps > 0 && valid) {
+        uint32_t* dst = reinterpret_cast<uint32_t*>(spins + (size_t)slot * d.stride);
+        for (int row = 0; row < G::NROWS; ++row) {
+            uint32_t word = 0;
+#pragma unroll
+            for (int xx = 0; xx < L; ++xx) word |= ((S[row * L + xx] >> lane) & 1u) << xx;
+            dst[row] = word;
+        }
+    }
+    if (valid) {
+        d.ebin[x.cur][slot] = U >> 1;
+        d.mag[x.cur][slot] = M;
+        if ((U & 1u) != x.parity) atomicOr(&d.st->status, ST_INVARIANT);
+    }
+    hist_flush(d.hist, U >> 1, nvalid, lane);
+    long long a = valid ? (long long)(M < 0 ? -M : M) : 0ll;
+    long long q = valid ? (long long)M * M : 0ll;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        q += __shfl_xor_sync(0xffffffffu, q, o);
+    }
+    sAbsM += a;
+    sM2 += q;
+    __syncwarp();  // S is reused by the next chunk
+}
+
+// Coupling pattern of every site, bit d of JS[s] = J(s, dir d) is -1, dirs
+// in the order of rs_nbrs.
+template <int DIM, int L>
+__device__ __forceinline__ void rs_couplings(const RunDev& d, uint8_t* JS, int lane) {
+    constexpr int N = DIM == 2 ? L * L : L * L * L;
+    const int nw = (int)d.nwords;
+    for (int s = lane; s < N; s += 32) {
+        int nb[2 * DIM];
+        rs_nbrs<DIM, L>(s, nb);
+        uint32_t jp = 0;
+#pragma unroll
+        for (int dd = 0; dd < DIM; ++dd) {
+            const int tp = s, tm = nb[2 * dd + 1];  // bond (s, +d) and bond (s - e_d, +d)
+            jp |= ((d.jpk[dd * nw + tp / L] >> (tp % L)) & 1u) << (2 * dd);
+            jp |= ((d.jpk[dd * nw + tm / L] >> (tm % L)) & 1u) << (2 * dd + 1);
+        }
+        JS[s] = (uint8_t)jp;
+    }
+    __syncwarp();
+}
+
+template <int DIM, int L, bool PMJ, int RSW>
+__global__ void __launch_bounds__(RSW * 32) k_sweep_rs(RunDev d, int nsweeps) {
+    extern __shared__ uint32_t smem[];
+    using G = RSGeo<DIM, L, PMJ>;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint32_t* S = smem + wib * G::WORDS;
+    uint8_t* JS = reinterpret_cast<uint8_t*>(S + G::N);
+    if constexpr (PMJ) rs_couplings<DIM, L>(d, JS, lane);
+    const SweepCtx x = sweep_ctx(d);
+    const RSKeys K{d.rk0, d.rk1};
+    long long sAbsM = 0, sM2 = 0;
+    for (uint32_t ch = blockIdx.x * RSW + wib; ch * 32u < x.R; ch += gridDim.x * RSW)
+        rs_chunk<DIM, L, PMJ>(d, x, ch * 32u, nsweeps, S, JS, K, lane, sAbsM, sM2);
+    if (lane == 0 && (sAbsM | sM2)) {
+        atomicAdd(&d.accum[0], (unsigned long long)sAbsM);
+        atomicAdd(&d.accum[1], (unsigned long long)sM2);
+    }
+}
+
+// Batched: 32-slot chunks claimed from the class's slot space (run capacities
+// are rounded up to 32, so a chunk never straddles two runs).
+template <int DIM, int L, bool PMJ, int BW>
+__global__ void __launch_bounds__(BW * 32) k_sweep_rs_batched(BatchSweepArgs a) {
+    extern __shared__ uint32_t smem[];
+    using G = RSGeo<DIM, L, PMJ>;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint32_t* S = smem + wib * G::WORDS;
+    uint8_t* JS = reinterpret_cast<uint8_t*>(S + G::N);
+    uint32_t* keys = S + G::N + G::JWORDS;
+    uint32_t have = 0xffffffffu;  // run whose keys and couplings are staged
+    const RunDev* dp = nullptr;
+    long long sAbsM = 0, sM2 = 0;
+    for (;;) {
+        uint32_t chunk = 0;
+        if (lane == 0) chunk = atomicAdd(a.counter, 1u);
+        chunk = __shfl_sync(0xffffffffu, chunk, 0);
+        const uint32_t g = chunk * 32u;
+        if (g >= a.total_slots) break;
+        uint32_t lo = 0, hi = a.n;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (a.slot_base[mid] <= g) lo = mid;
+            else hi = mid;
+        }
+        const uint32_t run = a.run_ids[lo];
+        const RunDev& d = a.runs[run];
+        if (run != have) {
+            if (dp && lane == 0 && (sAbsM | sM2)) {
+                atomicAdd(&dp->accum[0], (unsigned long long)sAbsM);
+                atomicAdd(&dp->accum[1], (unsigned long long)sM2);
+            }
+            sAbsM = sM2 = 0;
+            have = run;
+            dp = &d;
+            if (lane < 10) {
+                keys[lane] = d.rk0[lane];
+                keys[10 + lane] = d.rk1[lane];
+            }
+            if constexpr (PMJ) rs_couplings<DIM, L>(d, JS, lane);
+            __syncwarp();
+        }
+        const SweepCtx x = sweep_ctx(d);
+        const uint32_t b0 = g - a.slot_base[lo];
+        if (b0 < x.R) {
+            const RSKeys K{keys, keys + 10};
+            rs_chunk<DIM, L, PMJ>(d, x, b0, d.theta, S, JS, K, lane, sAbsM, sM2);
+        }
+    }
+    if (dp && lane == 0 && (sAbsM | sM2)) {
+        atomicAdd(&dp->accum[0], (unsigned long long)sAbsM);
+        atomicAdd(&dp->accum[1], (unsigned long long)sM2);
+    }
+}
+
+// --------------------------------------------------------------------------
 // Initial population (Sec. 2: uniform states at beta0 = 0, or the ground
 // state for heating from near T = 0) and couplings.
 // Site s of replica `slot` takes the top bit of word s & 3 of the Philox
@@ -758,8 +1142,26 @@ struct KInfo {
     int smem;
 };
 
+// Replica-sliced kernels for the packed layout where they apply (PA_RS = 0
+// keeps the row / word kernels, for comparison).
+#ifndef PA_RS
+#define PA_RS 1
+#endif
+constexpr int RSW = 4;  // warps per block of the plain replica-sliced kernel
+
+template <int DIM, int L>
+constexpr bool rs_applies() {
+    return PA_RS && RSGeo<DIM, L, false>::OK;
+}
+
 template <int DIM, int L>
 KInfo pick_plain(int layout, bool pmj) {
+    if constexpr (rs_applies<DIM, L>()) {
+        if (layout == PA_LAYOUT_PACKED)
+            return {pmj ? (const void*)k_sweep_rs<DIM, L, true, RSW>
+                        : (const void*)k_sweep_rs<DIM, L, false, RSW>,
+                    RSW * (pmj ? RSGeo<DIM, L, true>::WORDS : RSGeo<DIM, L, false>::WORDS) * 4};
+    }
     if (layout == PA_LAYOUT_PACKED) {
         const int smem = WARPS * warp_words<DIM, L, PA_LAYOUT_PACKED>() * 4;
         return {pmj ? (const void*)k_sweep<DIM, L, PA_LAYOUT_PACKED, true>
@@ -780,8 +1182,23 @@ KInfo pick_batched_w(bool pmj) {
             smem};
 }
 
+template <int DIM, int L, int BW>
+KInfo pick_rs_batched_w(bool pmj) {
+    return {pmj ? (const void*)k_sweep_rs_batched<DIM, L, true, BW>
+                : (const void*)k_sweep_rs_batched<DIM, L, false, BW>,
+            BW * (pmj ? RSGeo<DIM, L, true>::WORDS : RSGeo<DIM, L, false>::WORDS) * 4};
+}
+
 template <int DIM, int L>
 KInfo pick_batched(int layout, bool pmj, int warps) {
+    if constexpr (rs_applies<DIM, L>()) {
+        if (layout == PA_LAYOUT_PACKED) {
+            if (warps == 2) return pick_rs_batched_w<DIM, L, 2>(pmj);
+            if (warps == 4) return pick_rs_batched_w<DIM, L, 4>(pmj);
+            if (warps == 8) return pick_rs_batched_w<DIM, L, 8>(pmj);
+            return {nullptr, 0};
+        }
+    }
     if (layout == PA_LAYOUT_PACKED) {
         if (warps == 2) return pick_batched_w<DIM, L, PA_LAYOUT_PACKED, 2>(pmj);
         if (warps == 4) return pick_batched_w<DIM, L, PA_LAYOUT_PACKED, 4>(pmj);
@@ -837,10 +1254,21 @@ bool sweep_supported(int layout, int dim, int L) {
     return find_kernel(layout, dim, L, false).fn != nullptr;
 }
 
+// Replica-sliced kernels take 32 replicas per warp.
+bool rs_kernel(const RunDev& d) {
+    if (d.layout != PA_LAYOUT_PACKED) return false;
+#define PA_CASE(D_, L_) \
+    if (d.dim == D_ && d.L == L_) return rs_applies<D_, L_>();
+    PA_SIZES(PA_CASE)
+#undef PA_CASE
+    return false;
+}
+
 int sweep_grid(const RunDev& d) {
     if (l64_applies(d)) return l64_grid(d);
     const KInfo k = find_kernel(d.layout, d.dim, d.L, d.model == PA_MODEL_PMJ);
-    return grid_for(k, WARPS * 32, ((int64_t)d.cap + WARPS - 1) / WARPS);
+    const int64_t per_block = rs_kernel(d) ? 32 * RSW : WARPS;
+    return grid_for(k, WARPS * 32, ((int64_t)d.cap + per_block - 1) / per_block);
 }
 
 cudaError_t launch_sweep(const RunDev& d, int nsweeps, int grid, cudaStream_t s) {
