@@ -672,15 +672,29 @@ __global__ void __launch_bounds__(BW * 32) k_sweep_batched(BatchSweepArgs a) {
 // replica r if its class has dE <= 0, or if bit r of the chain of its class
 // is clear (u < T).
 // --------------------------------------------------------------------------
+// Shared-memory index of site word s.  The lanes of a half-sweep touch sites
+// about 8 apart (four pairs each), so one padding word per 32 sites spreads
+// them over all banks.
+#ifndef PA_RS_PAD
+#define PA_RS_PAD 1
+#endif
+// Classes whose chain runs on the FMA pipe (multiply-add with carry-out and a
+// multiply-add with carry-in by 2) instead of the ALU (bit c for class c).
+#ifndef PA_RS_FMA
+#define PA_RS_FMA 0
+#endif
+__device__ __forceinline__ int rs_ix(int s) { return PA_RS_PAD ? s + (s >> 5) : s; }
+
 template <int DIM, int L, bool PMJ>
 struct RSGeo {
     static constexpr int N = DIM == 2 ? L * L : L * L * L;
+    static constexpr int NS = PA_RS_PAD ? N + (N + 31) / 32 : N;  // site words with padding
     static constexpr int HALF = N / 2;
     static constexpr int NGROUPS = HALF / 4;
     static constexpr int NROWS = DIM == 2 ? L : L * L;
     static constexpr int NCLS = DIM == 2 ? 2 : 3;
     static constexpr int JWORDS = PMJ ? (N + 3) / 4 : 0;  // coupling pattern, one byte per site
-    static constexpr int WORDS = N + JWORDS + 20;         // + round keys (batched form)
+    static constexpr int WORDS = NS + JWORDS + 20;        // + round keys (batched form)
     static constexpr int SPL = (N + 31) / 32;             // sites per lane in the measurement
     static constexpr int bits(int v) { return v <= 1 ? 1 : 1 + bits(v >> 1); }
     static constexpr int KU = bits(DIM * SPL);
@@ -721,6 +735,16 @@ __device__ __forceinline__ uint32_t rs_chain(uint32_t acc, uint32_t u, uint32_t 
     uint32_t out;
     asm("{\n\t.reg .u32 t;\n\tsub.cc.u32 t, %1, %2;\n\taddc.u32 %0, %3, %3;\n\t}"
         : "=r"(out) : "r"(u), "r"(T), "r"(acc));
+    return out;
+}
+
+// The same on the FMA pipe: u * 1 + (2^32 - T) carries iff u >= T (T > 0;
+// T = 0 never carries and is handled by the caller), then acc * 2 + carry.
+__device__ __forceinline__ uint32_t rs_chain_fma(uint32_t acc, uint32_t u, uint32_t one,
+                                                 uint32_t negT, uint32_t two) {
+    uint32_t out;
+    asm("{\n\t.reg .u32 t;\n\tmad.lo.cc.u32 t, %1, %2, %3;\n\tmadc.lo.u32 %0, %4, %5, 0;\n\t}"
+        : "=r"(out) : "r"(u), "r"(one), "r"(negT), "r"(acc), "r"(two));
     return out;
 }
 
@@ -765,6 +789,8 @@ __device__ __forceinline__ void rs_group(uint32_t* S, const uint8_t* JS, int k, 
     constexpr int NC = G::NCLS;
     constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
     const uint32_t T[3] = {x.T0, x.T1, x.T2};
+    const uint32_t nT[3] = {x.nT0, x.nT1, x.nT2};
+    const uint32_t two = x.one << 1;
     uint32_t acc[4][NC];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -802,8 +828,16 @@ __device__ __forceinline__ void rs_group(uint32_t* S, const uint8_t* JS, int k, 
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int cl = 0; cl < NC; ++cl) acc[i][cl] = rs_chain(acc[i][cl], w[i], T[cl]);
+            for (int cl = 0; cl < NC; ++cl)
+                acc[i][cl] = ((PA_RS_FMA >> cl) & 1) ? rs_chain_fma(acc[i][cl], w[i], x.one, nT[cl], two)
+                                                      : rs_chain(acc[i][cl], w[i], T[cl]);
     }
+    // the FMA form reports T = 0 as "below" for every u: nothing is below 0
+#pragma unroll
+    for (int cl = 0; cl < NC; ++cl)
+        if (((PA_RS_FMA >> cl) & 1) && T[cl] == 0u)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[i][cl] = 0xffffffffu;
     // flips: count the unsatisfied bonds of every replica bit-sliced
     uint32_t full[3];
 #pragma unroll
@@ -813,13 +847,13 @@ __device__ __forceinline__ void rs_group(uint32_t* S, const uint8_t* JS, int k, 
         const int s = rs_site<DIM, L>(4 * k + i, c);
         int nb[2 * DIM];
         rs_nbrs<DIM, L>(s, nb);
-        const uint32_t W = S[s];
+        const uint32_t W = S[rs_ix(s)];
         uint32_t v[2 * DIM];
         const uint32_t jp = PMJ ? (uint32_t)JS[s] : 0u;
 #pragma unroll
         for (int d = 0; d < 2 * DIM; ++d) {
             const uint32_t jm = PMJ ? (0u - ((jp >> d) & 1u)) : 0u;
-            v[d] = W ^ S[nb[d]] ^ jm;
+            v[d] = W ^ S[rs_ix(nb[d])] ^ jm;
         }
         uint32_t b0c, b1c, b2c;
         if constexpr (DIM == 2) {
@@ -850,7 +884,7 @@ __device__ __forceinline__ void rs_group(uint32_t* S, const uint8_t* JS, int k, 
             flip = alw | (m0 & (~acc[i][0] | full[0])) | (m1 & (~acc[i][1] | full[1])) |
                    (m2 & (~acc[i][NC - 1] | full[2]));
         }
-        S[s] = W ^ flip;
+        S[rs_ix(s)] = W ^ flip;
     }
 }
 
@@ -877,11 +911,11 @@ __device__ __forceinline__ void rs_chunk(const RunDev& d, const SweepCtx& x, uin
             const int s = row * L + xx;
             const uint32_t bits = __ballot_sync(0xffffffffu, (word >> xx) & 1u);
             if ((s & 31) == lane) keep = bits;
-            if ((s & 31) == 31) S[s - 31 + lane] = keep;
+            if ((s & 31) == 31) S[rs_ix(s - 31 + lane)] = keep;
         }
     }
     if (N & 31) {
-        if (lane < (N & 31)) S[(N & ~31) + lane] = keep;
+        if (lane < (N & 31)) S[rs_ix((N & ~31) + lane)] = keep;
     }
     __syncwarp();
     const uint32_t ctr3 = x.ctr3;
@@ -904,13 +938,13 @@ __device__ __forceinline__ void rs_chunk(const RunDev& d, const SweepCtx& x, uin
     for (int s = lane; s < N; s += 32) {
         int nb[2 * DIM];
         rs_nbrs<DIM, L>(s, nb);
-        const uint32_t W = S[s];
+        const uint32_t W = S[rs_ix(s)];
         const uint32_t jp = PMJ ? (uint32_t)JS[s] : 0u;
         rs_count<G::KM>(CM, W);
 #pragma unroll
         for (int dd = 0; dd < DIM; ++dd) {
             const uint32_t jm = PMJ ? (0u - ((jp >> (2 * dd)) & 1u)) : 0u;
-            rs_count<G::KU>(CU, W ^ S[nb[2 * dd]] ^ jm);
+            rs_count<G::KU>(CU, W ^ S[rs_ix(nb[2 * dd])] ^ jm);
         }
     }
     const uint32_t U = rs_total<G::KU>(CU, lane);
@@ -922,7 +956,7 @@ __device__ __forceinline__ void rs_chunk(const RunDev& d, const SweepCtx& x, uin
         for (int row = 0; row < G::NROWS; ++row) {
             uint32_t word = 0;
 #pragma unroll
-            for (int xx = 0; xx < L; ++xx) word |= ((S[row * L + xx] >> lane) & 1u) << xx;
+            for (int xx = 0; xx < L; ++xx) word |= ((S[rs_ix(row * L + xx)] >> lane) & 1u) << xx;
             dst[row] = word;
         }
     }
@@ -971,7 +1005,7 @@ __global__ void __launch_bounds__(RSW * 32) k_sweep_rs(RunDev d, int nsweeps) {
     using G = RSGeo<DIM, L, PMJ>;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     uint32_t* S = smem + wib * G::WORDS;
-    uint8_t* JS = reinterpret_cast<uint8_t*>(S + G::N);
+    uint8_t* JS = reinterpret_cast<uint8_t*>(S + G::NS);
     if constexpr (PMJ) rs_couplings<DIM, L>(d, JS, lane);
     const SweepCtx x = sweep_ctx(d);
     const RSKeys K{d.rk0, d.rk1};
@@ -992,8 +1026,8 @@ __global__ void __launch_bounds__(BW * 32) k_sweep_rs_batched(BatchSweepArgs a) 
     using G = RSGeo<DIM, L, PMJ>;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     uint32_t* S = smem + wib * G::WORDS;
-    uint8_t* JS = reinterpret_cast<uint8_t*>(S + G::N);
-    uint32_t* keys = S + G::N + G::JWORDS;
+    uint8_t* JS = reinterpret_cast<uint8_t*>(S + G::NS);
+    uint32_t* keys = S + G::NS + G::JWORDS;
     uint32_t have = 0xffffffffu;  // run whose keys and couplings are staged
     const RunDev* dp = nullptr;
     long long sAbsM = 0, sM2 = 0;
