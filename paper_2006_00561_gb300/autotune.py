@@ -48,7 +48,10 @@ def tune(batch, steps_left: int, cache_path: str | None = DEFAULT_CACHE, verbose
         for w in CANDIDATES:
             if used >= steps_left:
                 break
-            batch.set_warps(ci, w)
+            try:
+                batch.set_warps(ci, w)
+            except RuntimeError:       # a shape this class's kernel does not take
+                continue
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             batch.sync()
             e0.record(batch.stream)

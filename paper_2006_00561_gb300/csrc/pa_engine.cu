@@ -1141,7 +1141,7 @@ int pa_batch_init(pa_run* const* runs, int32_t nruns, void* ws, size_t bytes, vo
             k.L = d.L;
             k.model = d.model;
             k.proto = d;
-            k.warps = pa::l64_batched_applies(d) ? 16 : 4;
+            k.warps = pa::l64_batched_applies(d) ? pa::l64_block_warps(d) : 4;
             k.stream = nullptr;
             k.done = nullptr;
             b->cls.push_back(k);
@@ -1278,7 +1278,7 @@ int pa_batch_set_shape(pa_batch* b, int32_t c, int32_t warps, int32_t chunk) {
     auto& k = b->cls[c];
     int w = warps == 0 ? k.warps : warps;
     if (pa::l64_batched_applies(k.proto)) {
-        if (w != 16) return PA_ERR_INVALID_ARG;
+        if (w != pa::l64_block_warps(k.proto)) return PA_ERR_INVALID_ARG;
     } else if ((w != 2 && w != 4 && w != 8) || !pa::batched_warps_valid(k.proto, w)) {
         return PA_ERR_INVALID_ARG;
     }

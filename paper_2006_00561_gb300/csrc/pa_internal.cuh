@@ -166,8 +166,9 @@ int sweep_grid(const RunDev& d);
 cudaError_t launch_tau(const RunDev& d, cudaStream_t s);
 cudaError_t launch_resample(const RunDev& d, cudaStream_t s);
 cudaError_t launch_obs(const RunDev& d, int nsweeps, cudaStream_t s);
-// specialised 2D ferromagnet, L = 64, packed (pa_sweep_l64.cu)
+// specialised 2D ferromagnet, L = 64 or 128, packed (pa_sweep_l64.cu)
 bool l64_applies(const RunDev& d);
+int l64_block_warps(const RunDev& d);
 int l64_grid(const RunDev& d);
 cudaError_t launch_sweep_l64(const RunDev& d, int nsweeps, int grid, cudaStream_t s);
 // batched forms (one launch for every run of a batch, or of one class)
@@ -182,8 +183,9 @@ cudaError_t launch_sweep_batched(const BatchSweepArgs& a, const RunDev& proto, i
 int batched_sweep_grid(const RunDev& proto, int warps);
 bool batched_warps_valid(const RunDev& proto, int warps);
 bool l64_batched_applies(const RunDev& proto);
-cudaError_t launch_sweep_l64_batched(const BatchSweepArgs& a, int grid, cudaStream_t s);
-int l64_batched_grid();
+cudaError_t launch_sweep_l64_batched(const BatchSweepArgs& a, const RunDev& proto, int grid,
+                                     cudaStream_t s);
+int l64_batched_grid(const RunDev& proto);
 
 constexpr int RS_THREADS = 256;
 constexpr int RS_ITEMS = 8;

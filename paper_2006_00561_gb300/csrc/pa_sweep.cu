@@ -1322,14 +1322,14 @@ bool batched_warps_valid(const RunDev& proto, int warps) {
 }
 
 int batched_sweep_grid(const RunDev& proto, int warps) {
-    if (l64_batched_applies(proto)) return l64_batched_grid();
+    if (l64_batched_applies(proto)) return l64_batched_grid(proto);
     const KInfo k = find_batched(proto.layout, proto.dim, proto.L, proto.model == PA_MODEL_PMJ, warps);
     return grid_for(k, warps * 32, 0);
 }
 
 cudaError_t launch_sweep_batched(const BatchSweepArgs& a, const RunDev& proto, int warps, int grid,
                                  cudaStream_t s) {
-    if (l64_batched_applies(proto)) return launch_sweep_l64_batched(a, grid, s);
+    if (l64_batched_applies(proto)) return launch_sweep_l64_batched(a, proto, grid, s);
     const KInfo k = find_batched(proto.layout, proto.dim, proto.L, proto.model == PA_MODEL_PMJ, warps);
     if (!k.fn) return cudaErrorInvalidValue;
     BatchSweepArgs aa = a;

@@ -513,45 +513,286 @@ __global__ void __launch_bounds__(WARPS64 * 32, PA_L64_MIN_BLOCKS) k_sweep_l64_b
     }
 }
 
-}  // namespace
+// --------------------------------------------------------------------------
+// L = 128: the same scheme with a row of two 64-bit words (lo: x = 0..63,
+// hi: x = 64..127) and four rows per lane (rows 4l .. 4l + 3, one coalesced
+// 64-byte span per lane).  A row has 64 sites of each colour = 16 Philox
+// blocks (16y .. 16y + 15), taken in four groups of four blocks, each group
+// filling one 32-bit quarter of the row's masks.  Rows are updated in place
+// one after the other: the sites a half-sweep flips have the active colour,
+// and the classes of active-colour sites depend only on the other colour.
+// --------------------------------------------------------------------------
+#ifndef PA_L128_WARPS
+#define PA_L128_WARPS 8
+#endif
+constexpr int WARPS128 = PA_L128_WARPS;
 
-bool l64_applies(const RunDev& d) {
-    return d.layout == PA_LAYOUT_PACKED && d.dim == 2 && d.L == 64 && d.model == PA_MODEL_FERRO &&
-           d.stride == 512;
+struct Row2 {
+    uint64_t lo, hi;
+};
+
+__device__ __forceinline__ Row2 shfl_row(const Row2& r, int src) {
+    return Row2{shfl64(r.lo, src), shfl64(r.hi, src)};
 }
 
-int l64_grid(const RunDev& d) {
+// Acceptance masks of the 64 colour-c sites of row y, P = (y + c) & 1: site
+// x = 32q + 8j + 2m + P takes word m of Philox block 16y + 4q + j.
+template <int P>
+__device__ __forceinline__ void row_accepts128(const Keys& d, const HalfSweepGen& gen, uint32_t y,
+                                               const Thr& t4, const Thr& t8, Row2& a4, Row2& a8) {
+    const uint32_t one = d.one;
+    constexpr uint32_t EV = 0x55555555u;
+    uint32_t h4[4], h8[4];
+#pragma unroll 1
+    for (uint32_t q = 0; q < 4; ++q) {
+        uint32_t kc = 0;
+        const uint64_t base = (uint64_t)PM0 * (16u * y + 4u * q);
+#pragma unroll
+        for (int h = 3; h >= 0; --h) {
+            const uint4 u = philox_block(d, gen, base + (uint64_t)PM0 * (uint64_t)h);
+            const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+            for (int m = 3; m >= 0; --m) kc = site_chain<false, false>(kc, w[m], one, t4.T, t8.T);
+        }
+        const uint32_t b4 = (~(kc >> 1) & EV) << P, b8 = (~kc & EV) << P;
+        if (q == 0) {
+            h4[0] = b4;
+            h8[0] = b8;
+        } else if (q == 1) {
+            h4[1] = b4;
+            h8[1] = b8;
+        } else if (q == 2) {
+            h4[2] = b4;
+            h8[2] = b8;
+        } else {
+            h4[3] = b4;
+            h8[3] = b8;
+        }
+    }
+    a4.lo = ((uint64_t)h4[1] << 32) | h4[0];
+    a4.hi = ((uint64_t)h4[3] << 32) | h4[2];
+    a8.lo = ((uint64_t)h8[1] << 32) | h8[0];
+    a8.hi = ((uint64_t)h8[3] << 32) | h8[2];
+}
+
+// Flip mask of one 64-bit word of a row, from its bonds to x + 1 (a), x - 1
+// (b), y - 1 (e) and y + 1 (f).
+__device__ __forceinline__ uint64_t word_flips(uint64_t a, uint64_t b, uint64_t e, uint64_t f,
+                                               uint64_t a4, uint64_t a8, uint64_t cm) {
+    const uint64_t s1 = a ^ b, s2 = e ^ f;
+    const uint64_t ge2 = (a & b) | (e & f) | (s1 & s2);
+    const uint64_t zero = ~(a | b | e | f);
+    const uint64_t one = (s1 ^ s2) & ~ge2;
+    return (ge2 | (one & a4) | (zero & a8)) & cm;
+}
+
+// Flips the colour sites (parity P) of row y in place.
+template <int P>
+__device__ __forceinline__ void row_update128(const Keys& d, const HalfSweepGen& gen, Row2& own,
+                                              const Row2& up, const Row2& dn, uint32_t y,
+                                              const Thr& t4, const Thr& t8, uint32_t full) {
+    constexpr uint64_t cm = P ? 0xAAAAAAAAAAAAAAAAull : 0x5555555555555555ull;
+    Row2 a4, a8;
+    row_accepts128<P>(d, gen, y, t4, t8, a4, a8);
+    if (full & 1u) a4.lo = a4.hi = ~0ull;
+    if (full & 2u) a8.lo = a8.hi = ~0ull;
+    // bit x of the rotations: own bit x + 1 (rp) and x - 1 (rm), mod 128
+    const uint64_t rp_lo = (own.lo >> 1) | (own.hi << 63), rp_hi = (own.hi >> 1) | (own.lo << 63);
+    const uint64_t rm_lo = (own.lo << 1) | (own.hi >> 63), rm_hi = (own.hi << 1) | (own.lo >> 63);
+    const uint64_t f_lo = word_flips(own.lo ^ rp_lo, own.lo ^ rm_lo, own.lo ^ up.lo, own.lo ^ dn.lo,
+                                     a4.lo, a8.lo, cm);
+    const uint64_t f_hi = word_flips(own.hi ^ rp_hi, own.hi ^ rm_hi, own.hi ^ up.hi, own.hi ^ dn.hi,
+                                     a4.hi, a8.hi, cm);
+    own.lo ^= f_lo;
+    own.hi ^= f_hi;
+}
+
+__device__ __forceinline__ uint32_t bonds_x128(const Row2& r) {
+    return __popcll(r.lo ^ ((r.lo >> 1) | (r.hi << 63))) + __popcll(r.hi ^ ((r.hi >> 1) | (r.lo << 63)));
+}
+
+// One replica at L = 128: theta sweeps in registers, then the measurement.
+__device__ __forceinline__ uint32_t l128_replica(const Keys& K, uint4* spins, uint32_t slot,
+                                                 int nsweeps, uint32_t g0, uint32_t ctr3,
+                                                 const Thr& t4, const Thr& t8, uint32_t full,
+                                                 int lane, int& M) {
+    const uint32_t y0 = 4u * (uint32_t)lane;
+    const int lup = (lane + 31) & 31, ldn = (lane + 1) & 31;
+    uint4* p = spins + (size_t)slot * 128 + 4 * lane;  // 2048 bytes per replica
+    Row2 r[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const uint4 v = p[j];
+        r[j].lo = ((uint64_t)v.y << 32) | v.x;
+        r[j].hi = ((uint64_t)v.w << 32) | v.z;
+    }
+    for (int t = 0; t < nsweeps; ++t) {
+        const uint32_t g = g0 + (uint32_t)t;
+        {  // colour 0: rows 4l and 4l + 2 have parity 0
+            const Row2 up = shfl_row(r[3], lup), dn = shfl_row(r[0], ldn);
+            const HalfSweepGen gen = half_sweep_gen(K, 2u * g, slot, ctr3);
+            row_update128<0>(K, gen, r[0], up, r[1], y0, t4, t8, full);
+            row_update128<1>(K, gen, r[1], r[0], r[2], y0 + 1u, t4, t8, full);
+            row_update128<0>(K, gen, r[2], r[1], r[3], y0 + 2u, t4, t8, full);
+            row_update128<1>(K, gen, r[3], r[2], dn, y0 + 3u, t4, t8, full);
+        }
+        {  // colour 1
+            const Row2 up = shfl_row(r[3], lup), dn = shfl_row(r[0], ldn);
+            const HalfSweepGen gen = half_sweep_gen(K, 2u * g + 1u, slot, ctr3);
+            row_update128<1>(K, gen, r[0], up, r[1], y0, t4, t8, full);
+            row_update128<0>(K, gen, r[1], r[0], r[2], y0 + 1u, t4, t8, full);
+            row_update128<1>(K, gen, r[2], r[1], r[3], y0 + 2u, t4, t8, full);
+            row_update128<0>(K, gen, r[3], r[2], dn, y0 + 3u, t4, t8, full);
+        }
+    }
+    // measurement: bonds to x + 1 and to y + 1 of the four rows
+    const Row2 dn = shfl_row(r[0], ldn);
+    uint32_t U = 0, down = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const Row2& nx = j < 3 ? r[j + 1] : dn;
+        U += bonds_x128(r[j]) + __popcll(r[j].lo ^ nx.lo) + __popcll(r[j].hi ^ nx.hi);
+        down += __popcll(r[j].lo) + __popcll(r[j].hi);
+    }
+    U = warp_sum(U);
+    down = warp_sum(down);
+    M = 16384 - 2 * (int)down;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        p[j] = make_uint4((uint32_t)r[j].lo, (uint32_t)(r[j].lo >> 32), (uint32_t)r[j].hi,
+                          (uint32_t)(r[j].hi >> 32));
+    return U;
+}
+
+__global__ void __launch_bounds__(WARPS128 * 32, 1)
+    k_sweep_l128(__grid_constant__ const RunDev d, int nsweeps) {
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    DevState* st = d.st;
+    const uint32_t R = st->R;
+    const uint32_t cur = st->cur;
+    const uint32_t g0 = st->sweep_base;
+    Thr t4, t8;
+    uint32_t full;
+    thresholds(d, st->step, t4, t8, full);
+    const uint32_t ctr3 = (TAG_SWEEP << 28) | d.instance;
+    const Keys K{d.rk0, d.rk1, d.one};
+    uint4* spins = reinterpret_cast<uint4*>(d.spins[cur]);
+    L64Tally tally;
+    const uint32_t nwarps = gridDim.x * WARPS128;
+    for (uint32_t slot = blockIdx.x * WARPS128 + wib; slot < R; slot += nwarps) {
+        int M = 0;
+        const uint32_t U = l128_replica(K, spins, slot, nsweeps, g0, ctr3, t4, t8, full, lane, M);
+        if (lane == 0) {
+            d.ebin[cur][slot] = U >> 1;
+            d.mag[cur][slot] = M;
+            if (U & 1u) atomicOr(&st->status, ST_INVARIANT);
+        }
+        tally.add(d.hist, U, M, lane);
+    }
+    tally.finish(d.hist, d.accum, lane);
+}
+
+__global__ void __launch_bounds__(WARPS128 * 32, 1) k_sweep_l128_batched(BatchSweepArgs a) {
+    __shared__ uint32_t s_keys[WARPS128][24];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    L64Tally tally;
+    for (;;) {
+        uint32_t chunk = 0;
+        if (lane == 0) chunk = atomicAdd(a.counter, 1u);
+        chunk = __shfl_sync(0xffffffffu, chunk, 0);
+        const uint32_t g = chunk * a.chunk;
+        if (g >= a.total_slots) break;
+        uint32_t lo = 0, hi = a.n;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (a.slot_base[mid] <= g) lo = mid;
+            else hi = mid;
+        }
+        const RunDev& d = a.runs[a.run_ids[lo]];
+        DevState* st = d.st;
+        const uint32_t R = st->R, cur = st->cur, g0 = st->sweep_base;
+        Thr t4, t8;
+        uint32_t full;
+        thresholds(d, st->step, t4, t8, full);
+        if (lane < 10) {
+            s_keys[wib][lane] = d.rk0[lane];
+            s_keys[wib][10 + lane] = d.rk1[lane];
+        }
+        __syncwarp();
+        const Keys K{&s_keys[wib][0], &s_keys[wib][10], d.one};
+        const uint32_t ctr3 = (TAG_SWEEP << 28) | d.instance;
+        uint4* spins = reinterpret_cast<uint4*>(d.spins[cur]);
+        const uint32_t first = g - a.slot_base[lo];
+        for (uint32_t slot = first; slot < first + a.chunk && slot < R; ++slot) {
+            int M = 0;
+            const uint32_t U = l128_replica(K, spins, slot, d.theta, g0, ctr3, t4, t8, full, lane, M);
+            if (lane == 0) {
+                d.ebin[cur][slot] = U >> 1;
+                d.mag[cur][slot] = M;
+                if (U & 1u) atomicOr(&st->status, ST_INVARIANT);
+            }
+            tally.add(d.hist, U, M, lane);
+        }
+        tally.finish(d.hist, d.accum, lane);
+        __syncwarp();
+    }
+}
+
+bool is_l128(const RunDev& d) {
+    return d.layout == PA_LAYOUT_PACKED && d.dim == 2 && d.L == 128 && d.model == PA_MODEL_FERRO &&
+           d.stride == 2048;
+}
+
+}  // namespace
+
+// The register-resident row kernels: 2D ferromagnet, packed, L = 64 or 128.
+bool l64_applies(const RunDev& d) {
+    return (d.layout == PA_LAYOUT_PACKED && d.dim == 2 && d.L == 64 && d.model == PA_MODEL_FERRO &&
+            d.stride == 512) ||
+           is_l128(d);
+}
+
+int l64_block_warps(const RunDev& d) { return is_l128(d) ? WARPS128 : WARPS64; }
+
+static int wave(const void* fn, int threads) {
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_l64, WARPS64 * 32, 0) !=
-        cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0) != cudaSuccess)
         return 0;
-    if (per_sm < 1) return 0;
-    const int64_t need = ((int64_t)d.cap + WARPS64 - 1) / WARPS64;
-    const int64_t full = (int64_t)sms * per_sm;
+    return per_sm < 1 ? 0 : sms * per_sm;
+}
+
+int l64_grid(const RunDev& d) {
+    const int w = l64_block_warps(d);
+    const int full = is_l128(d) ? wave((const void*)k_sweep_l128, w * 32)
+                                : wave((const void*)k_sweep_l64, w * 32);
+    if (full <= 0) return 0;
+    const int64_t need = ((int64_t)d.cap + w - 1) / w;
     return (int)(need < full ? need : full);
 }
 
 cudaError_t launch_sweep_l64(const RunDev& d, int nsweeps, int grid, cudaStream_t s) {
-    k_sweep_l64<<<grid, WARPS64 * 32, 0, s>>>(d, nsweeps);
+    if (is_l128(d))
+        k_sweep_l128<<<grid, WARPS128 * 32, 0, s>>>(d, nsweeps);
+    else
+        k_sweep_l64<<<grid, WARPS64 * 32, 0, s>>>(d, nsweeps);
     return cudaGetLastError();
 }
 
 bool l64_batched_applies(const RunDev& proto) { return l64_applies(proto); }
 
-int l64_batched_grid() {
-    int dev = 0, sms = 0, per_sm = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_l64_batched, WARPS64 * 32,
-                                                      0) != cudaSuccess)
-        return 0;
-    return per_sm < 1 ? 0 : sms * per_sm;
+int l64_batched_grid(const RunDev& proto) {
+    return is_l128(proto) ? wave((const void*)k_sweep_l128_batched, WARPS128 * 32)
+                          : wave((const void*)k_sweep_l64_batched, WARPS64 * 32);
 }
 
-cudaError_t launch_sweep_l64_batched(const BatchSweepArgs& a, int grid, cudaStream_t s) {
-    k_sweep_l64_batched<<<grid, WARPS64 * 32, 0, s>>>(a);
+cudaError_t launch_sweep_l64_batched(const BatchSweepArgs& a, const RunDev& proto, int grid,
+                                     cudaStream_t s) {
+    if (is_l128(proto))
+        k_sweep_l128_batched<<<grid, WARPS128 * 32, 0, s>>>(a);
+    else
+        k_sweep_l64_batched<<<grid, WARPS64 * 32, 0, s>>>(a);
     return cudaGetLastError();
 }
 
