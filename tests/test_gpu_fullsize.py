@@ -34,7 +34,7 @@ def P():
 
 
 def check_step(P, run, ocfg, rng, nsample=48):
-    N = 4096
+    N = ocfg.L ** ocfg.dim
     st0 = run.state()
     R_prev = st0["R"]
     ebin = run.dump(P.DUMP_EBIN)
@@ -42,7 +42,8 @@ def check_step(P, run, ocfg, rng, nsample=48):
     hist = run.dump(P.DUMP_HIST)
     assert np.array_equal(hist, np.bincount(ebin, minlength=st0["bins"]))
     obs = run.observables()
-    E = 2 * (2 * ebin.astype(np.int64)) - 2 * N
+    par = run.state()["parity"]
+    E = 2 * (2 * ebin.astype(np.int64) + par) - ocfg.dim * N
     assert obs["sumE"] == E.sum() and obs["sumE2"] == (E * E).sum()
     assert obs["sumAbsM"] == np.abs(mag.astype(np.int64)).sum()
     assert obs["sumM2"] == (mag.astype(np.int64) ** 2).sum()
@@ -79,7 +80,7 @@ def check_step(P, run, ocfg, rng, nsample=48):
     g0 = st["sweeps_done"]
     run.sweep(ocfg.theta)
     T = [O.threshold(O.beta(ocfg, step), 4 * (c + 1)) for c in range(3)]
-    J = np.ones(2 * N, dtype=np.int8)
+    J = O.couplings(ocfg)
     for s, spins in pre.items():
         O.sweep_replica(ocfg, J, spins, s, g0, ocfg.theta, T)
         assert np.array_equal(run.dump_range(P.DUMP_SPINS, s, 1)[0], spins), (step, s)
@@ -105,4 +106,25 @@ def test_fullsize_parity(P, R0, seed, checks, resample):
         assert run.status() == 0
     st = run.state()
     assert abs(st["R"] - R0) < 5 * np.sqrt(R0)
+    run.close()
+
+
+@pytest.mark.parametrize("L,R0", [(10, 1 << 16), (16, (1 << 14) + 77)])
+def test_fullsize_parity_3d_pm_j(P, L, R0):
+    """The replica-sliced kernel at scale: a 3D +-J run with 2^11 or more
+    32-replica chunks (and a partial last chunk), checked like the 2D runs
+    above."""
+    ocfg = O.make_config(dim=3, L=L, model=O.MODEL_PMJ, R0=R0, K=150, theta=10, beta_max=3.0,
+                         seed=40 + L, coupling_seed=50 + L, instance_id=7)
+    run = P.Run(P.make_config(dim=3, L=L, model=P.MODEL_PMJ, layout=P.LAYOUT_PACKED, R0=R0,
+                              K=150, theta=10, beta_max=3.0, seed=40 + L, coupling_seed=50 + L,
+                              instance_id=7))
+    rng = np.random.default_rng(L)
+    for s in rng.choice(R0, size=8, replace=False):
+        assert np.array_equal(run.dump_range(P.DUMP_SPINS, int(s), 1)[0],
+                              O.init_replica(ocfg, int(s)))
+    for c in range(3):
+        check_step(P, run, ocfg, rng, nsample=16)
+        run.run_steps(5 + 10 * c)
+        assert run.status() == 0
     run.close()

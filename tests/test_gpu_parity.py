@@ -250,3 +250,28 @@ def test_workspace_too_small_is_rejected(P):
     with pytest.raises(P.PaError) as e:
         P.pa_init(gcfg, ws.data_ptr() + 16, n, torch.cuda.current_stream().cuda_stream)
     assert e.value.code == -7
+
+
+def test_run_cli_prints_observables(P):
+    """python -m paper_2006_00561_gb300.run: one small run, one JSON line equal
+    to the oracle's observables."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    proc = subprocess.run([sys.executable, "-m", "paper_2006_00561_gb300.run", "--dim", "3", "--L",
+                           "6", "--model", "pmj", "--R0", "500", "--K", "6", "--theta", "2",
+                           "--beta-max", "2", "--seed", "31", "--coupling-seed", "32"],
+                          cwd=root, capture_output=True, text=True, timeout=600)
+    assert proc.returncode == 0, proc.stderr[-1500:]
+    got = json.loads(proc.stdout.strip().splitlines()[-1])
+    orun = O.Run(O.make_config(dim=3, L=6, model=1, R0=500, K=6, theta=2, beta_max=2.0, seed=31,
+                               coupling_seed=32))
+    for _ in range(6):
+        assert orun.step() == 0
+    want = orun.observables()
+    for k in ("step", "R", "sumE", "sumE2", "sumAbsM", "sumM2"):
+        assert got[k] == want[k], k
+    assert abs(got["lnZ"] - want["lnZ"]) <= 1e-12 * abs(want["lnZ"])
+    assert got["ms_per_step"] > 0
