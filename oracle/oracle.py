@@ -46,7 +46,7 @@ class Config(C.Structure):
 
 
 INIT_RANDOM, INIT_GROUND = 0, 1
-RESAMPLE_NEAREST, RESAMPLE_POISSON = 0, 1
+RESAMPLE_NEAREST, RESAMPLE_POISSON, RESAMPLE_MULTINOMIAL = 0, 1, 2
 
 
 class Obs(C.Structure):
@@ -95,6 +95,8 @@ def lib():
                                      u32p]
         L.or_copy_counts_poisson.argtypes = [C.POINTER(Config), C.c_int32, u32p, C.c_int64,
                                              u32p, u32p, u32p]
+        L.or_copy_counts_multinomial.argtypes = [C.POINTER(Config), C.c_int32, u32p, C.c_int64,
+                                                 u32p, u32p, u32p]
         L.or_poisson1_thresholds.argtypes = [u32p, C.c_int32]
         L.or_poisson1_thresholds.restype = C.c_int32
         L.or_derive_obs.argtypes = [C.POINTER(Obs), C.c_int64]
@@ -242,6 +244,18 @@ def copy_counts_poisson(cfg: Config, step: int, ebin: np.ndarray, n: np.ndarray,
     r = np.zeros(ebin.size, dtype=np.uint32)
     lib().or_copy_counts_poisson(C.byref(cfg), step, _ptr(ebin, C.c_uint32), ebin.size,
                                  _ptr(n, C.c_uint32), _ptr(F, C.c_uint32), _ptr(r, C.c_uint32))
+    return r
+
+
+def copy_counts_multinomial(cfg: Config, step: int, ebin: np.ndarray, n: np.ndarray,
+                            F: np.ndarray):
+    ebin = np.ascontiguousarray(ebin, dtype=np.uint32)
+    n = np.ascontiguousarray(n, dtype=np.uint32)
+    F = np.ascontiguousarray(F, dtype=np.uint32)
+    r = np.zeros(ebin.size, dtype=np.uint32)
+    lib().or_copy_counts_multinomial(C.byref(cfg), step, _ptr(ebin, C.c_uint32), ebin.size,
+                                     _ptr(n, C.c_uint32), _ptr(F, C.c_uint32),
+                                     _ptr(r, C.c_uint32))
     return r
 
 

@@ -431,6 +431,45 @@ void or_copy_counts_poisson(const or_config* c, int32_t step, const uint32_t* eb
     }
 }
 
+/* Multinomial resampling, a variant of the Poisson draw (Sec. 2 refers to
+ * the review of Machta for these modifications): the new population is R0
+ * independent draws from the old one, replica i drawn with probability
+ * tau_i / sum_j tau_j, so its size is exactly R0.  tau_i enters in 32.32
+ * fixed point, t_i = n_k 2^32 + F_k for the level k of replica i, which makes
+ * the cumulative weights C_i = t_0 + ... + t_i exact integers.  Draw j
+ * (j = 0 .. R0 - 1) takes the 64-bit uniform v = w[2(j & 1)] + 2^32
+ * w[2(j & 1) + 1] of the Philox block (j >> 1, step, 0, MULTINOMIAL|id), the
+ * point x = floor(v C_{R-1} / 2^64) in [0, C_{R-1}), and gives one copy to the
+ * first replica i with C_i > x. */
+void or_copy_counts_multinomial(const or_config* c, int32_t step, const uint32_t* ebin, int64_t R,
+                                const uint32_t* n, const uint32_t* F, uint32_t* r)
+{
+    uint64_t* C = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(R > 0 ? R : 1));
+    uint64_t total = 0;
+    for (int64_t i = 0; i < R; ++i) {
+        uint32_t k = ebin[i];
+        total += ((uint64_t)n[k] << 32) + (uint64_t)F[k];
+        C[i] = total;
+        r[i] = 0;
+    }
+    if (R < 1 || total == 0) { free(C); return; }
+    for (int64_t j = 0; j < c->R0; ++j) {
+        uint32_t out[4];
+        draw(c->seed, (uint32_t)(j >> 1), (uint32_t)step, 0u, OR_TAG_MULTINOMIAL, c->instance_id,
+             out);
+        uint64_t v = (uint64_t)out[2 * (j & 1)] | ((uint64_t)out[2 * (j & 1) + 1] << 32);
+        uint64_t x = (uint64_t)(((unsigned __int128)v * (unsigned __int128)total) >> 64);
+        int64_t lo = 0, hi = R - 1;          /* first i with C[i] > x */
+        while (lo < hi) {
+            int64_t mid = lo + (hi - lo) / 2;
+            if (C[mid] > x) hi = mid;
+            else lo = mid + 1;
+        }
+        r[lo] += 1;
+    }
+    free(C);
+}
+
 /* Population averages (Sec. 2) from exact integer sums. */
 void or_derive_obs(or_obs* o, int64_t N)
 {
@@ -498,7 +537,9 @@ or_run* or_create(const or_config* c)
     if (c->instance_id < 0 || c->instance_id >= (1 << 28)) return NULL;
     if (c->init != OR_INIT_RANDOM && c->init != OR_INIT_GROUND) return NULL;
     if (c->init == OR_INIT_GROUND && c->model != OR_MODEL_FERRO) return NULL;
-    if (c->resample != OR_RESAMPLE_NEAREST && c->resample != OR_RESAMPLE_POISSON) return NULL;
+    if (c->resample != OR_RESAMPLE_NEAREST && c->resample != OR_RESAMPLE_POISSON &&
+        c->resample != OR_RESAMPLE_MULTINOMIAL)
+        return NULL;
     or_run* r = (or_run*)calloc(1, sizeof(or_run));
     r->c = *c;
     r->N = site_count(c->dim, c->L);
@@ -594,6 +635,8 @@ int or_resample(or_run* r)
     r->lnZ = r->lnZ + r->lnQ;                                          /* Eq. 5 */
     if (c->resample == OR_RESAMPLE_POISSON)
         or_copy_counts_poisson(c, i, r->ebin, r->R, r->tn, r->tF, r->r);
+    else if (c->resample == OR_RESAMPLE_MULTINOMIAL)
+        or_copy_counts_multinomial(c, i, r->ebin, r->R, r->tn, r->tF, r->r);
     else
         or_copy_counts(c, i, r->ebin, r->R, r->tn, r->tF, r->r);
     int64_t total = 0;

@@ -38,10 +38,12 @@ extern "C" {
 #define OR_TAG_RESAMPLE 3u
 #define OR_TAG_COUPLING 4u
 #define OR_TAG_POISSON  5u
+#define OR_TAG_MULTINOMIAL 6u
 
 /* Copy-count rules of the resampling step (Sec. 2). */
 #define OR_RESAMPLE_NEAREST 0  /* r = floor(tau) + [u < frac(tau)]        */
 #define OR_RESAMPLE_POISSON 1  /* r ~ Poisson(tau)                         */
+#define OR_RESAMPLE_MULTINOMIAL 2  /* R0 draws, replica i w.p. tau_i / sum tau */
 
 #define OR_MODEL_FERRO 0   /* J_ij = +1 on every bond (Eq. 6)            */
 #define OR_MODEL_PMJ   1   /* J_ij = +-1 with p = 1/2, one draw per bond */
@@ -59,7 +61,7 @@ typedef struct {
     uint64_t seed;          /* Philox key of init / sweep / resample     */
     uint64_t coupling_seed; /* Philox key of the +-J bonds               */
     int32_t  init;          /* OR_INIT_RANDOM | OR_INIT_GROUND           */
-    int32_t  resample;      /* OR_RESAMPLE_NEAREST | OR_RESAMPLE_POISSON */
+    int32_t  resample;      /* OR_RESAMPLE_NEAREST | _POISSON | _MULTINOMIAL */
 } or_config;
 
 /* Initial population: uniform random states (cooling from beta0 = 0) or the
@@ -102,6 +104,10 @@ void     or_copy_counts(const or_config* c, int32_t step, const uint32_t* ebin, 
  * for m = 0, 1, ... up to and including the first entry that reaches
  * 2^32 - 1 (at most cap entries).  Returns the number of entries. */
 int32_t  or_poisson1_thresholds(uint32_t* T, int32_t cap);
+/* Multinomial copy counts: R0 draws, replica i with probability
+ * t_i / sum_j t_j, t_i = n_k 2^32 + F_k (k = level of replica i). */
+void     or_copy_counts_multinomial(const or_config* c, int32_t step, const uint32_t* ebin,
+                                    int64_t R, const uint32_t* n, const uint32_t* F, uint32_t* r);
 /* Poisson copy counts r_i ~ Poisson(tau_k), tau_k = n_k + F_k / 2^32. */
 void     or_copy_counts_poisson(const or_config* c, int32_t step, const uint32_t* ebin,
                                 int64_t R, const uint32_t* n, const uint32_t* F, uint32_t* r);

@@ -74,6 +74,18 @@ MUTANTS = [
      "for (uint32_t j = 1; j < n[k]; ++j)", "poisson_counts"),
     ("poisson_one_stream_for_all", "or_ustream s = { c, (uint32_t)i,", "or_ustream s = { c, 0u,",
      "poisson_counts_are_independent"),
+    ("multinomial_last_replica_never_drawn", "int64_t lo = 0, hi = R - 1;          /* first i",
+     "int64_t lo = 0, hi = R - 2;          /* first i", "multinomial"),
+    ("multinomial_low_word_only",
+     "uint64_t v = (uint64_t)out[2 * (j & 1)] | ((uint64_t)out[2 * (j & 1) + 1] << 32);",
+     "uint64_t v = (uint64_t)out[2 * (j & 1)];", "multinomial"),
+    ("multinomial_one_draw_short", "for (int64_t j = 0; j < c->R0; ++j) {\n        uint32_t out[4];\n"
+     "        draw(c->seed, (uint32_t)(j >> 1)",
+     "for (int64_t j = 0; j < c->R0 - 1; ++j) {\n        uint32_t out[4];\n"
+     "        draw(c->seed, (uint32_t)(j >> 1)", "multinomial"),
+    ("multinomial_pair_shares_words",
+     "uint64_t v = (uint64_t)out[2 * (j & 1)] | ((uint64_t)out[2 * (j & 1) + 1] << 32);",
+     "uint64_t v = (uint64_t)out[0] | ((uint64_t)out[1] << 32);", "multinomial"),
     ("ground_state_lnZ_wrong_sign", "r->lnZ = log(2.0) + c->beta0 *",
      "r->lnZ = log(2.0) - c->beta0 *", "heating_starts"),
 ]

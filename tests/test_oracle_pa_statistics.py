@@ -40,6 +40,14 @@ def _run_seed(args):
         cfg = O.make_config(dim=2, L=4, R0=3000, K=40, theta=4, beta_max=1.2, seed=seed,
                             resample=O.RESAMPLE_POISSON)
         checks = (10, 20, 40)
+    elif kind == "L4_multinomial":
+        cfg = O.make_config(dim=2, L=4, R0=3000, K=40, theta=4, beta_max=1.2, seed=seed,
+                            resample=O.RESAMPLE_MULTINOMIAL)
+        checks = (10, 20, 40)
+    elif kind == "L16_multinomial":
+        cfg = O.make_config(dim=2, L=16, R0=1000, K=100, theta=10, seed=seed,
+                            resample=O.RESAMPLE_MULTINOMIAL)
+        checks = CHECK_STEPS_L16
     elif kind == "L16_poisson":
         cfg = O.make_config(dim=2, L=16, R0=1000, K=100, theta=10, seed=seed,
                             resample=O.RESAMPLE_POISSON)
@@ -147,6 +155,28 @@ def test_pa_poisson_resampling_matches_kaufman_L16():
     assert abs(allR.var() / 1000 - 1.0) < 0.2
     for out, fails, _ in res:
         assert fails == 0
+    for i in CHECK_STEPS_L16:
+        beta = res[0][0][i][0]
+        _assert_within([r[0][i][1] for r in res], float(exact.kaufman_lnZ(16, beta)))
+        _assert_within([r[0][i][2] / 256 for r in res], exact.kaufman_energy_per_site(16, beta))
+
+
+@pytest.mark.slow
+def test_pa_multinomial_resampling_matches_bruteforce_2d_L4():
+    """Multinomial resampling: ln Z and <E> within 3 SE of brute force, and the
+    population is exactly R0 after every step."""
+    from oracle import oracle as O
+    J = np.ones(32, dtype=np.int8)
+    dos = exact.density_of_states(2 * O.energy(2, 4, J, s)[0] - 32 for s in exact.all_states(16))
+    _pa_vs_dos("L4_multinomial", dos, pop_sigmas=0.0)
+
+
+@pytest.mark.slow
+def test_pa_multinomial_resampling_matches_kaufman_L16():
+    res = _runs("L16_multinomial", list(range(800, 816)))
+    for out, fails, Rs in res:
+        assert fails == 0
+        assert all(r == 1000 for r in Rs)
     for i in CHECK_STEPS_L16:
         beta = res[0][0][i][0]
         _assert_within([r[0][i][1] for r in res], float(exact.kaufman_lnZ(16, beta)))

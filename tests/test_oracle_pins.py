@@ -454,6 +454,75 @@ def test_poisson_counts_are_independent_across_replicas_and_steps():
     assert abs(np.corrcoef(a, b)[0, 1]) < 5 / np.sqrt(R)
 
 
+def test_multinomial_counts_follow_the_multinomial_law():
+    """Multinomial resampling: exactly R0 copies per step, and over 20 steps the
+    copies per level pass a chi-square test against the multinomial law with
+    p_k = H_k t_k / sum_j H_j t_j (t = tau in 32.32 fixed point)."""
+    from scipy import stats
+    R0 = 20000
+    cfg = O.make_config(R0=R0, seed=3, resample=O.RESAMPLE_MULTINOMIAL)
+    ebin = np.array([0, 1, 1, 2, 0, 3] * 700, dtype=np.uint32)
+    n = np.array([1, 0, 2, 0], dtype=np.uint32)
+    F = np.array([0, 1 << 31, 0, 1 << 30], dtype=np.uint32)
+    t = n.astype(np.float64) + F / 2.0 ** 32
+    H = np.bincount(ebin, minlength=4)
+    p = H * t / (H * t).sum()
+    tot = np.zeros(4)
+    for step in range(1, 21):
+        r = O.copy_counts_multinomial(cfg, step, ebin, n, F).astype(np.int64)
+        assert r.sum() == R0
+        tot += np.bincount(ebin, weights=r, minlength=4)
+    exp = p * 20 * R0
+    chi2 = ((tot - exp) ** 2 / exp).sum()
+    assert stats.chi2.sf(chi2, 3) > 1e-4, (tot, exp)
+
+
+def test_multinomial_counts_of_equal_replicas_are_binomial():
+    """All R replicas on one level: r_i ~ Binomial(R0, 1/R), mean R0/R and
+    variance R0/R (1 - 1/R) within 5 standard errors; a zero-weight level gets
+    no copy."""
+    R, R0 = 4000, 8000
+    cfg = O.make_config(R0=R0, seed=9, resample=O.RESAMPLE_MULTINOMIAL)
+    ebin = np.zeros(R, dtype=np.uint32)
+    ebin[::50] = 1
+    n = np.array([1, 0], dtype=np.uint32)
+    F = np.array([0, 0], dtype=np.uint32)
+    r = O.copy_counts_multinomial(cfg, 2, ebin, n, F).astype(np.float64)
+    assert r.sum() == R0 and (r[ebin == 1] == 0).all()
+    live = r[ebin == 0]
+    m = live.size
+    mu, var = R0 / m, R0 / m * (1 - 1 / m)
+    assert abs(live.mean() - mu) < 1e-12
+    # Var of the sample variance of a nearly Poisson(mu) count: about (mu + 2 mu^2) / m
+    assert abs(live.var(ddof=1) - var) < 5 * np.sqrt((mu + 2 * mu * mu) / m)
+
+
+def test_multinomial_draws_match_big_integer_arithmetic():
+    """The point of draw j is floor(v_j C / 2^64) with the exact 128-bit product,
+    and its copy goes to the first replica with C_i > x: recomputed here with
+    Python integers and bisect for a small population."""
+    import bisect
+    R0 = 300
+    cfg = O.make_config(R0=R0, seed=77, instance_id=5, resample=O.RESAMPLE_MULTINOMIAL)
+    rng = np.random.default_rng(1)
+    ebin = rng.integers(0, 5, size=37).astype(np.uint32)
+    n = rng.integers(0, 4, size=5).astype(np.uint32)
+    F = rng.integers(0, 2 ** 32, size=5, dtype=np.uint64).astype(np.uint32)
+    got = O.copy_counts_multinomial(cfg, 11, ebin, n, F)
+    C, acc = [], 0
+    for k in ebin:
+        acc += (int(n[k]) << 32) + int(F[k])
+        C.append(acc)
+    want = [0] * len(ebin)
+    key = [cfg.seed & 0xFFFFFFFF, cfg.seed >> 32]
+    for j in range(R0):
+        w = O.philox([j >> 1, 11, 0, (6 << 28) | 5], key)
+        v = int(w[2 * (j & 1)]) | (int(w[2 * (j & 1) + 1]) << 32)
+        x = (v * acc) >> 64
+        want[bisect.bisect_right(C, x)] += 1
+    assert got.tolist() == want
+
+
 def test_zero_temperature_step_resample_is_identity():
     """beta_i = beta_{i-1} and R = R0: tau = 1 everywhere, every replica is
     copied once into its own slot (Eq. 4 with a zero temperature step)."""
