@@ -297,7 +297,9 @@ def next_items_measure(P, steps: int = 5, R0: int = WORKLOAD["R0"]) -> dict:
     """The extensions of the fixed-schedule path, each on the headline workload
     (2D Ising L = 64 packed, theta = 10, beta 0 -> 1 in 400 steps):
       poisson    -- Poisson copy counts (Sec. 2's draw): graph-replayed step rate
-                    and k_resample time per launch (kernel events);
+                    and resample time per step (kernel events);
+      multinomial -- the same for multinomial resampling (cumulative-weight scan,
+                    R0 draws, then the scan and gather);
       adaptive   -- adaptive temperature steps (overlap target 0.9): host time of
                     the decision (histogram read + bisection) and wall time of a
                     whole adaptive step (decision, resample, sweeps, synchronise);
@@ -310,31 +312,33 @@ def next_items_measure(P, steps: int = 5, R0: int = WORKLOAD["R0"]) -> dict:
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     out = {"workload": f"2D Ising L=64 packed, R0={R0}, theta=10, beta 0->1 in K=400"}
 
-    run = P.Run(P.make_config(layout=P.LAYOUT_PACKED, resample=P.RESAMPLE_POISSON, **wl),
-                stream=stream)
-    run.run_steps(3)
-    run.observables()
-    first = run.state()["step"] + 1
-    torch.cuda.synchronize()
-    e0.record(stream)
-    run.run_steps(steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    h = run.history(first - 1, steps + 1)
-    att = sum(x["R"] for x in h[1:]) * N * theta
-    P.pa_profile(run.h, True)
-    P.pa_profile_read(run.h, reset=True)
-    for _ in range(steps):
-        run.step()
-    prof = P.pa_profile_read(run.h, reset=True)
-    P.pa_profile(run.h, False)
-    run.observables()
-    out["poisson"] = {
-        "attempts_per_ns": att / (ms * 1e6), "ms_per_step": ms / steps,
-        "k_resample_ms": prof["resample"][1] / max(prof["resample"][0], 1),
-        "k_tau_ms": prof["tau"][1] / max(prof["tau"][0], 1),
-        "R_per_step": [x["R"] for x in h[1:]]}
+    for name, rule in (("multinomial", P.RESAMPLE_MULTINOMIAL), ("poisson", P.RESAMPLE_POISSON)):
+        run = P.Run(P.make_config(layout=P.LAYOUT_PACKED, resample=rule, **wl), stream=stream)
+        run.run_steps(3)
+        run.observables()
+        first = run.state()["step"] + 1
+        torch.cuda.synchronize()
+        e0.record(stream)
+        run.run_steps(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        h = run.history(first - 1, steps + 1)
+        att = sum(x["R"] for x in h[1:]) * N * theta
+        P.pa_profile(run.h, True)
+        P.pa_profile_read(run.h, reset=True)
+        for _ in range(steps):
+            run.step()
+        prof = P.pa_profile_read(run.h, reset=True)
+        P.pa_profile(run.h, False)
+        run.observables()
+        out[name] = {
+            "attempts_per_ns": att / (ms * 1e6), "ms_per_step": ms / steps,
+            "resample_ms": prof["resample"][1] / max(prof["resample"][0], 1),
+            "k_tau_ms": prof["tau"][1] / max(prof["tau"][0], 1),
+            "R_per_step": [x["R"] for x in h[1:]]}
+        if name == "multinomial":
+            run.close()
 
     t0 = time.perf_counter()
     blob = run.checkpoint()

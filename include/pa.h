@@ -82,6 +82,14 @@ extern "C" {
  *     and its thinning draws first.  The population is then Poisson(R0). */
 #define PA_RESAMPLE_NEAREST 0
 #define PA_RESAMPLE_POISSON 1
+/*   PA_RESAMPLE_MULTINOMIAL  the new population is R0 independent draws from
+ *     the old one, replica i with probability t_i / sum_j t_j where
+ *     t_i = n_k 2^32 + F_k (tau in 32.32 fixed point, so the cumulative weights
+ *     C_i are exact); draw j uses the 64-bit uniform v of Philox block
+ *     (j >> 1, step, 0, MULTINOMIAL|id) (words 2(j & 1) low, 2(j & 1) + 1 high),
+ *     the point x = floor(v C_{R-1} / 2^64) and the first replica with C_i > x.
+ *     The population stays exactly R0.  Not available in batches. */
+#define PA_RESAMPLE_MULTINOMIAL 2
 typedef struct {
     int32_t  dim;           /* 2 or 3                                  */
     int32_t  L;             /* linear size, even                        */
@@ -96,7 +104,7 @@ typedef struct {
     double   beta0, beta_max;
     uint64_t seed;          /* Philox key: init, sweeps, resampling     */
     uint64_t coupling_seed; /* Philox key of the +-J couplings          */
-    int32_t  resample;      /* PA_RESAMPLE_NEAREST | PA_RESAMPLE_POISSON */
+    int32_t  resample;      /* PA_RESAMPLE_NEAREST | _POISSON | _MULTINOMIAL */
     int32_t  reserved;      /* must be 0                                */
 } pa_config;
 

@@ -55,6 +55,7 @@ size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
     int64_t N, bins, nrows, NW, nwords, stride, cap, tiles, ndist;
+    size_t mn_cum, mn_tiles;
     size_t state, obs, thr, beta, dbeta, dsel, dtab, accum, tabn, tabF, desc, coup, ebin[2], mag[2],
         counts, offsets, spins[2], total;
 };
@@ -90,7 +91,8 @@ int validate(const pa_config* c) {
     if (c->K < 1 || c->theta < 0) return PA_ERR_INVALID_ARG;
     if (c->init != PA_INIT_RANDOM && c->init != PA_INIT_GROUND) return PA_ERR_INVALID_ARG;
     if (c->init == PA_INIT_GROUND && c->model != PA_MODEL_FERRO) return PA_ERR_INVALID_ARG;
-    if (c->resample != PA_RESAMPLE_NEAREST && c->resample != PA_RESAMPLE_POISSON)
+    if (c->resample != PA_RESAMPLE_NEAREST && c->resample != PA_RESAMPLE_POISSON &&
+        c->resample != PA_RESAMPLE_MULTINOMIAL)
         return PA_ERR_INVALID_ARG;
     if (c->reserved != 0) return PA_ERR_INVALID_ARG;
     if (c->instance_id < 0 || c->instance_id >= (1 << 28)) return PA_ERR_INVALID_ARG;
@@ -186,6 +188,11 @@ int make_layout(const pa_config* c, Layout* Lo, std::vector<double>* beta, std::
     l.tabn = take((size_t)l.bins * 4);
     l.tabF = take((size_t)l.bins * 4);
     l.desc = take((size_t)l.tiles * 8);
+    l.mn_cum = l.mn_tiles = 0;
+    if (c->resample == PA_RESAMPLE_MULTINOMIAL) {
+        l.mn_cum = take((size_t)l.cap * 8);
+        l.mn_tiles = take((size_t)(l.tiles + 1) * 8);
+    }
     if (c->model == PA_MODEL_PMJ)
         l.coup = take(c->layout == PA_LAYOUT_PACKED ? (size_t)(c->dim * l.nwords * 4)
                                                     : (size_t)(l.N * c->dim));
@@ -258,7 +265,13 @@ int enqueue_sweep(pa_run* r, cudaStream_t s, int32_t nsweeps) {
 int enqueue_resample(pa_run* r, cudaStream_t s) {
     int rc = timed(r, s, 0, [&] { return pa::launch_tau(r->d, s); });
     if (rc) return rc;
-    return timed(r, s, 1, [&] { return pa::launch_resample(r->d, s); });
+    return timed(r, s, 1, [&] {
+        if (r->cfg.resample == PA_RESAMPLE_MULTINOMIAL) {
+            const cudaError_t e = pa::launch_multinomial(r->d, s);
+            if (e != cudaSuccess) return e;
+        }
+        return pa::launch_resample(r->d, s);
+    });
 }
 
 // Metropolis thresholds of the three dE classes at beta, and the mask of the
@@ -441,6 +454,8 @@ int pa_init(const pa_config* cfg, void* ws, size_t bytes, void* stream, pa_run**
     d.cap_alloc = (uint32_t)l.cap;
     d.R0 = (uint32_t)cfg->R0;
     d.tiles = (uint32_t)l.tiles;
+    d.mn_cum = l.mn_cum ? (unsigned long long*)(base + l.mn_cum) : nullptr;
+    d.mn_tiles = l.mn_tiles ? (unsigned long long*)(base + l.mn_tiles) : nullptr;
     r->hist_bytes = 16 + (size_t)l.bins * 4;
 
     r->sweep_grid = pa::sweep_grid(d);
@@ -1109,6 +1124,10 @@ int pa_batch_init(pa_run* const* runs, int32_t nruns, void* ws, size_t bytes, vo
         if (!r) {
             batch_release(b);
             return PA_ERR_INVALID_ARG;
+        }
+        if (r->cfg.resample == PA_RESAMPLE_MULTINOMIAL) {  // stepped alone only
+            batch_release(b);
+            return PA_ERR_UNSUPPORTED;
         }
         for (int32_t j = 0; j < i; ++j)
             if (runs[j] == r) {

@@ -18,6 +18,7 @@ constexpr uint32_t TAG_SWEEP = 2u;
 constexpr uint32_t TAG_RESAMPLE = 3u;
 constexpr uint32_t TAG_COUPLING = 4u;
 constexpr uint32_t TAG_POISSON = 5u;
+constexpr uint32_t TAG_MULTINOMIAL = 6u;
 constexpr int P1_MAX = 16;  // entries of the Poisson(1) inversion table
 
 // Sticky status bits of DevState::status.
@@ -68,6 +69,8 @@ struct RunDev {
     const double* beta;         // [K+1]
     const double* dbeta;        // [K+1] beta_i - beta_{i-1} (negative when heating)
     unsigned long long* desc;   // [tiles] lookback descriptors
+    unsigned long long* mn_cum;   // multinomial: [cap] cumulative fixed-point weights C_i
+    unsigned long long* mn_tiles; // multinomial: [tiles + 1] tile prefixes, then the total
     pa_obs* obs;                // [K+1] per-step records
     uint32_t* jpk;              // packed couplings [dim][nwords] (bit set: J = -1), PMJ only
     int8_t* j8;                 // int8 couplings [N][dim], PMJ only
@@ -165,6 +168,7 @@ cudaError_t launch_sweep(const RunDev& d, int nsweeps, int grid, cudaStream_t s)
 int sweep_grid(const RunDev& d);
 cudaError_t launch_tau(const RunDev& d, cudaStream_t s);
 cudaError_t launch_resample(const RunDev& d, cudaStream_t s);
+cudaError_t launch_multinomial(const RunDev& d, cudaStream_t s);
 cudaError_t launch_obs(const RunDev& d, int nsweeps, cudaStream_t s);
 // specialised 2D ferromagnet, L = 64 or 128, packed (pa_sweep_l64.cu)
 bool l64_applies(const RunDev& d);

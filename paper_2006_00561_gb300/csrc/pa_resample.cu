@@ -197,9 +197,10 @@ __device__ __noinline__ uint32_t poisson_count(const RunDev& d, uint32_t i, uint
     return count;
 }
 
-// POISSON = false compiles the nearest-integer rule alone (the register
-// budget of the HBM-bound default path); true adds the per-run Poisson branch.
-template <bool POISSON>
+// RULE 0 compiles the nearest-integer rule alone (the register budget of the
+// HBM-bound default path); 1 adds the per-run Poisson branch; 2 takes the
+// counts that the multinomial draw has left in d.counts.
+template <int RULE>
 __device__ __forceinline__ void resample_tile(const RunDev& d, uint32_t tile, ResampleSmem& sm) {
     DevState* st = d.st;
     uint32_t* s_r = sm.r;
@@ -218,7 +219,15 @@ __device__ __forceinline__ void resample_tile(const RunDev& d, uint32_t tile, Re
     const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
     uint32_t r[RS_ITEMS];
     uint32_t sum = 0;
-    if (POISSON && d.resample == PA_RESAMPLE_POISSON) {
+    if (RULE == 2) {
+#pragma unroll
+        for (int j = 0; j < RS_ITEMS; ++j) {
+            const uint32_t i = base + (uint32_t)t * RS_ITEMS + j;
+            const uint32_t v = i < R ? d.counts[i] : 0u;
+            r[j] = v;
+            sum += v;
+        }
+    } else if (RULE == 1 && d.resample == PA_RESAMPLE_POISSON) {
 #pragma unroll
         for (int j = 0; j < RS_ITEMS; ++j) {
             const uint32_t i = base + (uint32_t)t * RS_ITEMS + j;
@@ -377,7 +386,7 @@ __device__ __forceinline__ void resample_tile(const RunDev& d, uint32_t tile, Re
 // Persistent: one wave of CTAs, each claiming tiles until none is left.
 // Claims come in increasing order, so a tile's lookback only waits on tiles
 // already claimed by running CTAs.
-template <bool POISSON>
+template <int RULE>
 __global__ void __launch_bounds__(RS_THREADS) k_resample(RunDev d) {
     __shared__ ResampleSmem sm;
     if (!d.st->active) return;
@@ -387,7 +396,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_resample(RunDev d) {
         __syncthreads();
         const uint32_t tile = sm.tile;
         if (tile * (uint32_t)RS_TILE >= R) break;
-        resample_tile<POISSON>(d, tile, sm);
+        resample_tile<RULE>(d, tile, sm);
         __syncthreads();  // sm is reused by the next tile
     }
 }
@@ -395,7 +404,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_resample(RunDev d) {
 // Batched: global tile ids are claimed in increasing order; run r owns ids
 // tile_base[r] .. tile_base[r+1]-1, so within a run tiles are claimed in order
 // and the lookback only ever waits on tiles already running.
-template <bool POISSON>
+template <int RULE>
 __global__ void __launch_bounds__(RS_THREADS) k_resample_batched(BatchDev b) {
     __shared__ ResampleSmem sm;
     __shared__ uint32_t s_run;
@@ -418,7 +427,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_resample_batched(BatchDev b) {
         __syncthreads();
         if (s_run == 0xffffffffu) break;
         const RunDev& d = b.runs[s_run];
-        if (d.st->active) resample_tile<POISSON>(d, sm.tile, sm);
+        if (d.st->active) resample_tile<RULE>(d, sm.tile, sm);
         __syncthreads();
     }
 }
@@ -504,7 +513,7 @@ cudaError_t launch_tau(const RunDev& d, cudaStream_t s) {
 // One wave of resident CTAs (capped by the number of tiles), looked up once
 // per device and kernel.
 static int resample_wave(const void* fn, int which, uint32_t tiles) {
-    static int cache[64][4];
+    static int cache[64][6];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
     int wave = cache[dev][which];
@@ -521,14 +530,179 @@ static int resample_wave(const void* fn, int which, uint32_t tiles) {
 
 cudaError_t launch_resample(const RunDev& d, cudaStream_t s) {
     if (d.resample == PA_RESAMPLE_POISSON) {
-        const int grid = resample_wave((const void*)k_resample<true>, 2, d.tiles);
+        const int grid = resample_wave((const void*)k_resample<1>, 2, d.tiles);
         if (grid <= 0) return cudaErrorInvalidValue;
-        k_resample<true><<<grid, RS_THREADS, 0, s>>>(d);
+        k_resample<1><<<grid, RS_THREADS, 0, s>>>(d);
+    } else if (d.resample == PA_RESAMPLE_MULTINOMIAL) {
+        const int grid = resample_wave((const void*)k_resample<2>, 4, d.tiles);
+        if (grid <= 0) return cudaErrorInvalidValue;
+        k_resample<2><<<grid, RS_THREADS, 0, s>>>(d);
     } else {
-        const int grid = resample_wave((const void*)k_resample<false>, 0, d.tiles);
+        const int grid = resample_wave((const void*)k_resample<0>, 0, d.tiles);
         if (grid <= 0) return cudaErrorInvalidValue;
-        k_resample<false><<<grid, RS_THREADS, 0, s>>>(d);
+        k_resample<0><<<grid, RS_THREADS, 0, s>>>(d);
     }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Multinomial resampling: the copy counts of all replicas come from R0
+// independent draws.  Replica i weighs t_i = n_k 2^32 + F_k (k = its level);
+// C_i = t_0 + ... + t_i are exact 64-bit integers, built by a three-pass scan
+// over tiles of RS_TILE replicas (tile sums, one-CTA scan of the tile sums,
+// per-tile prefix).  Draw j: v = words 2(j & 1) (low) and 2(j & 1) + 1 (high)
+// of Philox block (j >> 1, step, 0, MULTINOMIAL|id), x = floor(v C_{R-1} /
+// 2^64), one copy (atomic add) to the first replica with C_i > x.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long mn_weight(const RunDev& d, uint32_t k) {
+    return ((unsigned long long)d.tab_n[k] << 32) + (unsigned long long)d.tab_F[k];
+}
+
+__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v, unsigned long long* sw) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sw[wid] = v;
+    __syncthreads();
+    unsigned long long tot = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += sw[w];
+    __syncthreads();
+    return tot;
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_mn_tile_sums(RunDev d) {
+    __shared__ unsigned long long sw[RS_THREADS / 32];
+    const DevState* st = d.st;
+    if (!st->active) return;
+    const uint32_t R = st->R_prev, src = st->src;
+    const uint32_t ntiles = (R + RS_TILE - 1) / RS_TILE;
+    const uint32_t* eb = d.ebin[src];
+    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        unsigned long long part = 0;
+        for (uint32_t j = threadIdx.x; j < (uint32_t)RS_TILE; j += RS_THREADS) {
+            const uint32_t i = tile * RS_TILE + j;
+            if (i < R) part += mn_weight(d, eb[i]);
+        }
+        const unsigned long long tot = block_sum_u64(part, sw);
+        if (threadIdx.x == 0) d.mn_tiles[tile] = tot;
+    }
+}
+
+// Exclusive scan of the tile sums in place; mn_tiles[ntiles] = the total.
+__global__ void __launch_bounds__(1024) k_mn_scan(RunDev d) {
+    __shared__ unsigned long long s[1024];
+    const DevState* st = d.st;
+    if (!st->active) return;
+    const uint32_t R = st->R_prev;
+    const uint32_t ntiles = (R + RS_TILE - 1) / RS_TILE;
+    const uint32_t t = threadIdx.x;
+    const uint32_t per = (ntiles + 1023) / 1024;
+    const uint32_t lo = t * per, hi = min(ntiles, lo + per);
+    unsigned long long part = 0;
+    for (uint32_t k = lo; k < hi; ++k) part += d.mn_tiles[k];
+    s[t] = part;
+    __syncthreads();
+    for (uint32_t o = 1; o < 1024; o <<= 1) {  // inclusive Hillis-Steele scan
+        const unsigned long long v = t >= o ? s[t - o] : 0ull;
+        __syncthreads();
+        s[t] += v;
+        __syncthreads();
+    }
+    unsigned long long run = s[t] - part;
+    for (uint32_t k = lo; k < hi; ++k) {
+        const unsigned long long v = d.mn_tiles[k];
+        d.mn_tiles[k] = run;
+        run += v;
+    }
+    if (t == 1023) d.mn_tiles[ntiles] = s[1023];
+}
+
+// C_i per replica (inclusive), and the copy counts cleared for the draws.
+__global__ void __launch_bounds__(RS_THREADS) k_mn_cum(RunDev d) {
+    __shared__ unsigned long long sw[RS_THREADS / 32];
+    const DevState* st = d.st;
+    if (!st->active) return;
+    const uint32_t R = st->R_prev, src = st->src;
+    const uint32_t ntiles = (R + RS_TILE - 1) / RS_TILE;
+    const uint32_t* eb = d.ebin[src];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const uint32_t i0 = tile * RS_TILE + threadIdx.x * RS_ITEMS;
+        unsigned long long w[RS_ITEMS], part = 0;
+#pragma unroll
+        for (int j = 0; j < RS_ITEMS; ++j) {
+            w[j] = i0 + j < R ? mn_weight(d, eb[i0 + j]) : 0ull;
+            part += w[j];
+        }
+        unsigned long long incl = part;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) sw[wid] = incl;
+        __syncthreads();
+        unsigned long long before = d.mn_tiles[tile];
+        for (int k = 0; k < wid; ++k) before += sw[k];
+        unsigned long long run = before + incl - part;
+#pragma unroll
+        for (int j = 0; j < RS_ITEMS; ++j) {
+            if (i0 + j < R) {
+                run += w[j];
+                d.mn_cum[i0 + j] = run;
+                d.counts[i0 + j] = 0u;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256) k_mn_draw(RunDev d) {
+    const DevState* st = d.st;
+    if (!st->active) return;
+    const uint32_t R = st->R_prev, step = st->step;
+    const uint32_t ntiles = (R + RS_TILE - 1) / RS_TILE;
+    const unsigned long long total = d.mn_tiles[ntiles];
+    if (total == 0ull) return;
+    const uint32_t ctr3 = (TAG_MULTINOMIAL << 28) | d.instance;
+    const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
+    const uint32_t pairs = (d.R0 + 1u) / 2u;
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < pairs;
+         p += gridDim.x * blockDim.x) {
+        const uint4 u = philox(p, step, 0u, ctr3, k0, k1);
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const uint32_t j = 2u * p + (uint32_t)e;
+            if (j >= d.R0) break;
+            const unsigned long long v = e == 0 ? (((unsigned long long)u.y << 32) | u.x)
+                                                : (((unsigned long long)u.w << 32) | u.z);
+            const unsigned long long x = __umul64hi(v, total);
+            uint32_t lo = 0, hi = R - 1;  // first i with C_i > x
+            while (lo < hi) {
+                const uint32_t mid = lo + (hi - lo) / 2;
+                if (d.mn_cum[mid] > x) hi = mid;
+                else lo = mid + 1;
+            }
+            atomicAdd(&d.counts[lo], 1u);
+        }
+    }
+}
+
+cudaError_t launch_multinomial(const RunDev& d, cudaStream_t s) {
+    if (!d.mn_cum || !d.mn_tiles) return cudaErrorInvalidValue;
+    const int wave = resample_wave((const void*)k_mn_cum, 5, d.tiles);
+    if (wave <= 0) return cudaErrorInvalidValue;
+    k_mn_tile_sums<<<wave, RS_THREADS, 0, s>>>(d);
+    k_mn_scan<<<1, 1024, 0, s>>>(d);
+    k_mn_cum<<<wave, RS_THREADS, 0, s>>>(d);
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return cudaErrorInvalidValue;
+    const uint32_t pairs = (d.R0 + 1u) / 2u;
+    const uint32_t want = (pairs + 255u) / 256u;
+    const uint32_t cap = (uint32_t)sms * 8u;
+    k_mn_draw<<<want < cap ? (want ? want : 1u) : cap, 256, 0, s>>>(d);
     return cudaGetLastError();
 }
 
@@ -544,13 +718,13 @@ cudaError_t launch_tau_batched(const BatchDev& b, cudaStream_t s) {
 
 cudaError_t launch_resample_batched(const BatchDev& b, cudaStream_t s) {
     if (b.any_poisson) {
-        const int grid = resample_wave((const void*)k_resample_batched<true>, 3, b.total_tiles);
+        const int grid = resample_wave((const void*)k_resample_batched<1>, 3, b.total_tiles);
         if (grid <= 0) return cudaErrorInvalidValue;
-        k_resample_batched<true><<<grid, RS_THREADS, 0, s>>>(b);
+        k_resample_batched<1><<<grid, RS_THREADS, 0, s>>>(b);
     } else {
-        const int grid = resample_wave((const void*)k_resample_batched<false>, 1, b.total_tiles);
+        const int grid = resample_wave((const void*)k_resample_batched<0>, 1, b.total_tiles);
         if (grid <= 0) return cudaErrorInvalidValue;
-        k_resample_batched<false><<<grid, RS_THREADS, 0, s>>>(b);
+        k_resample_batched<0><<<grid, RS_THREADS, 0, s>>>(b);
     }
     return cudaGetLastError();
 }

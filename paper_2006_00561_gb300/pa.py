@@ -25,7 +25,7 @@ ERRORS = {
 }
 MODEL_FERRO, MODEL_PMJ = 0, 1
 INIT_RANDOM, INIT_GROUND = 0, 1
-RESAMPLE_NEAREST, RESAMPLE_POISSON = 0, 1
+RESAMPLE_NEAREST, RESAMPLE_POISSON, RESAMPLE_MULTINOMIAL = 0, 1, 2
 LAYOUT_INT8, LAYOUT_PACKED = 0, 1
 (DUMP_SPINS, DUMP_EBIN, DUMP_MAG, DUMP_HIST, DUMP_COUNTS, DUMP_OFFSETS, DUMP_TAB_N, DUMP_TAB_F,
  DUMP_COUPLINGS, DUMP_SPINS_RAW, DUMP_STATE) = range(11)

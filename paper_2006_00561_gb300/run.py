@@ -30,7 +30,7 @@ def main(argv=None) -> dict:
     ap.add_argument("--beta-max", type=float, default=1.0)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--coupling-seed", type=int, default=0)
-    ap.add_argument("--resample", choices=["nearest", "poisson"], default="nearest")
+    ap.add_argument("--resample", choices=["nearest", "poisson", "multinomial"], default="nearest")
     ap.add_argument("--heat", action="store_true", help="start from the ground state")
     ap.add_argument("--steps", type=int, default=None)
     a = ap.parse_args(argv)
@@ -39,7 +39,8 @@ def main(argv=None) -> dict:
         layout=P.LAYOUT_PACKED if a.layout == "packed" else P.LAYOUT_INT8, K=a.K, theta=a.theta,
         R0=a.R0, beta0=a.beta0, beta_max=a.beta_max, seed=a.seed, coupling_seed=a.coupling_seed,
         init=P.INIT_GROUND if a.heat else P.INIT_RANDOM,
-        resample=P.RESAMPLE_POISSON if a.resample == "poisson" else P.RESAMPLE_NEAREST)
+        resample={"nearest": P.RESAMPLE_NEAREST, "poisson": P.RESAMPLE_POISSON,
+                  "multinomial": P.RESAMPLE_MULTINOMIAL}[a.resample])
     stream = torch.cuda.Stream()
     run = P.Run(cfg, stream=stream)
     steps = a.K if a.steps is None else min(a.steps, a.K)

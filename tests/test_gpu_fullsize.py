@@ -61,7 +61,8 @@ def check_step(P, run, ocfg, rng, nsample=48):
     assert np.array_equal(run.dump(P.DUMP_TAB_N), n)
     assert np.array_equal(run.dump(P.DUMP_TAB_F), F)
     counts = run.dump(P.DUMP_COUNTS)
-    draw = O.copy_counts_poisson if ocfg.resample == O.RESAMPLE_POISSON else O.copy_counts
+    draw = {O.RESAMPLE_POISSON: O.copy_counts_poisson,
+            O.RESAMPLE_MULTINOMIAL: O.copy_counts_multinomial}.get(ocfg.resample, O.copy_counts)
     assert np.array_equal(counts, draw(ocfg, step, ebin, n, F))
     offsets = run.dump(P.DUMP_OFFSETS)
     csum = np.cumsum(counts.astype(np.int64))
@@ -88,8 +89,8 @@ def check_step(P, run, ocfg, rng, nsample=48):
 
 
 @pytest.mark.parametrize("R0,seed,checks,resample", [(1 << 21, 3, 3, 0), (1 << 17, 2, 4, 0),
-                                                     (1 << 21, 3, 3, 1)],
-                         ids=["2p21", "2p17", "2p21_poisson"])
+                                                     (1 << 21, 3, 3, 1), (1 << 21, 3, 3, 2)],
+                         ids=["2p21", "2p17", "2p21_poisson", "2p21_multinomial"])
 def test_fullsize_parity(P, R0, seed, checks, resample):
     K = 400 if R0 == 1 << 21 else 200
     ocfg = O.make_config(dim=2, L=64, R0=R0, K=K, theta=10, seed=seed, resample=resample)

@@ -158,6 +158,34 @@ def test_poisson_resampling(P, spec):
     run_lockstep(P, steps=8, resample=1, **spec)
 
 
+@pytest.mark.parametrize("spec", [
+    dict(dim=2, L=16, layout=1, R0=1000, K=100, theta=10, seed=121),
+    dict(dim=2, L=16, layout=0, R0=1000, K=100, theta=10, seed=122),
+    dict(dim=2, L=64, layout=1, R0=2300, K=20, theta=2, seed=123),
+    dict(dim=2, L=8, layout=1, R0=5001, K=16, theta=2, beta_max=1.5, seed=124),
+    dict(dim=3, L=8, model=1, layout=1, R0=900, K=10, theta=3, beta_max=3.0, seed=125,
+         coupling_seed=126, instance_id=3),
+    dict(dim=2, L=16, layout=1, R0=1500, K=40, theta=2, beta0=2.0, beta_max=0.0, init=1,
+         seed=127),
+    dict(dim=2, L=16, layout=1, R0=1, K=6, theta=2, beta_max=0.5, seed=128),
+], ids=["2d_L16_packed", "2d_L16_int8", "2d_L64", "ragged_tiles", "3d_L8_pmj", "heating",
+        "single_replica"])
+def test_multinomial_resampling(P, spec):
+    """Multinomial resampling: R0 draws by exact fixed-point cumulative weights;
+    copy counts, offsets, population (exactly R0) bit for bit with the oracle."""
+    run_lockstep(P, steps=8 if spec["K"] >= 8 else spec["K"], resample=2, **spec)
+
+
+def test_multinomial_graph_replay_and_batch_refusal(P):
+    run_lockstep(P, steps=6, use_graph=True, resample=2, dim=2, L=64, layout=1, R0=3000, K=20,
+                 theta=2, beta_max=1.0, seed=129)
+    run = P.Run(P.make_config(dim=2, L=16, R0=100, K=4, resample=2))
+    with pytest.raises(P.PaError) as e:
+        P.Batch([run])
+    assert e.value.code == -3  # PA_ERR_UNSUPPORTED: multinomial runs step alone
+    run.close()
+
+
 def test_poisson_resampling_graph_replay(P):
     run_lockstep(P, steps=8, use_graph=True, resample=1, dim=2, L=64, layout=1, R0=3000, K=20,
                  theta=2, beta_max=1.0, seed=28)
