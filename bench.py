@@ -187,6 +187,55 @@ def oracle_rate(seconds: float = None, R0=512, procs: int = 1, warmup: int = 0, 
             "resampled_replicas_per_s": rs / t_res if t_res else None}
 
 
+CONFIG1 = dict(dim=2, L=16, R0=1000, K=100, theta=10, beta0=0.0, beta_max=1.0, seed=1)
+
+
+def _config1_oracle(seed):
+    """One whole config-1 run of the oracle (2D L = 16 int8, R0 = 1000, beta
+    0 -> 1 in 100 steps, theta = 10); returns (attempts, seconds, lnZ)."""
+    sys.path.insert(0, ROOT)
+    from oracle import oracle as O
+    run = O.Run(O.make_config(**dict(CONFIG1, seed=seed)))
+    t0 = time.perf_counter()
+    att = 0
+    for _ in range(CONFIG1["K"]):
+        assert run.step() == 0
+        att += run.R * 256 * CONFIG1["theta"]
+    return att, time.perf_counter() - t0, run.lnZ
+
+
+def config1_measure(P, procs: int) -> dict:
+    """Config 1 in full: the whole run on the GPU (int8 layout, plain steps,
+    device time) and on the oracle, one process and one per host core
+    (different seeds; the seed-1 process is the GPU run's twin)."""
+    import multiprocessing as mp
+
+    import torch
+    stream = torch.cuda.Stream()
+    run = P.Run(P.make_config(layout=P.LAYOUT_INT8, **CONFIG1), stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(CONFIG1["K"]):
+        run.step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    hist = run.history(1, CONFIG1["K"])
+    att = sum(h["R"] for h in hist) * 256 * CONFIG1["theta"]
+    gpu_lnZ = run.observables()["lnZ"]
+    run.close()
+    a1, s1, o_lnZ = _config1_oracle(CONFIG1["seed"])
+    with mp.get_context("spawn").Pool(procs) as pool:
+        res = pool.map(_config1_oracle, [CONFIG1["seed"] + 1000 * k for k in range(procs)])
+    wall = max(r[1] for r in res)
+    return {"workload": "2D Ising L=16 int8, R0=1000, beta 0->1 in K=100 steps, theta=10, seed 1",
+            "gpu_attempts_per_ns": att / (ms * 1e6), "gpu_run_ms": ms,
+            "oracle_attempts_per_ns": a1 / s1 / 1e9, "oracle_run_s": s1,
+            "oracle_procs": procs, "oracle_procs_attempts_per_ns": sum(r[0] for r in res) / wall / 1e9,
+            "lnZ_gpu": gpu_lnZ, "lnZ_oracle": o_lnZ}
+
+
 def host_info() -> dict:
     import platform
     info = {"nproc": os.cpu_count(), "machine": platform.machine()}
@@ -566,6 +615,9 @@ def main():
                                  "steps": r1["steps"], "seconds": r1["seconds"],
                                  "resampled_replicas_per_s": r1["resampled_replicas_per_s"]},
                "host": host_info()}
+        cfg1 = config1_measure(P, procs)
+    else:
+        cfg1 = None
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -611,6 +663,8 @@ def main():
         line["next_items"] = nxt
     if cpu:
         line["cpu_baseline"] = cpu
+    if cfg1:
+        line["config1"] = cfg1
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
