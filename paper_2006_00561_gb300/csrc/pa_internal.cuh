@@ -191,8 +191,12 @@ cudaError_t launch_sweep_l64_batched(const BatchSweepArgs& a, const RunDev& prot
                                      cudaStream_t s);
 int l64_batched_grid(const RunDev& proto);
 
+// Resample tiles: RS_ITEMS consecutive replicas per thread, RS_THREADS threads.
+#ifndef PA_RS_ITEMS
+#define PA_RS_ITEMS 8
+#endif
 constexpr int RS_THREADS = 256;
-constexpr int RS_ITEMS = 8;
+constexpr int RS_ITEMS = PA_RS_ITEMS;
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
 
 }  // namespace pa

@@ -160,6 +160,11 @@ struct ResampleSmem {
     uint32_t tile, excl;
 };
 
+// 16-byte loads in flight per thread in the gather.
+#ifndef PA_RS_GU
+#define PA_RS_GU 4
+#endif
+
 // Counts, scan and gather of tile `tile` of one run (all threads of the CTA).
 // Poisson(tau_k) copy count of replica i (Sec. 2), tau_k = n + F / 2^32: the
 // event count of a unit-rate Poisson process on [0, tau_k].  The fractional
@@ -334,7 +339,7 @@ __device__ __forceinline__ void resample_tile(const RunDev& d, uint32_t tile, Re
 
     // gather: 16-byte chunks, consecutive threads on consecutive chunks; GU
     // independent loads in flight per thread before their stores
-    constexpr int GU = 4;
+    constexpr int GU = PA_RS_GU;
     const uint32_t CH = d.stride >> 4;
     const uint4* __restrict__ srcp = reinterpret_cast<const uint4*>(d.spins[src]) + (size_t)base * CH;
     uint4* __restrict__ dstp = reinterpret_cast<uint4*>(d.spins[src ^ 1u]);

@@ -103,7 +103,11 @@ def test_poisson1_table_equals_oracle_and_exact(P):
 
 def test_resample_rule_is_validated(P):
     assert P.pa_workspace_size(P.make_config(resample=1)) > 0
-    for bad in (dict(resample=2), dict(resample=-1)):
+    # multinomial runs add the cumulative weights (8 B per slot) and tile prefixes
+    cap = 1000 + 16 * 32 + 1024
+    assert (P.pa_workspace_size(P.make_config(R0=1000, resample=2)) >=
+            P.pa_workspace_size(P.make_config(R0=1000, resample=0)) + 8 * cap)
+    for bad in (dict(resample=3), dict(resample=-1)):
         assert P.pa_workspace_size(P.make_config(**bad)) == 0
     cfg = P.make_config()
     cfg.reserved = 1
