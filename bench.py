@@ -353,7 +353,8 @@ def next_items_measure(P, steps: int = 5, R0: int = WORKLOAD["R0"]) -> dict:
                     the decision (histogram read + bisection) and wall time of a
                     whole adaptive step (decision, resample, sweeps, synchronise);
       checkpoint -- pa_checkpoint / pa_restore of the whole run to and from
-                    pageable host memory."""
+                    pageable host memory;
+      host_link  -- pinned host <-> HBM copy bandwidth (the link e2e crosses)."""
     import torch
     wl = dict(WORKLOAD, R0=R0)
     N, theta = wl["L"] ** 2, wl["theta"]
@@ -399,6 +400,25 @@ def next_items_measure(P, steps: int = 5, R0: int = WORKLOAD["R0"]) -> dict:
                          "restore_gbs": len(blob) / (t2 - t1) / 1e9}
     del blob
     run.close()
+
+    # the host link the e2e copies cross: 1 GiB each way between pinned host
+    # memory and HBM, timed with events on one stream
+    nbytes = 1 << 30
+    host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    dev = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    link = {}
+    for name, dst, src in (("h2d_gbs", dev, host), ("d2h_gbs", host, dev)):
+        with torch.cuda.stream(stream):
+            dst.copy_(src, non_blocking=True)  # warm-up
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(3):
+                dst.copy_(src, non_blocking=True)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        link[name] = 3 * nbytes / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    out["host_link"] = link
+    del host, dev
 
     run = P.Run(P.make_config(layout=P.LAYOUT_PACKED, **wl), stream=stream)
     run.run_steps(3)

@@ -326,20 +326,34 @@ __device__ __forceinline__ void row_accepts(const Keys& d, const HalfSweepGen& g
     a8 = ((uint64_t)h8[1] << 32) | h8[0];
 }
 
+// +-J couplings of one row (bit x set: J = -1) for its four bonds: to x + 1,
+// to x - 1, to y - 1 and to y + 1.  All zero for the ferromagnet.
+struct RowJ {
+    uint64_t xp, xm, up, dn;
+};
+
 // Flip mask of the colour sites (parity P) of one row, given the rows above
 // and below.  c_u >= 2 flips outright (dE <= 0); c_u = 1 needs u < T4; c_u = 0
 // needs u < T8.  full bit 0 / 1: T4 / T8 equal 2^32 (beta = 0), always accept.
-template <int P>
+// A bond is unsatisfied when the spins' xor differs from its coupling bit.
+template <int P, bool PMJ>
 __device__ __forceinline__ uint64_t row_flips(const Keys& d, const HalfSweepGen& gen,
                                               uint64_t own, uint64_t up, uint64_t dn, uint32_t y,
-                                              const Thr& t4, const Thr& t8, uint32_t full) {
+                                              const Thr& t4, const Thr& t8, uint32_t full,
+                                              const RowJ& j) {
     constexpr uint64_t cm = P ? 0xAAAAAAAAAAAAAAAAull : 0x5555555555555555ull;
     uint64_t a4, a8;
     row_accepts<P>(d, gen, y, t4, t8, a4, a8);
-    const uint64_t a = own ^ ((own >> 1) | (own << 63));  // bond to x + 1
-    const uint64_t b = own ^ ((own << 1) | (own >> 63));  // bond to x - 1
-    const uint64_t e = own ^ up;
-    const uint64_t f = own ^ dn;
+    uint64_t a = own ^ ((own >> 1) | (own << 63));  // bond to x + 1
+    uint64_t b = own ^ ((own << 1) | (own >> 63));  // bond to x - 1
+    uint64_t e = own ^ up;
+    uint64_t f = own ^ dn;
+    if constexpr (PMJ) {
+        a ^= j.xp;
+        b ^= j.xm;
+        e ^= j.up;
+        f ^= j.dn;
+    }
     const uint64_t s1 = a ^ b, s2 = e ^ f;
     const uint64_t ge2 = (a & b) | (e & f) | (s1 & s2);
     const uint64_t zero = ~(a | b | e | f);
@@ -358,12 +372,26 @@ __device__ __forceinline__ void hist_flush(uint32_t* hist, uint32_t level, int n
     }
 }
 
+// Couplings of lane l's rows 2l and 2l + 1 from the packed tables (J(+x) and
+// J(+y) bit-planes, two 32-bit words per row).
+__device__ __forceinline__ void l64_couplings(const RunDev& d, int lane, RowJ& ja, RowJ& jb) {
+    const uint32_t* jx = d.jpk;
+    const uint32_t* jy = d.jpk + d.nwords;
+    auto row = [](const uint32_t* t, int y) { return ((uint64_t)t[2 * y + 1] << 32) | t[2 * y]; };
+    auto rot_m = [](uint64_t v) { return (v << 1) | (v >> 63); };  // bit x <- bit x - 1
+    const int ya = 2 * lane, yb = ya + 1;
+    const uint64_t xa = row(jx, ya), xb = row(jx, yb);
+    ja = RowJ{xa, rot_m(xa), row(jy, (ya + 63) & 63), row(jy, ya)};
+    jb = RowJ{xb, rot_m(xb), row(jy, ya), row(jy, yb)};
+}
+
 // One replica: theta sweeps in registers, then the measurement.  Returns U
 // (all lanes), M through the reference; writes the replica back.
+template <bool PMJ>
 __device__ __forceinline__ uint32_t l64_replica(const Keys& K, uint4* spins, uint32_t slot,
                                                 int nsweeps, uint32_t g0, uint32_t ctr3,
                                                 const Thr& t4, const Thr& t8, uint32_t full,
-                                                int lane, int& M) {
+                                                int lane, int& M, const RowJ& ja, const RowJ& jb) {
     const uint32_t ya = 2u * (uint32_t)lane, yb = ya + 1u;
     const int lup = (lane + 31) & 31, ldn = (lane + 1) & 31;
     const uint4 v = spins[(size_t)slot * 32 + lane];
@@ -375,8 +403,8 @@ __device__ __forceinline__ uint32_t l64_replica(const Keys& K, uint4* spins, uin
             const uint64_t up = shfl64(rb, lup);  // row ya - 1
             const uint64_t dn = shfl64(ra, ldn);  // row yb + 1
             const HalfSweepGen gen = half_sweep_gen(K, 2u * g, slot, ctr3);
-            const uint64_t fa = row_flips<0>(K, gen, ra, up, rb, ya, t4, t8, full);
-            const uint64_t fb = row_flips<1>(K, gen, rb, ra, dn, yb, t4, t8, full);
+            const uint64_t fa = row_flips<0, PMJ>(K, gen, ra, up, rb, ya, t4, t8, full, ja);
+            const uint64_t fb = row_flips<1, PMJ>(K, gen, rb, ra, dn, yb, t4, t8, full, jb);
             ra ^= fa;
             rb ^= fb;
         }
@@ -384,16 +412,16 @@ __device__ __forceinline__ uint32_t l64_replica(const Keys& K, uint4* spins, uin
             const uint64_t up = shfl64(rb, lup);
             const uint64_t dn = shfl64(ra, ldn);
             const HalfSweepGen gen = half_sweep_gen(K, 2u * g + 1u, slot, ctr3);
-            const uint64_t fa = row_flips<1>(K, gen, ra, up, rb, ya, t4, t8, full);
-            const uint64_t fb = row_flips<0>(K, gen, rb, ra, dn, yb, t4, t8, full);
+            const uint64_t fa = row_flips<1, PMJ>(K, gen, ra, up, rb, ya, t4, t8, full, ja);
+            const uint64_t fb = row_flips<0, PMJ>(K, gen, rb, ra, dn, yb, t4, t8, full, jb);
             ra ^= fa;
             rb ^= fb;
         }
     }
     // measurement: bonds to x + 1 and to y + 1 of both rows
     const uint64_t dn = shfl64(ra, ldn);
-    uint32_t U = __popcll(ra ^ ((ra >> 1) | (ra << 63))) + __popcll(ra ^ rb) +
-                 __popcll(rb ^ ((rb >> 1) | (rb << 63))) + __popcll(rb ^ dn);
+    uint32_t U = __popcll(ra ^ ((ra >> 1) | (ra << 63)) ^ ja.xp) + __popcll(ra ^ rb ^ ja.dn) +
+                 __popcll(rb ^ ((rb >> 1) | (rb << 63)) ^ jb.xp) + __popcll(rb ^ dn ^ jb.dn);
     uint32_t down = __popcll(ra) + __popcll(rb);
     U = warp_sum(U);
     down = warp_sum(down);
@@ -438,6 +466,7 @@ __device__ __forceinline__ void thresholds(const RunDev& d, uint32_t step, Thr& 
     full = d.thr[step * 4 + 3];
 }
 
+template <bool PMJ>
 __global__ void __launch_bounds__(WARPS64 * 32, PA_L64_MIN_BLOCKS)
     k_sweep_l64(__grid_constant__ const RunDev d, int nsweeps) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -451,15 +480,19 @@ __global__ void __launch_bounds__(WARPS64 * 32, PA_L64_MIN_BLOCKS)
     const uint32_t ctr3 = (TAG_SWEEP << 28) | d.instance;
     const Keys K{d.rk0, d.rk1, d.one};
     uint4* spins = reinterpret_cast<uint4*>(d.spins[cur]);
+    RowJ ja{0, 0, 0, 0}, jb{0, 0, 0, 0};
+    if constexpr (PMJ) l64_couplings(d, lane, ja, jb);
+    const uint32_t parity = st->negbonds & 1u;
     L64Tally tally;
     const uint32_t nwarps = gridDim.x * WARPS64;
     for (uint32_t slot = blockIdx.x * WARPS64 + wib; slot < R; slot += nwarps) {
         int M = 0;
-        const uint32_t U = l64_replica(K, spins, slot, nsweeps, g0, ctr3, t4, t8, full, lane, M);
+        const uint32_t U =
+            l64_replica<PMJ>(K, spins, slot, nsweeps, g0, ctr3, t4, t8, full, lane, M, ja, jb);
         if (lane == 0) {
             d.ebin[cur][slot] = U >> 1;
             d.mag[cur][slot] = M;
-            if (U & 1u) atomicOr(&st->status, ST_INVARIANT);
+            if ((U & 1u) != parity) atomicOr(&st->status, ST_INVARIANT);
         }
         tally.add(d.hist, U, M, lane);
     }
@@ -467,6 +500,7 @@ __global__ void __launch_bounds__(WARPS64 * 32, PA_L64_MIN_BLOCKS)
 }
 
 // Batched: chunks of a.chunk slots of one run from a class's slot space.
+template <bool PMJ>
 __global__ void __launch_bounds__(WARPS64 * 32, PA_L64_MIN_BLOCKS) k_sweep_l64_batched(BatchSweepArgs a) {
     __shared__ uint32_t s_keys[WARPS64][24];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -498,13 +532,17 @@ __global__ void __launch_bounds__(WARPS64 * 32, PA_L64_MIN_BLOCKS) k_sweep_l64_b
         const uint32_t ctr3 = (TAG_SWEEP << 28) | d.instance;
         uint4* spins = reinterpret_cast<uint4*>(d.spins[cur]);
         const uint32_t first = g - a.slot_base[lo];
+        RowJ ja{0, 0, 0, 0}, jb{0, 0, 0, 0};
+        if constexpr (PMJ) l64_couplings(d, lane, ja, jb);
+        const uint32_t parity = st->negbonds & 1u;
         for (uint32_t slot = first; slot < first + a.chunk && slot < R; ++slot) {
             int M = 0;
-            const uint32_t U = l64_replica(K, spins, slot, d.theta, g0, ctr3, t4, t8, full, lane, M);
+            const uint32_t U =
+                l64_replica<PMJ>(K, spins, slot, d.theta, g0, ctr3, t4, t8, full, lane, M, ja, jb);
             if (lane == 0) {
                 d.ebin[cur][slot] = U >> 1;
                 d.mag[cur][slot] = M;
-                if (U & 1u) atomicOr(&st->status, ST_INVARIANT);
+                if ((U & 1u) != parity) atomicOr(&st->status, ST_INVARIANT);
             }
             tally.add(d.hist, U, M, lane);
         }
@@ -586,11 +624,18 @@ __device__ __forceinline__ uint64_t word_flips(uint64_t a, uint64_t b, uint64_t 
     return (ge2 | (one & a4) | (zero & a8)) & cm;
 }
 
+// +-J couplings of one L = 128 row (bit x set: J = -1): bonds to x + 1, x - 1,
+// y - 1, y + 1, two words each.
+struct RowJ2 {
+    Row2 xp, xm, up, dn;
+};
+
 // Flips the colour sites (parity P) of row y in place.
-template <int P>
+template <int P, bool PMJ>
 __device__ __forceinline__ void row_update128(const Keys& d, const HalfSweepGen& gen, Row2& own,
                                               const Row2& up, const Row2& dn, uint32_t y,
-                                              const Thr& t4, const Thr& t8, uint32_t full) {
+                                              const Thr& t4, const Thr& t8, uint32_t full,
+                                              const RowJ2& j) {
     constexpr uint64_t cm = P ? 0xAAAAAAAAAAAAAAAAull : 0x5555555555555555ull;
     Row2 a4, a8;
     row_accepts128<P>(d, gen, y, t4, t8, a4, a8);
@@ -599,71 +644,98 @@ __device__ __forceinline__ void row_update128(const Keys& d, const HalfSweepGen&
     // bit x of the rotations: own bit x + 1 (rp) and x - 1 (rm), mod 128
     const uint64_t rp_lo = (own.lo >> 1) | (own.hi << 63), rp_hi = (own.hi >> 1) | (own.lo << 63);
     const uint64_t rm_lo = (own.lo << 1) | (own.hi >> 63), rm_hi = (own.hi << 1) | (own.lo >> 63);
-    const uint64_t f_lo = word_flips(own.lo ^ rp_lo, own.lo ^ rm_lo, own.lo ^ up.lo, own.lo ^ dn.lo,
-                                     a4.lo, a8.lo, cm);
-    const uint64_t f_hi = word_flips(own.hi ^ rp_hi, own.hi ^ rm_hi, own.hi ^ up.hi, own.hi ^ dn.hi,
-                                     a4.hi, a8.hi, cm);
-    own.lo ^= f_lo;
-    own.hi ^= f_hi;
+    uint64_t a_lo = own.lo ^ rp_lo, b_lo = own.lo ^ rm_lo, e_lo = own.lo ^ up.lo, f_lo = own.lo ^ dn.lo;
+    uint64_t a_hi = own.hi ^ rp_hi, b_hi = own.hi ^ rm_hi, e_hi = own.hi ^ up.hi, f_hi = own.hi ^ dn.hi;
+    if constexpr (PMJ) {
+        a_lo ^= j.xp.lo, b_lo ^= j.xm.lo, e_lo ^= j.up.lo, f_lo ^= j.dn.lo;
+        a_hi ^= j.xp.hi, b_hi ^= j.xm.hi, e_hi ^= j.up.hi, f_hi ^= j.dn.hi;
+    }
+    const uint64_t fl_lo = word_flips(a_lo, b_lo, e_lo, f_lo, a4.lo, a8.lo, cm);
+    const uint64_t fl_hi = word_flips(a_hi, b_hi, e_hi, f_hi, a4.hi, a8.hi, cm);
+    own.lo ^= fl_lo;
+    own.hi ^= fl_hi;
 }
 
-__device__ __forceinline__ uint32_t bonds_x128(const Row2& r) {
-    return __popcll(r.lo ^ ((r.lo >> 1) | (r.hi << 63))) + __popcll(r.hi ^ ((r.hi >> 1) | (r.lo << 63)));
+__device__ __forceinline__ uint32_t bonds_x128(const Row2& r, const Row2& jx) {
+    return __popcll(r.lo ^ ((r.lo >> 1) | (r.hi << 63)) ^ jx.lo) +
+           __popcll(r.hi ^ ((r.hi >> 1) | (r.lo << 63)) ^ jx.hi);
+}
+
+// Couplings of lane l's rows 4l .. 4l + 3 (four 32-bit words per row).
+__device__ __forceinline__ void l128_couplings(const RunDev& d, int lane, RowJ2 (&j)[4]) {
+    const uint32_t* jx = d.jpk;
+    const uint32_t* jy = d.jpk + d.nwords;
+    auto row = [](const uint32_t* t, int y) {
+        return Row2{((uint64_t)t[4 * y + 1] << 32) | t[4 * y], ((uint64_t)t[4 * y + 3] << 32) | t[4 * y + 2]};
+    };
+    const int y0 = 4 * lane;
+    Row2 prev = row(jy, (y0 + 127) & 127);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const Row2 x = row(jx, y0 + k), y = row(jy, y0 + k);
+        // bit x of xm: the bond to x - 1, i.e. J(+x) of site x - 1 (mod 128)
+        const Row2 xm{(x.lo << 1) | (x.hi >> 63), (x.hi << 1) | (x.lo >> 63)};
+        j[k] = RowJ2{x, xm, prev, y};
+        prev = y;
+    }
 }
 
 // One replica at L = 128: theta sweeps in registers, then the measurement.
+template <bool PMJ>
 __device__ __forceinline__ uint32_t l128_replica(const Keys& K, uint4* spins, uint32_t slot,
                                                  int nsweeps, uint32_t g0, uint32_t ctr3,
                                                  const Thr& t4, const Thr& t8, uint32_t full,
-                                                 int lane, int& M) {
+                                                 int lane, int& M, const RowJ2 (&j)[4]) {
     const uint32_t y0 = 4u * (uint32_t)lane;
     const int lup = (lane + 31) & 31, ldn = (lane + 1) & 31;
     uint4* p = spins + (size_t)slot * 128 + 4 * lane;  // 2048 bytes per replica
     Row2 r[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const uint4 v = p[j];
-        r[j].lo = ((uint64_t)v.y << 32) | v.x;
-        r[j].hi = ((uint64_t)v.w << 32) | v.z;
+    for (int k = 0; k < 4; ++k) {
+        const uint4 v = p[k];
+        r[k].lo = ((uint64_t)v.y << 32) | v.x;
+        r[k].hi = ((uint64_t)v.w << 32) | v.z;
     }
     for (int t = 0; t < nsweeps; ++t) {
         const uint32_t g = g0 + (uint32_t)t;
         {  // colour 0: rows 4l and 4l + 2 have parity 0
             const Row2 up = shfl_row(r[3], lup), dn = shfl_row(r[0], ldn);
             const HalfSweepGen gen = half_sweep_gen(K, 2u * g, slot, ctr3);
-            row_update128<0>(K, gen, r[0], up, r[1], y0, t4, t8, full);
-            row_update128<1>(K, gen, r[1], r[0], r[2], y0 + 1u, t4, t8, full);
-            row_update128<0>(K, gen, r[2], r[1], r[3], y0 + 2u, t4, t8, full);
-            row_update128<1>(K, gen, r[3], r[2], dn, y0 + 3u, t4, t8, full);
+            row_update128<0, PMJ>(K, gen, r[0], up, r[1], y0, t4, t8, full, j[0]);
+            row_update128<1, PMJ>(K, gen, r[1], r[0], r[2], y0 + 1u, t4, t8, full, j[1]);
+            row_update128<0, PMJ>(K, gen, r[2], r[1], r[3], y0 + 2u, t4, t8, full, j[2]);
+            row_update128<1, PMJ>(K, gen, r[3], r[2], dn, y0 + 3u, t4, t8, full, j[3]);
         }
         {  // colour 1
             const Row2 up = shfl_row(r[3], lup), dn = shfl_row(r[0], ldn);
             const HalfSweepGen gen = half_sweep_gen(K, 2u * g + 1u, slot, ctr3);
-            row_update128<1>(K, gen, r[0], up, r[1], y0, t4, t8, full);
-            row_update128<0>(K, gen, r[1], r[0], r[2], y0 + 1u, t4, t8, full);
-            row_update128<1>(K, gen, r[2], r[1], r[3], y0 + 2u, t4, t8, full);
-            row_update128<0>(K, gen, r[3], r[2], dn, y0 + 3u, t4, t8, full);
+            row_update128<1, PMJ>(K, gen, r[0], up, r[1], y0, t4, t8, full, j[0]);
+            row_update128<0, PMJ>(K, gen, r[1], r[0], r[2], y0 + 1u, t4, t8, full, j[1]);
+            row_update128<1, PMJ>(K, gen, r[2], r[1], r[3], y0 + 2u, t4, t8, full, j[2]);
+            row_update128<0, PMJ>(K, gen, r[3], r[2], dn, y0 + 3u, t4, t8, full, j[3]);
         }
     }
     // measurement: bonds to x + 1 and to y + 1 of the four rows
     const Row2 dn = shfl_row(r[0], ldn);
     uint32_t U = 0, down = 0;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const Row2& nx = j < 3 ? r[j + 1] : dn;
-        U += bonds_x128(r[j]) + __popcll(r[j].lo ^ nx.lo) + __popcll(r[j].hi ^ nx.hi);
-        down += __popcll(r[j].lo) + __popcll(r[j].hi);
+    for (int k = 0; k < 4; ++k) {
+        const Row2& nx = k < 3 ? r[k + 1] : dn;
+        U += bonds_x128(r[k], j[k].xp) + __popcll(r[k].lo ^ nx.lo ^ j[k].dn.lo) +
+             __popcll(r[k].hi ^ nx.hi ^ j[k].dn.hi);
+        down += __popcll(r[k].lo) + __popcll(r[k].hi);
     }
     U = warp_sum(U);
     down = warp_sum(down);
     M = 16384 - 2 * (int)down;
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-        p[j] = make_uint4((uint32_t)r[j].lo, (uint32_t)(r[j].lo >> 32), (uint32_t)r[j].hi,
-                          (uint32_t)(r[j].hi >> 32));
+    for (int k = 0; k < 4; ++k)
+        p[k] = make_uint4((uint32_t)r[k].lo, (uint32_t)(r[k].lo >> 32), (uint32_t)r[k].hi,
+                          (uint32_t)(r[k].hi >> 32));
     return U;
 }
 
+template <bool PMJ>
 __global__ void __launch_bounds__(WARPS128 * 32, 1)
     k_sweep_l128(__grid_constant__ const RunDev d, int nsweeps) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -677,21 +749,26 @@ __global__ void __launch_bounds__(WARPS128 * 32, 1)
     const uint32_t ctr3 = (TAG_SWEEP << 28) | d.instance;
     const Keys K{d.rk0, d.rk1, d.one};
     uint4* spins = reinterpret_cast<uint4*>(d.spins[cur]);
+    RowJ2 j[4] = {};
+    if constexpr (PMJ) l128_couplings(d, lane, j);
+    const uint32_t parity = st->negbonds & 1u;
     L64Tally tally;
     const uint32_t nwarps = gridDim.x * WARPS128;
     for (uint32_t slot = blockIdx.x * WARPS128 + wib; slot < R; slot += nwarps) {
         int M = 0;
-        const uint32_t U = l128_replica(K, spins, slot, nsweeps, g0, ctr3, t4, t8, full, lane, M);
+        const uint32_t U =
+            l128_replica<PMJ>(K, spins, slot, nsweeps, g0, ctr3, t4, t8, full, lane, M, j);
         if (lane == 0) {
             d.ebin[cur][slot] = U >> 1;
             d.mag[cur][slot] = M;
-            if (U & 1u) atomicOr(&st->status, ST_INVARIANT);
+            if ((U & 1u) != parity) atomicOr(&st->status, ST_INVARIANT);
         }
         tally.add(d.hist, U, M, lane);
     }
     tally.finish(d.hist, d.accum, lane);
 }
 
+template <bool PMJ>
 __global__ void __launch_bounds__(WARPS128 * 32, 1) k_sweep_l128_batched(BatchSweepArgs a) {
     __shared__ uint32_t s_keys[WARPS128][24];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -723,13 +800,17 @@ __global__ void __launch_bounds__(WARPS128 * 32, 1) k_sweep_l128_batched(BatchSw
         const uint32_t ctr3 = (TAG_SWEEP << 28) | d.instance;
         uint4* spins = reinterpret_cast<uint4*>(d.spins[cur]);
         const uint32_t first = g - a.slot_base[lo];
+        RowJ2 j[4] = {};
+        if constexpr (PMJ) l128_couplings(d, lane, j);
+        const uint32_t parity = st->negbonds & 1u;
         for (uint32_t slot = first; slot < first + a.chunk && slot < R; ++slot) {
             int M = 0;
-            const uint32_t U = l128_replica(K, spins, slot, d.theta, g0, ctr3, t4, t8, full, lane, M);
+            const uint32_t U =
+                l128_replica<PMJ>(K, spins, slot, d.theta, g0, ctr3, t4, t8, full, lane, M, j);
             if (lane == 0) {
                 d.ebin[cur][slot] = U >> 1;
                 d.mag[cur][slot] = M;
-                if (U & 1u) atomicOr(&st->status, ST_INVARIANT);
+                if ((U & 1u) != parity) atomicOr(&st->status, ST_INVARIANT);
             }
             tally.add(d.hist, U, M, lane);
         }
@@ -739,16 +820,14 @@ __global__ void __launch_bounds__(WARPS128 * 32, 1) k_sweep_l128_batched(BatchSw
 }
 
 bool is_l128(const RunDev& d) {
-    return d.layout == PA_LAYOUT_PACKED && d.dim == 2 && d.L == 128 && d.model == PA_MODEL_FERRO &&
-           d.stride == 2048;
+    return d.layout == PA_LAYOUT_PACKED && d.dim == 2 && d.L == 128 && d.stride == 2048;
 }
 
 }  // namespace
 
 // The register-resident row kernels: 2D ferromagnet, packed, L = 64 or 128.
 bool l64_applies(const RunDev& d) {
-    return (d.layout == PA_LAYOUT_PACKED && d.dim == 2 && d.L == 64 && d.model == PA_MODEL_FERRO &&
-            d.stride == 512) ||
+    return (d.layout == PA_LAYOUT_PACKED && d.dim == 2 && d.L == 64 && d.stride == 512) ||
            is_l128(d);
 }
 
@@ -763,36 +842,53 @@ static int wave(const void* fn, int threads) {
     return per_sm < 1 ? 0 : sms * per_sm;
 }
 
+template <typename K64, typename K128>
+static const void* pick(const RunDev& d, K64 f64f, K64 f64j, K128 f128f, K128 f128j) {
+    const bool pmj = d.model == PA_MODEL_PMJ;
+    if (is_l128(d)) return pmj ? (const void*)f128j : (const void*)f128f;
+    return pmj ? (const void*)f64j : (const void*)f64f;
+}
+
 int l64_grid(const RunDev& d) {
     const int w = l64_block_warps(d);
-    const int full = is_l128(d) ? wave((const void*)k_sweep_l128, w * 32)
-                                : wave((const void*)k_sweep_l64, w * 32);
+    const int full = wave(pick(d, k_sweep_l64<false>, k_sweep_l64<true>, k_sweep_l128<false>,
+                               k_sweep_l128<true>),
+                          w * 32);
     if (full <= 0) return 0;
     const int64_t need = ((int64_t)d.cap + w - 1) / w;
     return (int)(need < full ? need : full);
 }
 
 cudaError_t launch_sweep_l64(const RunDev& d, int nsweeps, int grid, cudaStream_t s) {
-    if (is_l128(d))
-        k_sweep_l128<<<grid, WARPS128 * 32, 0, s>>>(d, nsweeps);
-    else
-        k_sweep_l64<<<grid, WARPS64 * 32, 0, s>>>(d, nsweeps);
+    const bool pmj = d.model == PA_MODEL_PMJ;
+    if (is_l128(d)) {
+        if (pmj) k_sweep_l128<true><<<grid, WARPS128 * 32, 0, s>>>(d, nsweeps);
+        else k_sweep_l128<false><<<grid, WARPS128 * 32, 0, s>>>(d, nsweeps);
+    } else {
+        if (pmj) k_sweep_l64<true><<<grid, WARPS64 * 32, 0, s>>>(d, nsweeps);
+        else k_sweep_l64<false><<<grid, WARPS64 * 32, 0, s>>>(d, nsweeps);
+    }
     return cudaGetLastError();
 }
 
 bool l64_batched_applies(const RunDev& proto) { return l64_applies(proto); }
 
 int l64_batched_grid(const RunDev& proto) {
-    return is_l128(proto) ? wave((const void*)k_sweep_l128_batched, WARPS128 * 32)
-                          : wave((const void*)k_sweep_l64_batched, WARPS64 * 32);
+    return wave(pick(proto, k_sweep_l64_batched<false>, k_sweep_l64_batched<true>,
+                     k_sweep_l128_batched<false>, k_sweep_l128_batched<true>),
+                l64_block_warps(proto) * 32);
 }
 
 cudaError_t launch_sweep_l64_batched(const BatchSweepArgs& a, const RunDev& proto, int grid,
                                      cudaStream_t s) {
-    if (is_l128(proto))
-        k_sweep_l128_batched<<<grid, WARPS128 * 32, 0, s>>>(a);
-    else
-        k_sweep_l64_batched<<<grid, WARPS64 * 32, 0, s>>>(a);
+    const bool pmj = proto.model == PA_MODEL_PMJ;
+    if (is_l128(proto)) {
+        if (pmj) k_sweep_l128_batched<true><<<grid, WARPS128 * 32, 0, s>>>(a);
+        else k_sweep_l128_batched<false><<<grid, WARPS128 * 32, 0, s>>>(a);
+    } else {
+        if (pmj) k_sweep_l64_batched<true><<<grid, WARPS64 * 32, 0, s>>>(a);
+        else k_sweep_l64_batched<false><<<grid, WARPS64 * 32, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 

@@ -33,6 +33,7 @@ MIX = [
     dict(dim=2, L=64, model=0, layout=1, R0=300, seed=16, instance_id=6),
     dict(dim=3, L=4, model=1, layout=0, R0=5001, seed=17, coupling_seed=107, instance_id=7),
     dict(dim=2, L=128, model=0, layout=1, R0=40, seed=18, instance_id=8),
+    dict(dim=2, L=64, model=1, layout=1, R0=200, seed=19, coupling_seed=109, instance_id=9),
 ]
 COMMON = dict(K=12, theta=3, beta_max=2.0)
 
@@ -56,7 +57,7 @@ def test_batched_steps_equal_plain_steps(P):
     batched = _runs(P, MIX)
     batch = P.Batch(batched)
     cls = batch.classes()
-    assert len(cls) == 7 and sum(c["runs"] for c in cls) == len(MIX)
+    assert len(cls) == 8 and sum(c["runs"] for c in cls) == len(MIX)
     for step in range(1, 7):
         for r in plain:
             r.step()

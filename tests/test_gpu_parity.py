@@ -66,6 +66,13 @@ def test_ea_2d_pm_j(P):
                  beta_max=2.0, seed=9, coupling_seed=10)
 
 
+@pytest.mark.parametrize("L,R0", [(64, 400), (128, 70)])
+def test_ea_2d_pm_j_register_kernels(P, L, R0):
+    """2D +-J at L = 64 and 128 through the register-resident kernels."""
+    run_lockstep(P, steps=6, dim=2, L=L, model=1, layout=1, R0=R0, K=12, theta=3,
+                 beta_max=2.0, seed=90 + L, coupling_seed=91 + L, instance_id=L)
+
+
 def test_ferromagnet_3d(P):
     run_lockstep(P, steps=5, dim=3, L=8, model=0, layout=1, R0=700, K=10, theta=3,
                  beta_max=0.6, seed=12)
