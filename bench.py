@@ -48,10 +48,10 @@ OPS_PER_ATTEMPT = 19.5
 # the FMA-heavy pipe (integer multiply-add), 152 SMs, 2070 MHz maximum clock.
 ALU_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12
 # DRAM bytes of one sweep launch, from the ncu capture of the same kernel at
-# 2^18 replicas (profiles/k_sweep_l64_ising2d_L64_R2p18.md: 134.27 MB read +
-# 75.69 MB written), scaled by the replica count to 2^21.  None whenever the
+# 2^18 replicas (profiles/k_sweep_l64_ising2d_L64_R2p18.md: 134.22 MB read +
+# 75.77 MB written), scaled by the replica count to 2^21.  None whenever the
 # kernel changes, until the next capture.
-SWEEP_TRAFFIC_BYTES_2P21 = (134.27e6 + 75.69e6) * 8
+SWEEP_TRAFFIC_BYTES_2P21 = (134.22e6 + 75.77e6) * 8
 
 
 def rank_workload(rank: int, R0: int) -> dict:
