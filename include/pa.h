@@ -88,7 +88,8 @@ extern "C" {
  *     C_i are exact); draw j uses the 64-bit uniform v of Philox block
  *     (j >> 1, step, 0, MULTINOMIAL|id) (words 2(j & 1) low, 2(j & 1) + 1 high),
  *     the point x = floor(v C_{R-1} / 2^64) and the first replica with C_i > x.
- *     The population stays exactly R0.  Not available in batches. */
+ *     The population stays exactly R0.  In a batch, the draws of each such
+ *     run are launched per run between the batched reweight and resample. */
 #define PA_RESAMPLE_MULTINOMIAL 2
 typedef struct {
     int32_t  dim;           /* 2 or 3                                  */

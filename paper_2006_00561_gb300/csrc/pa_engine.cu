@@ -1030,6 +1030,7 @@ struct pa_batch {
         cudaEvent_t done;
     };
     std::vector<Cls> cls;
+    std::vector<pa::RunDev> mn_runs;  // runs on multinomial draws (their draws launch per run)
     cudaEvent_t fork;
     cudaStream_t cap_stream;
     cudaGraphExec_t graph;
@@ -1066,6 +1067,7 @@ uint32_t auto_chunk(uint32_t total_slots, int grid, int warps) {
 // observables of every run on s.
 int enqueue_batch_step(pa_batch* b, cudaStream_t s) {
     CK(pa::launch_tau_batched(b->bd, s));
+    for (const auto& d : b->mn_runs) CK(pa::launch_multinomial(d, s));
     CK(pa::launch_resample_batched(b->bd, s));
     if (b->cls.size() == 1) {
         const auto& c = b->cls[0];
@@ -1124,10 +1126,6 @@ int pa_batch_init(pa_run* const* runs, int32_t nruns, void* ws, size_t bytes, vo
         if (!r) {
             batch_release(b);
             return PA_ERR_INVALID_ARG;
-        }
-        if (r->cfg.resample == PA_RESAMPLE_MULTINOMIAL) {  // stepped alone only
-            batch_release(b);
-            return PA_ERR_UNSUPPORTED;
         }
         for (int32_t j = 0; j < i; ++j)
             if (runs[j] == r) {
@@ -1207,8 +1205,14 @@ int pa_batch_init(pa_run* const* runs, int32_t nruns, void* ws, size_t bytes, vo
     b->bd.tile_base = d_tile_base;
     b->bd.total_tiles = tile_base.back();
     b->bd.any_poisson = 0;
-    for (const auto& h : h_runs)
+    b->bd.any_multinomial = 0;
+    for (const auto& h : h_runs) {
         if (h.resample == PA_RESAMPLE_POISSON) b->bd.any_poisson = 1;
+        if (h.resample == PA_RESAMPLE_MULTINOMIAL) {
+            b->bd.any_multinomial = 1;
+            b->mn_runs.push_back(h);
+        }
+    }
     b->bd.counters = d_counters;
     b->bd.ncounters = (uint32_t)(1 + b->cls.size());
     cudaStream_t s = b->stream;

@@ -102,6 +102,7 @@ struct BatchDev {
     const uint32_t* tile_base;   // [nruns + 1] prefix sums of each run's resample tiles
     uint32_t total_tiles;
     uint32_t any_poisson;        // some run resamples by the Poisson rule
+    uint32_t any_multinomial;    // some run resamples by multinomial draws
     uint32_t* counters;          // [0]: resample tiles, [1 + c]: sweep chunks of class c
     uint32_t ncounters;
 };

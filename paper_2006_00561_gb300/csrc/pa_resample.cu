@@ -204,7 +204,8 @@ __device__ __noinline__ uint32_t poisson_count(const RunDev& d, uint32_t i, uint
 
 // RULE 0 compiles the nearest-integer rule alone (the register budget of the
 // HBM-bound default path); 1 adds the per-run Poisson branch; 2 takes the
-// counts that the multinomial draw has left in d.counts.
+// counts that the multinomial draw has left in d.counts; 3 chooses among the
+// three per run (batches that mix the rules).
 template <int RULE>
 __device__ __forceinline__ void resample_tile(const RunDev& d, uint32_t tile, ResampleSmem& sm) {
     DevState* st = d.st;
@@ -224,7 +225,7 @@ __device__ __forceinline__ void resample_tile(const RunDev& d, uint32_t tile, Re
     const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
     uint32_t r[RS_ITEMS];
     uint32_t sum = 0;
-    if (RULE == 2) {
+    if (RULE == 2 || (RULE == 3 && d.resample == PA_RESAMPLE_MULTINOMIAL)) {
 #pragma unroll
         for (int j = 0; j < RS_ITEMS; ++j) {
             const uint32_t i = base + (uint32_t)t * RS_ITEMS + j;
@@ -232,7 +233,7 @@ __device__ __forceinline__ void resample_tile(const RunDev& d, uint32_t tile, Re
             r[j] = v;
             sum += v;
         }
-    } else if (RULE == 1 && d.resample == PA_RESAMPLE_POISSON) {
+    } else if ((RULE == 1 || RULE == 3) && d.resample == PA_RESAMPLE_POISSON) {
 #pragma unroll
         for (int j = 0; j < RS_ITEMS; ++j) {
             const uint32_t i = base + (uint32_t)t * RS_ITEMS + j;
@@ -518,7 +519,7 @@ cudaError_t launch_tau(const RunDev& d, cudaStream_t s) {
 // One wave of resident CTAs (capped by the number of tiles), looked up once
 // per device and kernel.
 static int resample_wave(const void* fn, int which, uint32_t tiles) {
-    static int cache[64][6];
+    static int cache[64][7];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
     int wave = cache[dev][which];
@@ -722,7 +723,11 @@ cudaError_t launch_tau_batched(const BatchDev& b, cudaStream_t s) {
 }
 
 cudaError_t launch_resample_batched(const BatchDev& b, cudaStream_t s) {
-    if (b.any_poisson) {
+    if (b.any_multinomial) {
+        const int grid = resample_wave((const void*)k_resample_batched<3>, 6, b.total_tiles);
+        if (grid <= 0) return cudaErrorInvalidValue;
+        k_resample_batched<3><<<grid, RS_THREADS, 0, s>>>(b);
+    } else if (b.any_poisson) {
         const int grid = resample_wave((const void*)k_resample_batched<1>, 3, b.total_tiles);
         if (grid <= 0) return cudaErrorInvalidValue;
         k_resample_batched<1><<<grid, RS_THREADS, 0, s>>>(b);

@@ -106,10 +106,11 @@ def test_batched_run_matches_oracle(P):
     batch.close()
 
 
-def test_batch_mixing_resampling_rules(P):
-    """Runs on the Poisson rule and on the nearest-integer rule in one batch:
-    each run equals its plain twin, and a Poisson run equals the oracle."""
-    specs = [dict(MIX[i], resample=i % 2) for i in (1, 4, 5, 6)]
+@pytest.mark.parametrize("rules", [(0, 1, 0, 1), (2, 1, 0, 2)], ids=["poisson", "all_three"])
+def test_batch_mixing_resampling_rules(P, rules):
+    """Runs on the nearest-integer, Poisson and multinomial rules in one batch:
+    each run equals its plain twin, and the second run equals the oracle."""
+    specs = [dict(MIX[i], resample=rule) for i, rule in zip((1, 4, 5, 6), rules)]
     plain = _runs(P, specs)
     batched = _runs(P, specs)
     spec = dict(COMMON, **specs[1])

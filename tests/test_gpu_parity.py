@@ -183,14 +183,9 @@ def test_multinomial_resampling(P, spec):
     run_lockstep(P, steps=8 if spec["K"] >= 8 else spec["K"], resample=2, **spec)
 
 
-def test_multinomial_graph_replay_and_batch_refusal(P):
+def test_multinomial_graph_replay(P):
     run_lockstep(P, steps=6, use_graph=True, resample=2, dim=2, L=64, layout=1, R0=3000, K=20,
                  theta=2, beta_max=1.0, seed=129)
-    run = P.Run(P.make_config(dim=2, L=16, R0=100, K=4, resample=2))
-    with pytest.raises(P.PaError) as e:
-        P.Batch([run])
-    assert e.value.code == -3  # PA_ERR_UNSUPPORTED: multinomial runs step alone
-    run.close()
 
 
 def test_poisson_resampling_graph_replay(P):
