@@ -775,15 +775,26 @@ __device__ __forceinline__ uint32_t rs_total(const uint32_t (&C)[K], int lane) {
     return tot;
 }
 
+// Philox round keys: pointers into the kernel parameters (plain kernel, so
+// that the xors take them as constant-bank operands) or into the warp's
+// shared-memory copy of the chunk's run (batched kernel).  PA_RS_KEYREG = 1
+// copies them into registers instead; on GB300 that ran 1.4 % slower on the
+// 3D ensemble (the extra registers cost more than the loads).
 struct RSKeys {
     const uint32_t* rk0;
     const uint32_t* rk1;
 };
+struct RSKeyRegs {
+    uint32_t rk0[10], rk1[10];
+};
+#ifndef PA_RS_KEYREG
+#define PA_RS_KEYREG 0
+#endif
 
 // One half-sweep group: sites of pairs 4k .. 4k + 3, colour c, 32 replicas.
-template <int DIM, int L, bool PMJ>
+template <int DIM, int L, bool PMJ, typename KT>
 __device__ __forceinline__ void rs_group(uint32_t* S, const uint8_t* JS, int k, int c, uint32_t g,
-                                         uint32_t b0, uint32_t ctr3, const RSKeys& K,
+                                         uint32_t b0, uint32_t ctr3, const KT& K,
                                          const SweepCtx& x) {
     using G = RSGeo<DIM, L, PMJ>;
     constexpr int NC = G::NCLS;
@@ -890,10 +901,10 @@ __device__ __forceinline__ void rs_group(uint32_t* S, const uint8_t* JS, int k, 
 
 // One chunk of 32 replicas (slots b0 .. b0 + 31, those below R valid): load
 // and transpose, theta sweeps, measurement, transpose back and store.
-template <int DIM, int L, bool PMJ>
+template <int DIM, int L, bool PMJ, typename KT>
 __device__ __forceinline__ void rs_chunk(const RunDev& d, const SweepCtx& x, uint32_t b0,
                                          int nsweeps, uint32_t* S, const uint8_t* JS,
-                                         const RSKeys& K, int lane, long long& sAbsM,
+                                         const KT& K, int lane, long long& sAbsM,
                                          long long& sM2) {
     using G = RSGeo<DIM, L, PMJ>;
     constexpr int N = G::N;
@@ -924,7 +935,7 @@ __device__ __forceinline__ void rs_chunk(const RunDev& d, const SweepCtx& x, uin
 #pragma unroll 1
         for (int c = 0; c < 2; ++c) {
             for (int k = lane; k < G::NGROUPS; k += 32)
-                rs_group<DIM, L, PMJ>(S, JS, k, c, g, b0, ctr3, K, x);
+                rs_group<DIM, L, PMJ, KT>(S, JS, k, c, g, b0, ctr3, K, x);
             __syncwarp();
         }
     }
@@ -1000,7 +1011,7 @@ __device__ __forceinline__ void rs_couplings(const RunDev& d, uint8_t* JS, int l
 }
 
 template <int DIM, int L, bool PMJ, int RSW>
-__global__ void __launch_bounds__(RSW * 32) k_sweep_rs(RunDev d, int nsweeps) {
+__global__ void __launch_bounds__(RSW * 32) k_sweep_rs(__grid_constant__ const RunDev d, int nsweeps) {
     extern __shared__ uint32_t smem[];
     using G = RSGeo<DIM, L, PMJ>;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -1011,7 +1022,7 @@ __global__ void __launch_bounds__(RSW * 32) k_sweep_rs(RunDev d, int nsweeps) {
     const RSKeys K{d.rk0, d.rk1};
     long long sAbsM = 0, sM2 = 0;
     for (uint32_t ch = blockIdx.x * RSW + wib; ch * 32u < x.R; ch += gridDim.x * RSW)
-        rs_chunk<DIM, L, PMJ>(d, x, ch * 32u, nsweeps, S, JS, K, lane, sAbsM, sM2);
+        rs_chunk<DIM, L, PMJ, RSKeys>(d, x, ch * 32u, nsweeps, S, JS, K, lane, sAbsM, sM2);
     if (lane == 0 && (sAbsM | sM2)) {
         atomicAdd(&d.accum[0], (unsigned long long)sAbsM);
         atomicAdd(&d.accum[1], (unsigned long long)sM2);
@@ -1063,8 +1074,18 @@ __global__ void __launch_bounds__(BW * 32) k_sweep_rs_batched(BatchSweepArgs a) 
         const SweepCtx x = sweep_ctx(d);
         const uint32_t b0 = g - a.slot_base[lo];
         if (b0 < x.R) {
-            const RSKeys K{keys, keys + 10};
-            rs_chunk<DIM, L, PMJ>(d, x, b0, d.theta, S, JS, K, lane, sAbsM, sM2);
+            if constexpr (PA_RS_KEYREG) {
+                RSKeyRegs K;
+#pragma unroll
+                for (int r = 0; r < 10; ++r) {
+                    K.rk0[r] = keys[r];
+                    K.rk1[r] = keys[10 + r];
+                }
+                rs_chunk<DIM, L, PMJ, RSKeyRegs>(d, x, b0, d.theta, S, JS, K, lane, sAbsM, sM2);
+            } else {
+                const RSKeys K{keys, keys + 10};
+                rs_chunk<DIM, L, PMJ, RSKeys>(d, x, b0, d.theta, S, JS, K, lane, sAbsM, sM2);
+            }
         }
     }
     if (dp && lane == 0 && (sAbsM | sM2)) {
