@@ -205,8 +205,8 @@ def _config1_oracle(seed):
 
 
 def config1_measure(P, procs: int) -> dict:
-    """Config 1 in full: the whole run on the GPU (int8 layout, plain steps,
-    device time) and on the oracle, one process and one per host core
+    """Config 1 in full: the whole run on the GPU (int8 layout, graph-replayed
+    steps, device time) and on the oracle, one process and one per host core
     (different seeds; the seed-1 process is the GPU run's twin)."""
     import multiprocessing as mp
 
@@ -216,8 +216,7 @@ def config1_measure(P, procs: int) -> dict:
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
-    for _ in range(CONFIG1["K"]):
-        run.step()
+    run.run_steps(CONFIG1["K"])  # one CUDA graph per step
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
