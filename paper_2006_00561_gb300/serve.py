@@ -56,13 +56,15 @@ class Server:
 
     def __init__(self, hbm_budget: int, quantum: int = 8, layout: int = P.LAYOUT_PACKED,
                  keep_history: bool = True, keep_spins: bool = False, stream=None):
-        import torch
+        if stream is None:
+            import torch
+            stream = torch.cuda.Stream()
         self.budget = int(hbm_budget)
         self.quantum = int(quantum)
         self.layout = layout
         self.keep_history = keep_history
         self.keep_spins = keep_spins
-        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.stream = stream
         self.queue: list[Request] = []
         self.resident: list[Request] = []
         self.done: list[Request] = []
@@ -79,7 +81,7 @@ class Server:
     # -- requests --------------------------------------------------------------
     def _cfg(self, spec: dict) -> P.Config:
         keys = ("dim", "L", "model", "K", "theta", "instance_id", "R0", "beta0", "beta_max",
-                "seed", "coupling_seed", "init")
+                "seed", "coupling_seed", "init", "resample")
         return P.make_config(layout=self.layout, **{k: spec[k] for k in keys if k in spec})
 
     def footprint(self, spec: dict) -> int:
