@@ -11,8 +11,10 @@ The timed steps are steps W+1 .. W+K of that schedule.
 value     = spin-flip attempts per ns over the whole step (device time, CUDA
             events on the run's stream, graph-replayed steps).
 e2e       = the same metric through the C ABI with host buffers: every step
-            uploads the population from pinned host memory (pa_load), steps,
-            and downloads it again (pa_dump_range) with the observables.
+            uploads the population from pinned host memory (pa_load), steps
+            with the new population copied back to that memory range by range
+            while the later ranges sweep (pa_step_stream), and reads the
+            observables.
 roofline  = the sweep kernel (dominant), integer-ALU bound.
 cpu_baseline = the CPU oracle (single thread) on a bounded slice.
 next_items = Poisson resampling, adaptive temperature steps and checkpoints
@@ -48,10 +50,13 @@ OPS_PER_ATTEMPT = 19.5
 # the FMA-heavy pipe (integer multiply-add), 152 SMs, 2070 MHz maximum clock.
 ALU_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12
 # DRAM bytes of one sweep launch, from the ncu capture of the same kernel at
-# 2^18 replicas (profiles/k_sweep_l64_ising2d_L64_R2p18.md: 134.22 MB read +
-# 75.77 MB written), scaled by the replica count to 2^21.  None whenever the
+# 2^18 replicas (profiles/k_sweep_l64_ising2d_L64_R2p18.md: 134.59 MB read +
+# 75.96 MB written), scaled by the replica count to 2^21.  None whenever the
 # kernel changes, until the next capture.
-SWEEP_TRAFFIC_BYTES_2P21 = (134.22e6 + 75.77e6) * 8
+SWEEP_TRAFFIC_BYTES_2P21 = (134.59e6 + 75.96e6) * 8
+# Slot ranges of the e2e step: each range's copy to the host (~0.7 ms at 1/8 of
+# 1 GiB) runs while the next range sweeps (~7 ms).
+E2E_CHUNKS = 8
 
 
 def rank_workload(rank: int, R0: int) -> dict:
@@ -604,6 +609,7 @@ def main():
         hv = host.numpy()
         got = run.dump_range(P.DUMP_SPINS_RAW, 0, R_now)
         hv[: got.size] = got.reshape(-1)
+        copy_stream = torch.cuda.Stream()
         barrier()
         t0 = time.perf_counter()
         h2d = d2h = 0
@@ -611,22 +617,21 @@ def main():
         for _ in range(args.steps):
             P.pa_load_ptr(run.h, P.DUMP_SPINS_RAW, host.data_ptr(), R_now, R_now * stride)
             h2d += R_now * stride
-            run.step()
-            o = run.observables()
+            # the step, with the new population copied back range by range
+            # while the later ranges sweep
+            run.step_stream(host, E2E_CHUNKS, copy_stream)
+            o = run.observables()  # returns once the copies are done
             R_now = o["R"]
             e2e_attempts += R_now * N * theta
-            buf = P.lib()
-            rc = buf.pa_dump_range(P.C.c_void_p(run.h), P.DUMP_SPINS_RAW, 0, R_now,
-                                   P.C.c_void_p(host.data_ptr()), host.numel())
-            assert rc == 0
             d2h += R_now * stride + 104
         barrier()
         dt = time.perf_counter() - t0
         dt, e2e_attempts = aggregate(dist, dt, e2e_attempts, "cuda")
         e2e = {"value": e2e_attempts / (dt * 1e9), "unit": UNIT,
                "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps,
-               "path": "pa_load(pinned host population) + pa_step + pa_observables + "
-                       "pa_dump_range(pinned host) every step"}
+               "path": "pa_load(pinned host population) + pa_step_stream(population back "
+                       f"to pinned host in {E2E_CHUNKS} ranges, copies overlapping the sweeps) + "
+                       "pa_observables every step"}
 
     run.close()
     del run

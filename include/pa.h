@@ -155,6 +155,28 @@ int pa_sweep(pa_run* run, int32_t nsweeps);
 /* pa_resample followed by pa_sweep(theta). */
 int pa_step(pa_run* run);
 
+/* pa_step with the new population streamed to host memory while it is swept
+ * (Sec. 2's step; the copy out is for callers that keep the population on the
+ * host).  The reweight and resample of step i run on the run's stream, and the
+ * call waits for them to learn R_i and the buffer of the new population.  The
+ * theta sweeps then run over `chunks` ranges of consecutive slots (bounds are
+ * multiples of 32; the last range ends at R_i), and after each range its
+ * replicas are copied in the device layout (stride bytes each, as
+ * PA_DUMP_SPINS_RAW gives them) to host_dst + first_slot * stride on
+ * copy_stream, while the next range sweeps.  The measurement follows on the
+ * run's stream, which then waits for the last copy: once pa_observables (or
+ * any synchronising call) returns, host_dst holds replicas 0 .. R_i - 1.
+ * Results are bit-identical to pa_step.
+ *   host_dst     pinned host memory for the copies to overlap the sweeps;
+ *                bytes >= capacity * stride;
+ *   chunks       1 .. 64;
+ *   copy_stream  a cudaStream_t other than the run's;
+ *   R_out        receives R_i (may be NULL).
+ * PA_ERR_INVALID_ARG for bad arguments (nothing enqueued); the sticky error of
+ * the resample (e.g. PA_ERR_CAPACITY) if it failed, with nothing swept. */
+int pa_step_stream(pa_run* run, void* host_dst, size_t bytes, int32_t chunks, void* copy_stream,
+                   int64_t* R_out);
+
 /* nsteps calls of pa_step, replayed from a CUDA graph of one step that is
  * captured on first use (on a private stream, then launched on the run's
  * stream).  Same results as nsteps pa_step calls. */

@@ -45,6 +45,8 @@ struct pa_run {
     int64_t prof_n[4];
     double prof_ms[4];
     uint32_t load_R;  // source of the population size written by pa_load
+    // pa_step_stream: a range's sweeps are done / the last copy is done
+    cudaEvent_t ev_range, ev_copied;
 };
 
 namespace {
@@ -390,6 +392,7 @@ int pa_init(const pa_config* cfg, void* ws, size_t bytes, void* stream, pa_run**
     r->ndist = (uint32_t)l.ndist;
     r->cap_stream = nullptr;
     r->graph = nullptr;
+    r->ev_range = r->ev_copied = nullptr;
     r->prof = false;
     for (int k = 0; k < 4; ++k) {
         r->prof_n[k] = 0;
@@ -432,6 +435,8 @@ int pa_init(const pa_config* cfg, void* ws, size_t bytes, void* stream, pa_run**
     d.seed = cfg->seed;
     d.coupling_seed = cfg->coupling_seed;
     d.one = 1u;
+    d.slot_lo = 0u;
+    d.slot_hi = 0xffffffffu;
     d.theta = cfg->theta;
     d.init = cfg->init;
     d.resample = cfg->resample;
@@ -514,6 +519,51 @@ int pa_sweep(pa_run* r, int32_t nsweeps) {
 int pa_step(pa_run* r) {
     if (!r) return PA_ERR_INVALID_ARG;
     return enqueue_step(r, r->stream);
+}
+
+int pa_step_stream(pa_run* r, void* host_dst, size_t bytes, int32_t chunks, void* copy_stream,
+                   int64_t* R_out) {
+    if (!r || !host_dst || !copy_stream || chunks < 1 || chunks > 64) return PA_ERR_INVALID_ARG;
+    const cudaStream_t copy = (cudaStream_t)copy_stream;
+    const RunDev& d = r->d;
+    if (copy == r->stream || bytes < (size_t)d.cap * d.stride) return PA_ERR_INVALID_ARG;
+    if (!r->ev_range) CK(cudaEventCreateWithFlags(&r->ev_range, cudaEventDisableTiming));
+    if (!r->ev_copied) CK(cudaEventCreateWithFlags(&r->ev_copied, cudaEventDisableTiming));
+    int rc = enqueue_resample(r, r->stream);
+    if (rc) return rc;
+    // the host needs R_i and the buffer that holds the new population
+    DevState st;
+    rc = read_state(r, &st);
+    if (rc) return rc;
+    if (st.status) return sticky_to_code(st.status);
+    if (st.R > d.cap) return PA_ERR_CAPACITY;
+    if (R_out) *R_out = st.R;
+    CK(cudaMemsetAsync(d.accum, 0, r->hist_bytes, r->stream));
+    const uint8_t* src = d.spins[st.cur];
+    uint8_t* out = (uint8_t*)host_dst;
+    for (int32_t c = 0; c < chunks; ++c) {
+        // range bounds are multiples of 32 (32-replica warps of the
+        // replica-sliced kernel); the last range ends at R
+        const uint32_t lo = (uint32_t)((uint64_t)st.R * c / chunks) & ~31u;
+        const uint32_t hi =
+            c + 1 == chunks ? st.R : (uint32_t)((uint64_t)st.R * (c + 1) / chunks) & ~31u;
+        if (hi <= lo) continue;
+        RunDev dd = d;
+        dd.slot_lo = lo;
+        dd.slot_hi = hi;
+        rc = timed(r, r->stream, 2,
+                   [&] { return pa::launch_sweep(dd, r->cfg.theta, r->sweep_grid, r->stream); });
+        if (rc) return rc;
+        CK(cudaEventRecord(r->ev_range, r->stream));
+        CK(cudaStreamWaitEvent(copy, r->ev_range, 0));
+        CK(cudaMemcpyAsync(out + (size_t)lo * d.stride, src + (size_t)lo * d.stride,
+                           (size_t)(hi - lo) * d.stride, cudaMemcpyDeviceToHost, copy));
+    }
+    rc = timed(r, r->stream, 3, [&] { return pa::launch_obs(d, r->cfg.theta, r->stream); });
+    if (rc) return rc;
+    CK(cudaEventRecord(r->ev_copied, copy));
+    CK(cudaStreamWaitEvent(r->stream, r->ev_copied, 0));
+    return PA_OK;
 }
 
 int pa_run_steps(pa_run* r, int32_t nsteps) {
@@ -989,6 +1039,8 @@ void pa_free(pa_run* r) {
         r->ev_pool.push_back(p.b);
     }
     for (cudaEvent_t e : r->ev_pool) cudaEventDestroy(e);
+    if (r->ev_range) cudaEventDestroy(r->ev_range);
+    if (r->ev_copied) cudaEventDestroy(r->ev_copied);
     if (r->graph) cudaGraphExecDestroy(r->graph);
     if (r->cap_stream) cudaStreamDestroy(r->cap_stream);
     delete r;

@@ -91,6 +91,10 @@ struct RunDev {
     int32_t resample;           // PA_RESAMPLE_NEAREST | PA_RESAMPLE_POISSON
     uint32_t p1_len;            // entries of p1
     uint32_t p1[P1_MAX];        // Poisson(1) thresholds floor(2^32 P(X <= m))
+    // Slots the plain sweep kernels visit: [slot_lo, min(R, slot_hi)).  0 and
+    // 0xffffffff (the whole population) except in the launches of a
+    // streamed step, whose bounds are multiples of 32.
+    uint32_t slot_lo, slot_hi;
 };
 
 // A batch of runs stepped together (pa_batch_* in include/pa.h).  Arrays in

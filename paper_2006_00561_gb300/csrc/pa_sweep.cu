@@ -610,7 +610,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_sweep(RunDev d, int nsweeps) {
     const SweepCtx x = sweep_ctx(d);
     Tally tally;
     const uint32_t nwarps = gridDim.x * WARPS;
-    for (uint32_t slot = blockIdx.x * WARPS + wib; slot < x.R; slot += nwarps) {
+    const uint32_t end = min(x.R, d.slot_hi);
+    for (uint32_t slot = d.slot_lo + blockIdx.x * WARPS + wib; slot < end; slot += nwarps) {
         int M = 0;
         const uint32_t U = one_replica<DIM, L, LAYOUT, PMJ>(d, x, slot, nsweeps, ws, lane, M);
         record(d, x, slot, U, M, lane);
@@ -1021,7 +1022,9 @@ __global__ void __launch_bounds__(RSW * 32) k_sweep_rs(__grid_constant__ const R
     const SweepCtx x = sweep_ctx(d);
     const RSKeys K{d.rk0, d.rk1};
     long long sAbsM = 0, sM2 = 0;
-    for (uint32_t ch = blockIdx.x * RSW + wib; ch * 32u < x.R; ch += gridDim.x * RSW)
+    const uint32_t end = min(x.R, d.slot_hi);
+    for (uint32_t ch = (d.slot_lo >> 5) + blockIdx.x * RSW + wib; ch * 32u < end;
+         ch += gridDim.x * RSW)
         rs_chunk<DIM, L, PMJ, RSKeys>(d, x, ch * 32u, nsweeps, S, JS, K, lane, sAbsM, sM2);
     if (lane == 0 && (sAbsM | sM2)) {
         atomicAdd(&d.accum[0], (unsigned long long)sAbsM);

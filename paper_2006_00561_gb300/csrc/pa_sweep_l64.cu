@@ -485,7 +485,8 @@ __global__ void __launch_bounds__(WARPS64 * 32, PA_L64_MIN_BLOCKS)
     const uint32_t parity = st->negbonds & 1u;
     L64Tally tally;
     const uint32_t nwarps = gridDim.x * WARPS64;
-    for (uint32_t slot = blockIdx.x * WARPS64 + wib; slot < R; slot += nwarps) {
+    const uint32_t end = min(R, d.slot_hi);
+    for (uint32_t slot = d.slot_lo + blockIdx.x * WARPS64 + wib; slot < end; slot += nwarps) {
         int M = 0;
         const uint32_t U =
             l64_replica<PMJ>(K, spins, slot, nsweeps, g0, ctr3, t4, t8, full, lane, M, ja, jb);
@@ -769,7 +770,8 @@ __global__ void __launch_bounds__(warps128<PMJ>() * 32, 1)
     L64Tally tally;
     constexpr int W = warps128<PMJ>();
     const uint32_t nwarps = gridDim.x * W;
-    for (uint32_t slot = blockIdx.x * W + wib; slot < R; slot += nwarps) {
+    const uint32_t end = min(R, d.slot_hi);
+    for (uint32_t slot = d.slot_lo + blockIdx.x * W + wib; slot < end; slot += nwarps) {
         int M = 0;
         const uint32_t U =
             l128_replica<PMJ>(K, spins, slot, nsweeps, g0, ctr3, t4, t8, full, lane, M, j);

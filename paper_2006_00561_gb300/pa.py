@@ -38,7 +38,7 @@ EXPORTS = [
     "pa_batch_workspace_size", "pa_batch_init", "pa_batch_step", "pa_batch_run_steps",
     "pa_batch_sync", "pa_batch_num_classes", "pa_batch_class_info", "pa_batch_set_shape",
     "pa_batch_free", "pa_checkpoint_size", "pa_checkpoint", "pa_restore",
-    "pa_adaptive_beta", "pa_resample_to", "pa_poisson1_table",
+    "pa_adaptive_beta", "pa_resample_to", "pa_poisson1_table", "pa_step_stream",
 ]
 NOALLOC_MAX_REPLICAS = 8388608
 
@@ -111,6 +111,7 @@ def lib():
             getattr(L, n).argtypes = [vp]
         L.pa_sweep.argtypes = [vp, C.c_int32]
         L.pa_run_steps.argtypes = [vp, C.c_int32]
+        L.pa_step_stream.argtypes = [vp, vp, C.c_size_t, C.c_int32, vp, C.POINTER(C.c_int64)]
         L.pa_observables.argtypes = [vp, C.POINTER(Obs)]
         L.pa_observables_history.argtypes = [vp, C.c_int32, C.c_int32, C.POINTER(Obs)]
         L.pa_dump_size.argtypes = [vp, C.c_int32]
@@ -212,6 +213,14 @@ def pa_step(h: int):
 
 def pa_run_steps(h: int, nsteps: int):
     _check(lib().pa_run_steps(C.c_void_p(h), nsteps), "pa_run_steps")
+
+
+def pa_step_stream(h: int, host_ptr: int, nbytes: int, chunks: int, copy_stream_handle: int) -> int:
+    """pa_step with the population copied to host_ptr range by range; returns R_i."""
+    R = C.c_int64(-1)
+    _check(lib().pa_step_stream(C.c_void_p(h), C.c_void_p(host_ptr), nbytes, chunks,
+                                C.c_void_p(copy_stream_handle), C.byref(R)), "pa_step_stream")
+    return R.value
 
 
 def pa_observables(h: int, check: bool = True) -> dict:
@@ -347,6 +356,12 @@ class Run:
 
     def run_steps(self, n: int):
         pa_run_steps(self.h, n)
+
+    def step_stream(self, host, chunks: int, copy_stream) -> int:
+        """pa_step_stream into a pinned host uint8 tensor of at least
+        capacity * stride bytes, copies on copy_stream; returns R_i."""
+        return pa_step_stream(self.h, host.data_ptr(), host.numel() * host.element_size(), chunks,
+                              copy_stream.cuda_stream)
 
     def observables(self, check: bool = True) -> dict:
         return pa_observables(self.h, check)

@@ -58,10 +58,18 @@ def compare_state(P, grun, orun, step: int, full_spins=True):
     compare_obs(grun.observables(), orun.observables(), where)
 
 
-def run_lockstep(P, steps: int, use_graph=False, every=1, **kw):
+def run_lockstep(P, steps: int, use_graph=False, every=1, stream_chunks=0, **kw):
+    """stream_chunks > 0 steps the engine by pa_step_stream with that many
+    ranges and checks the host copy of every step against pa_dump."""
     ocfg, gcfg = configs(P, **kw)
     orun = O.Run(ocfg)
     grun = P.Run(gcfg)
+    host = copy_stream = None
+    if stream_chunks:
+        import torch
+        st = grun.state()
+        host = torch.zeros(st["capacity"] * st["stride"], dtype=torch.uint8, pin_memory=True)
+        copy_stream = torch.cuda.Stream()
     try:
         assert np.array_equal(grun.dump(P.DUMP_COUPLINGS), orun.couplings())
         compare_state(P, grun, orun, 0)
@@ -69,6 +77,13 @@ def run_lockstep(P, steps: int, use_graph=False, every=1, **kw):
             assert orun.step() == 0
             if use_graph:
                 grun.run_steps(1)
+            elif stream_chunks:
+                R = grun.step_stream(host, stream_chunks, copy_stream)
+                assert R == orun.R
+                grun.observables()  # waits for the copies
+                stride = grun.state()["stride"]
+                raw = grun.dump(P.DUMP_SPINS_RAW).reshape(-1)
+                assert np.array_equal(host.numpy()[: R * stride], raw[: R * stride]), i
             else:
                 grun.step()
             if i % every == 0 or i == steps:

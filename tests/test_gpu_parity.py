@@ -239,6 +239,58 @@ def test_graph_replay_equals_plain_steps(P):
                  beta_max=1.0, seed=17)
 
 
+@pytest.mark.parametrize("spec,chunks", [
+    (dict(dim=2, L=64, layout=1, R0=2300, K=20, theta=2, seed=17), 7),           # L = 64 kernel
+    (dict(dim=2, L=128, layout=1, R0=150, K=8, theta=2, seed=18), 3),            # L = 128 kernel
+    (dict(dim=2, L=16, layout=1, R0=1000, K=12, theta=3, seed=19), 5),           # replica-sliced
+    (dict(dim=3, L=10, model=1, layout=1, R0=300, K=8, theta=2, beta_max=3.0, seed=20,
+          coupling_seed=21), 4),                                                  # row kernel
+    (dict(dim=2, L=16, layout=0, R0=700, K=10, theta=2, seed=22), 64),           # int8, ranges < 32
+    (dict(dim=2, L=8, layout=1, R0=40, K=6, theta=2, seed=23), 1),
+])
+def test_streamed_step_equals_the_oracle(P, spec, chunks):
+    """pa_step_stream: the sweeps of a step in slot ranges with the copy of
+    each range to host memory on a second stream.  Same run as pa_step (and the
+    oracle), and the host copy equals the device population."""
+    run_lockstep(P, steps=min(spec["K"], 6), stream_chunks=chunks, beta_max=spec.pop("beta_max", 1.0),
+                 **spec)
+
+
+def test_streamed_step_rejects_bad_arguments(P):
+    import torch
+    _, gcfg = configs(P, dim=2, L=16, R0=100, K=4)
+    run = P.Run(gcfg)
+    st = run.state()
+    host = torch.zeros(st["capacity"] * st["stride"], dtype=torch.uint8, pin_memory=True)
+    cs = torch.cuda.Stream()
+    for chunks in (0, 65):
+        with pytest.raises(P.PaError) as e:
+            run.step_stream(host, chunks, cs)
+        assert e.value.code == -1
+    with pytest.raises(P.PaError) as e:  # too small for the capacity
+        P.pa_step_stream(run.h, host.data_ptr(), host.numel() - 1, 2, cs.cuda_stream)
+    assert e.value.code == -1
+    with pytest.raises(P.PaError) as e:  # the run's own stream
+        P.pa_step_stream(run.h, host.data_ptr(), host.numel(), 2, run.stream.cuda_stream)
+    assert e.value.code == -1
+    assert run.state()["step"] == 0  # nothing was enqueued
+    run.close()
+
+
+def test_streamed_step_reports_capacity_overflow(P):
+    import torch
+    _, gcfg = configs(P, dim=2, L=8, R0=200, capacity=200, K=50, theta=1, beta_max=3.0, seed=1)
+    run = P.Run(gcfg)
+    st = run.state()
+    host = torch.zeros(st["capacity"] * st["stride"], dtype=torch.uint8, pin_memory=True)
+    cs = torch.cuda.Stream()
+    with pytest.raises(P.PaError) as e:
+        for _ in range(50):
+            run.step_stream(host, 4, cs)
+    assert e.value.code == -4  # PA_ERR_CAPACITY
+    run.close()
+
+
 def test_capacity_overflow_is_reported(P):
     ocfg, gcfg = configs(P, dim=2, L=8, R0=200, capacity=200, K=50, theta=1, beta_max=3.0,
                          seed=1)
