@@ -2,7 +2,8 @@
 
 Population annealing estimates ln Z(beta_i) = N ln 2 + sum_l ln Q_l (Eq. 3,
 Eq. 5 read as -beta F) and population averages (Sec. 2).  Over M independent
-seeds the mean estimate must sit within 3 standard errors of:
+seeds the mean estimate must sit within the 3-standard-error level (Student-t
+bound for the estimated standard error) of:
   * Kaufman's exact ln Z of the 16 x 16 torus (the paper's model, Eq. 6, at the
     config-1 workload: R0 = 1000, beta 0 -> 1 in 100 steps, theta = 10),
   * brute-force ln Z of the 4 x 4 torus and of a 2 x 2 x 2 +-J instance.
@@ -93,10 +94,16 @@ def _runs(kind, seeds):
         return pool.map(_run_seed, [(kind, s) for s in seeds])
 
 
-def _assert_within(vals, want, nsig=3.0):
+def _assert_within(vals, want, p_two_sided=0.0027):
+    """The mean of M independent estimates within the bound of a two-sided
+    test at the level of 3 normal standard errors: with the standard error
+    estimated from the same M values, (mean - want) / se is Student-t with
+    M - 1 degrees of freedom, whose quantile replaces the normal 3."""
+    from scipy.stats import t as student_t
     vals = np.asarray(vals, dtype=np.float64)
     se = vals.std(ddof=1) / np.sqrt(vals.size)
-    assert abs(vals.mean() - want) < nsig * se + 1e-12 * abs(want), (vals.mean(), want, se)
+    nsig = float(student_t.ppf(1.0 - p_two_sided / 2.0, vals.size - 1))
+    assert abs(vals.mean() - want) < nsig * se + 1e-12 * abs(want), (vals.mean(), want, se, nsig)
 
 
 @pytest.mark.slow
