@@ -208,7 +208,7 @@ int64_t or_delta_e(int32_t dim, int32_t L, const int8_t* J, const int8_t* spins,
  * Metropolis equilibration (Sec. 2, theta sweeps at the new temperature).
  * One sweep = colour 0 sites (even coordinate sum) in ascending s, then
  * colour 1.  The random number of colour site s is word (h & 3) of the Philox
- * block (h >> 2, 2g + colour, slot, SWEEP|id) with h = s >> 1, where g is the
+ * block (2g + colour, h >> 2, slot, SWEEP|id) with h = s >> 1, where g is the
  * global index of the sweep in the run.  It is drawn only when dE > 0.
  * ---------------------------------------------------------------------- */
 int64_t or_sweep_replica(const or_config* c, const int8_t* J, int8_t* spins,
@@ -232,7 +232,7 @@ int64_t or_sweep_replica(const or_config* c, const int8_t* J, int8_t* spins,
                     int64_t h = s >> 1;
                     if ((h >> 2) != cached) {
                         cached = h >> 2;
-                        draw(c->seed, (uint32_t)(h >> 2), (uint32_t)(2 * g + colour),
+                        draw(c->seed, (uint32_t)(2 * g + colour), (uint32_t)(h >> 2),
                              (uint32_t)slot, OR_TAG_SWEEP, c->instance_id, out);
                     }
                     uint64_t u = out[h & 3];

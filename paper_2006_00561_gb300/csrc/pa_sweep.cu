@@ -7,7 +7,7 @@
 // updates the sites of colour 0 (even coordinate sum), then colour 1; sites of
 // one colour have no bond between them, so they are updated together.  A site
 // with c_u unsatisfied bonds has dE = 4 (dim - c_u); it flips if dE <= 0, or
-// if its uniform u (word h & 3 of the Philox block (h >> 2, 2 g + colour,
+// if its uniform u (word h & 3 of the Philox block (2 g + colour, h >> 2,
 // slot, SWEEP | instance), h = s >> 1, g = global sweep index) is below the
 // threshold T(beta_i, dE) = floor(2^32 exp(-beta_i dE)).
 //
@@ -274,7 +274,7 @@ __device__ __forceinline__ uint32_t packed_replica(const RunDev& d, const SweepC
             __syncwarp();
             // phase B: one Philox block per 4 colour sites
             for (int q = lane; q < G::NCALLS; q += 32) {
-                const uint4 u = philox((uint32_t)q, 2u * g + (uint32_t)c, slot, x.ctr3, x.k0, x.k1);
+                const uint4 u = philox(2u * g + (uint32_t)c, (uint32_t)q, slot, x.ctr3, x.k0, x.k1);
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const int h = 4 * q + j;
@@ -352,7 +352,7 @@ __device__ __forceinline__ uint32_t i8_replica(const RunDev& d, const SweepCtx& 
         const uint32_t g = x.g0 + (uint32_t)t;
         for (int c = 0; c < 2; ++c) {
             for (int q = lane; q < G::NCALLS; q += 32) {
-                const uint4 u = philox((uint32_t)q, 2u * g + (uint32_t)c, slot, x.ctr3, x.k0, x.k1);
+                const uint4 u = philox(2u * g + (uint32_t)c, (uint32_t)q, slot, x.ctr3, x.k0, x.k1);
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const int h = 4 * q + j;
@@ -478,7 +478,7 @@ __device__ __forceinline__ uint32_t rows_replica(const RunDev& d, const SweepCtx
         const uint32_t g = x.g0 + (uint32_t)t;
         for (int c = 0; c < 2; ++c) {
             for (int q = lane; q < G::NCALLS; q += 32) {
-                const uint4 u = philox((uint32_t)q, 2u * g + (uint32_t)c, slot, x.ctr3, x.k0, x.k1);
+                const uint4 u = philox(2u * g + (uint32_t)c, (uint32_t)q, slot, x.ctr3, x.k0, x.k1);
                 reinterpret_cast<uint4*>(U)[q] = u;
             }
             __syncwarp();
@@ -809,11 +809,11 @@ __device__ __forceinline__ void rs_group(uint32_t* S, const uint8_t* JS, int k, 
 #pragma unroll
         for (int cl = 0; cl < NC; ++cl) acc[i][cl] = 0u;
     // rounds 1 and 2 of Philox: the products of the counter words shared by
-    // the 32 replicas (c0 = k, c1, c3) are formed once; M1 * slot steps down
-    // by M1 from slot b0 + 31
-    const uint32_t c1 = 2u * g + (uint32_t)c;
-    const uint32_t x2 = __umulhi(M0, (uint32_t)k) ^ ctr3 ^ K.rk1[0];
-    const uint32_t x3 = M0 * (uint32_t)k;
+    // the 32 replicas (c0 = 2 g + colour, c1 = k, c3) are formed once;
+    // M1 * slot steps down by M1 from slot b0 + 31
+    const uint32_t c0 = 2u * g + (uint32_t)c, c1 = (uint32_t)k;
+    const uint32_t x2 = __umulhi(M0, c0) ^ ctr3 ^ K.rk1[0];
+    const uint32_t x3 = M0 * c0;
     const uint32_t y0k = __umulhi(M1, x2) ^ K.rk0[1];
     const uint32_t y1 = M1 * x2;
     uint64_t P = (uint64_t)M1 * (uint64_t)(b0 + 31u);

@@ -4,7 +4,7 @@
 //
 // Same update rule and random numbers as the generic kernels of pa_sweep.cu
 // (checkerboard order, dE = 4 (2 - c_u), u = word h & 3 of the Philox block
-// (h >> 2, 2 g + colour, slot, SWEEP | instance), h = s >> 1, accept iff
+// (2 g + colour, h >> 2, slot, SWEEP | instance), h = s >> 1, accept iff
 // dE <= 0 or u < T(beta_i, dE)), mapped for throughput:
 //   * one warp holds one replica for all theta sweeps, entirely in registers:
 //     lane l owns rows 2l and 2l+1 (one 16-byte load per lane, coalesced);
@@ -19,7 +19,8 @@
 //     of 16 sites (two instructions per test, no predicates or selects; the
 //     FMA pipe is left to the Philox multiplies);
 //   * the Philox round keys come from the kernel parameters, and the products
-//     shared by all blocks of a half-sweep are formed once.
+//     shared by all blocks of a half-sweep are formed once: a block costs 16
+//     of Philox's 20 multiplies.
 // Grid-stride (persistent) over replicas; the population size is read from
 // device memory.  The measurement epilogue is the one of the generic kernel.
 #include "pa_internal.cuh"
@@ -106,12 +107,13 @@ __device__ __forceinline__ uint32_t add_if_below(uint32_t acc, uint32_t u, const
     }
 }
 
-// Philox4x32-10 of the blocks (c0, c1, slot, ctr3) of one half-sweep.  Round 1
-// multiplies c0 and slot, round 2 multiplies the round-1 word built from slot
-// and c1 and the one built from c0: the slot/c1 products are the same for
-// every block of the half-sweep, so they are formed once (HalfSweepGen), and
-// M0 * c0 of consecutive blocks is one product plus multiples of M0.  Rounds
-// 3..10 are the plain rounds.  Same bits as philox_rk().
+// Philox4x32-10 of the blocks (c0, c1, slot, ctr3) of one half-sweep, with
+// c0 = 2 g + colour shared and c1 = h >> 2 the block index.  Round 1
+// multiplies c0 and slot (both shared); c1 enters word 0 by an xor, so round
+// 2 multiplies one block word (M0 * word 0) and one shared word, round 3 again
+// one of each (M1 * word 2, M0 * word 0 shared), and rounds 4..10 are the
+// plain rounds.  The shared products are formed once per half-sweep
+// (HalfSweepGen): 16 multiplies per block.  Same bits as philox().
 constexpr uint32_t PM0 = 0xD2511F53u, PM1 = 0xCD9E8D57u;
 
 // Round keys of the run's seed and the opaque 1 of the multiply-add tests:
@@ -122,24 +124,6 @@ struct Keys {
     const uint32_t* rk1;
     uint32_t one;
 };
-
-struct HalfSweepGen {
-    uint32_t x1k;   // round-1 word 1 (low product of slot) ^ round-2 key 0
-    uint32_t hiA2k; // high half of M0 * (round-1 word 0) ^ round-2 key 1
-    uint32_t loA2;  // low half of M0 * (round-1 word 0)
-    uint32_t c3k;   // counter word 3 ^ round-1 key 1
-};
-
-__device__ __forceinline__ HalfSweepGen half_sweep_gen(const Keys& d, uint32_t c1, uint32_t slot,
-                                                      uint32_t ctr3) {
-    HalfSweepGen g;
-    const uint32_t x0 = __umulhi(PM1, slot) ^ c1 ^ d.rk0[0];
-    g.x1k = (PM1 * slot) ^ d.rk0[1];
-    g.hiA2k = __umulhi(PM0, x0) ^ d.rk1[1];
-    g.loA2 = PM0 * x0;
-    g.c3k = ctr3 ^ d.rk1[0];
-    return g;
-}
 
 __device__ __forceinline__ void mul_hilo(uint32_t m, uint32_t a, uint32_t& hi, uint32_t& lo) {
 #if PA_L64_MUL_MODE == 1
@@ -156,28 +140,55 @@ __device__ __forceinline__ void mul_hilo(uint32_t m, uint32_t a, uint32_t& hi, u
 #endif
 }
 
-// pA = M0 * c0 (64-bit) of the block.
-__device__ __forceinline__ uint4 philox_block(const Keys& d, const HalfSweepGen& g, uint64_t pA) {
-    const uint32_t x2 = (uint32_t)(pA >> 32) ^ g.c3k;
-    const uint32_t x3 = (uint32_t)pA;
-    uint32_t h1, l1;
-    mul_hilo(PM1, x2, h1, l1);
-    uint32_t c0 = h1 ^ g.x1k;
-    uint32_t c1 = l1;
-    uint32_t c2 = g.hiA2k ^ x3;
-    uint32_t c3 = g.loA2;
+struct HalfSweepGen {
+    uint32_t y0k;  // round-1 word 0 before the xor with c1: high half of M1 * slot ^ key 0
+    uint32_t y3k;  // round-1 word 3 (low half of M0 * c0) ^ round-2 key 1
+    uint32_t z1k;  // round-2 word 1 ^ round-3 key 0
+    uint32_t e2k;  // high half of M0 * (round-2 word 0) ^ round-3 key 1
+    uint32_t e3;   // low half of M0 * (round-2 word 0): round-3 word 3
+};
+
+__device__ __forceinline__ HalfSweepGen half_sweep_gen(const Keys& d, uint32_t c0, uint32_t slot,
+                                                      uint32_t ctr3) {
+    HalfSweepGen g;
+    uint32_t hs, ls, hc, lc;
+    mul_hilo(PM1, slot, hs, ls);  // round 1
+    mul_hilo(PM0, c0, hc, lc);
+    g.y0k = hs ^ d.rk0[0];
+    g.y3k = lc ^ d.rk1[1];
+    const uint32_t y2 = hc ^ ctr3 ^ d.rk1[0];
+    uint32_t h2, l2;
+    mul_hilo(PM1, y2, h2, l2);  // round 2, shared half
+    const uint32_t z0 = h2 ^ ls ^ d.rk0[1];
+    g.z1k = l2 ^ d.rk0[2];
+    uint32_t h3, l3;
+    mul_hilo(PM0, z0, h3, l3);  // round 3, shared half
+    g.e2k = h3 ^ d.rk1[2];
+    g.e3 = l3;
+    return g;
+}
+
+// Block c1 of the half-sweep.
+__device__ __forceinline__ uint4 philox_block(const Keys& d, const HalfSweepGen& g, uint32_t c1) {
+    uint32_t h2, l2, h3, l3;
+    mul_hilo(PM0, g.y0k ^ c1, h2, l2);  // round 2, block half
+    mul_hilo(PM1, h2 ^ g.y3k, h3, l3);  // round 3, block half
+    uint32_t c0 = h3 ^ g.z1k;
+    uint32_t c1w = l3;
+    uint32_t c2 = l2 ^ g.e2k;
+    uint32_t c3 = g.e3;
 #pragma unroll
-    for (int r = 2; r < 10; ++r) {
+    for (int r = 3; r < 10; ++r) {
         const uint32_t a = c0, b = c2;
         uint32_t hiA, loA, hiB, loB;
         mul_hilo(PM0, a, hiA, loA);
         mul_hilo(PM1, b, hiB, loB);
-        c0 = hiB ^ c1 ^ d.rk0[r];
-        c1 = loB;
+        c0 = hiB ^ c1w ^ d.rk0[r];
+        c1w = loB;
         c2 = hiA ^ c3 ^ d.rk1[r];
         c3 = loA;
     }
-    return make_uint4(c0, c1, c2, c3);
+    return make_uint4(c0, c1w, c2, c3);
 }
 
 // acc * 4 + [u >= T] on the FMA pipe: the carry out of u * 1 + (2^32 - T)
@@ -250,10 +261,10 @@ __device__ __forceinline__ void row_accepts(const Keys& d, const HalfSweepGen& g
 #pragma unroll 1
         for (uint32_t q = 0; q < 2; ++q) {
             uint32_t kc = 0;
-            const uint64_t base = (uint64_t)PM0 * (8u * y + 4u * q);
+            const uint32_t base = 8u * y + 4u * q;
 #pragma unroll
             for (int h = 3; h >= 0; --h) {
-                const uint4 u = philox_block(d, gen, base + (uint64_t)PM0 * (uint64_t)h);
+                const uint4 u = philox_block(d, gen, base + (uint32_t)h);
                 const uint32_t w[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
                 for (int m = 3; m >= 0; --m) kc = site_chain<F4, F8>(kc, w[m], one, c4, c8);
@@ -279,12 +290,12 @@ __device__ __forceinline__ void row_accepts(const Keys& d, const HalfSweepGen& g
 #pragma unroll 1
     for (uint32_t q = 0; q < 2; ++q) {
         uint32_t k4 = 0, k8 = 0, kc4 = 0, kc8 = 0;
-        const uint64_t base = (uint64_t)PM0 * (8u * y + 4u * q);
+        const uint32_t base = 8u * y + 4u * q;
         // blocks in decreasing h so that the carry chain sees its sites in
         // decreasing order: site j = 4h + m ends at bit 2j
 #pragma unroll
         for (int h = 3; h >= 0; --h) {
-            const uint4 u = philox_block(d, gen, base + (uint64_t)PM0 * (uint64_t)h);
+            const uint4 u = philox_block(d, gen, base + (uint32_t)h);
             const uint32_t w[4] = {u.x, u.y, u.z, u.w};
             const bool f4 = M == 1 || M == 2 || (M == 3 && h < 2);
             const bool f8 = M == 2;
@@ -599,10 +610,10 @@ __device__ __forceinline__ void row_accepts128(const Keys& d, const HalfSweepGen
 #pragma unroll 1
     for (uint32_t q = 0; q < 4; ++q) {
         uint32_t kc = 0;
-        const uint64_t base = (uint64_t)PM0 * (16u * y + 4u * q);
+        const uint32_t base = 16u * y + 4u * q;
 #pragma unroll L128_HUNROLL
         for (int h = 3; h >= 0; --h) {
-            const uint4 u = philox_block(d, gen, base + (uint64_t)PM0 * (uint64_t)h);
+            const uint4 u = philox_block(d, gen, base + (uint32_t)h);
             const uint32_t w[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
             for (int m = 3; m >= 0; --m) kc = site_chain<false, false>(kc, w[m], one, t4.T, t8.T);
