@@ -437,8 +437,9 @@ __device__ __forceinline__ uint32_t l64_replica(const Keys& K, uint4* spins, uin
     U = warp_sum(U);
     down = warp_sum(down);
     M = 4096 - 2 * (int)down;
-    spins[(size_t)slot * 32 + lane] =
-        make_uint4((uint32_t)ra, (uint32_t)(ra >> 32), (uint32_t)rb, (uint32_t)(rb >> 32));
+    if (nsweeps > 0)  // a measurement alone leaves the replica as it is
+        spins[(size_t)slot * 32 + lane] =
+            make_uint4((uint32_t)ra, (uint32_t)(ra >> 32), (uint32_t)rb, (uint32_t)(rb >> 32));
     return U;
 }
 
@@ -754,10 +755,11 @@ __device__ __forceinline__ uint32_t l128_replica(const Keys& K, uint4* spins, ui
     U = warp_sum(U);
     down = warp_sum(down);
     M = 16384 - 2 * (int)down;
+    if (nsweeps > 0)  // a measurement alone leaves the replica as it is
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-        p[k] = make_uint4((uint32_t)r[k].lo, (uint32_t)(r[k].lo >> 32), (uint32_t)r[k].hi,
-                          (uint32_t)(r[k].hi >> 32));
+        for (int k = 0; k < 4; ++k)
+            p[k] = make_uint4((uint32_t)r[k].lo, (uint32_t)(r[k].lo >> 32), (uint32_t)r[k].hi,
+                              (uint32_t)(r[k].hi >> 32));
     return U;
 }
 
