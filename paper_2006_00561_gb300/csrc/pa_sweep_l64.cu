@@ -238,6 +238,48 @@ __device__ __forceinline__ uint32_t site_chain(uint32_t acc, uint32_t u, uint32_
 #define PA_L64_CHAIN 3
 #endif
 
+// PA_L64_SEL_BLOCKS (0..3): with the chains of PA_L64_CHAIN, the tests of
+// the last that many blocks of every group of four (h < PA_L64_SEL_BLOCKS)
+// run as compare and select instead, instructions that only the ALU pipe
+// executes; the carry chains are integer adds, which the compiler may move
+// to the FMA pipe.
+#ifndef PA_L64_SEL_BLOCKS
+#define PA_L64_SEL_BLOCKS 0
+#endif
+static_assert(PA_L64_SEL_BLOCKS >= 0 && PA_L64_SEL_BLOCKS < 4, "PA_L64_SEL_BLOCKS: 0 .. 3");
+
+// The tests of one group of four Philox blocks (block(h), h = 3 .. 0): the
+// carries [u >= T4], [u >= T8] of site j = 4h + m end at bits 2j + 1, 2j.
+// Chain blocks come first (the chain shifts its accumulator by two bits per
+// site), then the compare-and-select blocks OR their bits in place.
+template <bool F4, bool F8, int UNROLL, typename Block>
+__device__ __forceinline__ uint32_t group_tests(const Block& block, uint32_t one, uint32_t c4,
+                                                uint32_t c8, uint32_t T4, uint32_t T8) {
+    constexpr int XS = PA_L64_SEL_BLOCKS;
+    uint32_t kc = 0;
+#pragma unroll UNROLL
+    for (int h = 3; h >= XS; --h) {
+        const uint4 u = block(h);
+        const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int m = 3; m >= 0; --m) kc = site_chain<F4, F8>(kc, w[m], one, c4, c8);
+    }
+    if constexpr (XS > 0) {
+        kc <<= 8 * XS;
+#pragma unroll
+        for (int h = XS - 1; h >= 0; --h) {
+            const uint4 u = block(h);
+            const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const int j = 4 * h + m;
+                kc |= (w[m] >= T4 ? 2u << (2 * j) : 0u) | (w[m] >= T8 ? 1u << (2 * j) : 0u);
+            }
+        }
+    }
+    return kc;
+}
+
 // Acceptance masks of the 32 colour-c sites of row y, P = (y + c) & 1: sites
 // x = 8j + 2m + P take word m of Philox block 8y + j; bit x of a4 / a8 is set
 // when that uniform is below T4 / T8.  Four blocks per iteration fill one
@@ -260,15 +302,10 @@ __device__ __forceinline__ void row_accepts(const Keys& d, const HalfSweepGen& g
         const uint32_t c4 = F4 ? negT4 : t4.T, c8 = F8 ? negT8 : t8.T;
 #pragma unroll 1
         for (uint32_t q = 0; q < 2; ++q) {
-            uint32_t kc = 0;
             const uint32_t base = 8u * y + 4u * q;
-#pragma unroll
-            for (int h = 3; h >= 0; --h) {
-                const uint4 u = philox_block(d, gen, base + (uint32_t)h);
-                const uint32_t w[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-                for (int m = 3; m >= 0; --m) kc = site_chain<F4, F8>(kc, w[m], one, c4, c8);
-            }
+            const uint32_t kc = group_tests<F4, F8, 4>(
+                [&](int h) { return philox_block(d, gen, base + (uint32_t)h); }, one, c4, c8, t4.T,
+                t8.T);
             // site j = 4h + m: dE = 4 carry at bit 2j + 1, dE = 8 carry at bit 2j
             constexpr uint32_t EV = 0x55555555u;
             const uint32_t r4 = (kc >> 1) & EV, r8 = kc & EV;
@@ -610,15 +647,10 @@ __device__ __forceinline__ void row_accepts128(const Keys& d, const HalfSweepGen
     uint32_t h4[4], h8[4];
 #pragma unroll 1
     for (uint32_t q = 0; q < 4; ++q) {
-        uint32_t kc = 0;
         const uint32_t base = 16u * y + 4u * q;
-#pragma unroll L128_HUNROLL
-        for (int h = 3; h >= 0; --h) {
-            const uint4 u = philox_block(d, gen, base + (uint32_t)h);
-            const uint32_t w[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-            for (int m = 3; m >= 0; --m) kc = site_chain<false, false>(kc, w[m], one, t4.T, t8.T);
-        }
+        const uint32_t kc = group_tests<false, false, L128_HUNROLL>(
+            [&](int h) { return philox_block(d, gen, base + (uint32_t)h); }, one, t4.T, t8.T, t4.T,
+            t8.T);
         const uint32_t b4 = (~(kc >> 1) & EV) << P, b8 = (~kc & EV) << P;
         if (q == 0) {
             h4[0] = b4;
