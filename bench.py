@@ -50,10 +50,10 @@ OPS_PER_ATTEMPT = 19.5
 # the FMA-heavy pipe (integer multiply-add), 152 SMs, 2070 MHz maximum clock.
 ALU_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12
 # DRAM bytes of one sweep launch, from the ncu capture of the same kernel at
-# 2^18 replicas (profiles/k_sweep_l64_ising2d_L64_R2p18.md: 134.93 MB read +
-# 76.19 MB written), scaled by the replica count to 2^21.  None whenever the
+# 2^18 replicas (profiles/k_sweep_l64_ising2d_L64_R2p18.md: 134.50 MB read +
+# 76.06 MB written), scaled by the replica count to 2^21.  None whenever the
 # kernel changes, until the next capture.
-SWEEP_TRAFFIC_BYTES_2P21 = (134.93e6 + 76.19e6) * 8
+SWEEP_TRAFFIC_BYTES_2P21 = (134.50e6 + 76.06e6) * 8
 # Slot ranges of the e2e step: each range's copy to the host (~0.7 ms at 1/8 of
 # 1 GiB) runs while the next range sweeps (~7 ms).
 E2E_CHUNKS = 8

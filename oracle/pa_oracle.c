@@ -208,8 +208,9 @@ int64_t or_delta_e(int32_t dim, int32_t L, const int8_t* J, const int8_t* spins,
  * Metropolis equilibration (Sec. 2, theta sweeps at the new temperature).
  * One sweep = colour 0 sites (even coordinate sum) in ascending s, then
  * colour 1.  The random number of colour site s is word (h & 3) of the Philox
- * block (2g + colour, h >> 2, slot, SWEEP|id) with h = s >> 1, where g is the
- * global index of the sweep in the run.  It is drawn only when dE > 0.
+ * block with counter (2g + colour, h >> 2, SWEEP|id, slot), h = s >> 1, where
+ * g is the global index of the sweep in the run.  It is drawn only when
+ * dE > 0.
  * ---------------------------------------------------------------------- */
 int64_t or_sweep_replica(const or_config* c, const int8_t* J, int8_t* spins,
                          int64_t slot, int64_t g0, int32_t nsweeps, const uint64_t T[3])
@@ -232,8 +233,12 @@ int64_t or_sweep_replica(const or_config* c, const int8_t* J, int8_t* spins,
                     int64_t h = s >> 1;
                     if ((h >> 2) != cached) {
                         cached = h >> 2;
-                        draw(c->seed, (uint32_t)(2 * g + colour), (uint32_t)(h >> 2),
-                             (uint32_t)slot, OR_TAG_SWEEP, c->instance_id, out);
+                        const uint32_t ctr[4] = {
+                            (uint32_t)(2 * g + colour), (uint32_t)(h >> 2),
+                            (OR_TAG_SWEEP << 28) | (uint32_t)c->instance_id, (uint32_t)slot };
+                        const uint32_t key[2] = { (uint32_t)(c->seed & 0xffffffffu),
+                                                  (uint32_t)(c->seed >> 32) };
+                        or_philox4x32_10(ctr, key, out);
                     }
                     uint64_t u = out[h & 3];
                     accept = u < T[dE / 4 - 1];

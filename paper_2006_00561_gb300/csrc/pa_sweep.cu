@@ -7,8 +7,8 @@
 // updates the sites of colour 0 (even coordinate sum), then colour 1; sites of
 // one colour have no bond between them, so they are updated together.  A site
 // with c_u unsatisfied bonds has dE = 4 (dim - c_u); it flips if dE <= 0, or
-// if its uniform u (word h & 3 of the Philox block (2 g + colour, h >> 2,
-// slot, SWEEP | instance), h = s >> 1, g = global sweep index) is below the
+// if its uniform u (word h & 3 of the Philox block with counter (2 g + colour,
+// h >> 2, SWEEP | instance, slot), h = s >> 1, g = global sweep index) is below the
 // threshold T(beta_i, dE) = floor(2^32 exp(-beta_i dE)).
 //
 // One warp owns one replica at a time; the replica is staged whole in shared
@@ -117,7 +117,7 @@ __device__ __forceinline__ void count_add(uint32_t& b0, uint32_t& b1, uint32_t& 
 
 // Per-run scalars of one sweep launch, read from the run's device state.
 struct SweepCtx {
-    uint32_t R, cur, step, g0, parity, T0, T1, T2, full, ctr3, k0, k1;
+    uint32_t R, cur, step, g0, parity, T0, T1, T2, full, ctag, k0, k1;
     uint32_t nT0, nT1, nT2, one, four;  // 2^32 - T_c, and opaque 1 and 4 (carry-chain tests)
 };
 
@@ -155,7 +155,7 @@ __device__ __forceinline__ SweepCtx sweep_ctx(const RunDev& d) {
     x.T1 = d.thr[x.step * 4 + 1];
     x.T2 = d.thr[x.step * 4 + 2];
     x.full = d.thr[x.step * 4 + 3];
-    x.ctr3 = (TAG_SWEEP << 28) | d.instance;
+    x.ctag = (TAG_SWEEP << 28) | d.instance;  // counter word 2 of the sweep
     x.k0 = (uint32_t)d.seed;
     x.k1 = (uint32_t)(d.seed >> 32);
     x.nT0 = 0u - x.T0;
@@ -274,7 +274,7 @@ __device__ __forceinline__ uint32_t packed_replica(const RunDev& d, const SweepC
             __syncwarp();
             // phase B: one Philox block per 4 colour sites
             for (int q = lane; q < G::NCALLS; q += 32) {
-                const uint4 u = philox(2u * g + (uint32_t)c, (uint32_t)q, slot, x.ctr3, x.k0, x.k1);
+                const uint4 u = philox(2u * g + (uint32_t)c, (uint32_t)q, x.ctag, slot, x.k0, x.k1);
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const int h = 4 * q + j;
@@ -352,7 +352,7 @@ __device__ __forceinline__ uint32_t i8_replica(const RunDev& d, const SweepCtx& 
         const uint32_t g = x.g0 + (uint32_t)t;
         for (int c = 0; c < 2; ++c) {
             for (int q = lane; q < G::NCALLS; q += 32) {
-                const uint4 u = philox(2u * g + (uint32_t)c, (uint32_t)q, slot, x.ctr3, x.k0, x.k1);
+                const uint4 u = philox(2u * g + (uint32_t)c, (uint32_t)q, x.ctag, slot, x.k0, x.k1);
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const int h = 4 * q + j;
@@ -478,7 +478,7 @@ __device__ __forceinline__ uint32_t rows_replica(const RunDev& d, const SweepCtx
         const uint32_t g = x.g0 + (uint32_t)t;
         for (int c = 0; c < 2; ++c) {
             for (int q = lane; q < G::NCALLS; q += 32) {
-                const uint4 u = philox(2u * g + (uint32_t)c, (uint32_t)q, slot, x.ctr3, x.k0, x.k1);
+                const uint4 u = philox(2u * g + (uint32_t)c, (uint32_t)q, x.ctag, slot, x.k0, x.k1);
                 reinterpret_cast<uint4*>(U)[q] = u;
             }
             __syncwarp();
@@ -795,7 +795,7 @@ struct RSKeyRegs {
 // One half-sweep group: sites of pairs 4k .. 4k + 3, colour c, 32 replicas.
 template <int DIM, int L, bool PMJ, typename KT>
 __device__ __forceinline__ void rs_group(uint32_t* S, const uint8_t* JS, int k, int c, uint32_t g,
-                                         uint32_t b0, uint32_t ctr3, const KT& K,
+                                         uint32_t b0, uint32_t ctag, const KT& K,
                                          const SweepCtx& x) {
     using G = RSGeo<DIM, L, PMJ>;
     constexpr int NC = G::NCLS;
@@ -808,26 +808,31 @@ __device__ __forceinline__ void rs_group(uint32_t* S, const uint8_t* JS, int k, 
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int cl = 0; cl < NC; ++cl) acc[i][cl] = 0u;
-    // rounds 1 and 2 of Philox: the products of the counter words shared by
-    // the 32 replicas (c0 = 2 g + colour, c1 = k, c3) are formed once;
-    // M1 * slot steps down by M1 from slot b0 + 31
-    const uint32_t c0 = 2u * g + (uint32_t)c, c1 = (uint32_t)k;
-    const uint32_t x2 = __umulhi(M0, c0) ^ ctr3 ^ K.rk1[0];
-    const uint32_t x3 = M0 * c0;
-    const uint32_t y0k = __umulhi(M1, x2) ^ K.rk0[1];
-    const uint32_t y1 = M1 * x2;
-    uint64_t P = (uint64_t)M1 * (uint64_t)(b0 + 31u);
+    // Philox of the 32 replicas' blocks, counter (2 g + colour, k, SWEEP |
+    // instance, slot): round 1 multiplies only words the 32 blocks share (the
+    // slot enters word 2 by an xor), rounds 2 and 3 multiply one shared and
+    // one replica word each; the shared products are formed once here, so a
+    // block costs 16 multiplies
+    const uint32_t c0 = 2u * g + (uint32_t)c;
+    const uint32_t y0 = __umulhi(M1, ctag) ^ (uint32_t)k ^ K.rk0[0];  // round 1
+    const uint32_t y1 = M1 * ctag;
+    const uint32_t y2s = __umulhi(M0, c0) ^ K.rk1[0];  // word 2 before the xor with the slot
+    const uint32_t y3 = M0 * c0;
+    const uint32_t z2 = __umulhi(M0, y0) ^ y3 ^ K.rk1[1];  // round 2, shared half
+    const uint32_t z3k = (M0 * y0) ^ K.rk1[2];
+    const uint32_t w0s = __umulhi(M1, z2) ^ K.rk0[2];  // round 3, shared half
+    const uint32_t w1 = M1 * z2;
 #pragma unroll 2
     for (int r = 31; r >= 0; --r) {
-        const uint32_t x0 = (uint32_t)(P >> 32) ^ c1 ^ K.rk0[0];
-        const uint32_t x1 = (uint32_t)P;
-        P -= M1;
-        uint32_t c0w = y0k ^ x1;
-        uint32_t c1w = y1;
-        uint32_t c2w = __umulhi(M0, x0) ^ x3 ^ K.rk1[1];
-        uint32_t c3w = M0 * x0;
+        const uint32_t y2 = y2s ^ (b0 + (uint32_t)r);
+        const uint32_t z0 = __umulhi(M1, y2) ^ y1 ^ K.rk0[1];  // round 2, replica half
+        const uint32_t z1 = M1 * y2;
+        uint32_t c0w = w0s ^ z1;                                // round 3, replica half
+        uint32_t c1w = w1;
+        uint32_t c2w = __umulhi(M0, z0) ^ z3k;
+        uint32_t c3w = M0 * z0;
 #pragma unroll
-        for (int rr = 2; rr < 10; ++rr) {
+        for (int rr = 3; rr < 10; ++rr) {
             const uint32_t a = c0w, b = c2w;
             const uint32_t hiA = __umulhi(M0, a), loA = M0 * a;
             const uint32_t hiB = __umulhi(M1, b), loB = M1 * b;
@@ -930,13 +935,13 @@ __device__ __forceinline__ void rs_chunk(const RunDev& d, const SweepCtx& x, uin
         if (lane < (N & 31)) S[rs_ix((N & ~31) + lane)] = keep;
     }
     __syncwarp();
-    const uint32_t ctr3 = x.ctr3;
+    const uint32_t ctag = x.ctag;
     for (int t = 0; t < nsweeps; ++t) {
         const uint32_t g = x.g0 + (uint32_t)t;
 #pragma unroll 1
         for (int c = 0; c < 2; ++c) {
             for (int k = lane; k < G::NGROUPS; k += 32)
-                rs_group<DIM, L, PMJ, KT>(S, JS, k, c, g, b0, ctr3, K, x);
+                rs_group<DIM, L, PMJ, KT>(S, JS, k, c, g, b0, ctag, K, x);
             __syncwarp();
         }
     }

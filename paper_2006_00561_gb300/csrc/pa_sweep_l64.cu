@@ -4,7 +4,7 @@
 //
 // Same update rule and random numbers as the generic kernels of pa_sweep.cu
 // (checkerboard order, dE = 4 (2 - c_u), u = word h & 3 of the Philox block
-// (2 g + colour, h >> 2, slot, SWEEP | instance), h = s >> 1, accept iff
+// with counter (2 g + colour, h >> 2, SWEEP | instance, slot), h = s >> 1, accept iff
 // dE <= 0 or u < T(beta_i, dE)), mapped for throughput:
 //   * one warp holds one replica for all theta sweeps, entirely in registers:
 //     lane l owns rows 2l and 2l+1 (one 16-byte load per lane, coalesced);
@@ -107,13 +107,14 @@ __device__ __forceinline__ uint32_t add_if_below(uint32_t acc, uint32_t u, const
     }
 }
 
-// Philox4x32-10 of the blocks (c0, c1, slot, ctr3) of one half-sweep, with
-// c0 = 2 g + colour shared and c1 = h >> 2 the block index.  Round 1
-// multiplies c0 and slot (both shared); c1 enters word 0 by an xor, so round
-// 2 multiplies one block word (M0 * word 0) and one shared word, round 3 again
-// one of each (M1 * word 2, M0 * word 0 shared), and rounds 4..10 are the
-// plain rounds.  The shared products are formed once per half-sweep
-// (HalfSweepGen): 16 multiplies per block.  Same bits as philox().
+// Philox4x32-10 of the blocks (c0, c1, ctag, slot) of one half-sweep of one
+// replica, with c0 = 2 g + colour, c1 = h >> 2 the block index and ctag =
+// SWEEP | instance.  Round 1 multiplies c0 and ctag (both shared); c1 enters
+// word 0 by an xor, so round 2 multiplies one block word (M0 * word 0) and one
+// shared word, round 3 again one of each (M1 * word 2, M0 * word 0 shared),
+// and rounds 4..10 are the plain rounds.  The shared products are formed once
+// per half-sweep (HalfSweepGen): 16 multiplies per block.  Same bits as
+// philox().
 constexpr uint32_t PM0 = 0xD2511F53u, PM1 = 0xCD9E8D57u;
 
 // Round keys of the run's seed and the opaque 1 of the multiply-add tests:
@@ -141,7 +142,7 @@ __device__ __forceinline__ void mul_hilo(uint32_t m, uint32_t a, uint32_t& hi, u
 }
 
 struct HalfSweepGen {
-    uint32_t y0k;  // round-1 word 0 before the xor with c1: high half of M1 * slot ^ key 0
+    uint32_t y0k;  // round-1 word 0 before the xor with c1: high half of M1 * ctag ^ key 0
     uint32_t y3k;  // round-1 word 3 (low half of M0 * c0) ^ round-2 key 1
     uint32_t z1k;  // round-2 word 1 ^ round-3 key 0
     uint32_t e2k;  // high half of M0 * (round-2 word 0) ^ round-3 key 1
@@ -149,17 +150,17 @@ struct HalfSweepGen {
 };
 
 __device__ __forceinline__ HalfSweepGen half_sweep_gen(const Keys& d, uint32_t c0, uint32_t slot,
-                                                      uint32_t ctr3) {
+                                                      uint32_t ctag) {
     HalfSweepGen g;
-    uint32_t hs, ls, hc, lc;
-    mul_hilo(PM1, slot, hs, ls);  // round 1
+    uint32_t ht, lt, hc, lc;
+    mul_hilo(PM1, ctag, ht, lt);  // round 1
     mul_hilo(PM0, c0, hc, lc);
-    g.y0k = hs ^ d.rk0[0];
+    g.y0k = ht ^ d.rk0[0];
     g.y3k = lc ^ d.rk1[1];
-    const uint32_t y2 = hc ^ ctr3 ^ d.rk1[0];
+    const uint32_t y2 = hc ^ slot ^ d.rk1[0];
     uint32_t h2, l2;
     mul_hilo(PM1, y2, h2, l2);  // round 2, shared half
-    const uint32_t z0 = h2 ^ ls ^ d.rk0[1];
+    const uint32_t z0 = h2 ^ lt ^ d.rk0[1];
     g.z1k = l2 ^ d.rk0[2];
     uint32_t h3, l3;
     mul_hilo(PM0, z0, h3, l3);  // round 3, shared half
@@ -437,7 +438,7 @@ __device__ __forceinline__ void l64_couplings(const RunDev& d, int lane, RowJ& j
 // (all lanes), M through the reference; writes the replica back.
 template <bool PMJ>
 __device__ __forceinline__ uint32_t l64_replica(const Keys& K, uint4* spins, uint32_t slot,
-                                                int nsweeps, uint32_t g0, uint32_t ctr3,
+                                                int nsweeps, uint32_t g0, uint32_t ctag,
                                                 const Thr& t4, const Thr& t8, uint32_t full,
                                                 int lane, int& M, const RowJ& ja, const RowJ& jb) {
     const uint32_t ya = 2u * (uint32_t)lane, yb = ya + 1u;
@@ -450,7 +451,7 @@ __device__ __forceinline__ uint32_t l64_replica(const Keys& K, uint4* spins, uin
         {  // colour 0: even rows have parity 0, odd rows parity 1
             const uint64_t up = shfl64(rb, lup);  // row ya - 1
             const uint64_t dn = shfl64(ra, ldn);  // row yb + 1
-            const HalfSweepGen gen = half_sweep_gen(K, 2u * g, slot, ctr3);
+            const HalfSweepGen gen = half_sweep_gen(K, 2u * g, slot, ctag);
             const uint64_t fa = row_flips<0, PMJ>(K, gen, ra, up, rb, ya, t4, t8, full, ja);
             const uint64_t fb = row_flips<1, PMJ>(K, gen, rb, ra, dn, yb, t4, t8, full, jb);
             ra ^= fa;
@@ -459,7 +460,7 @@ __device__ __forceinline__ uint32_t l64_replica(const Keys& K, uint4* spins, uin
         {  // colour 1
             const uint64_t up = shfl64(rb, lup);
             const uint64_t dn = shfl64(ra, ldn);
-            const HalfSweepGen gen = half_sweep_gen(K, 2u * g + 1u, slot, ctr3);
+            const HalfSweepGen gen = half_sweep_gen(K, 2u * g + 1u, slot, ctag);
             const uint64_t fa = row_flips<1, PMJ>(K, gen, ra, up, rb, ya, t4, t8, full, ja);
             const uint64_t fb = row_flips<0, PMJ>(K, gen, rb, ra, dn, yb, t4, t8, full, jb);
             ra ^= fa;
@@ -526,7 +527,7 @@ __global__ void __launch_bounds__(WARPS64 * 32, PA_L64_MIN_BLOCKS)
     Thr t4, t8;
     uint32_t full;
     thresholds(d, st->step, t4, t8, full);
-    const uint32_t ctr3 = (TAG_SWEEP << 28) | d.instance;
+    const uint32_t ctag = (TAG_SWEEP << 28) | d.instance;
     const Keys K{d.rk0, d.rk1, d.one};
     uint4* spins = reinterpret_cast<uint4*>(d.spins[cur]);
     RowJ ja{0, 0, 0, 0}, jb{0, 0, 0, 0};
@@ -538,7 +539,7 @@ __global__ void __launch_bounds__(WARPS64 * 32, PA_L64_MIN_BLOCKS)
     for (uint32_t slot = d.slot_lo + blockIdx.x * WARPS64 + wib; slot < end; slot += nwarps) {
         int M = 0;
         const uint32_t U =
-            l64_replica<PMJ>(K, spins, slot, nsweeps, g0, ctr3, t4, t8, full, lane, M, ja, jb);
+            l64_replica<PMJ>(K, spins, slot, nsweeps, g0, ctag, t4, t8, full, lane, M, ja, jb);
         if (lane == 0) {
             d.ebin[cur][slot] = U >> 1;
             d.mag[cur][slot] = M;
@@ -579,7 +580,7 @@ __global__ void __launch_bounds__(WARPS64 * 32, PA_L64_MIN_BLOCKS) k_sweep_l64_b
         }
         __syncwarp();
         const Keys K{&s_keys[wib][0], &s_keys[wib][10], d.one};
-        const uint32_t ctr3 = (TAG_SWEEP << 28) | d.instance;
+        const uint32_t ctag = (TAG_SWEEP << 28) | d.instance;
         uint4* spins = reinterpret_cast<uint4*>(d.spins[cur]);
         const uint32_t first = g - a.slot_base[lo];
         RowJ ja{0, 0, 0, 0}, jb{0, 0, 0, 0};
@@ -588,7 +589,7 @@ __global__ void __launch_bounds__(WARPS64 * 32, PA_L64_MIN_BLOCKS) k_sweep_l64_b
         for (uint32_t slot = first; slot < first + a.chunk && slot < R; ++slot) {
             int M = 0;
             const uint32_t U =
-                l64_replica<PMJ>(K, spins, slot, d.theta, g0, ctr3, t4, t8, full, lane, M, ja, jb);
+                l64_replica<PMJ>(K, spins, slot, d.theta, g0, ctag, t4, t8, full, lane, M, ja, jb);
             if (lane == 0) {
                 d.ebin[cur][slot] = U >> 1;
                 d.mag[cur][slot] = M;
@@ -742,7 +743,7 @@ __device__ __forceinline__ void l128_couplings(const RunDev& d, int lane, RowJ2 
 // One replica at L = 128: theta sweeps in registers, then the measurement.
 template <bool PMJ>
 __device__ __forceinline__ uint32_t l128_replica(const Keys& K, uint4* spins, uint32_t slot,
-                                                 int nsweeps, uint32_t g0, uint32_t ctr3,
+                                                 int nsweeps, uint32_t g0, uint32_t ctag,
                                                  const Thr& t4, const Thr& t8, uint32_t full,
                                                  int lane, int& M, const RowJ2 (&j)[4]) {
     const uint32_t y0 = 4u * (uint32_t)lane;
@@ -759,7 +760,7 @@ __device__ __forceinline__ uint32_t l128_replica(const Keys& K, uint4* spins, ui
         const uint32_t g = g0 + (uint32_t)t;
         {  // colour 0: rows 4l and 4l + 2 have parity 0
             const Row2 up = shfl_row(r[3], lup), dn = shfl_row(r[0], ldn);
-            const HalfSweepGen gen = half_sweep_gen(K, 2u * g, slot, ctr3);
+            const HalfSweepGen gen = half_sweep_gen(K, 2u * g, slot, ctag);
             row_update128<0, PMJ>(K, gen, r[0], up, r[1], y0, t4, t8, full, j[0]);
             row_update128<1, PMJ>(K, gen, r[1], r[0], r[2], y0 + 1u, t4, t8, full, j[1]);
             row_update128<0, PMJ>(K, gen, r[2], r[1], r[3], y0 + 2u, t4, t8, full, j[2]);
@@ -767,7 +768,7 @@ __device__ __forceinline__ uint32_t l128_replica(const Keys& K, uint4* spins, ui
         }
         {  // colour 1
             const Row2 up = shfl_row(r[3], lup), dn = shfl_row(r[0], ldn);
-            const HalfSweepGen gen = half_sweep_gen(K, 2u * g + 1u, slot, ctr3);
+            const HalfSweepGen gen = half_sweep_gen(K, 2u * g + 1u, slot, ctag);
             row_update128<1, PMJ>(K, gen, r[0], up, r[1], y0, t4, t8, full, j[0]);
             row_update128<0, PMJ>(K, gen, r[1], r[0], r[2], y0 + 1u, t4, t8, full, j[1]);
             row_update128<1, PMJ>(K, gen, r[2], r[1], r[3], y0 + 2u, t4, t8, full, j[2]);
@@ -806,7 +807,7 @@ __global__ void __launch_bounds__(warps128<PMJ>() * 32, 1)
     Thr t4, t8;
     uint32_t full;
     thresholds(d, st->step, t4, t8, full);
-    const uint32_t ctr3 = (TAG_SWEEP << 28) | d.instance;
+    const uint32_t ctag = (TAG_SWEEP << 28) | d.instance;
     const Keys K{d.rk0, d.rk1, d.one};
     uint4* spins = reinterpret_cast<uint4*>(d.spins[cur]);
     RowJ2 j[4] = {};
@@ -819,7 +820,7 @@ __global__ void __launch_bounds__(warps128<PMJ>() * 32, 1)
     for (uint32_t slot = d.slot_lo + blockIdx.x * W + wib; slot < end; slot += nwarps) {
         int M = 0;
         const uint32_t U =
-            l128_replica<PMJ>(K, spins, slot, nsweeps, g0, ctr3, t4, t8, full, lane, M, j);
+            l128_replica<PMJ>(K, spins, slot, nsweeps, g0, ctag, t4, t8, full, lane, M, j);
         if (lane == 0) {
             d.ebin[cur][slot] = U >> 1;
             d.mag[cur][slot] = M;
@@ -859,7 +860,7 @@ __global__ void __launch_bounds__(warps128<PMJ>() * 32, 1) k_sweep_l128_batched(
         }
         __syncwarp();
         const Keys K{&s_keys[wib][0], &s_keys[wib][10], d.one};
-        const uint32_t ctr3 = (TAG_SWEEP << 28) | d.instance;
+        const uint32_t ctag = (TAG_SWEEP << 28) | d.instance;
         uint4* spins = reinterpret_cast<uint4*>(d.spins[cur]);
         const uint32_t first = g - a.slot_base[lo];
         RowJ2 j[4] = {};
@@ -868,7 +869,7 @@ __global__ void __launch_bounds__(warps128<PMJ>() * 32, 1) k_sweep_l128_batched(
         for (uint32_t slot = first; slot < first + a.chunk && slot < R; ++slot) {
             int M = 0;
             const uint32_t U =
-                l128_replica<PMJ>(K, spins, slot, d.theta, g0, ctr3, t4, t8, full, lane, M, j);
+                l128_replica<PMJ>(K, spins, slot, d.theta, g0, ctag, t4, t8, full, lane, M, j);
             if (lane == 0) {
                 d.ebin[cur][slot] = U >> 1;
                 d.mag[cur][slot] = M;
