@@ -667,7 +667,7 @@ __global__ void __launch_bounds__(BW * 32) k_sweep_batched(BatchSweepArgs a) {
 // Random numbers and update rule are those of the other kernels: in a
 // half-sweep of colour c, lane k of the work takes the group of the four
 // colour-c sites with h = s >> 1 in 4k .. 4k + 3 (Philox counter
-// (k, 2g + c, slot, SWEEP | instance), word h & 3), draws the 32 replicas'
+// (2g + c, k, SWEEP | instance, slot), word h & 3), draws the 32 replicas'
 // blocks and folds every uniform into carry chains, one per (site, class):
 // acc = 2 acc + [u >= T_class], replica r ending at bit r.  A site flips in
 // replica r if its class has dE <= 0, or if bit r of the chain of its class
