@@ -177,6 +177,18 @@ int pa_step(pa_run* run);
 int pa_step_stream(pa_run* run, void* host_dst, size_t bytes, int32_t chunks, void* copy_stream,
                    int64_t* R_out);
 
+/* Test hooks for the failure paths (0 in normal operation).
+ * PA_DEBUG_WITHHOLD_PREFIX: the resample's tile 0 does not publish its
+ * lookback prefix, so tile 1's wait for it (at most 2^22 polls, about a
+ * second or two) runs out: the kernel sets the sticky PA_ERR_TIMEOUT, gives up
+ * that lookback and finishes (its copies land inside the population
+ * buffer, at wrong offsets), and the next synchronising call returns
+ * PA_ERR_TIMEOUT.  No fault, no hang: the context stays usable.  Takes effect
+ * from the next enqueued step; not for graph replay.  Returns PA_OK, or
+ * PA_ERR_INVALID_ARG for unknown bits. */
+#define PA_DEBUG_WITHHOLD_PREFIX 1u
+int pa_debug(pa_run* run, uint32_t flags);
+
 /* nsteps calls of pa_step, replayed from a CUDA graph of one step that is
  * captured on first use (on a private stream, then launched on the run's
  * stream).  Same results as nsteps pa_step calls. */

@@ -566,6 +566,12 @@ int pa_step_stream(pa_run* r, void* host_dst, size_t bytes, int32_t chunks, void
     return PA_OK;
 }
 
+int pa_debug(pa_run* r, uint32_t flags) {
+    if (!r || (flags & ~PA_DEBUG_WITHHOLD_PREFIX)) return PA_ERR_INVALID_ARG;
+    r->d.debug = flags;
+    return PA_OK;
+}
+
 int pa_run_steps(pa_run* r, int32_t nsteps) {
     if (!r || nsteps < 0) return PA_ERR_INVALID_ARG;
     if (!r->graph) {

@@ -95,6 +95,7 @@ struct RunDev {
     // 0xffffffff (the whole population) except in the launches of a
     // streamed step, whose bounds are multiples of 32.
     uint32_t slot_lo, slot_hi;
+    uint32_t debug;  // PA_DEBUG_* test hooks, 0 in normal operation
 };
 
 // A batch of runs stepped together (pa_batch_* in include/pa.h).  Arrays in

@@ -286,7 +286,10 @@ __device__ __forceinline__ void resample_tile(const RunDev& d, uint32_t tile, Re
         if (lane == 0) {
             uint32_t excl = 0;
             if (tile == 0) {
-                st_release(&d.desc[0], desc_make(DESC_PREFIX, epoch, total));
+                // the test hook withholds tile 0's prefix, so that tile 1's
+                // bounded wait runs out (PA_DEBUG_WITHHOLD_PREFIX)
+                if (!(d.debug & PA_DEBUG_WITHHOLD_PREFIX))
+                    st_release(&d.desc[0], desc_make(DESC_PREFIX, epoch, total));
             } else {
                 st_release(&d.desc[tile], desc_make(DESC_AGG, epoch, total));
                 int p = (int)tile - 1;

@@ -38,8 +38,9 @@ EXPORTS = [
     "pa_batch_workspace_size", "pa_batch_init", "pa_batch_step", "pa_batch_run_steps",
     "pa_batch_sync", "pa_batch_num_classes", "pa_batch_class_info", "pa_batch_set_shape",
     "pa_batch_free", "pa_checkpoint_size", "pa_checkpoint", "pa_restore",
-    "pa_adaptive_beta", "pa_resample_to", "pa_poisson1_table", "pa_step_stream",
+    "pa_adaptive_beta", "pa_resample_to", "pa_poisson1_table", "pa_step_stream", "pa_debug",
 ]
+DEBUG_WITHHOLD_PREFIX = 1
 NOALLOC_MAX_REPLICAS = 8388608
 
 
@@ -112,6 +113,7 @@ def lib():
         L.pa_sweep.argtypes = [vp, C.c_int32]
         L.pa_run_steps.argtypes = [vp, C.c_int32]
         L.pa_step_stream.argtypes = [vp, vp, C.c_size_t, C.c_int32, vp, C.POINTER(C.c_int64)]
+        L.pa_debug.argtypes = [vp, C.c_uint32]
         L.pa_observables.argtypes = [vp, C.POINTER(Obs)]
         L.pa_observables_history.argtypes = [vp, C.c_int32, C.c_int32, C.POINTER(Obs)]
         L.pa_dump_size.argtypes = [vp, C.c_int32]
@@ -213,6 +215,11 @@ def pa_step(h: int):
 
 def pa_run_steps(h: int, nsteps: int):
     _check(lib().pa_run_steps(C.c_void_p(h), nsteps), "pa_run_steps")
+
+
+def pa_debug(h: int, flags: int):
+    """Test hooks of the failure paths (DEBUG_WITHHOLD_PREFIX)."""
+    _check(lib().pa_debug(C.c_void_p(h), flags), "pa_debug")
 
 
 def pa_step_stream(h: int, host_ptr: int, nbytes: int, chunks: int, copy_stream_handle: int) -> int:

@@ -291,6 +291,27 @@ def test_streamed_step_reports_capacity_overflow(P):
     run.close()
 
 
+def test_lookback_timeout_is_reported_and_the_context_survives(P):
+    """The resample's only wait (tile t waits for tile t - 1's prefix) is
+    bounded.  With tile 0's prefix withheld (test hook), tile 1's wait runs out
+    after its poll limit: the step finishes, the sticky PA_ERR_TIMEOUT is
+    reported, and the context keeps working (a fresh run matches the oracle)."""
+    import time
+    _, gcfg = configs(P, dim=2, L=16, R0=5000, K=4, theta=1, seed=3)  # 3 resample tiles
+    run = P.Run(gcfg)
+    run.step()
+    assert run.status() == 0
+    with pytest.raises(P.PaError):
+        P.pa_debug(run.h, 2)  # unknown bit
+    P.pa_debug(run.h, P.DEBUG_WITHHOLD_PREFIX)
+    t0 = time.perf_counter()
+    run.step()
+    assert run.status() == -5  # PA_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 60.0
+    run.close()
+    run_lockstep(P, steps=2, dim=2, L=16, R0=5000, K=4, theta=1, seed=3)
+
+
 def test_capacity_overflow_is_reported(P):
     ocfg, gcfg = configs(P, dim=2, L=8, R0=200, capacity=200, K=50, theta=1, beta_max=3.0,
                          seed=1)
