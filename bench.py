@@ -498,6 +498,35 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def philox_ceiling(P, sweep_attempts_per_ns: float) -> dict:
+    """The register kernels' generator alone (pa_bench_philox): the same
+    Philox blocks in k_sweep_l64's launch shape with no acceptance tests and
+    no lattice work.  A sweep attempt consumes one uniform, so the sweep
+    kernel's attempts/ns over this kernel's uniforms/ns is the fraction of the
+    generator's own ceiling that the sweep reaches."""
+    import torch
+    n = P.pa_bench_philox_threads()
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    s = torch.cuda.current_stream()
+    halfsweeps, reps = 4000, 5
+    for _ in range(2):
+        P.pa_bench_philox(7, halfsweeps, out.data_ptr(), n, s.cuda_stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(reps):
+        P.pa_bench_philox(7, halfsweeps, out.data_ptr(), n, s.cuda_stream)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    uniforms = n * halfsweeps * 64
+    rate = uniforms / (ms * 1e6)
+    return {"kernel": "k_philox_rate", "uniforms_per_ns": rate, "ms_per_launch": ms,
+            "uniforms_per_launch": uniforms, "sweep_fraction": sweep_attempts_per_ns / rate,
+            "note": "Philox4x32-10 blocks of k_sweep_l64 (16 multiplies each), 1 block of "
+                    "16 warps per SM, outputs xor-folded: the generator's ceiling"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -636,6 +665,7 @@ def main():
     run.close()
     del run
     torch.cuda.empty_cache()
+    rng_ceiling = philox_ceiling(P, sweep_attempts_per_launch / (sweep_ms * 1e6))
     ens = srv = nxt = None
     if not args.no_ensemble and world == 1:
         ens = ensemble_compare(P, steps=3)
@@ -692,6 +722,7 @@ def main():
                      "ops_per_attempt": OPS_PER_ATTEMPT,
                      "peak_note": "152 SMs x (64 ALU + 64 FMA-heavy) int32 lanes x 2070 MHz "
                                   "(derived from unit counts and the maximum clock)"},
+        "philox_ceiling": rng_ceiling,
         "resample_roofline": {"bound": "hbm", "achieved": res_gbs, "peak": hbm, "unit": "GB/s",
                               "frac": res_gbs / hbm, "traffic": None,
                               "kernel": "k_resample (counts + lookback scan + gather)",

@@ -177,6 +177,21 @@ int pa_step(pa_run* run);
 int pa_step_stream(pa_run* run, void* host_dst, size_t bytes, int32_t chunks, void* copy_stream,
                    int64_t* R_out);
 
+/* The random-number ceiling of the register sweep kernels (a measurement,
+ * not part of a run): the Philox4x32-10 blocks of the L = 64 kernel, in its
+ * launch shape (one persistent 16-warp block per SM, one warp per replica,
+ * each lane drawing 16 blocks per half-sweep with the half-sweep products
+ * shared), with nothing done to the uniforms but an xor into one word per
+ * thread.  Thread t writes out_dev[t] = xor over half-sweeps g < halfsweeps
+ * and blocks b = 16 (t mod 32) .. + 15 of the four words of the block with
+ * counter (2g, b, SWEEP << 28, t / 32) under key `seed`.  Uniforms drawn:
+ * pa_bench_philox_threads() * halfsweeps * 64.  out_dev: device memory of
+ * at least pa_bench_philox_threads() words, else PA_ERR_INVALID_ARG.
+ * Asynchronous on `stream` (cudaStream_t). */
+int64_t pa_bench_philox_threads(void);
+int pa_bench_philox(uint64_t seed, int32_t halfsweeps, void* out_dev, int64_t out_words,
+                    void* stream);
+
 /* Test hooks for the failure paths (0 in normal operation).
  * PA_DEBUG_WITHHOLD_PREFIX: the resample's tile 0 does not publish its
  * lookback prefix, so tile 1's wait for it (at most 2^22 polls, about a

@@ -566,6 +566,15 @@ int pa_step_stream(pa_run* r, void* host_dst, size_t bytes, int32_t chunks, void
     return PA_OK;
 }
 
+int64_t pa_bench_philox_threads(void) { return (int64_t)pa::philox_rate_threads(); }
+
+int pa_bench_philox(uint64_t seed, int32_t halfsweeps, void* out, int64_t out_words, void* stream) {
+    const int64_t need = pa::philox_rate_threads();
+    if (!out || halfsweeps < 1 || need <= 0 || out_words < need) return PA_ERR_INVALID_ARG;
+    CK(pa::launch_philox_rate(seed, (uint32_t)halfsweeps, (uint32_t*)out, (cudaStream_t)stream));
+    return PA_OK;
+}
+
 int pa_debug(pa_run* r, uint32_t flags) {
     if (!r || (flags & ~PA_DEBUG_WITHHOLD_PREFIX)) return PA_ERR_INVALID_ARG;
     r->d.debug = flags;

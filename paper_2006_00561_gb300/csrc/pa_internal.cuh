@@ -181,6 +181,9 @@ bool l64_applies(const RunDev& d);
 int l64_block_warps(const RunDev& d);
 int l64_grid(const RunDev& d);
 cudaError_t launch_sweep_l64(const RunDev& d, int nsweeps, int grid, cudaStream_t s);
+// The register kernels' generator alone (pa_bench_philox).
+int philox_rate_threads();
+cudaError_t launch_philox_rate(uint64_t seed, uint32_t halfsweeps, uint32_t* out, cudaStream_t s);
 // batched forms (one launch for every run of a batch, or of one class)
 cudaError_t launch_tau_batched(const BatchDev& b, cudaStream_t s);
 cudaError_t launch_resample_batched(const BatchDev& b, cudaStream_t s);

@@ -899,6 +899,37 @@ int l64_block_warps(const RunDev& d) {
     return d.model == PA_MODEL_PMJ ? warps128<true>() : warps128<false>();
 }
 
+// --------------------------------------------------------------------------
+// The generator's own ceiling in the register kernels' launch shape: the
+// Philox blocks of k_sweep_l64 (half-sweep products shared, 16 multiplies per
+// block, 16 blocks per half-sweep and lane) with nothing else done to the
+// uniforms but an xor into one word per thread.  One warp stands for one
+// replica (slot = global warp index); half-sweep g of lane l draws blocks
+// 16 l .. 16 l + 15 of counter (2 g, block, SWEEP, slot).
+struct PhiloxRateArgs {
+    uint32_t rk0[10], rk1[10];
+    uint32_t one;
+    uint32_t halfsweeps;
+    uint32_t* out;
+};
+
+__global__ void __launch_bounds__(WARPS64 * 32, PA_L64_MIN_BLOCKS)
+    k_philox_rate(__grid_constant__ const PhiloxRateArgs a) {
+    const Keys K{a.rk0, a.rk1, a.one};
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t slot = tid >> 5, base = (threadIdx.x & 31u) * 16u;
+    uint32_t acc = 0;
+    for (uint32_t g = 0; g < a.halfsweeps; ++g) {
+        const HalfSweepGen gen = half_sweep_gen(K, 2u * g, slot, TAG_SWEEP << 28);
+#pragma unroll 4
+        for (uint32_t h = 0; h < 16u; ++h) {
+            const uint4 u = philox_block(K, gen, base + h);
+            acc ^= u.x ^ u.y ^ u.z ^ u.w;
+        }
+    }
+    a.out[tid] = acc;
+}
+
 static int wave(const void* fn, int threads) {
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
@@ -934,6 +965,31 @@ cudaError_t launch_sweep_l64(const RunDev& d, int nsweeps, int grid, cudaStream_
         if (pmj) k_sweep_l64<true><<<grid, WARPS64 * 32, 0, s>>>(d, nsweeps);
         else k_sweep_l64<false><<<grid, WARPS64 * 32, 0, s>>>(d, nsweeps);
     }
+    return cudaGetLastError();
+}
+
+// One 16-warp block per SM, as k_sweep_l64 runs.
+static int philox_rate_grid() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    return sms;
+}
+
+int philox_rate_threads() { return philox_rate_grid() * WARPS64 * 32; }
+
+cudaError_t launch_philox_rate(uint64_t seed, uint32_t halfsweeps, uint32_t* out, cudaStream_t s) {
+    const int grid = philox_rate_grid();
+    if (grid <= 0) return cudaErrorInvalidValue;
+    PhiloxRateArgs a;
+    for (int k = 0; k < 10; ++k) {
+        a.rk0[k] = (uint32_t)seed + (uint32_t)k * 0x9E3779B9u;
+        a.rk1[k] = (uint32_t)(seed >> 32) + (uint32_t)k * 0xBB67AE85u;
+    }
+    a.one = 1u;
+    a.halfsweeps = halfsweeps;
+    a.out = out;
+    k_philox_rate<<<grid, WARPS64 * 32, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -39,6 +39,7 @@ EXPORTS = [
     "pa_batch_sync", "pa_batch_num_classes", "pa_batch_class_info", "pa_batch_set_shape",
     "pa_batch_free", "pa_checkpoint_size", "pa_checkpoint", "pa_restore",
     "pa_adaptive_beta", "pa_resample_to", "pa_poisson1_table", "pa_step_stream", "pa_debug",
+    "pa_bench_philox_threads", "pa_bench_philox",
 ]
 DEBUG_WITHHOLD_PREFIX = 1
 NOALLOC_MAX_REPLICAS = 8388608
@@ -114,6 +115,9 @@ def lib():
         L.pa_run_steps.argtypes = [vp, C.c_int32]
         L.pa_step_stream.argtypes = [vp, vp, C.c_size_t, C.c_int32, vp, C.POINTER(C.c_int64)]
         L.pa_debug.argtypes = [vp, C.c_uint32]
+        L.pa_bench_philox_threads.argtypes = []
+        L.pa_bench_philox_threads.restype = C.c_int64
+        L.pa_bench_philox.argtypes = [C.c_uint64, C.c_int32, vp, C.c_int64, vp]
         L.pa_observables.argtypes = [vp, C.POINTER(Obs)]
         L.pa_observables_history.argtypes = [vp, C.c_int32, C.c_int32, C.POINTER(Obs)]
         L.pa_dump_size.argtypes = [vp, C.c_int32]
@@ -215,6 +219,16 @@ def pa_step(h: int):
 
 def pa_run_steps(h: int, nsteps: int):
     _check(lib().pa_run_steps(C.c_void_p(h), nsteps), "pa_run_steps")
+
+
+def pa_bench_philox_threads() -> int:
+    return int(lib().pa_bench_philox_threads())
+
+
+def pa_bench_philox(seed: int, halfsweeps: int, out_ptr: int, out_words: int, stream_handle: int):
+    """The register kernels' generator alone: one xor word per thread at out_ptr."""
+    _check(lib().pa_bench_philox(seed, halfsweeps, C.c_void_p(out_ptr), out_words,
+                                 C.c_void_p(stream_handle)), "pa_bench_philox")
 
 
 def pa_debug(h: int, flags: int):

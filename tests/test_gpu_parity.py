@@ -291,6 +291,29 @@ def test_streamed_step_reports_capacity_overflow(P):
     run.close()
 
 
+def test_philox_ceiling_kernel_draws_the_sweep_blocks(P):
+    """pa_bench_philox (the generator alone, in the L = 64 kernel's launch
+    shape): each thread's xor word equals the xor of the oracle's Philox
+    blocks (2g, b, SWEEP << 28, warp) over its half-sweeps and its 16 blocks."""
+    import torch
+    n = P.pa_bench_philox_threads()
+    assert n > 0 and n % 512 == 0
+    out = torch.zeros(n, dtype=torch.int32, device="cuda")
+    seed = 0x0123456789ABCDEF
+    P.pa_bench_philox(seed, 3, out.data_ptr(), n, torch.cuda.current_stream().cuda_stream)
+    got = out.cpu().numpy().view(np.uint32)
+    key = (seed & 0xFFFFFFFF, seed >> 32)
+    for t in (0, 1, 31, 32, 513, n - 1):
+        want = 0
+        for g in range(3):
+            for b in range(16 * (t % 32), 16 * (t % 32) + 16):
+                w = O.philox((2 * g, b, 2 << 28, t // 32), key)
+                want ^= int(w[0]) ^ int(w[1]) ^ int(w[2]) ^ int(w[3])
+        assert int(got[t]) == want, t
+    with pytest.raises(P.PaError):
+        P.pa_bench_philox(seed, 3, out.data_ptr(), n - 1, 0)
+
+
 def test_lookback_timeout_is_reported_and_the_context_survives(P):
     """The resample's only wait (tile t waits for tile t - 1's prefix) is
     bounded.  With tile 0's prefix withheld (test hook), tile 1's wait runs out
