@@ -153,9 +153,21 @@ __global__ void __launch_bounds__(256) k_tau_batched(BatchDev b) {
     if (threadIdx.x < 2) d.accum[threadIdx.x] = 0ull;
 }
 
+// PA_RS_COMPACT = 1: the gather walks only the tile's surviving replicas
+// (count > 0), listed in order in shared memory, so that every 16-byte item a
+// thread takes has a load behind it; 0 walks every replica of the tile.
+#ifndef PA_RS_COMPACT
+#define PA_RS_COMPACT 1
+#endif
+
 struct ResampleSmem {
     uint32_t r[RS_TILE];
     uint32_t o[RS_TILE];
+#if PA_RS_COMPACT
+    uint32_t surv[RS_TILE];             // tile indices of the surviving replicas
+    uint32_t warp_nz[RS_THREADS / 32];  // survivors before each warp
+    uint32_t nsurv;
+#endif
     uint32_t warp[RS_THREADS / 32];
     uint32_t tile, excl;
 };
@@ -271,7 +283,33 @@ __device__ __forceinline__ void resample_tile(const RunDev& d, uint32_t tile, Re
         if (lane >= o) incl += y;
     }
     if (lane == 31) s_warp[wid] = incl;
+#if PA_RS_COMPACT
+    // and of the per-thread survivor counts
+    uint32_t nz = 0;
+#pragma unroll
+    for (int j = 0; j < RS_ITEMS; ++j) nz += r[j] ? 1u : 0u;
+    uint32_t nzi = nz;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, nzi, o);
+        if (lane >= o) nzi += y;
+    }
+    if (lane == 31) sm.warp_nz[wid] = nzi;
+#endif
     __syncthreads();
+#if PA_RS_COMPACT
+    if (wid == 1) {
+        const uint32_t w = lane < RS_THREADS / 32 ? sm.warp_nz[lane] : 0u;
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < RS_THREADS / 32) sm.warp_nz[lane] = wi - w;
+        if (lane == RS_THREADS / 32 - 1) sm.nsurv = wi;
+    }
+#endif
     if (wid == 0) {
         uint32_t w = lane < RS_THREADS / 32 ? s_warp[lane] : 0u;
         uint32_t wi = w;
@@ -321,10 +359,16 @@ __device__ __forceinline__ void resample_tile(const RunDev& d, uint32_t tile, Re
     }
     __syncthreads();
     uint32_t o = s_excl + s_warp[wid] + (incl - sum);
+#if PA_RS_COMPACT
+    uint32_t p = sm.warp_nz[wid] + (nzi - nz);
+#endif
 #pragma unroll
     for (int j = 0; j < RS_ITEMS; ++j) {
         const uint32_t li = (uint32_t)t * RS_ITEMS + j;
         const uint32_t i = base + li;
+#if PA_RS_COMPACT
+        if (r[j]) sm.surv[p++] = li;  // r[j] = 0 beyond R
+#endif
         if (i < R) {
             s_r[li] = r[j];
             s_o[li] = o;
@@ -347,7 +391,12 @@ __device__ __forceinline__ void resample_tile(const RunDev& d, uint32_t tile, Re
     const uint32_t CH = d.stride >> 4;
     const uint4* __restrict__ srcp = reinterpret_cast<const uint4*>(d.spins[src]) + (size_t)base * CH;
     uint4* __restrict__ dstp = reinterpret_cast<uint4*>(d.spins[src ^ 1u]);
-    const uint32_t items = n_in * CH;
+#if PA_RS_COMPACT
+    const uint32_t nlist = sm.nsurv;  // gather item j of the list: replica surv[j]
+#else
+    const uint32_t nlist = n_in;
+#endif
+    const uint32_t items = nlist * CH;
     const bool pow2 = (CH & (CH - 1)) == 0;
     const int shift = __ffs(CH) - 1;
     for (uint32_t it0 = t; it0 < items; it0 += RS_THREADS * GU) {
@@ -358,8 +407,13 @@ __device__ __forceinline__ void resample_tile(const RunDev& d, uint32_t tile, Re
             const uint32_t it = it0 + (uint32_t)u * RS_THREADS;
             rr[u] = 0;
             if (it < items) {
-                const uint32_t li = pow2 ? (it >> shift) : (it / CH);
-                cc[u] = it - li * CH;
+                const uint32_t jl = pow2 ? (it >> shift) : (it / CH);
+                cc[u] = it - jl * CH;
+#if PA_RS_COMPACT
+                const uint32_t li = sm.surv[jl];
+#else
+                const uint32_t li = jl;
+#endif
                 rr[u] = s_r[li];
                 d0[u] = s_o[li];
                 if (rr[u]) v[u] = __ldg(srcp + (size_t)li * CH + cc[u]);
@@ -377,7 +431,12 @@ __device__ __forceinline__ void resample_tile(const RunDev& d, uint32_t tile, Re
     const int32_t* msrc = d.mag[src] + base;
     uint32_t* edst = d.ebin[src ^ 1u];
     int32_t* mdst = d.mag[src ^ 1u];
-    for (uint32_t li = t; li < n_in; li += RS_THREADS) {
+    for (uint32_t jl = t; jl < nlist; jl += RS_THREADS) {
+#if PA_RS_COMPACT
+        const uint32_t li = sm.surv[jl];
+#else
+        const uint32_t li = jl;
+#endif
         const uint32_t rr = s_r[li];
         if (rr == 0) continue;
         const uint32_t e = esrc[li];
@@ -395,8 +454,13 @@ __device__ __forceinline__ void resample_tile(const RunDev& d, uint32_t tile, Re
 // Persistent: one wave of CTAs, each claiming tiles until none is left.
 // Claims come in increasing order, so a tile's lookback only waits on tiles
 // already claimed by running CTAs.
+// Resident CTAs per SM the register budget of the nearest-integer and
+// counts-from-memory rules is sized for (the Poisson rule takes 2).
+#ifndef PA_RS_MINB
+#define PA_RS_MINB 4
+#endif
 template <int RULE>
-__global__ void __launch_bounds__(RS_THREADS) k_resample(RunDev d) {
+__global__ void __launch_bounds__(RS_THREADS, RULE == 1 ? 2 : PA_RS_MINB) k_resample(RunDev d) {
     __shared__ ResampleSmem sm;
     if (!d.st->active) return;
     const uint32_t R = d.st->R_prev;
