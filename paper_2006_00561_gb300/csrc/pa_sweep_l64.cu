@@ -28,34 +28,11 @@
 namespace pa {
 namespace {
 
-// Tuning knobs (compile time): warps per block, resident blocks per SM the
-// register budget is sized for, and how the threshold tests u < T run:
-//   PA_L64_CARRY4 / PA_L64_CARRY8 (0..4): the dE = 4 / dE = 8 tests of the
-//                   first that many of the four blocks of a group run as a
-//                   carry chain on the FMA pipe (mad.lo.cc + madc: the carry
-//                   of u + (2^32 - T) is [u >= T], shifted into an accumulator
-//                   two bits at a time).  Default: all of them (+9 % over the
-//                   compare-and-select forms below on GB300).
-//   PA_L64_CMP_MODE, for the remaining tests:
-//                   0: both tests as compare + predicated OR (ALU pipe);
-//                   1: the dE = 4 test on the FMA pipe, dE = 8 on the ALU;
-//                   2: both on the FMA pipe;
-//                   3: the dE = 4 test of half of the blocks on the FMA pipe.
-//   On the FMA pipe (modes 1-3), u < T is the high word of the 32x32+64
-//   multiply-add u * 1 + (2^64 - T) (all ones iff no carry out, i.e. u < T),
-//   and the site's bit is added to the mask by a second multiply-add with
-//   -(1 << bit).
+// Tuning knobs (compile time): warps per block and the resident blocks per SM
+// the register budget is sized for; the forms of the threshold tests are the
+// PA_L64_CHAIN and PA_L64_SEL_BLOCKS knobs further down.
 #ifndef PA_L64_MIN_BLOCKS
 #define PA_L64_MIN_BLOCKS 1
-#endif
-#ifndef PA_L64_CMP_MODE
-#define PA_L64_CMP_MODE 3
-#endif
-#ifndef PA_L64_CARRY4
-#define PA_L64_CARRY4 4
-#endif
-#ifndef PA_L64_CARRY8
-#define PA_L64_CARRY8 4
 #endif
 
 // How the Philox products are formed: 0 = high and low halves from C++
@@ -81,31 +58,10 @@ __device__ __forceinline__ uint32_t warp_sum(uint32_t v) {
     return v;
 }
 
-// Threshold of one energy class for the current step.
+// Threshold of one energy class for the current step: u < T accepts.
 struct Thr {
-    uint32_t T;       // threshold, u < T accepts
-    uint64_t cneg;    // 2^64 - T (0 when T = 0)
+    uint32_t T;
 };
-
-// acc + (u < T ? bit : 0), on the FMA pipe (see the knob comment).
-__device__ __forceinline__ uint32_t add_if_below_fma(uint32_t acc, uint32_t u, uint32_t one,
-                                                     uint64_t cneg, uint32_t negbit) {
-    uint64_t r;
-    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(r) : "r"(u), "r"(one), "l"(cneg));
-    uint32_t out;
-    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(out) : "r"((uint32_t)(r >> 32)), "r"(negbit), "r"(acc));
-    return out;
-}
-
-template <bool FMA>
-__device__ __forceinline__ uint32_t add_if_below(uint32_t acc, uint32_t u, const Thr& t,
-                                                 uint32_t one, int bit) {
-    if constexpr (FMA) {
-        return add_if_below_fma(acc, u, one, t.cneg, 0u - (1u << bit));
-    } else {
-        return u < t.T ? (acc | (1u << bit)) : acc;
-    }
-}
 
 // Philox4x32-10 of the blocks (c0, c1, ctag, slot) of one half-sweep of one
 // replica, with c0 = 2 g + colour, c1 = h >> 2 the block index and ctag =
@@ -192,17 +148,6 @@ __device__ __forceinline__ uint4 philox_block(const Keys& d, const HalfSweepGen&
     return make_uint4(c0, c1w, c2, c3);
 }
 
-// acc * 4 + [u >= T] on the FMA pipe: the carry out of u * 1 + (2^32 - T)
-// feeds the multiply-add that shifts the accumulator (T > 0).
-__device__ __forceinline__ uint32_t carry_ge(uint32_t acc, uint32_t u, uint32_t one,
-                                             uint32_t negT, uint32_t four) {
-    uint32_t out;
-    asm("{\n\t.reg .u32 t;\n\tmad.lo.cc.u32 t, %1, %2, %3;\n\tmadc.lo.u32 %0, %4, %5, 0;\n\t}"
-        : "=r"(out)
-        : "r"(u), "r"(one), "r"(negT), "r"(acc), "r"(four));
-    return out;
-}
-
 // Both tests of one site into a shared accumulator, two bits per site:
 // acc = 4 acc + 2 c4 + c8, where c is the carry of the compare, written by
 // mad.lo.cc (FMA pipe: u * 1 + (2^32 - T) carries iff u >= T, for T > 0) or
@@ -231,13 +176,14 @@ __device__ __forceinline__ uint32_t site_chain(uint32_t acc, uint32_t u, uint32_
     return out;
 }
 
-// PA_L64_CHAIN > 0: both tests of a site into one accumulator (site_chain);
-// 3 (compares on the ALU, default) runs 7.5 % faster on GB300 than the
-// separate FMA chains of PA_L64_CARRY4/8 and 17 % faster than compare and
-// select.  0 selects the PA_L64_CARRY4/8 and PA_L64_CMP_MODE forms.
+// PA_L64_CHAIN (1..4): both tests of a site go into one accumulator
+// (site_chain), each compare on the FMA or the ALU pipe.  3 (both on the ALU,
+// the default) ran 7.5 % faster on GB300 than separate accumulators per test
+// with FMA-pipe chains, and 17 % faster than compare and select.
 #ifndef PA_L64_CHAIN
 #define PA_L64_CHAIN 3
 #endif
+static_assert(PA_L64_CHAIN >= 1 && PA_L64_CHAIN <= 4, "PA_L64_CHAIN: 1 .. 4");
 
 // PA_L64_SEL_BLOCKS (0..3): with the chains of PA_L64_CHAIN, the tests of
 // the last that many blocks of every group of four (h < PA_L64_SEL_BLOCKS)
@@ -290,89 +236,35 @@ __device__ __forceinline__ void row_accepts(const Keys& d, const HalfSweepGen& g
                                             const Thr& t4, const Thr& t8, uint64_t& a4,
                                             uint64_t& a8) {
     const uint32_t one = d.one;
-    constexpr int M = PA_L64_CMP_MODE;
-    // blocks h < HC4 (HC8) take the dE = 4 (dE = 8) test as a carry chain
-    constexpr int HC4 = PA_L64_CARRY4, HC8 = PA_L64_CARRY8;
-    const uint32_t negT4 = 0u - t4.T, negT8 = 0u - t8.T, four = one << 2;
+    // PA_L64_CHAIN: 1 both compares on the FMA pipe, 2 dE = 4 on the FMA pipe
+    // and dE = 8 on the ALU, 3 both on the ALU, 4 the reverse of 2
+    constexpr bool F4 = PA_L64_CHAIN == 1 || PA_L64_CHAIN == 2;
+    constexpr bool F8 = PA_L64_CHAIN == 1 || PA_L64_CHAIN == 4;
+    const uint32_t c4 = F4 ? 0u - t4.T : t4.T, c8 = F8 ? 0u - t8.T : t8.T;
     uint32_t h4[2], h8[2];
-    if constexpr (PA_L64_CHAIN > 0) {
-        // PA_L64_CHAIN: 1 both compares on the FMA pipe, 2 dE = 4 on the FMA
-        // pipe and dE = 8 on the ALU, 3 both on the ALU, 4 the reverse of 2
-        constexpr bool F4 = PA_L64_CHAIN == 1 || PA_L64_CHAIN == 2;
-        constexpr bool F8 = PA_L64_CHAIN == 1 || PA_L64_CHAIN == 4;
-        const uint32_t c4 = F4 ? negT4 : t4.T, c8 = F8 ? negT8 : t8.T;
-#pragma unroll 1
-        for (uint32_t q = 0; q < 2; ++q) {
-            const uint32_t base = 8u * y + 4u * q;
-            const uint32_t kc = group_tests<F4, F8, 4>(
-                [&](int h) { return philox_block(d, gen, base + (uint32_t)h); }, one, c4, c8, t4.T,
-                t8.T);
-            // site j = 4h + m: dE = 4 carry at bit 2j + 1, dE = 8 carry at bit 2j
-            constexpr uint32_t EV = 0x55555555u;
-            const uint32_t r4 = (kc >> 1) & EV, r8 = kc & EV;
-            // a carry is [u >= T]; below is its complement (T = 0 on the FMA
-            // form carries never, and nothing is below it)
-            const uint32_t b4 = (F4 && !t4.T) ? 0u : (~r4 & EV);
-            const uint32_t b8 = (F8 && !t8.T) ? 0u : (~r8 & EV);
-            if (q == 0) {
-                h4[0] = b4 << P;
-                h8[0] = b8 << P;
-            } else {
-                h4[1] = b4 << P;
-                h8[1] = b8 << P;
-            }
-        }
-        a4 = ((uint64_t)h4[1] << 32) | h4[0];
-        a8 = ((uint64_t)h8[1] << 32) | h8[0];
-    } else {
 #pragma unroll 1
     for (uint32_t q = 0; q < 2; ++q) {
-        uint32_t k4 = 0, k8 = 0, kc4 = 0, kc8 = 0;
         const uint32_t base = 8u * y + 4u * q;
-        // blocks in decreasing h so that the carry chain sees its sites in
-        // decreasing order: site j = 4h + m ends at bit 2j
-#pragma unroll
-        for (int h = 3; h >= 0; --h) {
-            const uint4 u = philox_block(d, gen, base + (uint32_t)h);
-            const uint32_t w[4] = {u.x, u.y, u.z, u.w};
-            const bool f4 = M == 1 || M == 2 || (M == 3 && h < 2);
-            const bool f8 = M == 2;
-#pragma unroll
-            for (int m = 3; m >= 0; --m) {
-                const int bit = 8 * h + 2 * m + P;
-                if (h < HC4)
-                    kc4 = carry_ge(kc4, w[m], one, negT4, four);
-                else
-                    k4 = f4 ? add_if_below<true>(k4, w[m], t4, one, bit)
-                            : add_if_below<false>(k4, w[m], t4, one, bit);
-                if (h < HC8)
-                    kc8 = carry_ge(kc8, w[m], one, negT8, four);
-                else
-                    k8 = f8 ? add_if_below<true>(k8, w[m], t8, one, bit)
-                            : add_if_below<false>(k8, w[m], t8, one, bit);
-            }
-        }
-        // carry-chain site j = 4h + m sits at bit 2j; [u >= T] inverts to
-        // [u < T], and T = 0 has nothing below it
-        if (HC4 > 0) {
-            constexpr uint32_t even = HC4 >= 4 ? 0x55555555u : ((1u << (8 * HC4)) - 1u) & 0x55555555u;
-            k4 |= (t4.T ? (~kc4 & even) : 0u) << P;
-        }
-        if (HC8 > 0) {
-            constexpr uint32_t even = HC8 >= 4 ? 0x55555555u : ((1u << (8 * HC8)) - 1u) & 0x55555555u;
-            k8 |= (t8.T ? (~kc8 & even) : 0u) << P;
-        }
+        const uint32_t kc = group_tests<F4, F8, 4>(
+            [&](int h) { return philox_block(d, gen, base + (uint32_t)h); }, one, c4, c8, t4.T,
+            t8.T);
+        // site j = 4h + m: dE = 4 carry at bit 2j + 1, dE = 8 carry at bit 2j
+        constexpr uint32_t EV = 0x55555555u;
+        const uint32_t r4 = (kc >> 1) & EV, r8 = kc & EV;
+        // a carry is [u >= T]; below is its complement (T = 0 on the FMA
+        // form carries never, and nothing is below it)
+        const uint32_t b4 = (F4 && !t4.T) ? 0u : (~r4 & EV);
+        const uint32_t b8 = (F8 && !t8.T) ? 0u : (~r8 & EV);
         if (q == 0) {
-            h4[0] = k4;
-            h8[0] = k8;
+            h4[0] = b4 << P;
+            h8[0] = b8 << P;
         } else {
-            h4[1] = k4;
-            h8[1] = k8;
+            h4[1] = b4 << P;
+            h8[1] = b8 << P;
         }
     }
     a4 = ((uint64_t)h4[1] << 32) | h4[0];
     a8 = ((uint64_t)h8[1] << 32) | h8[0];
-    }
 }
 
 // +-J couplings of one row (bit x set: J = -1) for its four bonds: to x + 1,
@@ -511,8 +403,6 @@ __device__ __forceinline__ void thresholds(const RunDev& d, uint32_t step, Thr& 
                                            uint32_t& full) {
     t4.T = d.thr[step * 4 + 0];
     t8.T = d.thr[step * 4 + 1];
-    t4.cneg = t4.T ? (0ull - (uint64_t)t4.T) : 0ull;
-    t8.cneg = t8.T ? (0ull - (uint64_t)t8.T) : 0ull;
     full = d.thr[step * 4 + 3];
 }
 
