@@ -192,6 +192,39 @@ def oracle_rate(seconds: float = None, R0=512, procs: int = 1, warmup: int = 0, 
             "resampled_replicas_per_s": rs / t_res if t_res else None}
 
 
+def _ensemble_oracle_worker(job):
+    """One oracle process on one config-4 instance (its L, couplings, seeds and
+    schedule) at a small R0: full PA steps for `seconds`.  Returns (attempts,
+    seconds)."""
+    spec, seconds, R0 = job
+    sys.path.insert(0, ROOT)
+    from oracle import oracle as O
+    sp = dict(spec)
+    sp["R0"] = R0
+    run = O.Run(O.make_config(**sp))
+    attempts, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds and run.step_index < sp["K"]:
+        assert run.step() == 0
+        attempts += run.R * sp["L"] ** 3 * sp["theta"]
+    return attempts, time.perf_counter() - t0
+
+
+def ensemble_oracle_rate(procs: int, seconds: float = 4.0, R0: int = 256) -> dict:
+    """The oracle on config 4: the first `procs` instances of the 256, one
+    single-threaded process each (spawned), each running full PA steps at
+    R0 = 256 for `seconds`; attempts/ns over the slowest process's wall time."""
+    import multiprocessing as mp
+    from paper_2006_00561_gb300 import workloads
+    specs = workloads.ea_ensemble(256, seed=4)[:procs]
+    with mp.get_context("spawn").Pool(procs) as pool:
+        res = pool.map(_ensemble_oracle_worker, [(sp, seconds, R0) for sp in specs])
+    wall = max(r[1] for r in res)
+    return {"kind": "oracle", "cores": procs, "attempts_per_ns": sum(r[0] for r in res) / wall / 1e9,
+            "sample": f"the first {procs} of the 256 instances (their L, couplings, seeds and "
+                      f"schedule), one process each, full PA steps at R0={R0} for {seconds:.0f} s",
+            "seconds": wall}
+
+
 CONFIG1 = dict(dim=2, L=16, R0=1000, K=100, theta=10, beta0=0.0, beta_max=1.0, seed=1)
 
 
@@ -694,6 +727,8 @@ def main():
                                  "resampled_replicas_per_s": r1["resampled_replicas_per_s"]},
                "host": host_info()}
         cfg1 = config1_measure(P, procs)
+        if ens:
+            ens["oracle"] = ensemble_oracle_rate(procs)
     else:
         cfg1 = None
     cfg2 = config2_measure(P) if world == 1 else None
