@@ -190,6 +190,11 @@ static_assert(PA_L64_CHAIN >= 1 && PA_L64_CHAIN <= 4, "PA_L64_CHAIN: 1 .. 4");
 // run as compare and select instead, instructions that only the ALU pipe
 // executes; the carry chains are integer adds, which the compiler may move
 // to the FMA pipe.
+// Philox blocks of a group of four unrolled together in the L = 64 kernel.
+#ifndef PA_L64_HUNROLL
+#define PA_L64_HUNROLL 4
+#endif
+
 #ifndef PA_L64_SEL_BLOCKS
 #define PA_L64_SEL_BLOCKS 0
 #endif
@@ -245,7 +250,7 @@ __device__ __forceinline__ void row_accepts(const Keys& d, const HalfSweepGen& g
 #pragma unroll 1
     for (uint32_t q = 0; q < 2; ++q) {
         const uint32_t base = 8u * y + 4u * q;
-        const uint32_t kc = group_tests<F4, F8, 4>(
+        const uint32_t kc = group_tests<F4, F8, PA_L64_HUNROLL>(
             [&](int h) { return philox_block(d, gen, base + (uint32_t)h); }, one, c4, c8, t4.T,
             t8.T);
         // site j = 4h + m: dE = 4 carry at bit 2j + 1, dE = 8 carry at bit 2j
