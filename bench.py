@@ -50,10 +50,10 @@ OPS_PER_ATTEMPT = 19.5
 # the FMA-heavy pipe (integer multiply-add), 152 SMs, 2070 MHz maximum clock.
 ALU_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12
 # DRAM bytes of one sweep launch, from the ncu capture of the same kernel at
-# 2^18 replicas (profiles/k_sweep_l64_ising2d_L64_R2p18.md: 134.50 MB read +
-# 76.06 MB written), scaled by the replica count to 2^21.  None whenever the
-# kernel changes, until the next capture.
-SWEEP_TRAFFIC_BYTES_2P21 = (134.50e6 + 76.06e6) * 8
+# 2^20 replicas, four times L2 (profiles/k_sweep_l64_ising2d_L64_R2p18.md:
+# 542.1 MB read + 484.2 MB written), scaled by the replica count to 2^21.
+# None whenever the kernel changes, until the next capture.
+SWEEP_TRAFFIC_BYTES_2P21 = (542.106368e6 + 484.178432e6) * 2
 # Slot ranges of the e2e step: each range's copy to the host (~0.7 ms at 1/8 of
 # 1 GiB) runs while the next range sweeps (~7 ms).
 E2E_CHUNKS = 8
@@ -752,7 +752,7 @@ def main():
                      "unit": "Tops/s (32-bit int)", "frac": achieved_tops / ALU_PEAK_TOPS,
                      "traffic": (SWEEP_TRAFFIC_BYTES_2P21
                                  if wl["R0"] == 1 << 21 and SWEEP_TRAFFIC_BYTES_2P21 else None),
-                     "traffic_note": "ncu dram bytes at 2^18 replicas x 8 (profiles/)",
+                     "traffic_note": "ncu dram bytes at 2^20 replicas x 2 (profiles/)",
                      "kernel": "k_sweep_l64 (theta=10 sweeps + measurement)",
                      "ops_per_attempt": OPS_PER_ATTEMPT,
                      "peak_note": "152 SMs x (64 ALU + 64 FMA-heavy) int32 lanes x 2070 MHz "
