@@ -911,6 +911,7 @@ int pa_restore(pa_run* r, const void* src, size_t bytes) {
     st.src = 0;
     st.epoch = now.epoch;
     st.tile_counter = 0;
+    st.tau_done = 0;
     st.active = 0;
     st.status = 0;
     r->init_state = st;

@@ -44,7 +44,8 @@ struct DevState {
     uint32_t negbonds;      // number of J = -1 bonds (U mod 2 = negbonds mod 2)
     double lnQ, lnZ, S;
     unsigned long long sweeps_done;
-    unsigned long long pad[3];
+    unsigned long long tau_done;  // CTAs of the running multi-CTA reweight that are done
+    unsigned long long pad[2];
 };
 static_assert(sizeof(DevState) <= 256, "DevState must fit its slot");
 

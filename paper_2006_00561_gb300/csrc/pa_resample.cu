@@ -43,9 +43,12 @@ __device__ __forceinline__ unsigned long long desc_make(unsigned long long flag,
     return (flag << 62) | ((unsigned long long)(epoch & 0x3fffffffu) << 32) | value;
 }
 
-// Reweight of one run by one 256-thread CTA (plain: k_tau, batched: one CTA
-// per run of k_tau_batched).
-__device__ __forceinline__ void tau_run(const RunDev& d) {
+// Reweight of one run by nblk 256-thread CTAs (plain: k_tau, batched: one
+// CTA per run of k_tau_batched).  Every CTA finds kref and S itself (the same
+// fixed order, so the same bits) and writes the tau entries of its share of
+// the levels; the last CTA to finish, when every CTA has read the step index
+// and R, advances the run's scalars.
+__device__ __forceinline__ void tau_run(const RunDev& d, uint32_t blk, uint32_t nblk) {
     DevState* st = d.st;
     __shared__ double part[256];
     __shared__ uint32_t s_kref;
@@ -107,7 +110,7 @@ __device__ __forceinline__ void tau_run(const RunDev& d) {
     }
     const double S = part[0];
     const double R0d = (double)d.R0;
-    for (uint32_t k = t; k < bins; k += 256) {
+    for (uint32_t k = blk * 256u + t; k < bins; k += nblk * 256u) {
         uint32_t n = 0, F = 0;
         const int64_t j = heating ? (int64_t)kref - (int64_t)k : (int64_t)k - (int64_t)kref;
         if (j >= 0) {
@@ -119,7 +122,18 @@ __device__ __forceinline__ void tau_run(const RunDev& d) {
         d.tab_n[k] = n;
         d.tab_F[k] = F;
     }
+    if (nblk > 1) {
+        __shared__ bool s_last;
+        __syncthreads();
+        if (t == 0) {
+            __threadfence();
+            s_last = atomicAdd(&st->tau_done, 1ull) == (unsigned long long)(nblk - 1);
+        }
+        __syncthreads();
+        if (!s_last) return;
+    }
     if (t == 0) {
+        st->tau_done = 0;
         if (s_sum != (unsigned long long)R) atomicOr(&st->status, ST_INVARIANT);
         const long long parity = st->negbonds & 1u;
         const long long Eref = 2 * (2 * (long long)kref + parity) - (long long)d.dim * d.N;
@@ -139,7 +153,7 @@ __device__ __forceinline__ void tau_run(const RunDev& d) {
     }
 }
 
-__global__ void __launch_bounds__(256) k_tau(RunDev d) { tau_run(d); }
+__global__ void __launch_bounds__(256) k_tau(RunDev d) { tau_run(d, blockIdx.x, gridDim.x); }
 
 // Batched reweight: CTA r handles run r, then clears that run's histogram and
 // magnetisation sums for the coming sweep (the reweight is their last
@@ -147,7 +161,7 @@ __global__ void __launch_bounds__(256) k_tau(RunDev d) { tau_run(d); }
 __global__ void __launch_bounds__(256) k_tau_batched(BatchDev b) {
     if (blockIdx.x == 0 && threadIdx.x < b.ncounters) b.counters[threadIdx.x] = 0u;
     const RunDev& d = b.runs[blockIdx.x];
-    tau_run(d);
+    tau_run(d, 0, 1);
     __syncthreads();
     for (uint32_t k = threadIdx.x; k < (uint32_t)d.bins; k += blockDim.x) d.hist[k] = 0u;
     if (threadIdx.x < 2) d.accum[threadIdx.x] = 0ull;
@@ -578,8 +592,12 @@ __global__ void __launch_bounds__(256) k_obs_batched(BatchDev b) {
 
 }  // namespace
 
+// CTAs of the plain reweight: one per 256 levels, at most 16 (the tau
+// divisions are FP64; each CTA also repeats the sum S, 16 FP64 terms a thread).
 cudaError_t launch_tau(const RunDev& d, cudaStream_t s) {
-    k_tau<<<1, 256, 0, s>>>(d);
+    const int64_t per = ((int64_t)d.bins + 255) / 256;
+    const int grid = (int)(per < 16 ? per : 16);
+    k_tau<<<grid < 1 ? 1 : grid, 256, 0, s>>>(d);
     return cudaGetLastError();
 }
 
