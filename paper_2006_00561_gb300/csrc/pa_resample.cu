@@ -1,7 +1,7 @@
 // pa_resample.cu -- reweighting and resampling of the population (Sec. 2,
 // Eq. 3 and Eq. 4) and the per-step observables (Sec. 2, Eq. 5).
 //
-//  k_tau       one CTA: the energy histogram H of the population at beta_{i-1}
+//  k_tau       up to 16 CTAs: the energy histogram H of the population at beta_{i-1}
 //              gives kref (lowest occupied level when cooling, highest when
 //              heating), S = sum_k H_k D[|k - kref|] with D[j] =
 //              exp(-|beta_i - beta_{i-1}| 4 j), Q = S exp(-dbeta E(kref)) / R
