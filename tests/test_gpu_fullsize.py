@@ -13,7 +13,8 @@
     function of its state, slot, sweep index and beta);
   * measurement: histogram == bincount(levels), integer observables == the
     sums over the dumped levels and magnetisations.
-Graph-replayed steps (pa_run_steps) run between the checked ones.
+Graph-replayed steps (pa_run_steps) run between the checked ones.  The e2e
+path's streamed step is checked at 2^21 against the graph step of a twin run.
 """
 from __future__ import annotations
 
@@ -129,3 +130,31 @@ def test_fullsize_parity_3d_pm_j(P, L, R0):
         run.run_steps(5 + 10 * c)
         assert run.status() == 0
     run.close()
+
+
+def test_fullsize_streamed_step_equals_the_graph_step(P):
+    """The e2e path at the bench size: pa_step_stream (8 slot ranges, each copied
+    to pinned host memory on a second stream while the next range sweeps)
+    gives the same run, bit for bit, as pa_run_steps on a twin run, and the
+    host copy is the whole new population."""
+    import torch
+    cfg = P.make_config(dim=2, L=64, layout=P.LAYOUT_PACKED, R0=1 << 21, K=400, theta=10,
+                        seed=3)
+    a, b = P.Run(cfg), P.Run(cfg)
+    try:
+        st = a.state()
+        host = torch.zeros(st["capacity"] * st["stride"], dtype=torch.uint8, pin_memory=True)
+        cs = torch.cuda.Stream()
+        for _ in range(2):
+            R = a.step_stream(host, 8, cs)
+            b.run_steps(1)
+            oa, ob = a.observables(), b.observables()
+            assert R == oa["R"] == ob["R"]
+            for k in ("sumE", "sumE2", "sumAbsM", "sumM2", "lnZ"):
+                assert oa[k] == ob[k], k
+            raw_a = a.dump(P.DUMP_SPINS_RAW).reshape(-1)
+            assert np.array_equal(raw_a[: R * st["stride"]], b.dump(P.DUMP_SPINS_RAW).reshape(-1)[: R * st["stride"]])
+            assert np.array_equal(host.numpy()[: R * st["stride"]], raw_a[: R * st["stride"]])
+    finally:
+        a.close()
+        b.close()
