@@ -14,7 +14,8 @@
   * measurement: histogram == bincount(levels), integer observables == the
     sums over the dumped levels and magnetisations.
 Graph-replayed steps (pa_run_steps) run between the checked ones.  The e2e
-path's streamed step is checked at 2^21 against the graph step of a twin run.
+path's streamed step is checked at 2^21 against the graph step of a twin run,
+and the whole 400-step run at 2^21 against Kaufman's exact ln Z and energy.
 """
 from __future__ import annotations
 
@@ -158,3 +159,23 @@ def test_fullsize_streamed_step_equals_the_graph_step(P):
     finally:
         a.close()
         b.close()
+
+
+def test_config3_whole_run_matches_kaufman(P):
+    """The whole paper-scale run (2D Ising L = 64, 2^21 replicas, beta 0 -> 1 in
+    400 steps, theta = 10, graph-replayed) ends at Kaufman's exact ln Z(1) and
+    <E>/N of the 64 x 64 torus.  Two seeds gave deviations of 0.009 / 0.003 in
+    ln Z and 8e-7 / 5e-7 in <E>/N; the bounds are about six times those."""
+    pytest.importorskip("mpmath")
+    import exact
+    cfg = P.make_config(dim=2, L=64, layout=P.LAYOUT_PACKED, R0=1 << 21, K=400, theta=10, seed=3)
+    run = P.Run(cfg)
+    try:
+        run.run_steps(400)
+        o = run.observables()
+    finally:
+        run.close()
+    assert o["step"] == 400 and o["beta"] == 1.0
+    assert abs(o["R"] - (1 << 21)) <= 5 * np.sqrt(1 << 21)
+    assert abs(o["lnZ"] - float(exact.kaufman_lnZ(64, 1.0))) < 0.05
+    assert abs(o["e"] - exact.kaufman_energy_per_site(64, 1.0)) < 5e-6
