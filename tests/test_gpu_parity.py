@@ -244,9 +244,12 @@ def test_graph_replay_equals_plain_steps(P):
     (dict(dim=2, L=128, layout=1, R0=150, K=8, theta=2, seed=18), 3),            # L = 128 kernel
     (dict(dim=2, L=16, layout=1, R0=1000, K=12, theta=3, seed=19), 5),           # replica-sliced
     (dict(dim=3, L=10, model=1, layout=1, R0=300, K=8, theta=2, beta_max=3.0, seed=20,
-          coupling_seed=21), 4),                                                  # row kernel
+          coupling_seed=21), 4),                                                  # replica-sliced, 3D +-J
     (dict(dim=2, L=16, layout=0, R0=700, K=10, theta=2, seed=22), 64),           # int8, ranges < 32
     (dict(dim=2, L=8, layout=1, R0=40, K=6, theta=2, seed=23), 1),
+    (dict(dim=2, L=64, layout=1, R0=900, K=10, theta=2, seed=24, resample=1), 5),  # Poisson
+    (dict(dim=3, L=8, model=1, layout=1, R0=700, K=8, theta=2, beta_max=3.0, seed=25,
+          coupling_seed=26, resample=2), 3),                                      # multinomial
 ])
 def test_streamed_step_equals_the_oracle(P, spec, chunks):
     """pa_step_stream: the sweeps of a step in slot ranges with the copy of
