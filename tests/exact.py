@@ -75,3 +75,56 @@ def boltzmann_from_dos(g: dict, beta) -> dict:
     b = mp.mpf(beta)
     Z = mp.fsum(c * mp.exp(-b * E) for E, c in g.items())
     return {E: float(c * mp.exp(-b * E) / Z) for E, c in g.items()}
+
+
+def kaufman_cv_per_site(L: int, K) -> float:
+    """Specific heat per site of the L x L torus from the thermodynamic
+    definition C = beta^2 d^2 ln Z / d beta^2, differentiated numerically
+    (60-digit arithmetic) through Kaufman's closed form."""
+    K = mp.mpf(K)
+    return float(K * K * mp.diff(lambda k: kaufman_lnZ(L, k), K, 2) / (L * L))
+
+
+def joint_dos_2d_torus(L: int) -> dict:
+    """g(E, M) of the L x L ferromagnetic torus by enumeration of all 2^(L^2)
+    states: E = -sum over the 2 L^2 bonds of s_i s_j (one term per bond,
+    periodic), M = sum of the spins.  Written with array shifts, independently
+    of any energy routine under test."""
+    S = all_states(L * L).reshape(-1, L, L).astype(np.int64)  # [state, y, x]
+    E = -(S * np.roll(S, -1, axis=2)).sum(axis=(1, 2)) - (S * np.roll(S, -1, axis=1)).sum(
+        axis=(1, 2))
+    M = S.sum(axis=(1, 2))
+    pairs, counts = np.unique(np.stack([E, M], axis=1), axis=0, return_counts=True)
+    return {(int(e), int(m)): int(c) for (e, m), c in zip(pairs, counts)}
+
+
+def exact_observables(g: dict, N: int, beta) -> dict:
+    """Boltzmann averages at inverse temperature beta > 0 from a joint density
+    of states g(E, M):
+      C_v per site   = beta^2 d^2 ln Z / d beta^2 / N (thermodynamic definition),
+      <|m|>          = sum |M| g e^{-beta E} / (N Z),
+      <M^2>          = d^2 ln Z(h) / d(beta h)^2 at h = 0, with
+                       Z(h) = sum g e^{-beta E + beta h M} (the field derivative;
+                       <M> = 0 by symmetry),
+      chi per site   = beta (<M^2> - <|M|>^2) / N, the finite-lattice
+                       susceptibility with |M| in place of M."""
+    b = mp.mpf(beta)
+    items = [(mp.mpf(E), mp.mpf(M), c) for (E, M), c in g.items()]
+
+    def lnZ_beta(bb):
+        return mp.log(mp.fsum(c * mp.exp(-bb * E) for E, M, c in items))
+
+    def lnZ_field(x):  # x = beta h
+        return mp.log(mp.fsum(c * mp.exp(-b * E + x * M) for E, M, c in items))
+
+    Z = mp.fsum(c * mp.exp(-b * E) for E, M, c in items)
+    mabs = mp.fsum(c * abs(M) * mp.exp(-b * E) for E, M, c in items) / Z
+    m2 = mp.diff(lnZ_field, mp.mpf(0), 2)
+    e = mp.fsum(c * E * mp.exp(-b * E) for E, M, c in items) / Z
+    return {
+        "e": float(e / N),
+        "cv": float(b * b * mp.diff(lnZ_beta, b, 2) / N),
+        "m_abs": float(mabs / N),
+        "m2": float(m2),
+        "chi": float(b * (m2 - mabs * mabs) / N),
+    }

@@ -54,6 +54,18 @@ MUTANTS = [
     ("init_one_word_per_block", "spins[s] = (out[s & 3] >> 31) ? -1 : 1;",
      "spins[s] = (out[0] >> 31) ? -1 : 1;", "fair_coins"),
     ("cv_sign", "(mE2 - mE * mE)", "(mE2 + mE * mE)", "observables"),
+    # observables against exact Boltzmann values (not against a restatement)
+    ("cv_missing_beta_squared", "o->cv = ((o->beta * o->beta) * (mE2 - mE * mE)) / Nd;",
+     "o->cv = (mE2 - mE * mE) / Nd;", "observables_match_bruteforce or specific_heat"),
+    ("cv_not_per_site", "o->cv = ((o->beta * o->beta) * (mE2 - mE * mE)) / Nd;",
+     "o->cv = (o->beta * o->beta) * (mE2 - mE * mE);",
+     "observables_match_bruteforce or specific_heat"),
+    ("chi_signed_mean_for_abs_mean", "o->chi = (o->beta * (mM2 - mA * mA)) / Nd;",
+     "o->chi = (o->beta * mM2) / Nd;", "observables_match_bruteforce"),
+    ("chi_missing_beta", "o->chi = (o->beta * (mM2 - mA * mA)) / Nd;",
+     "o->chi = (mM2 - mA * mA) / Nd;", "observables_match_bruteforce"),
+    ("m_abs_root_mean_square", "o->m_abs = mA / Nd;", "o->m_abs = sqrt(mM2) / Nd;",
+     "observables_match_bruteforce"),
     ("heating_uses_lowest_level",
      "{\n    int64_t kref = -1;\n    if (heating) {\n        for (int64_t k = bins - 1; k >= 0; --k)",
      "{\n    int64_t kref = -1;\n    if (heating) {\n        for (int64_t k = 0; k < bins; ++k)",

@@ -84,14 +84,23 @@ def _run_seed(args):
         o = run.observables()
         Rs.append(o["R"])
         if i in checks:
-            out[i] = (o["beta"], o["lnZ"], o["sumE"] / o["R"])
+            out[i] = (o["beta"], o["lnZ"], o["sumE"] / o["R"], o["cv"], o["m_abs"], o["chi"])
     return out, run.check_failures, Rs
 
 
+_RUNS_CACHE: dict = {}
+
+
 def _runs(kind, seeds):
-    ctx = mpc.get_context("spawn")
-    with ctx.Pool(min(len(seeds), os.cpu_count() or 1)) as pool:
-        return pool.map(_run_seed, [(kind, s) for s in seeds])
+    """Whole oracle runs of one kind, one per seed, in spawned processes; the
+    results are kept for the other tests of this module that read the same
+    runs."""
+    key = (kind, tuple(seeds))
+    if key not in _RUNS_CACHE:
+        ctx = mpc.get_context("spawn")
+        with ctx.Pool(min(len(seeds), os.cpu_count() or 1)) as pool:
+            _RUNS_CACHE[key] = pool.map(_run_seed, [(kind, s) for s in seeds])
+    return _RUNS_CACHE[key]
 
 
 def _assert_within(vals, want, p_two_sided=0.0027):
@@ -119,6 +128,18 @@ def test_pa_lnZ_and_energy_match_kaufman_L16():
         _assert_within([r[0][i][2] / 256 for r in res], exact.kaufman_energy_per_site(16, beta))
 
 
+@pytest.mark.slow
+def test_pa_specific_heat_matches_kaufman_L16():
+    """C_v per site of the config-1 population (R0 = 1000, 100 steps, theta =
+    10) at beta = 0.2, 0.44 (near the L = 16 peak) and 0.6 within 3 SE of
+    beta^2 d^2 ln Z / d beta^2 / N through Kaufman's closed form, over the same
+    20 runs as the ln Z pin."""
+    res = _runs("L16", list(range(100, 120)))
+    for i in (20, 44, 60):
+        beta = res[0][0][i][0]
+        _assert_within([r[0][i][3] for r in res], exact.kaufman_cv_per_site(16, beta))
+
+
 def _pa_vs_dos(kind, dos, pop_sigmas=2.5):
     res = _runs(kind, list(range(40, 56)))
     for out, fails, Rs in res:
@@ -139,6 +160,28 @@ def test_pa_lnZ_matches_bruteforce_2d_L4():
     J = np.ones(32, dtype=np.int8)
     dos = exact.density_of_states(2 * O.energy(2, 4, J, s)[0] - 32 for s in exact.all_states(16))
     _pa_vs_dos("L4", dos)
+
+
+@pytest.mark.slow
+def test_pa_observables_match_bruteforce_2d_L4():
+    """The population averages of Sec. 2 that the oracle reports -- specific
+    heat C_v, mean absolute magnetisation <|m|> and susceptibility chi -- within
+    3 SE of their exact Boltzmann values for the 4 x 4 torus at beta = 0.3, 0.6
+    and 1.2.  The exact values come from enumerating all 2^16 states with their
+    own energy and magnetisation (exact.joint_dos_2d_torus): C_v as
+    beta^2 d^2 ln Z / d beta^2 / N, <M^2> as the second field derivative of
+    ln Z, <|M|> as a direct Boltzmann sum; so a wrong formula for any of the
+    three (a lost beta, <M>^2 in place of <|M|>^2, a root-mean-square in place
+    of the mean of |M|) fails here, whatever the population.  The same runs
+    (16 seeds, R0 = 3000) serve the ln Z pin above."""
+    g = exact.joint_dos_2d_torus(4)
+    res = _runs("L4", list(range(40, 56)))
+    for i in res[0][0]:
+        beta = res[0][0][i][0]
+        want = exact.exact_observables(g, 16, beta)
+        _assert_within([r[0][i][3] for r in res], want["cv"])
+        _assert_within([r[0][i][4] for r in res], want["m_abs"])
+        _assert_within([r[0][i][5] for r in res], want["chi"])
 
 
 @pytest.mark.slow
