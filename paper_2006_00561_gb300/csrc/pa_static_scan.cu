@@ -35,11 +35,20 @@ struct StaticScanScratch {
 // The scratch.  Zero at load time; shared by every call in the process.
 static __device__ __align__(256) StaticScanScratch g_scan_scratch;
 
-__global__ void k_static_prepare(StaticScanScratch* s, uint32_t* total) {
-    s->tile_counter = 0;
-    s->epoch = s->epoch + 1;
-    s->status = 0;
-    *total = 0;
+// Clears the scratch a call reads before writing it: the tile counter, the
+// status bits and the descriptors of the call's tiles.  With every descriptor
+// cleared, a value left by an earlier call can never be taken as ready, even
+// once the 30-bit epoch tag has wrapped.
+__global__ void k_static_prepare(StaticScanScratch* s, uint32_t tiles, uint32_t* total) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < tiles;
+         i += gridDim.x * blockDim.x)
+        s->desc[i] = 0ull;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        s->tile_counter = 0;
+        s->epoch = s->epoch + 1;
+        s->status = 0;
+        *total = 0;
+    }
 }
 
 __device__ __forceinline__ void ss_store(unsigned long long* p, unsigned long long v) {
@@ -160,24 +169,81 @@ __global__ void __launch_bounds__(SS_THREADS)
     }
 }
 
-// Device address of the scratch, looked up once per device (host code may not
-// use the symbol itself as a pointer: on the host it only names the array).
+// Device address of the scratch in the current context.  Host code may not use
+// the symbol itself as a pointer: on the host it only names the array.  The
+// address belongs to the context that loaded the module, so it is cached per
+// context, keyed by the driver's context id, which is unique for the life of
+// the process: a caller running in its own (non-primary) context, or a
+// primary context re-created after cudaDeviceReset, gets a fresh lookup.
+// The two driver calls are reached through the runtime's entry-point query,
+// so the library does not link libcuda itself.
+typedef int (*CtxGetCurrentFn)(void** ctx);
+typedef int (*CtxGetIdFn)(void* ctx, unsigned long long* id);
+
+struct ScratchCacheEntry {
+    unsigned long long ctx_id;
+    void* addr;
+};
+constexpr int SCRATCH_CACHE = 16;
 std::mutex g_mu;
-void* g_addr[64] = {nullptr};
+ScratchCacheEntry g_cache[SCRATCH_CACHE];
+int g_cache_used = 0, g_cache_next = 0;
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+
+cudaError_t current_context_id(unsigned long long* id) {
+    if (!g_ctx_get_current || !g_ctx_get_id) {
+        void* f0 = nullptr;
+        void* f1 = nullptr;
+        cudaDriverEntryPointQueryResult q0, q1;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000,
+                                                         cudaEnableDefault, &q0);
+        if (e != cudaSuccess || q0 != cudaDriverEntryPointSuccess || !f0)
+            return e != cudaSuccess ? e : cudaErrorNotSupported;
+        e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault, &q1);
+        if (e != cudaSuccess || q1 != cudaDriverEntryPointSuccess || !f1)
+            return e != cudaSuccess ? e : cudaErrorNotSupported;
+        g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f0);
+        g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f1);
+    }
+    void* ctx = nullptr;
+    if (g_ctx_get_current(&ctx) != 0 || !ctx) return cudaErrorDeviceUninitialized;
+    if (g_ctx_get_id(ctx, id) != 0) return cudaErrorDeviceUninitialized;
+    return cudaSuccess;
+}
 
 cudaError_t scratch_address(void** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
+    unsigned long long id = 0;
+    cudaError_t e = current_context_id(&id);
+    if (e == cudaErrorDeviceUninitialized) {
+        // no context is current yet: the symbol lookup makes the runtime bind
+        // the device's primary context, after which the id can be read
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_scan_scratch);
         if (e != cudaSuccess) return e;
-        g_addr[dev] = p;
+        e = current_context_id(&id);
     }
-    *out = g_addr[dev];
+    if (e != cudaSuccess) return e;
+    for (int i = 0; i < g_cache_used; ++i) {
+        if (g_cache[i].ctx_id == id) {
+            *out = g_cache[i].addr;
+            return cudaSuccess;
+        }
+    }
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_scan_scratch);
+    if (e != cudaSuccess) return e;
+    int slot;
+    if (g_cache_used < SCRATCH_CACHE) {
+        slot = g_cache_used++;
+    } else {  // evict the oldest entry
+        slot = g_cache_next;
+        g_cache_next = (g_cache_next + 1) % SCRATCH_CACHE;
+    }
+    g_cache[slot].ctx_id = id;
+    g_cache[slot].addr = p;
+    *out = p;
     return cudaSuccess;
 }
 
@@ -200,10 +266,11 @@ extern "C" int pa_copy_counts_scan_noalloc(const uint32_t* d_ebin, int64_t R,
     if (pa::scratch_address(&addr) != cudaSuccess) return PA_ERR_CUDA;
     auto* s = static_cast<pa::StaticScanScratch*>(addr);
     cudaStream_t st = (cudaStream_t)stream;
-    pa::k_static_prepare<<<1, 1, 0, st>>>(s, d_total);
+    const uint32_t tiles = (uint32_t)((R + pa::SS_TILE - 1) / pa::SS_TILE);
+    pa::k_static_prepare<<<(tiles + 1023) / 1024 > 0 ? (tiles + 1023) / 1024 : 1, 1024, 0, st>>>(
+        s, tiles, d_total);
     if (cudaGetLastError() != cudaSuccess) return PA_ERR_CUDA;
     if (R == 0) return PA_OK;
-    const uint32_t tiles = (uint32_t)((R + pa::SS_TILE - 1) / pa::SS_TILE);
     const uint32_t ctr3 = (pa::TAG_RESAMPLE << 28) | (uint32_t)instance_id;
     pa::k_static_counts_scan<<<tiles, pa::SS_THREADS, 0, st>>>(
         s, d_ebin, (uint32_t)R, d_tab_n, d_tab_F, (uint32_t)bins, (uint32_t)step, ctr3,

@@ -4,10 +4,14 @@ capture, plugins whose host process owns every allocation, fixed-budget
 embedded callers).  Its scratch is a static device array inside the library,
 so the caller passes only inputs and outputs.
 
-Checked through the C ABI against the regular resample (pa_resample), which
-computes the same counts and offsets with scratch from the run's workspace:
-integers, so bit for bit, on two calls in a row (the second call reuses the
-static scratch the first one left behind)."""
+Checked through the C ABI, bit for bit (integers), on two calls in a row (the
+second call reuses the static scratch the first one left behind):
+  * against the CPU oracle's copy counts (or_copy_counts, the nearest-integer
+    rule of the resampling step) and the exclusive cumulative sum of those
+    counts, for a population of a real run and for R = 300 000 replicas with
+    synthetic levels and tables (about 150 scan tiles, so the lookback spans
+    many tiles);
+  * against the regular resample (pa_resample) on the same population."""
 from __future__ import annotations
 
 import numpy as np
@@ -26,16 +30,36 @@ def P():
 
 def _dev(a: np.ndarray):
     import torch
-    return torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).cuda()
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint32).view(np.int32)).cuda()
 
 
-def test_noalloc_counts_and_offsets_match_resample_two_calls(P):
+def _oracle_counts(seed, instance_id, step, ebin, n, F):
+    from oracle import oracle as O
+    cfg = O.make_config(seed=seed, instance_id=instance_id)
+    r = O.copy_counts(cfg, step, ebin, n, F)
+    o = np.zeros_like(r)
+    np.cumsum(r[:-1], out=o[1:], dtype=np.uint32)
+    return r, o, int(r.astype(np.int64).sum())
+
+
+def _call(P, ebin, n, F, seed, step, instance_id, counts, offsets, total):
+    import torch
+    d_ebin, d_n, d_F = _dev(ebin), _dev(n), _dev(F)
+    P.pa_copy_counts_scan_noalloc(d_ebin.data_ptr(), ebin.size, d_n.data_ptr(), d_F.data_ptr(),
+                                  n.size, seed, step, instance_id, counts.data_ptr(),
+                                  offsets.data_ptr(), total.data_ptr(),
+                                  torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    R = ebin.size
+    return (counts[:R].cpu().numpy().view(np.uint32), offsets[:R].cpu().numpy().view(np.uint32),
+            int(total.cpu().numpy().view(np.uint32)[0]))
+
+
+def test_noalloc_counts_and_offsets_match_oracle_and_resample_two_calls(P):
     import torch
     cfg = P.make_config(dim=2, L=16, layout=P.LAYOUT_PACKED, R0=5000, K=20, theta=2,
                         beta_max=1.5, seed=21, instance_id=7)
     run = P.Run(cfg)
-    stream = torch.cuda.current_stream()
-    bins = P.pa_num_bins(cfg.dim, cfg.L)
     cap = run.state()["capacity"]
     counts = torch.full((cap,), -1, dtype=torch.int32, device="cuda")
     offsets = torch.full((cap,), -1, dtype=torch.int32, device="cuda")
@@ -47,21 +71,39 @@ def test_noalloc_counts_and_offsets_match_resample_two_calls(P):
         run.resample()
         st = run.state()
         assert st["status_bits"] == 0
-        want_counts = run.dump(P.DUMP_COUNTS)
-        want_offsets = run.dump(P.DUMP_OFFSETS)
-        d_ebin, d_n, d_F = _dev(ebin), _dev(run.dump(P.DUMP_TAB_N)), _dev(run.dump(P.DUMP_TAB_F))
-        P.pa_copy_counts_scan_noalloc(d_ebin.data_ptr(), R, d_n.data_ptr(), d_F.data_ptr(), bins,
-                                      cfg.seed, st["step"], cfg.instance_id, counts.data_ptr(),
-                                      offsets.data_ptr(), total.data_ptr(), stream.cuda_stream)
-        torch.cuda.synchronize()
-        got_counts = counts[:R].cpu().numpy().view(np.uint32)
-        got_offsets = offsets[:R].cpu().numpy().view(np.uint32)
-        assert np.array_equal(got_counts, want_counts), f"call {call}"
-        assert np.array_equal(got_offsets, want_offsets), f"call {call}"
-        assert int(total.item()) == st["R"], f"call {call}"
+        n, F = run.dump(P.DUMP_TAB_N), run.dump(P.DUMP_TAB_F)
+        got_r, got_o, got_total = _call(P, ebin, n, F, cfg.seed, st["step"], cfg.instance_id,
+                                        counts, offsets, total)
+        want_r, want_o, want_total = _oracle_counts(cfg.seed, cfg.instance_id, st["step"], ebin,
+                                                    n, F)
+        assert np.array_equal(got_r, want_r), f"call {call}: counts differ from the oracle"
+        assert np.array_equal(got_o, want_o), f"call {call}: offsets differ from the cumsum"
+        assert got_total == want_total == st["R"], f"call {call}"
+        assert np.array_equal(got_r, run.dump(P.DUMP_COUNTS)), f"call {call}"
+        assert np.array_equal(got_o, run.dump(P.DUMP_OFFSETS)), f"call {call}"
         assert R > 2048  # more than one scan tile
         run.sweep(cfg.theta)
     run.close()
+
+
+def test_noalloc_many_tiles_match_oracle_two_calls(P):
+    """R = 300 000 synthetic replicas (levels and tables from a seeded numpy
+    generator), about 150 scan tiles, two calls with different inputs."""
+    import torch
+    R, bins = 300_000, 4097
+    counts = torch.full((R,), -1, dtype=torch.int32, device="cuda")
+    offsets = torch.full((R,), -1, dtype=torch.int32, device="cuda")
+    total = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    rng = np.random.default_rng(2006)
+    for call, (seed, step, inst) in enumerate(((3, 17, 0), (0x123456789ABCDEF, 401, 5))):
+        ebin = rng.integers(0, bins, size=R, dtype=np.uint32)
+        n = rng.integers(0, 3, size=bins, dtype=np.uint32)
+        F = rng.integers(0, 1 << 32, size=bins, dtype=np.uint64).astype(np.uint32)
+        got_r, got_o, got_total = _call(P, ebin, n, F, seed, step, inst, counts, offsets, total)
+        want_r, want_o, want_total = _oracle_counts(seed, inst, step, ebin, n, F)
+        assert np.array_equal(got_r, want_r), f"call {call}: counts differ from the oracle"
+        assert np.array_equal(got_o, want_o), f"call {call}: offsets differ from the cumsum"
+        assert got_total == want_total, f"call {call}"
 
 
 def test_noalloc_rejects_sizes_above_its_static_scratch(P):
