@@ -310,17 +310,51 @@ def host_info() -> dict:
     return info
 
 
-def ensemble_compare(P, steps: int, tune_cache=None) -> dict:
+def _ensemble_oracle_twin(job):
+    """The oracle's run of one config-4 instance at its full size, for the
+    steps the GPU arms take; returns its observables and a hash of its spins
+    after the last step."""
+    spec, steps = job
+    sys.path.insert(0, ROOT)
+    import hashlib
+    from oracle import oracle as O
+    run = O.Run(O.make_config(**spec))
+    for _ in range(steps):
+        assert run.step() == 0
+    o = run.observables()
+    return {"step": run.step_index, "R": o["R"], "sumE": o["sumE"], "lnZ": o["lnZ"],
+            "spins_sha": hashlib.sha256(run.spins().tobytes()).hexdigest()[:16]}
+
+
+def _spins_sha(run) -> str:
+    import hashlib
+    return hashlib.sha256(run.spins().tobytes()).hexdigest()[:16]
+
+
+def ensemble_compare(P, steps: int, tune_cache=None, oracle_pool=None) -> dict:
     """Config 4: 256 +-J instances (L in {6,8,10}, R0 in {2^14..2^16}, beta
     0 -> 3, K = 150, theta = 10) stepped plain (four launches per run per step)
-    and batched (one CUDA graph per step, autotuned sweep shapes).  Both sets
-    start from the same seeds; throughput = attempts / device time."""
+    and batched (one CUDA graph per step, autotuned sweep shapes).  Both arms
+    start from fresh runs of the same seeds, take one untimed step, and time
+    the same steps 2 .. steps + 1; throughput = attempts / device time.  The
+    autotuner runs first on a throwaway copy of the ensemble, so its timed
+    steps do not shift the batched arm's step range.  Parity: after the timed
+    steps the sampled instances hold the same spins in both arms, and the
+    smallest instance equals the oracle's run (started in `oracle_pool` before
+    the GPU work).  Breakdown: device time per phase of two more batched steps
+    (reweight, resample, sweep classes, observables)."""
     import torch
     from paper_2006_00561_gb300 import autotune, workloads
     specs = workloads.ea_ensemble(256, seed=4)
     stream = torch.cuda.Stream()
     out = {"workload": "256 3D +-J EA instances, L in {6,8,10}, R0 in {2^14,2^15,2^16}, "
-                       "beta 0->3, K=150, theta=10 (numpy PCG64 seed 4)"}
+                       "beta 0->3, K=150, theta=10 (numpy PCG64 seed 4)",
+           "timed_steps": f"2..{steps + 1} in both arms"}
+    sample = sorted({0, 37, 101, 163, 255} | {min(range(len(specs)),
+                    key=lambda i: (specs[i]["L"] ** 3 * specs[i]["R0"], i))})
+    twin = min(range(len(specs)), key=lambda i: (specs[i]["L"] ** 3 * specs[i]["R0"], i))
+    twin_job = oracle_pool.apply_async(_ensemble_oracle_twin, ((specs[twin], steps + 1),)) \
+        if oracle_pool is not None else None
 
     def attempts(runs, first, n):
         tot = 0
@@ -329,12 +363,23 @@ def ensemble_compare(P, steps: int, tune_cache=None) -> dict:
             tot += sum(x["R"] for x in h) * sp["L"] ** 3 * sp["theta"]
         return tot
 
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    # autotuner on a throwaway copy of the ensemble
+    tmp = [P.Run(P.make_config(layout=P.LAYOUT_PACKED, **sp), stream=stream) for sp in specs]
+    tb = P.Batch(tmp, stream=stream)
+    tuned = autotune.tune(tb, steps_left=specs[0]["K"], cache_path=tune_cache)
+    tb.close()
+    for r in tmp:
+        r.close()
+    del tmp, tb
+    torch.cuda.empty_cache()
+
+    # plain arm
     plain = [P.Run(P.make_config(layout=P.LAYOUT_PACKED, **sp), stream=stream) for sp in specs]
     for r in plain:
         r.step()
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    first = plain[0].state()["step"] + 1
     e0.record(stream)
     for _ in range(steps):
         for r in plain:
@@ -342,64 +387,111 @@ def ensemble_compare(P, steps: int, tune_cache=None) -> dict:
     e1.record(stream)
     torch.cuda.synchronize()
     ms_plain = e0.elapsed_time(e1)
-    a_plain = attempts(plain, first, steps)
+    a_plain = attempts(plain, 2, steps)
+    plain_sha = {i: _spins_sha(plain[i]) for i in sample}
+    plain_obs = {i: plain[i].observables() for i in sample}
     for r in plain:
         r.close()
     del plain
     torch.cuda.empty_cache()
 
+    # batched arm, with the tuned shapes
     runs = [P.Run(P.make_config(layout=P.LAYOUT_PACKED, **sp), stream=stream) for sp in specs]
     batch = P.Batch(runs, stream=stream)
-    tuned = autotune.tune(batch, steps_left=specs[0]["K"] - steps - 2, cache_path=tune_cache)
-    batch.run_steps(1)
+    for ci, shape in tuned["shapes"].items():
+        batch.set_shape(ci, shape[0], shape[1])
+    batch.run_steps(1)  # also captures the step's graph
     assert batch.sync() == 0
-    first = runs[0].state()["step"] + 1
     torch.cuda.synchronize()
     e0.record(stream)
     batch.run_steps(steps)
     e1.record(stream)
     assert batch.sync() == 0
     ms_b = e0.elapsed_time(e1)
-    a_b = attempts(runs, first, steps)
+    a_b = attempts(runs, 2, steps)
+    same = all(_spins_sha(runs[i]) == plain_sha[i] and
+               runs[i].observables()["lnZ"] == plain_obs[i]["lnZ"] for i in sample)
+    twin_gpu = {"step": runs[twin].observables()["step"], "sha": _spins_sha(runs[twin]),
+                "obs": runs[twin].observables()}
+    # phase breakdown of two more (non-graph) batched steps
+    batch.profile(True)
+    batch.profile_read(reset=True)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(2):
+        batch.step()
+    t1.record(stream)
+    prof = batch.profile_read(reset=True)
+    batch.profile(False)
+    assert batch.sync() == 0
+    ms_two = t0.elapsed_time(t1)
+    phases = {k: prof[k] / max(prof["steps"], 1) for k in ("reweight", "resample", "sweep", "obs")}
+    step_ms = ms_two / 2
     out.update({
         "plain_attempts_per_ns": a_plain / (ms_plain * 1e6),
         "batched_attempts_per_ns": a_b / (ms_b * 1e6),
-        "plain_ms_per_step": ms_plain / steps, "batched_ms_per_step": ms_b / steps,
         "speedup": (a_b / ms_b) / (a_plain / ms_plain),
+        "plain_ms_per_step": ms_plain / steps, "batched_ms_per_step": ms_b / steps,
         "launches_per_step": {"plain": 4 * len(specs), "batched": 3 + len(batch.classes())},
-        "autotune": {"choice": tuned["choice"], "steps_used": tuned["steps_used"],
-                     "classes": batch.classes()},
+        "phase_ms_per_step": phases,
+        "non_sweep_share": 1.0 - phases["sweep"] / step_ms,
+        "autotune": {"shapes": {str(k): v for k, v in tuned["shapes"].items()},
+                     "steps_used": tuned["steps_used"]},
+        "parity": {"sampled_instances": sample, "batched_equals_plain": bool(same)},
         "replicas": sum(r.state()["R"] for r in runs),
     })
+    if twin_job is not None:
+        o = twin_job.get()
+        g = twin_gpu["obs"]
+        out["parity"]["oracle_instance"] = twin
+        out["parity"]["batched_equals_oracle"] = bool(
+            o["spins_sha"] == twin_gpu["sha"] and o["step"] == twin_gpu["step"] and
+            o["R"] == g["R"] and o["sumE"] == g["sumE"] and
+            abs(o["lnZ"] - g["lnZ"]) <= 1e-12 * abs(o["lnZ"]))
     batch.close()
     for r in runs:
         r.close()
     return out
 
 
-def serving_measure(P, n: int = 48, rates=(400.0, 40.0)) -> dict:
-    """Config 5 in miniature: the serving mix (2D L in {16,32,64,128}, 3D +-J
-    L in {6,8,10}, beta_max in {1,3}, theta = 10, Poisson arrivals) with R0 =
-    2^U, U in 8..14 and K in 25..75 (the full trace's R0 2^12..2^18 and K
-    100..300 scaled down so a run ends in seconds).  Served through the
-    continuous-batching loop with an HBM budget of 8 GB, at an offered rate
-    above and one below the GPU's capacity."""
+def serving_measure(P, prefix: int = 24) -> dict:
+    """Config 5: the first `prefix` requests of the 256-request trace (Poisson
+    arrivals at 50 req/s, seed 5; the 7 (dim, L) classes, R0 = 2^12..2^18, K =
+    100..300, beta_max in {1, 3}, theta = 10), served in real time under a
+    64 GiB HBM budget twice: by the pipelined server (two quanta in flight,
+    admission and batch building while the device runs) and by the
+    synchronous one (the device idles during every host phase).  Then a
+    sub-saturating load: the miniature mix (R0 = 2^8..2^14, K = 25..75) at
+    40 req/s, pipelined.  Reported per run: latency p50 / p99, offered and
+    served attempts/ns, the GPU-idle fraction between the first quantum's
+    start and the last one's end."""
     from paper_2006_00561_gb300 import serve, workloads
-    out = {"workload": f"{n} requests, serving mix, R0=2^8..2^14, K=25..75, theta=10",
-           "hbm_budget_bytes": 8 << 30}
-    for rate in rates:
-        trace = workloads.serving_trace(n, rate=rate, seed=5, R0_exp=(8, 14), K_range=(25, 75))
-        offered = sum(t["R0"] * t["L"] ** t["dim"] * t["theta"] * t["K"] for t in trace)
-        span = trace[-1]["arrival"]
-        srv = serve.Server(hbm_budget=8 << 30, quantum=4)
-        st = srv.run_trace(trace)
-        out[f"rate_{int(rate)}_per_s"] = {
-            "offered_attempts_per_ns": offered / (span * 1e9),
-            "served_attempts_per_ns": st.get("served_attempts_per_ns"),
-            "p50_latency_s": st.get("p50_latency_s"), "p99_latency_s": st.get("p99_latency_s"),
-            "served": st["served"], "max_resident": st["max_resident"],
-            "iterations": st["iterations"], "wall_s": st["wall_s"],
-            "host_phase_s": st["host_phase_s"]}
+    full = workloads.serving_trace(256, rate=50.0, seed=5)
+    trace = full[:prefix]
+    offered = sum(t["R0"] * t["L"] ** t["dim"] * t["theta"] * t["K"] for t in trace)
+    span = trace[-1]["arrival"]
+    out = {"workload": f"the first {prefix} requests of the 256-request trace (50 req/s, seed "
+                       "5; R0 2^12..2^18, K 100..300, theta 10), 64 GiB budget",
+           "offered_attempts_per_ns": offered / (span * 1e9), "arrival_span_s": span}
+
+    def summary(st):
+        return {k: st.get(k) for k in ("served", "served_attempts_per_ns", "p50_latency_s",
+                                       "p99_latency_s", "max_resident", "iterations", "wall_s",
+                                       "gpu_idle_fraction", "device_busy_s")}
+    for name, cls in (("pipelined", serve.PipelinedServer), ("sync", serve.Server)):
+        srv = cls(hbm_budget=64 << 30, quantum=8)
+        st = srv.run_trace([dict(t) for t in trace])
+        out[name] = summary(st)
+        if name == "sync":
+            out[name]["host_phase_s"] = st["host_phase_s"]
+        del srv
+    mini = workloads.serving_trace(48, rate=40.0, seed=5, R0_exp=(8, 14), K_range=(25, 75))
+    srv = serve.PipelinedServer(hbm_budget=8 << 30, quantum=4)
+    st = srv.run_trace(mini)
+    off_mini = sum(t["R0"] * t["L"] ** t["dim"] * t["theta"] * t["K"] for t in mini)
+    out["miniature_40_per_s"] = dict(summary(st), offered_attempts_per_ns=off_mini /
+                                     (mini[-1]["arrival"] * 1e9))
     return out
 
 
@@ -447,7 +539,7 @@ def next_items_measure(P, steps: int = 5, R0: int = WORKLOAD["R0"]) -> dict:
             "attempts_per_ns": att / (ms * 1e6), "ms_per_step": ms / steps,
             "resample_ms": prof["resample"][1] / max(prof["resample"][0], 1),
             "k_tau_ms": prof["tau"][1] / max(prof["tau"][0], 1),
-            "R_per_step": [x["R"] for x in h[1:]]}
+            "R_min_max": [min(x["R"] for x in h[1:]), max(x["R"] for x in h[1:])]}
         if name == "multinomial":
             run.close()
 
@@ -498,7 +590,8 @@ def next_items_measure(P, steps: int = 5, R0: int = WORKLOAD["R0"]) -> dict:
         betas.append(b)
     run.observables()
     out["adaptive"] = {"target": 0.9, "decision_ms": statistics.median(dec),
-                       "step_wall_ms": statistics.median(wall), "betas": betas,
+                       "step_wall_ms": statistics.median(wall),
+                       "beta_first_last": [betas[0], betas[-1]],
                        "bins": P.pa_num_bins(2, 64)}
     run.close()
     return out
@@ -560,6 +653,56 @@ def philox_ceiling(P, sweep_attempts_per_ns: float) -> dict:
                     "16 warps per SM, outputs xor-folded: the generator's ceiling"}
 
 
+# (name, kind, 32-bit int ops per chain step, instructions per chain step):
+# a three-input logic op or a 32-bit multiply-add counts one op, a 32 x 32 ->
+# 64 multiply two (its high and low products)
+INTOPS_KINDS = (("lop3", 0, 1, 1), ("imad", 1, 1, 1), ("mad_wide", 2, 2, 1),
+                ("lop3+imad", 3, 1, 1), ("lop3+mad_wide", 4, 1.5, 1),
+                ("mul_wide+xor", 5, 3, 2))
+# Philox4x32-10 multiplies per attempt in the register sweep kernels: 16 of a
+# block's 20 products are formed per block (the rest are shared by every
+# block of a half-sweep), and a block serves 4 attempts
+MULTIPLIES_PER_ATTEMPT = 4.0
+
+
+def int_peaks(P, iters: int = 20000, reps: int = 3) -> dict:
+    """Integer throughput of this GPU, measured (pa_bench_intops): independent
+    chains of one instruction kind on every resident thread of every SM, CUDA
+    events on the launching stream.  Per kind: thread-instructions per second
+    and 32-bit integer ops per second in the sweep's own counting (a
+    three-input logic op or a 32-bit multiply-add is one op, a 32 x 32 -> 64
+    multiply two).  The interleaved lop3 + mad.wide stream is the instruction
+    mix of a Philox round, the bulk of the sweep kernel's work; its op rate is
+    the peak the sweep roofline is reported against."""
+    import torch
+    n = P.pa_bench_intops_threads()
+    per = P.pa_bench_intops_per_iter()
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = {}
+    for name, kind, ops_per_step, inst_per_step in INTOPS_KINDS:
+        P.pa_bench_intops(kind, iters // 10, out.data_ptr(), n, s.cuda_stream)  # warm-up
+        torch.cuda.synchronize()
+        e0.record(s)
+        for _ in range(reps):
+            P.pa_bench_intops(kind, iters, out.data_ptr(), n, s.cuda_stream)
+        e1.record(s)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        steps = n * iters * per
+        res[name] = {"tinst_per_s": steps * inst_per_step / (ms * 1e-3) / 1e12,
+                     "tops": steps * ops_per_step / (ms * 1e-3) / 1e12, "ms": ms}
+    res["threads"] = n
+    res["unit"] = "T per s (thread-instructions, 32-bit int ops)"
+    best = max((k for k, *_ in INTOPS_KINDS), key=lambda k: res[k]["tops"])
+    res["peak_kind"] = best
+    res["peak_tops"] = res[best]["tops"]
+    # 32 x 32 -> 64 products per second: one per mul_wide+xor step
+    res["multiply_peak_t_per_s"] = res["mul_wide+xor"]["tops"] / 3.0
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -577,10 +720,15 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
 
-    import numpy as np
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    ens_pool = None
+    if not args.no_ensemble and world == 1:
+        # the oracle's twin of one config-4 instance runs beside the GPU work
+        import multiprocessing as mp
+        ens_pool = mp.get_context("spawn").Pool(1)
+
     import torch
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
@@ -629,6 +777,7 @@ def main():
     # ---- timed region 2: plain launches with per-kernel events -------------
     P.pa_profile(run.h, True)
     P.pa_profile_read(run.h, reset=True)
+    sources0 = run.state()["sources"]
     first2 = run.state()["step"] + 1
     barrier()
     e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -651,13 +800,16 @@ def main():
     sweep_attempts_per_launch = attempts2 / max(n_sw, 1)
     achieved_tops = OPS_PER_ATTEMPT * sweep_attempts_per_launch / (sweep_ms * 1e-3) / 1e12
     resampled_per_s = resampled2 / ((prof["tau"][1] + prof["resample"][1]) * 1e-3)
-    # resample traffic per input replica (bytes): ebin read 4, counts/offsets
-    # write 8, source spins+ebin+mag read once per surviving replica, output
-    # spins + ebin + mag written once per slot
-    stride = run.state()["stride"]
+    # resample traffic (bytes per launch): per input replica the level read (4)
+    # and the count and offset writes (8); per surviving source (copy count >
+    # 0, counted on the device) its spins, level and magnetisation read once;
+    # per output slot spins, level and magnetisation written once
+    st_after = run.state()
+    stride = st_after["stride"]
+    sources = (st_after["sources"] - sources0) / args.steps
     R_in = resampled2 / args.steps
     R_out = sum(Rs2[1:]) / args.steps
-    res_bytes = R_in * 12 + R_in * (stride + 8) * 0.75 + R_out * (stride + 8)
+    res_bytes = R_in * 12 + sources * (stride + 8) + R_out * (stride + 8)
     peaks = load_peaks()
     hbm = peaks.get("hbm_gbs", 6778.0)
     res_gbs = res_bytes / (res_ms * 1e-3) / 1e9
@@ -699,9 +851,16 @@ def main():
     del run
     torch.cuda.empty_cache()
     rng_ceiling = philox_ceiling(P, sweep_attempts_per_launch / (sweep_ms * 1e6))
+    ipk = int_peaks(P)
+    int_peak = ipk["peak_tops"]
+    sweep_rate = sweep_attempts_per_launch / (sweep_ms * 1e6)  # attempts/ns
+    mult_rate = sweep_rate * MULTIPLIES_PER_ATTEMPT / 1e3  # T products/s
+    mult_peak = max(ipk["multiply_peak_t_per_s"], rng_ceiling["uniforms_per_ns"] / 1e3)
     ens = srv = nxt = None
     if not args.no_ensemble and world == 1:
-        ens = ensemble_compare(P, steps=3)
+        ens = ensemble_compare(P, steps=20, oracle_pool=ens_pool)
+        ens_pool.close()
+        ens_pool.join()
     if not args.no_serving and world == 1:
         srv = serving_measure(P)
     if not args.no_next and world == 1:
@@ -748,20 +907,30 @@ def main():
                     "note": "one CUDA graph per step (pa_run_steps)"},
         "kernels_ms_per_step": {k: (v[1] / max(v[0], 1)) for k, v in prof.items()},
         "sweep_attempts_per_ns_kernel": sweep_attempts_per_launch / (sweep_ms * 1e6),
-        "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": ALU_PEAK_TOPS,
-                     "unit": "Tops/s (32-bit int)", "frac": achieved_tops / ALU_PEAK_TOPS,
+        "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": int_peak,
+                     "unit": "Tops/s (32-bit int)", "frac": achieved_tops / int_peak,
                      "traffic": (SWEEP_TRAFFIC_BYTES_2P21
                                  if wl["R0"] == 1 << 21 and SWEEP_TRAFFIC_BYTES_2P21 else None),
                      "traffic_note": "ncu dram bytes at 2^20 replicas x 2 (profiles/)",
                      "kernel": "k_sweep_l64 (theta=10 sweeps + measurement)",
                      "ops_per_attempt": OPS_PER_ATTEMPT,
-                     "peak_note": "152 SMs x (64 ALU + 64 FMA-heavy) int32 lanes x 2070 MHz "
-                                  "(derived from unit counts and the maximum clock)"},
+                     "peak_note": "measured in this run: the fastest 32-bit integer op "
+                                  "stream of pa_bench_intops (int_peaks.peak_kind; of measured)",
+                     "derived_peak": ALU_PEAK_TOPS,
+                     "frac_of_derived": achieved_tops / ALU_PEAK_TOPS,
+                     "multiply_bound": {
+                         "achieved_t_products_per_s": mult_rate,
+                         "peak_t_products_per_s": mult_peak, "frac": mult_rate / mult_peak,
+                         "note": "the sweep's Philox multiplies (4 per attempt) against the "
+                                 "fastest measured 32x32->64 product rate (mul.wide+xor chains "
+                                 "or the generator alone, whichever is higher)"}},
+        "int_peaks": ipk,
         "philox_ceiling": rng_ceiling,
         "resample_roofline": {"bound": "hbm", "achieved": res_gbs, "peak": hbm, "unit": "GB/s",
                               "frac": res_gbs / hbm, "traffic": None,
                               "kernel": "k_resample (counts + lookback scan + gather)",
                               "bytes_per_launch": res_bytes,
+                              "sources_per_launch": sources, "R_in": R_in, "R_out": R_out,
                               "peak_note": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
         # kernels inside the headline timed region: k_tau, k_resample, the sweep
         # kernel and k_obs per graph-replayed step
@@ -770,18 +939,20 @@ def main():
     }
     if e2e:
         line["e2e"] = e2e
-    if ens:
-        line["batched_ensemble"] = ens
-    if srv:
-        line["serving"] = srv
-    if nxt:
-        line["next_items"] = nxt
     if cpu:
         line["cpu_baseline"] = cpu
+    if nxt:
+        line["next_items"] = nxt
     if cfg1:
         line["config1"] = cfg1
     if cfg2:
         line["config2"] = cfg2
+    if srv:
+        line["serving"] = srv
+    # last, so that the end of the line (what a log tail keeps) holds the
+    # batched-over-plain comparison of config 4 and its parity
+    if ens:
+        line["batched_ensemble"] = ens
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

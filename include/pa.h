@@ -141,8 +141,11 @@ int pa_init(const pa_config* cfg, void* dev_workspace, size_t bytes, void* strea
 
 /* Step i = current + 1 of the annealing (beta_{i-1} -> beta_i), first half:
  * energy histogram -> Q (Eq. 3) and the per-energy tau table (Eq. 4) ->
- * nearest-integer copy counts r_j = floor(tau) + [u_j < frac(tau)] ->
- * exclusive scan -> gather of exact copies into the other population buffer.
+ * copy counts r_j by the rule pa_config.resample selects (Sec. 2's
+ * resampling step): PA_RESAMPLE_NEAREST, r_j = floor(tau) + [u_j < frac(tau)];
+ * PA_RESAMPLE_POISSON, r_j ~ Poisson(tau), the draw Sec. 2 prescribes;
+ * PA_RESAMPLE_MULTINOMIAL, R0 independent draws weighted by tau -> exclusive
+ * scan -> gather of exact copies into the other population buffer.
  * Asynchronous on the run's stream; needs a measured population (a sweep,
  * possibly of 0 sweeps, since the last resample). */
 int pa_resample(pa_run* run);
@@ -151,6 +154,33 @@ int pa_resample(pa_run* run);
  * energy/magnetisation of every replica, the energy histogram and the
  * observables record of step i.  nsweeps = 0 only measures.  Asynchronous. */
 int pa_sweep(pa_run* run, int32_t nsweeps);
+
+/* Redistribution of the population between virtual GPUs (Sec. 3: after the
+ * resampling step the replicas are exchanged so that every GPU holds about
+ * R / N of them, by the main block algorithm or the naive per-replica one).
+ * On one GPU the N "GPUs" are consecutive slot ranges of the population, and
+ * the exchange is a permutation of the new population's slots.  It is split
+ * in two calls around the host's exchange plan:
+ *   pa_resample_begin  the first half of pa_resample (reweight, copy counts,
+ *                      exclusive scan) without the gather: afterwards
+ *                      PA_DUMP_COUNTS / PA_DUMP_OFFSETS and pa_dump(STATE)
+ *                      give R_i and the offspring ranges (the offspring of
+ *                      old slots [a, b) are new slots [o_a, o_b)).
+ *   pa_resample_finish the gather, into a slot order given as nseg segments
+ *                      of the new population: post-exchange slots are filled
+ *                      in order with new slots seg_src[q] ..
+ *                      seg_src[q] + seg_len[q] - 1 for q = 0 .. nseg - 1
+ *                      (host arrays; 1 <= nseg <= PA_MAX_SEGMENTS; each
+ *                      segment inside [0, R_i) and the lengths summing to
+ *                      R_i, else PA_ERR_INVALID_ARG).  One segment (0, R_i)
+ *                      is the plain step's order.  Synchronises (reads R_i).
+ * The replicas move in device memory: every slot's spins, energy level and
+ * magnetisation are written once, by the same gather that completes a plain
+ * resample.  Between the two calls every other stepping call, pa_load,
+ * pa_checkpoint, pa_restore and pa_batch_init return PA_ERR_INVALID_ARG. */
+#define PA_MAX_SEGMENTS 1024
+int pa_resample_begin(pa_run* run);
+int pa_resample_finish(pa_run* run, int32_t nseg, const int64_t* seg_src, const int64_t* seg_len);
 
 /* pa_resample followed by pa_sweep(theta). */
 int pa_step(pa_run* run);
@@ -191,6 +221,36 @@ int pa_step_stream(pa_run* run, void* host_dst, size_t bytes, int32_t chunks, vo
 int64_t pa_bench_philox_threads(void);
 int pa_bench_philox(uint64_t seed, int32_t halfsweeps, void* out_dev, int64_t out_words,
                     void* stream);
+
+/* Integer-pipe throughput of this GPU (a measurement, not part of a run): the
+ * peak the sweep kernels' integer work is reported against.  The paper has no
+ * counterpart; its kernels' bound (Sec. 2: theta Metropolis sweeps per step)
+ * is integer issue here.  One launch of pa_bench_intops_threads() resident
+ * threads, each running `iters` iterations of pa_bench_intops_per_iter()
+ * independent dependency chains, one instruction per chain and iteration, of
+ * the kind selected:
+ *   PA_INTOPS_LOP3       three-input logic op (lop3.b32)
+ *   PA_INTOPS_IMAD       32-bit multiply-add (mad.lo.u32)
+ *   PA_INTOPS_WIDE       32 x 32 -> 64 multiply with a 64-bit add (mad.wide.u32)
+ *   PA_INTOPS_LOP3_IMAD  the two interleaved 1:1
+ *   PA_INTOPS_LOP3_WIDE  lop3 and mad.wide interleaved 1:1
+ *   PA_INTOPS_MULWIDE_XOR  x <- hi(x b) xor lo(x b): mul.wide.u32 then a
+ *                        two-input xor, both halves consumed -- one multiply
+ *                        of a Philox4x32 round with its xor; two instructions
+ *                        per chain step
+ * Chain steps executed = threads * iters * per_iter.  out_dev: device memory
+ * of at least pa_bench_intops_threads() 32-bit words (one folded result per
+ * thread), else PA_ERR_INVALID_ARG; an unknown kind or iters < 1 is
+ * PA_ERR_INVALID_ARG.  Asynchronous on `stream` (cudaStream_t). */
+#define PA_INTOPS_LOP3      0
+#define PA_INTOPS_IMAD      1
+#define PA_INTOPS_WIDE      2
+#define PA_INTOPS_LOP3_IMAD 3
+#define PA_INTOPS_LOP3_WIDE 4
+#define PA_INTOPS_MULWIDE_XOR 5
+int64_t pa_bench_intops_threads(void);
+int64_t pa_bench_intops_per_iter(void);
+int pa_bench_intops(int32_t kind, int32_t iters, void* out_dev, int64_t out_words, void* stream);
 
 /* Test hooks for the failure paths (0 in normal operation).
  * PA_DEBUG_WITHHOLD_PREFIX: the resample's tile 0 does not publish its
@@ -246,11 +306,14 @@ int pa_dump(pa_run* run, int32_t what, void* host_dst, size_t bytes);
 int pa_dump_range(pa_run* run, int32_t what, int64_t first, int64_t count, void* host_dst,
                   size_t bytes);
 
-/* Scalar run state as seen by the device. */
+/* Scalar run state as seen by the device.  sources counts, over every
+ * resample of the run so far, the replicas that received at least one copy
+ * (the replicas whose spins the gather reads). */
 typedef struct {
     int64_t step, R, R_prev, kref, sweeps_done, status_bits;
     double  lnQ, lnZ, S;
     int64_t N, bins, stride, capacity, parity;
+    int64_t sources;
 } pa_state;
 
 /* Host-side tables the engine uploads, for bitwise comparison before any
@@ -344,11 +407,28 @@ typedef struct pa_batch pa_batch;
 size_t pa_batch_workspace_size(int32_t nruns);
 int pa_batch_init(pa_run* const* runs, int32_t nruns, void* dev_workspace, size_t bytes,
                   void* stream, pa_batch** out);
+/* pa_batch_init for callers that keep work in flight (a serving loop that
+ * builds the next batch while the current one runs): the remaining steps of
+ * every run come from the caller (steps_left[i], 0 .. K, host memory) instead
+ * of the device, and nothing is waited for -- the descriptor uploads are
+ * ordered on `stream` before the batch's first step.  The runs must not be
+ * stepped by other work on other streams between this call and the batch's
+ * steps unless the caller orders that work before them. */
+int pa_batch_init_async(pa_run* const* runs, int32_t nruns, const int32_t* steps_left,
+                        void* dev_workspace, size_t bytes, void* stream, pa_batch** out);
 /* One annealing step of every run (PA_ERR_DONE once any run reached K). */
 int pa_batch_step(pa_batch* batch);
 /* nsteps steps replayed from a CUDA graph of one batched step. */
 int pa_batch_run_steps(pa_batch* batch, int32_t nsteps);
 int pa_batch_sync(pa_batch* batch);
+/* Phase timing of a batched step (for benchmarks): while enabled, every step
+ * enqueued by pa_batch_step (not graph replays) is bracketed by CUDA events on
+ * the batch stream.  pa_batch_profile_read synchronises and returns the number
+ * of timed steps and their summed device time in ms per phase: 0 reweight of
+ * every run, 1 resample (multinomial draws, counts, scan, gather), 2 the sweep
+ * classes (fork to join of their parallel branches), 3 observables. */
+int pa_batch_profile(pa_batch* batch, int32_t enable);
+int pa_batch_profile_read(pa_batch* batch, int64_t* steps, double ms[4], int32_t reset);
 /* Sweep classes and their launch shape: info = {layout, dim, L, model,
  * number of runs, warps per block, slots, slots per claim}.  The classes of
  * one step run as parallel branches.  pa_batch_set_shape chooses one class's
@@ -382,11 +462,15 @@ void pa_batch_free(pa_batch* batch);
  * the process exits.  R may be at most PA_NOALLOC_MAX_REPLICAS; larger R (or a
  * negative one, NULL pointers, bins < 1, a negative step or an instance id
  * >= 2^28) returns PA_ERR_INVALID_ARG before anything is enqueued.
- * The first call on each device looks up the array's device address with that
- * device current; make that first call before any stream capture.  Every call
- * reuses the same array (the call clears what must start at zero), so two
- * calls whose kernels overlap on the GPU -- on different streams, or from
- * different threads -- race and give wrong results; serialise them.
+ * The first call in each CUDA context (a device's primary context, or a
+ * context the caller created and made current) looks up the array's address
+ * in that context and caches it under the context's id; make that first call
+ * before any stream capture.  Every call reuses the same array and clears what
+ * it reads before writing it (the tile counter, the status bits and the
+ * lookback descriptors of its tiles), so nothing an earlier call left behind
+ * can leak into its result; but two calls whose kernels overlap on the GPU --
+ * on different streams, or from different threads -- race and give wrong
+ * results: serialise them.
  * *d_total reads 0xFFFFFFFF if a level was >= bins (that replica counts 0
  * copies) or if a bounded wait inside the scan gave up. */
 #define PA_NOALLOC_MAX_REPLICAS 8388608

@@ -117,6 +117,9 @@ def lib():
             getattr(L, name).restype = C.c_int
         L.or_sweep.argtypes = [C.c_void_p, C.c_int32]
         L.or_sweep.restype = C.c_int
+        L.or_permute.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_int64),
+                                 C.POINTER(C.c_int64)]
+        L.or_permute.restype = C.c_int
         L.or_observables.argtypes = [C.c_void_p, C.POINTER(Obs)]
         for name in ("or_R", "or_N", "or_bins", "or_sweep_counter", "or_R_prev", "or_kref",
                      "or_parity", "or_check_failures"):
@@ -312,6 +315,15 @@ class Run:
 
     def sweep(self, n: int) -> int:
         return lib().or_sweep(self._h, n)
+
+    def permute(self, segments) -> int:
+        """Replica exchange (Sec. 3): new slot order from [(old first slot,
+        length), ...]."""
+        seg = np.asarray(segments, dtype=np.int64).reshape(-1, 2)
+        src = np.ascontiguousarray(seg[:, 0])
+        ln = np.ascontiguousarray(seg[:, 1])
+        return lib().or_permute(self._h, int(seg.shape[0]), _ptr(src, C.c_int64),
+                                _ptr(ln, C.c_int64))
 
     def resample_to(self, beta_next: float) -> int:
         return lib().or_resample_to(self._h, beta_next)

@@ -670,6 +670,37 @@ int or_resample(or_run* r)
     return 0;
 }
 
+/* Replica exchange between GPUs (Sec. 3), on a population whose N "GPUs" are
+ * consecutive slot ranges: after a resample the replicas are put in a new slot
+ * order, given as segments of the current order -- new slots are filled in
+ * order with old slots src[q] .. src[q] + len[q] - 1, q = 0 .. nseg - 1.  The
+ * population's states, levels, magnetisations and tracked energies move with
+ * the slots.  Returns 0, or -1 if a segment leaves [0, R) or the lengths do not
+ * add up to R. */
+int or_permute(or_run* r, int32_t nseg, const int64_t* src, const int64_t* len)
+{
+    int64_t total = 0;
+    for (int32_t q = 0; q < nseg; ++q) {
+        if (len[q] < 0 || src[q] < 0 || src[q] + len[q] > r->R) return -1;
+        total += len[q];
+    }
+    if (total != r->R) return -1;
+    int64_t dst = 0;
+    for (int32_t q = 0; q < nseg; ++q)
+        for (int64_t k = 0; k < len[q]; ++k, ++dst) {
+            int64_t from = src[q] + k;
+            memcpy(r->spins2 + dst * r->N, r->spins + from * r->N, (size_t)r->N);
+            r->ebin2[dst] = r->ebin[from];
+            r->M2[dst] = r->M[from];
+            r->U2[dst] = r->U[from];
+        }
+    int8_t* ts = r->spins; r->spins = r->spins2; r->spins2 = ts;
+    uint32_t* te = r->ebin; r->ebin = r->ebin2; r->ebin2 = te;
+    int32_t* tm = r->M; r->M = r->M2; r->M2 = tm;
+    int64_t* tu = r->U; r->U = r->U2; r->U2 = tu;
+    return 0;
+}
+
 int or_sweep(or_run* r, int32_t nsweeps)
 {
     if (nsweeps < 0) return -1;

@@ -134,6 +134,10 @@ int      or_resample(or_run* r);              /* beta_{i-1} -> beta_i; 0 ok, <0 
 int      or_resample_to(or_run* r, double beta_next);
 double   or_current_beta(const or_run* r);
 int      or_sweep(or_run* r, int32_t nsweeps);/* at beta_i, then measure           */
+/* Replica exchange between virtual GPUs (Sec. 3): reorders the population's
+ * slots; new slots take old slots src[q] .. src[q] + len[q] - 1 in order.
+ * 0 ok, -1 if the segments leave [0, R) or do not cover R slots. */
+int      or_permute(or_run* r, int32_t nseg, const int64_t* src, const int64_t* len);
 int      or_step(or_run* r);                  /* or_resample + or_sweep(theta)      */
 void     or_observables(const or_run* r, or_obs* out);
 /* views into the run's current state (valid until the next call) */

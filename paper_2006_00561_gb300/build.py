@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpa_gb300.so")
 SOURCES = ["pa_engine.cu", "pa_sweep.cu", "pa_sweep_l64.cu", "pa_resample.cu",
-           "pa_static_scan.cu"]
+           "pa_static_scan.cu", "pa_bench.cu"]
 HEADERS = ["pa_internal.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

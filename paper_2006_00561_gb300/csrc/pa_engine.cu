@@ -9,6 +9,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <cstring>
+#include <array>
 #include <new>
 #include <vector>
 
@@ -47,6 +48,9 @@ struct pa_run {
     uint32_t load_R;  // source of the population size written by pa_load
     // pa_step_stream: a range's sweeps are done / the last copy is done
     cudaEvent_t ev_range, ev_copied;
+    // pa_resample_begin has run the counts and scan; the gather waits for
+    // pa_resample_finish
+    bool gather_pending;
 };
 
 namespace {
@@ -59,7 +63,7 @@ struct Layout {
     int64_t N, bins, nrows, NW, nwords, stride, cap, tiles, ndist;
     size_t mn_cum, mn_tiles;
     size_t state, obs, thr, beta, dbeta, dsel, dtab, accum, tabn, tabF, desc, coup, ebin[2], mag[2],
-        counts, offsets, spins[2], total;
+        counts, offsets, srcmap, srcmap2, spins[2], total;
 };
 
 // beta_i = beta0 + (beta_max - beta0) * i / K (constant step, Sec. 3).
@@ -204,6 +208,8 @@ int make_layout(const pa_config* c, Layout* Lo, std::vector<double>* beta, std::
     for (int b2 = 0; b2 < 2; ++b2) l.mag[b2] = take((size_t)l.cap * 4);
     l.counts = take((size_t)l.cap * 4);
     l.offsets = take((size_t)l.cap * 4);
+    l.srcmap = take((size_t)l.cap * 4);
+    l.srcmap2 = take((size_t)l.cap * 4);
     for (int b2 = 0; b2 < 2; ++b2) l.spins[b2] = take((size_t)(l.cap * l.stride));
     l.total = off;
     return PA_OK;
@@ -417,6 +423,8 @@ int pa_init(const pa_config* cfg, void* ws, size_t bytes, void* stream, pa_run**
     }
     d.counts = (uint32_t*)(base + l.counts);
     d.offsets = (uint32_t*)(base + l.offsets);
+    d.srcmap = (uint32_t*)(base + l.srcmap);
+    d.srcmap2 = (uint32_t*)(base + l.srcmap2);
     d.accum = (unsigned long long*)(base + l.accum);
     d.hist = (uint32_t*)(base + l.accum + 16);
     d.tab_n = (uint32_t*)(base + l.tabn);
@@ -485,6 +493,8 @@ int pa_init(const pa_config* cfg, void* ws, size_t bytes, void* stream, pa_run**
               cudaMemsetAsync(d.obs, 0, K1 * sizeof(pa_obs), s) == cudaSuccess &&
               cudaMemsetAsync(d.counts, 0, (size_t)l.cap * 4, s) == cudaSuccess &&
               cudaMemsetAsync(d.offsets, 0, (size_t)l.cap * 4, s) == cudaSuccess &&
+              cudaMemsetAsync(d.srcmap, 0, (size_t)l.cap * 4, s) == cudaSuccess &&
+              cudaMemsetAsync(d.srcmap2, 0, (size_t)l.cap * 4, s) == cudaSuccess &&
               cudaMemsetAsync(d.tab_n, 0, (size_t)l.bins * 4, s) == cudaSuccess &&
               cudaMemsetAsync(d.tab_F, 0, (size_t)l.bins * 4, s) == cudaSuccess &&
               cudaMemcpyAsync((void*)d.thr, r->thr.data(), K1 * 16, cudaMemcpyHostToDevice, s) ==
@@ -507,23 +517,64 @@ int pa_init(const pa_config* cfg, void* ws, size_t bytes, void* stream, pa_run**
 }
 
 int pa_resample(pa_run* r) {
-    if (!r) return PA_ERR_INVALID_ARG;
+    if (!r || r->gather_pending) return PA_ERR_INVALID_ARG;
     return enqueue_resample(r, r->stream);
 }
 
 int pa_sweep(pa_run* r, int32_t nsweeps) {
-    if (!r || nsweeps < 0) return PA_ERR_INVALID_ARG;
+    if (!r || nsweeps < 0 || r->gather_pending) return PA_ERR_INVALID_ARG;
     return enqueue_sweep(r, r->stream, nsweeps);
 }
 
 int pa_step(pa_run* r) {
-    if (!r) return PA_ERR_INVALID_ARG;
+    if (!r || r->gather_pending) return PA_ERR_INVALID_ARG;
     return enqueue_step(r, r->stream);
+}
+
+int pa_resample_begin(pa_run* r) {
+    if (!r || r->gather_pending) return PA_ERR_INVALID_ARG;
+    int rc = timed(r, r->stream, 0, [&] { return pa::launch_tau(r->d, r->stream); });
+    if (rc) return rc;
+    rc = timed(r, r->stream, 1, [&] {
+        if (r->cfg.resample == PA_RESAMPLE_MULTINOMIAL) {
+            const cudaError_t e = pa::launch_multinomial(r->d, r->stream);
+            if (e != cudaSuccess) return e;
+        }
+        return pa::launch_resample_scan(r->d, r->stream);
+    });
+    if (rc) return rc;
+    r->gather_pending = true;
+    return PA_OK;
+}
+
+int pa_resample_finish(pa_run* r, int32_t nseg, const int64_t* seg_src, const int64_t* seg_len) {
+    if (!r || !r->gather_pending || nseg < 1 || nseg > pa::MAX_SEGMENTS || !seg_src || !seg_len)
+        return PA_ERR_INVALID_ARG;
+    DevState st;
+    int rc = read_state(r, &st);
+    if (rc) return rc;
+    pa::SegList segs;
+    segs.n = (uint32_t)nseg;
+    int64_t at = 0;
+    for (int32_t q = 0; q < nseg; ++q) {
+        if (seg_len[q] < 0 || seg_src[q] < 0 || seg_src[q] + seg_len[q] > (int64_t)st.R)
+            return PA_ERR_INVALID_ARG;
+        segs.dst[q] = (uint32_t)at;
+        segs.src[q] = (uint32_t)seg_src[q];
+        at += seg_len[q];
+    }
+    if (at != (int64_t)st.R) return PA_ERR_INVALID_ARG;
+    segs.dst[nseg] = (uint32_t)at;
+    rc = timed(r, r->stream, 1, [&] { return pa::launch_remap_gather(r->d, segs, r->stream); });
+    if (rc) return rc;
+    r->gather_pending = false;
+    return PA_OK;
 }
 
 int pa_step_stream(pa_run* r, void* host_dst, size_t bytes, int32_t chunks, void* copy_stream,
                    int64_t* R_out) {
-    if (!r || !host_dst || !copy_stream || chunks < 1 || chunks > 64) return PA_ERR_INVALID_ARG;
+    if (!r || !host_dst || !copy_stream || chunks < 1 || chunks > 64 || r->gather_pending)
+        return PA_ERR_INVALID_ARG;
     const cudaStream_t copy = (cudaStream_t)copy_stream;
     const RunDev& d = r->d;
     if (copy == r->stream || bytes < (size_t)d.cap * d.stride) return PA_ERR_INVALID_ARG;
@@ -582,7 +633,7 @@ int pa_debug(pa_run* r, uint32_t flags) {
 }
 
 int pa_run_steps(pa_run* r, int32_t nsteps) {
-    if (!r || nsteps < 0) return PA_ERR_INVALID_ARG;
+    if (!r || nsteps < 0 || r->gather_pending) return PA_ERR_INVALID_ARG;
     if (!r->graph) {
         if (!r->cap_stream) CK(cudaStreamCreateWithFlags(&r->cap_stream, cudaStreamNonBlocking));
         CK(cudaStreamBeginCapture(r->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -736,6 +787,7 @@ int pa_dump(pa_run* r, int32_t what, void* dst, size_t bytes) {
             ps.stride = d.stride;
             ps.capacity = d.cap;
             ps.parity = st.negbonds & 1u;
+            ps.sources = (int64_t)st.sources;
             std::memcpy(dst, &ps, sizeof(ps));
             break;
         }
@@ -790,7 +842,8 @@ int pa_dump_range(pa_run* r, int32_t what, int64_t first, int64_t count, void* d
 }
 
 int pa_load(pa_run* r, int32_t what, const void* src, int64_t count, size_t bytes) {
-    if (!r || !src || count < 1 || count > (int64_t)r->d.cap) return PA_ERR_INVALID_ARG;
+    if (!r || !src || count < 1 || count > (int64_t)r->d.cap || r->gather_pending)
+        return PA_ERR_INVALID_ARG;
     const RunDev& d = r->d;
     if (what != PA_DUMP_SPINS && what != PA_DUMP_SPINS_RAW) return PA_ERR_INVALID_ARG;
     const int64_t per = what == PA_DUMP_SPINS ? d.N : d.stride;
@@ -854,7 +907,7 @@ int64_t pa_checkpoint_size(pa_run* r) {
 }
 
 int pa_checkpoint(pa_run* r, void* dst, size_t bytes) {
-    if (!r || !dst) return PA_ERR_INVALID_ARG;
+    if (!r || !dst || r->gather_pending) return PA_ERR_INVALID_ARG;
     const int64_t need = pa_checkpoint_size(r);
     if (need < 0 || (int64_t)bytes < need) return PA_ERR_INVALID_ARG;
     DevState st;
@@ -891,7 +944,7 @@ int pa_checkpoint(pa_run* r, void* dst, size_t bytes) {
 }
 
 int pa_restore(pa_run* r, const void* src, size_t bytes) {
-    if (!r || !src || bytes < sizeof(CkptHeader)) return PA_ERR_INVALID_ARG;
+    if (!r || !src || bytes < sizeof(CkptHeader) || r->gather_pending) return PA_ERR_INVALID_ARG;
     CkptHeader h;
     std::memcpy(&h, src, sizeof(h));
     const RunDev& d = r->d;
@@ -1009,7 +1062,8 @@ int pa_adaptive_beta(pa_run* r, double target, double beta_end, double* beta_nex
 }
 
 int pa_resample_to(pa_run* r, double beta_next) {
-    if (!r || !std::isfinite(beta_next) || beta_next < 0.0) return PA_ERR_INVALID_ARG;
+    if (!r || !std::isfinite(beta_next) || beta_next < 0.0 || r->gather_pending)
+        return PA_ERR_INVALID_ARG;
     DevState st;
     int rc = read_state(r, &st);
     if (rc) return rc;
@@ -1103,6 +1157,14 @@ struct pa_batch {
     cudaStream_t cap_stream;
     cudaGraphExec_t graph;
     int64_t steps_left;
+    // phase timing of steps enqueued by pa_batch_step while profiling is on:
+    // events before the reweight, the resample, the sweeps, the observables
+    // and after them
+    bool prof;
+    std::vector<std::array<cudaEvent_t, 5>> pending;
+    std::vector<cudaEvent_t> ev_pool;
+    int64_t prof_steps;
+    double prof_ms[4];
 };
 
 namespace {
@@ -1133,10 +1195,33 @@ uint32_t auto_chunk(uint32_t total_slots, int grid, int warps) {
 // One batched step: reweight and resample of every run on s, then the sweep
 // classes as parallel branches (fork / join through events), then the
 // observables of every run on s.
+cudaEvent_t batch_event(pa_batch* b) {
+    if (!b->ev_pool.empty()) {
+        cudaEvent_t e = b->ev_pool.back();
+        b->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
 int enqueue_batch_step(pa_batch* b, cudaStream_t s) {
+    std::array<cudaEvent_t, 5> ev{};
+    const bool timing = b->prof && s == b->stream;
+    if (timing) {
+        for (auto& e : ev) {
+            e = batch_event(b);
+            if (!e) return PA_ERR_CUDA;
+        }
+    }
+    auto mark = [&](int k) { return timing ? cudaEventRecord(ev[k], s) : cudaSuccess; };
+    CK(mark(0));
     CK(pa::launch_tau_batched(b->bd, s));
+    CK(mark(1));
     for (const auto& d : b->mn_runs) CK(pa::launch_multinomial(d, s));
     CK(pa::launch_resample_batched(b->bd, s));
+    CK(mark(2));
     if (b->cls.size() == 1) {
         const auto& c = b->cls[0];
         CK(pa::launch_sweep_batched(c.args, c.proto, c.warps, c.grid, s));
@@ -1149,11 +1234,17 @@ int enqueue_batch_step(pa_batch* b, cudaStream_t s) {
         }
         for (const auto& c : b->cls) CK(cudaStreamWaitEvent(s, c.done, 0));
     }
+    CK(mark(3));
     CK(pa::launch_obs_batched(b->bd, s));
+    CK(mark(4));
+    if (timing) b->pending.push_back(ev);
     return PA_OK;
 }
 
 void batch_release(pa_batch* b) {
+    for (const auto& ev : b->pending)
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : b->ev_pool) cudaEventDestroy(e);
     if (b->graph) cudaGraphExecDestroy(b->graph);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     for (auto& c : b->cls) {
@@ -1173,8 +1264,30 @@ size_t pa_batch_workspace_size(int32_t nruns) {
     return batch_layout(nruns, off);
 }
 
+namespace {
+// Shared body of pa_batch_init (steps_left == nullptr: each run's remaining
+// steps read from the device, then the uploads are waited for) and
+// pa_batch_init_async (remaining steps given by the caller, nothing waited for).
+int batch_init(pa_run* const* runs, int32_t nruns, const int32_t* steps_left, void* ws,
+               size_t bytes, void* stream, pa_batch** out);
+}  // namespace
+
 int pa_batch_init(pa_run* const* runs, int32_t nruns, void* ws, size_t bytes, void* stream,
                   pa_batch** out) {
+    return batch_init(runs, nruns, nullptr, ws, bytes, stream, out);
+}
+
+int pa_batch_init_async(pa_run* const* runs, int32_t nruns, const int32_t* steps_left, void* ws,
+                        size_t bytes, void* stream, pa_batch** out) {
+    if (!steps_left) return PA_ERR_INVALID_ARG;
+    return batch_init(runs, nruns, steps_left, ws, bytes, stream, out);
+}
+
+}  // extern "C"
+
+namespace {
+int batch_init(pa_run* const* runs, int32_t nruns, const int32_t* steps_left, void* ws,
+               size_t bytes, void* stream, pa_batch** out) {
     if (!out || !runs || nruns < 1) return PA_ERR_INVALID_ARG;
     *out = nullptr;
     size_t off[5];
@@ -1187,11 +1300,14 @@ int pa_batch_init(pa_run* const* runs, int32_t nruns, void* ws, size_t bytes, vo
     b->graph = nullptr;
     b->fork = nullptr;
     b->steps_left = INT64_MAX;
+    b->prof = false;
+    b->prof_steps = 0;
+    for (double& m : b->prof_ms) m = 0.0;
     std::vector<pa::RunDev> h_runs;
     std::vector<uint32_t> tile_base(1, 0u);
     for (int32_t i = 0; i < nruns; ++i) {
         pa_run* r = runs[i];
-        if (!r) {
+        if (!r || r->gather_pending) {
             batch_release(b);
             return PA_ERR_INVALID_ARG;
         }
@@ -1200,12 +1316,21 @@ int pa_batch_init(pa_run* const* runs, int32_t nruns, void* ws, size_t bytes, vo
                 batch_release(b);
                 return PA_ERR_INVALID_ARG;
             }
-        DevState st;
-        if (read_state(r, &st) != PA_OK) {
-            batch_release(b);
-            return PA_ERR_CUDA;
+        int64_t left = 0;
+        if (steps_left) {
+            if (steps_left[i] < 0 || steps_left[i] > r->cfg.K) {
+                batch_release(b);
+                return PA_ERR_INVALID_ARG;
+            }
+            left = steps_left[i];
+        } else {
+            DevState st;
+            if (read_state(r, &st) != PA_OK) {
+                batch_release(b);
+                return PA_ERR_CUDA;
+            }
+            left = (int64_t)r->cfg.K - (int64_t)st.step;
         }
-        const int64_t left = (int64_t)r->cfg.K - (int64_t)st.step;
         if (left < b->steps_left) b->steps_left = left;
         b->runs.push_back(r);
         h_runs.push_back(r->d);
@@ -1294,12 +1419,43 @@ int pa_batch_init(pa_run* const* runs, int32_t nruns, void* ws, size_t bytes, vo
             cudaSuccess &&
         cudaMemcpyAsync(d_bases, bases.data(), bases.size() * 4, cudaMemcpyHostToDevice, s) ==
             cudaSuccess &&
-        cudaStreamSynchronize(s) == cudaSuccess;
+        (steps_left || cudaStreamSynchronize(s) == cudaSuccess);
     if (!ok) {
         batch_release(b);
         return PA_ERR_CUDA;
     }
     *out = b;
+    return PA_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int pa_batch_profile(pa_batch* b, int32_t enable) {
+    if (!b) return PA_ERR_INVALID_ARG;
+    b->prof = enable != 0;
+    return PA_OK;
+}
+
+int pa_batch_profile_read(pa_batch* b, int64_t* steps, double ms[4], int32_t reset) {
+    if (!b) return PA_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(b->stream));
+    for (const auto& ev : b->pending) {
+        for (int k = 0; k < 4; ++k) {
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, ev[k], ev[k + 1]));
+            b->prof_ms[k] += t;
+        }
+        b->prof_steps += 1;
+        for (cudaEvent_t e : ev) b->ev_pool.push_back(e);
+    }
+    b->pending.clear();
+    if (steps) *steps = b->prof_steps;
+    for (int k = 0; k < 4; ++k) {
+        if (ms) ms[k] = b->prof_ms[k];
+        if (reset) b->prof_ms[k] = 0.0;
+    }
+    if (reset) b->prof_steps = 0;
     return PA_OK;
 }
 

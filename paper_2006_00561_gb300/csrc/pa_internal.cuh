@@ -45,7 +45,8 @@ struct DevState {
     double lnQ, lnZ, S;
     unsigned long long sweeps_done;
     unsigned long long tau_done;  // CTAs of the running multi-CTA reweight that are done
-    unsigned long long pad[2];
+    unsigned long long sources;   // replicas with a copy count > 0, summed over all resamples
+    unsigned long long pad[1];
 };
 static_assert(sizeof(DevState) <= 256, "DevState must fit its slot");
 
@@ -60,6 +61,8 @@ struct RunDev {
     int32_t* mag[2];            // magnetisation per replica
     uint32_t* counts;           // copy counts of the last resample
     uint32_t* offsets;          // exclusive scan of the counts
+    uint32_t* srcmap;           // [cap] source replica of every slot the last resample filled
+    uint32_t* srcmap2;          // [cap] the same after a redistribution permuted the slots
     unsigned long long* accum;  // [2] = sum |M|, sum M^2 of the running measurement
     uint32_t* hist;             // [bins] energy histogram of the running measurement
     uint32_t* tab_n;            // [bins] floor(tau_k)
@@ -175,6 +178,18 @@ cudaError_t launch_sweep(const RunDev& d, int nsweeps, int grid, cudaStream_t s)
 int sweep_grid(const RunDev& d);
 cudaError_t launch_tau(const RunDev& d, cudaStream_t s);
 cudaError_t launch_resample(const RunDev& d, cudaStream_t s);
+// Redistribution between virtual GPUs (pa_resample_begin / pa_resample_finish):
+// the counts and scan alone, then the gather into a permuted slot order.
+// Post-exchange slots [dst[q], dst[q+1]) take the pre-exchange slots starting
+// at src[q].
+constexpr int MAX_SEGMENTS = 1024;
+struct SegList {
+    uint32_t n;
+    uint32_t dst[MAX_SEGMENTS + 1];
+    uint32_t src[MAX_SEGMENTS];
+};
+cudaError_t launch_resample_scan(const RunDev& d, cudaStream_t s);
+cudaError_t launch_remap_gather(const RunDev& d, const SegList& segs, cudaStream_t s);
 cudaError_t launch_multinomial(const RunDev& d, cudaStream_t s);
 cudaError_t launch_obs(const RunDev& d, int nsweeps, cudaStream_t s);
 // specialised 2D ferromagnet, L = 64 or 128, packed (pa_sweep_l64.cu)

@@ -232,7 +232,13 @@ __device__ __noinline__ uint32_t poisson_count(const RunDev& d, uint32_t i, uint
 // HBM-bound default path); 1 adds the per-run Poisson branch; 2 takes the
 // counts that the multinomial draw has left in d.counts; 3 chooses among the
 // three per run (batches that mix the rules).
-template <int RULE>
+//
+// SPLIT = false: the tile also gathers its replicas' spins (the batched form).
+// SPLIT = true: the tile writes, for each slot it fills, the index of the
+// source replica (srcmap) with the copied energy level and magnetisation, and
+// k_gather copies the spins afterwards over the whole new population (the
+// plain form).
+template <int RULE, bool SPLIT = false>
 __device__ __forceinline__ void resample_tile(const RunDev& d, uint32_t tile, ResampleSmem& sm) {
     DevState* st = d.st;
     uint32_t* s_r = sm.r;
@@ -398,18 +404,22 @@ __device__ __forceinline__ void resample_tile(const RunDev& d, uint32_t tile, Re
         o += r[j];
     }
     __syncthreads();
+#if PA_RS_COMPACT
+    if (t == 0) atomicAdd(&st->sources, (unsigned long long)sm.nsurv);
+#endif
 
-    // gather: 16-byte chunks, consecutive threads on consecutive chunks; GU
-    // independent loads in flight per thread before their stores
-    constexpr int GU = PA_RS_GU;
-    const uint32_t CH = d.stride >> 4;
-    const uint4* __restrict__ srcp = reinterpret_cast<const uint4*>(d.spins[src]) + (size_t)base * CH;
-    uint4* __restrict__ dstp = reinterpret_cast<uint4*>(d.spins[src ^ 1u]);
 #if PA_RS_COMPACT
     const uint32_t nlist = sm.nsurv;  // gather item j of the list: replica surv[j]
 #else
     const uint32_t nlist = n_in;
 #endif
+    // gather: 16-byte chunks, consecutive threads on consecutive chunks; GU
+    // independent loads in flight per thread before their stores
+    if (!SPLIT) {
+    constexpr int GU = PA_RS_GU;
+    const uint32_t CH = d.stride >> 4;
+    const uint4* __restrict__ srcp = reinterpret_cast<const uint4*>(d.spins[src]) + (size_t)base * CH;
+    uint4* __restrict__ dstp = reinterpret_cast<uint4*>(d.spins[src ^ 1u]);
     const uint32_t items = nlist * CH;
     const bool pow2 = (CH & (CH - 1)) == 0;
     const int shift = __ffs(CH) - 1;
@@ -441,6 +451,7 @@ __device__ __forceinline__ void resample_tile(const RunDev& d, uint32_t tile, Re
             }
         }
     }
+    }
     const uint32_t* esrc = d.ebin[src] + base;
     const int32_t* msrc = d.mag[src] + base;
     uint32_t* edst = d.ebin[src ^ 1u];
@@ -460,6 +471,7 @@ __device__ __forceinline__ void resample_tile(const RunDev& d, uint32_t tile, Re
             if (dst < d.cap) {
                 edst[dst] = e;
                 mdst[dst] = m;
+                if (SPLIT) d.srcmap[dst] = base + li;
             }
         }
     }
@@ -473,7 +485,7 @@ __device__ __forceinline__ void resample_tile(const RunDev& d, uint32_t tile, Re
 #ifndef PA_RS_MINB
 #define PA_RS_MINB 4
 #endif
-template <int RULE>
+template <int RULE, bool SPLIT>
 __global__ void __launch_bounds__(RS_THREADS, RULE == 1 ? 2 : PA_RS_MINB) k_resample(RunDev d) {
     __shared__ ResampleSmem sm;
     if (!d.st->active) return;
@@ -483,8 +495,132 @@ __global__ void __launch_bounds__(RS_THREADS, RULE == 1 ? 2 : PA_RS_MINB) k_resa
         __syncthreads();
         const uint32_t tile = sm.tile;
         if (tile * (uint32_t)RS_TILE >= R) break;
-        resample_tile<RULE>(d, tile, sm);
+        resample_tile<RULE, SPLIT>(d, tile, sm);
         __syncthreads();  // sm is reused by the next tile
+    }
+}
+
+// Gather of the new population (the plain form's second kernel): slot j of
+// the other buffer receives the spins of replica srcmap[j], for every slot j <
+// R_i, in 16-byte chunks.  Work item t is chunk t % CH of slot t / CH, so the
+// stores of consecutive threads are consecutive and the loads of one slot's
+// chunks are one contiguous source replica; a source with r copies is read
+// by r neighbouring slots at nearly the same time, so its later reads hit
+// L2.  Every thread keeps GA_U loads in flight: the map words first, then the
+// data they point to, then the streaming stores.  Persistent: one wave of
+// resident CTAs strides over all R_i * CH chunks.
+#ifndef PA_GA_U
+#define PA_GA_U 8
+#endif
+#ifndef PA_GA_MINB
+#define PA_GA_MINB 3
+#endif
+constexpr int GA_THREADS = 256;
+constexpr int GA_U = PA_GA_U;
+
+// EM = true (the redistribution's gather) also copies every slot's energy
+// level and magnetisation from the source replica.
+template <bool EM>
+__global__ void __launch_bounds__(GA_THREADS, PA_GA_MINB) k_gather(RunDev d) {
+    const DevState* st = d.st;
+    if (!st->active) return;
+    const uint32_t Rn = st->R;  // clamped to the capacity by the scan
+    const uint32_t src = st->src;
+    const uint32_t CH = d.stride >> 4;
+    const uint32_t last = d.cap_alloc - 1;
+    const uint4* __restrict__ sp = reinterpret_cast<const uint4*>(d.spins[src]);
+    uint4* __restrict__ dp = reinterpret_cast<uint4*>(d.spins[src ^ 1u]);
+    const uint32_t* __restrict__ map = d.srcmap;
+    if ((CH & 31u) == 0) {
+        // a replica is a whole number of warp rows (L = 64: one 512-byte row
+        // of 32 chunks): each warp takes groups of 32 consecutive slots, reads
+        // their 32 map words in one coalesced load, and then copies GA_U
+        // replicas at a time, lane l moving chunks l, l + 32, ... of each
+        const uint32_t lane = threadIdx.x & 31u;
+        const uint32_t rows = CH >> 5;
+        const uint32_t nwarps = gridDim.x * (GA_THREADS / 32);
+        for (uint32_t g = blockIdx.x * (GA_THREADS / 32) + (threadIdx.x >> 5); g * 32u < Rn;
+             g += nwarps) {
+            const uint32_t slot0 = g * 32u;
+            const uint32_t nslot = min(32u, Rn - slot0);
+            const uint32_t mine = lane < nslot ? min(__ldg(map + slot0 + lane), last) : 0u;
+            for (uint32_t row = 0; row < rows; ++row) {
+                const uint32_t c = row * 32u + lane;
+                for (uint32_t k0 = 0; k0 < nslot; k0 += GA_U) {
+                    uint4 v[GA_U];
+#pragma unroll
+                    for (int u = 0; u < GA_U; ++u) {
+                        const uint32_t sidx = __shfl_sync(0xffffffffu, mine, (k0 + u) & 31u);
+                        if (k0 + u < nslot) v[u] = __ldg(sp + (size_t)sidx * CH + c);
+                    }
+#pragma unroll
+                    for (int u = 0; u < GA_U; ++u)
+                        if (k0 + u < nslot) __stcs(dp + (size_t)(slot0 + k0 + u) * CH + c, v[u]);
+                }
+            }
+        }
+    } else {
+        const unsigned long long items = (unsigned long long)Rn * CH;
+        const unsigned long long nth = (unsigned long long)gridDim.x * GA_THREADS;
+        const bool pow2 = (CH & (CH - 1)) == 0;
+        const int shift = __ffs(CH) - 1;
+        for (unsigned long long it0 = (unsigned long long)blockIdx.x * GA_THREADS + threadIdx.x;
+             it0 < items; it0 += nth * GA_U) {
+            uint32_t sidx[GA_U], c[GA_U];
+#pragma unroll
+            for (int u = 0; u < GA_U; ++u) {
+                const unsigned long long it = it0 + (unsigned long long)u * nth;
+                sidx[u] = 0;
+                c[u] = 0;
+                if (it < items) {
+                    const uint32_t slot = pow2 ? (uint32_t)(it >> shift) : (uint32_t)(it / CH);
+                    c[u] = (uint32_t)(it - (unsigned long long)slot * CH);
+                    sidx[u] = min(__ldg(map + slot), last);  // a slot never holds more than cap_alloc
+                }
+            }
+            uint4 v[GA_U];
+#pragma unroll
+            for (int u = 0; u < GA_U; ++u) {
+                const unsigned long long it = it0 + (unsigned long long)u * nth;
+                if (it < items) v[u] = __ldg(sp + (size_t)sidx[u] * CH + c[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < GA_U; ++u) {
+                const unsigned long long it = it0 + (unsigned long long)u * nth;
+                if (it < items) __stcs(dp + it, v[u]);
+            }
+        }
+    }
+    if (EM) {
+        const uint32_t* es = d.ebin[src];
+        const int32_t* ms = d.mag[src];
+        uint32_t* ed = d.ebin[src ^ 1u];
+        int32_t* md = d.mag[src ^ 1u];
+        for (uint32_t j = blockIdx.x * GA_THREADS + threadIdx.x; j < Rn; j += gridDim.x * GA_THREADS) {
+            const uint32_t i = min(map[j], last);
+            ed[j] = es[i];
+            md[j] = ms[i];
+        }
+    }
+}
+
+// Slot permutation of a redistribution: post-exchange slot j in segment q
+// (dst[q] <= j < dst[q+1]) takes the source of pre-exchange slot
+// src[q] + j - dst[q].
+__global__ void __launch_bounds__(256) k_remap(RunDev d, const __grid_constant__ SegList segs) {
+    const DevState* st = d.st;
+    if (!st->active) return;
+    const uint32_t Rn = st->R;
+    const uint32_t last = d.cap_alloc - 1;
+    for (uint32_t j = blockIdx.x * 256 + threadIdx.x; j < Rn; j += gridDim.x * 256) {
+        uint32_t lo = 0, hi = segs.n;  // dst[lo] <= j < dst[hi]
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (segs.dst[mid] <= j) lo = mid;
+            else hi = mid;
+        }
+        const uint32_t pre = min(segs.src[lo] + (j - segs.dst[lo]), last);
+        d.srcmap2[j] = d.srcmap[pre];
     }
 }
 
@@ -604,7 +740,7 @@ cudaError_t launch_tau(const RunDev& d, cudaStream_t s) {
 // One wave of resident CTAs (capped by the number of tiles), looked up once
 // per device and kernel.
 static int resample_wave(const void* fn, int which, uint32_t tiles) {
-    static int cache[64][7];
+    static int cache[64][10];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
     int wave = cache[dev][which];
@@ -619,20 +755,76 @@ static int resample_wave(const void* fn, int which, uint32_t tiles) {
     return (int)((int64_t)tiles < wave ? (int64_t)tiles : wave);
 }
 
-cudaError_t launch_resample(const RunDev& d, cudaStream_t s) {
-    if (d.resample == PA_RESAMPLE_POISSON) {
-        const int grid = resample_wave((const void*)k_resample<1>, 2, d.tiles);
-        if (grid <= 0) return cudaErrorInvalidValue;
-        k_resample<1><<<grid, RS_THREADS, 0, s>>>(d);
-    } else if (d.resample == PA_RESAMPLE_MULTINOMIAL) {
-        const int grid = resample_wave((const void*)k_resample<2>, 4, d.tiles);
-        if (grid <= 0) return cudaErrorInvalidValue;
-        k_resample<2><<<grid, RS_THREADS, 0, s>>>(d);
-    } else {
-        const int grid = resample_wave((const void*)k_resample<0>, 0, d.tiles);
-        if (grid <= 0) return cudaErrorInvalidValue;
-        k_resample<0><<<grid, RS_THREADS, 0, s>>>(d);
+// PA_RS_SPLIT = 1: the plain resample is two kernels, counts + scan (with the
+// slot -> source map, levels and magnetisations) and then k_gather over the
+// whole new population; 0 (the default): one kernel that gathers tile by
+// tile.  Measured on GB300 at 2^21 replicas, L = 64, same bits: one kernel
+// 0.366 ms; two kernels 0.374 ms (16 loads in flight per thread, 2 CTAs of 256
+// per SM), 0.380 ms (4 loads, 4 CTAs), 0.385 ms (8 loads, 3 CTAs).  The split
+// form serves the redistribution's gather (pa_resample_finish), whose slot
+// order is only known after the host has read the scan.
+#ifndef PA_RS_SPLIT
+#define PA_RS_SPLIT 0
+#endif
+constexpr bool RS_SPLIT = PA_RS_SPLIT != 0;
+
+static int gather_grid() {
+    static int cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (cache[dev] <= 0) {
+        int sms = 0, per_sm = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_gather<false>,
+                                                          GA_THREADS, 0) != cudaSuccess)
+            return 0;
+        cache[dev] = sms * (per_sm < 1 ? 1 : per_sm);
     }
+    return cache[dev];
+}
+
+template <bool SPLIT>
+static cudaError_t launch_counts_scan(const RunDev& d, cudaStream_t s) {
+    // cache slots: 0/2/4 the one-kernel forms, 7/8/9 the split forms
+    const int slot = SPLIT ? 7 : 0;
+    if (d.resample == PA_RESAMPLE_POISSON) {
+        const int grid = resample_wave((const void*)k_resample<1, SPLIT>, SPLIT ? 8 : 2, d.tiles);
+        if (grid <= 0) return cudaErrorInvalidValue;
+        k_resample<1, SPLIT><<<grid, RS_THREADS, 0, s>>>(d);
+    } else if (d.resample == PA_RESAMPLE_MULTINOMIAL) {
+        const int grid = resample_wave((const void*)k_resample<2, SPLIT>, SPLIT ? 9 : 4, d.tiles);
+        if (grid <= 0) return cudaErrorInvalidValue;
+        k_resample<2, SPLIT><<<grid, RS_THREADS, 0, s>>>(d);
+    } else {
+        const int grid = resample_wave((const void*)k_resample<0, SPLIT>, slot, d.tiles);
+        if (grid <= 0) return cudaErrorInvalidValue;
+        k_resample<0, SPLIT><<<grid, RS_THREADS, 0, s>>>(d);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resample(const RunDev& d, cudaStream_t s) {
+    cudaError_t e = launch_counts_scan<RS_SPLIT>(d, s);
+    if (e != cudaSuccess || !RS_SPLIT) return e;
+    const int g = gather_grid();
+    if (g <= 0) return cudaErrorInvalidValue;
+    k_gather<false><<<g, GA_THREADS, 0, s>>>(d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resample_scan(const RunDev& d, cudaStream_t s) {
+    return launch_counts_scan<true>(d, s);
+}
+
+cudaError_t launch_remap_gather(const RunDev& d, const SegList& segs, cudaStream_t s) {
+    const int g = gather_grid();
+    if (g <= 0) return cudaErrorInvalidValue;
+    k_remap<<<g, 256, 0, s>>>(d, segs);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    RunDev dm = d;
+    dm.srcmap = d.srcmap2;
+    k_gather<true><<<g, GA_THREADS, 0, s>>>(dm);
     return cudaGetLastError();
 }
 

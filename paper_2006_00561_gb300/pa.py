@@ -39,8 +39,13 @@ EXPORTS = [
     "pa_batch_sync", "pa_batch_num_classes", "pa_batch_class_info", "pa_batch_set_shape",
     "pa_batch_free", "pa_checkpoint_size", "pa_checkpoint", "pa_restore",
     "pa_adaptive_beta", "pa_resample_to", "pa_poisson1_table", "pa_step_stream", "pa_debug",
-    "pa_bench_philox_threads", "pa_bench_philox",
+    "pa_bench_philox_threads", "pa_bench_philox", "pa_bench_intops_threads",
+    "pa_bench_intops_per_iter", "pa_bench_intops", "pa_batch_profile", "pa_batch_profile_read",
+    "pa_resample_begin", "pa_resample_finish", "pa_batch_init_async",
 ]
+MAX_SEGMENTS = 1024
+(INTOPS_LOP3, INTOPS_IMAD, INTOPS_WIDE, INTOPS_LOP3_IMAD, INTOPS_LOP3_WIDE,
+ INTOPS_MULWIDE_XOR) = range(6)
 DEBUG_WITHHOLD_PREFIX = 1
 NOALLOC_MAX_REPLICAS = 8388608
 
@@ -80,7 +85,7 @@ class State(C.Structure):
         ("sweeps_done", C.c_int64), ("status_bits", C.c_int64),
         ("lnQ", C.c_double), ("lnZ", C.c_double), ("S", C.c_double),
         ("N", C.c_int64), ("bins", C.c_int64), ("stride", C.c_int64), ("capacity", C.c_int64),
-        ("parity", C.c_int64),
+        ("parity", C.c_int64), ("sources", C.c_int64),
     ]
 
     def as_dict(self) -> dict:
@@ -109,8 +114,10 @@ def lib():
         L.pa_workspace_size.argtypes = [cfgp]
         L.pa_workspace_size.restype = C.c_size_t
         L.pa_init.argtypes = [cfgp, vp, C.c_size_t, vp, C.POINTER(vp)]
-        for n in ("pa_resample", "pa_step", "pa_status"):
+        for n in ("pa_resample", "pa_step", "pa_status", "pa_resample_begin"):
             getattr(L, n).argtypes = [vp]
+        L.pa_resample_finish.argtypes = [vp, C.c_int32, C.POINTER(C.c_int64),
+                                         C.POINTER(C.c_int64)]
         L.pa_sweep.argtypes = [vp, C.c_int32]
         L.pa_run_steps.argtypes = [vp, C.c_int32]
         L.pa_step_stream.argtypes = [vp, vp, C.c_size_t, C.c_int32, vp, C.POINTER(C.c_int64)]
@@ -118,6 +125,10 @@ def lib():
         L.pa_bench_philox_threads.argtypes = []
         L.pa_bench_philox_threads.restype = C.c_int64
         L.pa_bench_philox.argtypes = [C.c_uint64, C.c_int32, vp, C.c_int64, vp]
+        for n in ("pa_bench_intops_threads", "pa_bench_intops_per_iter"):
+            getattr(L, n).argtypes = []
+            getattr(L, n).restype = C.c_int64
+        L.pa_bench_intops.argtypes = [C.c_int32, C.c_int32, vp, C.c_int64, vp]
         L.pa_observables.argtypes = [vp, C.POINTER(Obs)]
         L.pa_observables_history.argtypes = [vp, C.c_int32, C.c_int32, C.POINTER(Obs)]
         L.pa_dump_size.argtypes = [vp, C.c_int32]
@@ -139,9 +150,14 @@ def lib():
         L.pa_batch_workspace_size.argtypes = [C.c_int32]
         L.pa_batch_workspace_size.restype = C.c_size_t
         L.pa_batch_init.argtypes = [C.POINTER(vp), C.c_int32, vp, C.c_size_t, vp, C.POINTER(vp)]
+        L.pa_batch_init_async.argtypes = [C.POINTER(vp), C.c_int32, C.POINTER(C.c_int32), vp,
+                                          C.c_size_t, vp, C.POINTER(vp)]
         for n in ("pa_batch_step", "pa_batch_sync", "pa_batch_num_classes"):
             getattr(L, n).argtypes = [vp]
         L.pa_batch_run_steps.argtypes = [vp, C.c_int32]
+        L.pa_batch_profile.argtypes = [vp, C.c_int32]
+        L.pa_batch_profile_read.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_double),
+                                            C.c_int32]
         L.pa_batch_class_info.argtypes = [vp, C.c_int32, C.POINTER(C.c_int32)]
         L.pa_batch_set_shape.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32]
         L.pa_batch_free.argtypes = [vp]
@@ -229,6 +245,19 @@ def pa_bench_philox(seed: int, halfsweeps: int, out_ptr: int, out_words: int, st
     """The register kernels' generator alone: one xor word per thread at out_ptr."""
     _check(lib().pa_bench_philox(seed, halfsweeps, C.c_void_p(out_ptr), out_words,
                                  C.c_void_p(stream_handle)), "pa_bench_philox")
+
+
+def pa_bench_intops_threads() -> int:
+    return int(lib().pa_bench_intops_threads())
+
+
+def pa_bench_intops_per_iter() -> int:
+    return int(lib().pa_bench_intops_per_iter())
+
+
+def pa_bench_intops(kind: int, iters: int, out_ptr: int, out_words: int, stream_handle: int):
+    _check(lib().pa_bench_intops(kind, iters, C.c_void_p(out_ptr), out_words,
+                                 C.c_void_p(stream_handle)), "pa_bench_intops")
 
 
 def pa_debug(h: int, flags: int):
@@ -369,6 +398,21 @@ class Run:
     def resample(self):
         pa_resample(self.h)
 
+    def resample_begin(self):
+        """Reweight, copy counts and scan of the next step, gather pending."""
+        _check(lib().pa_resample_begin(C.c_void_p(self.h)), "pa_resample_begin")
+
+    def resample_finish(self, segments):
+        """Gather of the pending resample into the slot order given by
+        [(first new slot, length), ...] (post-exchange order)."""
+        seg = np.asarray(segments, dtype=np.int64).reshape(-1, 2)
+        src = np.ascontiguousarray(seg[:, 0])
+        ln = np.ascontiguousarray(seg[:, 1])
+        _check(lib().pa_resample_finish(C.c_void_p(self.h), int(seg.shape[0]),
+                                        src.ctypes.data_as(C.POINTER(C.c_int64)),
+                                        ln.ctypes.data_as(C.POINTER(C.c_int64))),
+               "pa_resample_finish")
+
     def sweep(self, n: int):
         pa_sweep(self.h, n)
 
@@ -438,20 +482,33 @@ class Run:
 class Batch:
     """Several runs stepped together (pa_batch_* of include/pa.h)."""
 
-    def __init__(self, runs, stream=None):
+    def __init__(self, runs, stream=None, steps_left=None, workspace=None):
+        """steps_left: remaining steps of every run, known to the caller (the
+        batch is then built without waiting for the device, pa_batch_init_async);
+        workspace: a device tensor of at least pa_batch_workspace_size bytes
+        (allocated here when None)."""
         import torch
         self.runs = list(runs)
         n = len(self.runs)
         nbytes = int(lib().pa_batch_workspace_size(n))
         if nbytes == 0:
             raise PaError(-1, "pa_batch_workspace_size")
-        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        if workspace is None:
+            workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self.workspace = workspace
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         handles = (C.c_void_p * n)(*[r.h for r in self.runs])
         h = C.c_void_p()
-        _check(lib().pa_batch_init(handles, n, C.c_void_p(self.workspace.data_ptr()), nbytes,
-                                   C.c_void_p(self.stream.cuda_stream), C.byref(h)),
-               "pa_batch_init")
+        if steps_left is None:
+            _check(lib().pa_batch_init(handles, n, C.c_void_p(self.workspace.data_ptr()), nbytes,
+                                       C.c_void_p(self.stream.cuda_stream), C.byref(h)),
+                   "pa_batch_init")
+        else:
+            left = (C.c_int32 * n)(*[int(x) for x in steps_left])
+            _check(lib().pa_batch_init_async(handles, n, left,
+                                             C.c_void_p(self.workspace.data_ptr()), nbytes,
+                                             C.c_void_p(self.stream.cuda_stream), C.byref(h)),
+                   "pa_batch_init_async")
         self.h = h.value
 
     def close(self):
@@ -482,6 +539,19 @@ class Batch:
             out.append(dict(zip(("layout", "dim", "L", "model", "runs", "warps", "slots",
                                  "chunk"), list(info))))
         return out
+
+    def profile(self, enable: bool):
+        _check(lib().pa_batch_profile(C.c_void_p(self.h), 1 if enable else 0),
+               "pa_batch_profile")
+
+    def profile_read(self, reset: bool = True) -> dict:
+        """Timed steps and summed device ms per phase (non-graph steps)."""
+        n = C.c_int64()
+        ms = (C.c_double * 4)()
+        _check(lib().pa_batch_profile_read(C.c_void_p(self.h), C.byref(n), ms, 1 if reset else 0),
+               "pa_batch_profile_read")
+        return {"steps": n.value, "reweight": ms[0], "resample": ms[1], "sweep": ms[2],
+                "obs": ms[3]}
 
     def set_shape(self, cls: int, warps: int = 0, chunk: int = 0):
         _check(lib().pa_batch_set_shape(C.c_void_p(self.h), cls, warps, chunk),
