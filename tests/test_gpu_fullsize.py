@@ -179,3 +179,65 @@ def test_config3_whole_run_matches_kaufman(P):
     assert abs(o["R"] - (1 << 21)) <= 5 * np.sqrt(1 << 21)
     assert abs(o["lnZ"] - float(exact.kaufman_lnZ(64, 1.0))) < 0.05
     assert abs(o["e"] - exact.kaufman_energy_per_site(64, 1.0)) < 5e-6
+
+
+def _oracle_sweep_slice(job):
+    """The oracle's theta sweeps of consecutive replicas (slots slot0 ..) from
+    their pre-sweep states; runs in a spawned worker process."""
+    import os
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    from oracle import oracle as Ow
+    cfg_kw, spins, slot0, g0, T = job
+    cfg = Ow.make_config(**cfg_kw)
+    J = Ow.couplings(cfg)
+    out = np.ascontiguousarray(spins)
+    for k in range(out.shape[0]):
+        row = out[k]
+        Ow.sweep_replica(cfg, J, row, slot0 + k, g0, cfg.theta, T)
+    return out
+
+
+def test_config2_whole_step_every_replica_matches_the_oracle(P):
+    """Config 2 (2D L = 64 packed, R0 = 2^17, 200 steps, theta = 10, seed 2)
+    checked whole: from the device population after step 100, the oracle
+    recomputes step 101 for all ~131 000 replicas -- tau tables, every copy
+    count, the copies, and theta = 10 sweeps of every replica (spread over one
+    spawned process per host core) -- and the device's step 101 equals it
+    replica for replica."""
+    import multiprocessing as mpc
+    import os
+    kw = dict(dim=2, L=64, R0=1 << 17, K=200, theta=10, seed=2)
+    ocfg = O.make_config(**kw)
+    run = P.Run(P.make_config(layout=P.LAYOUT_PACKED, **kw))
+    run.run_steps(100)
+    st0 = run.state()
+    assert st0["status_bits"] == 0 and st0["step"] == 100
+    spins0 = run.dump(P.DUMP_SPINS).reshape(st0["R"], -1)
+    ebin0 = run.dump(P.DUMP_EBIN)
+    hist0 = run.dump(P.DUMP_HIST)
+    run.step()
+    st = run.state()
+    step = st["step"]
+    Dtab = np.array([O.weight(O.beta(ocfg, step) - O.beta(ocfg, step - 1), j)
+                     for j in range(st["bins"])])
+    S, kref, n, F = O.tau_table(hist0, Dtab, ocfg.R0)
+    assert st["S"] == S and st["kref"] == kref
+    counts = O.copy_counts(ocfg, step, ebin0, n, F)
+    assert np.array_equal(run.dump(P.DUMP_COUNTS), counts)
+    pre = np.repeat(spins0, counts, axis=0)  # the copies, in slot order
+    del spins0
+    assert pre.shape[0] == st["R"]
+    T = [O.threshold(O.beta(ocfg, step), 4 * (c + 1)) for c in range(3)]
+    g0 = (step - 1) * ocfg.theta
+    procs = max(1, min(32, os.cpu_count() or 1))
+    bounds = np.linspace(0, pre.shape[0], procs + 1).astype(int)
+    jobs = [(kw, pre[a:b], int(a), g0, T) for a, b in zip(bounds[:-1], bounds[1:])]
+    with mpc.get_context("spawn").Pool(procs) as pool:
+        want = np.concatenate(pool.map(_oracle_sweep_slice, jobs))
+    got = run.dump(P.DUMP_SPINS).reshape(st["R"], -1)
+    bad = np.nonzero((got != want).any(axis=1))[0]
+    assert bad.size == 0, f"{bad.size} replicas differ, first {bad[:5]}"
+    run.close()

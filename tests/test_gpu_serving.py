@@ -39,17 +39,27 @@ def _trace():
     return specs
 
 
-def test_each_result_is_the_same_alone_and_in_the_mix(P):
+@pytest.mark.parametrize("kind", ["sync", "pipelined"])
+def test_each_result_is_the_same_alone_and_in_the_mix(P, kind):
+    """Both servers: the synchronous loop, and the pipelined one that keeps two
+    quanta in flight, admits on a second stream and builds the next batch
+    while the device runs the current one."""
     from paper_2006_00561_gb300 import serve
     trace = _trace()
     sizes = sorted(P.pa_workspace_size(P.make_config(**{k: v for k, v in s.items()
                                                         if k != "arrival"})) for s in trace)
     budget = sum(sizes[-4:])  # about four requests resident at a time
-    srv = serve.Server(hbm_budget=budget, quantum=3, keep_spins=True)
+    if kind == "sync":
+        srv = serve.Server(hbm_budget=budget, quantum=3, keep_spins=True)
+    else:
+        srv = serve.PipelinedServer(hbm_budget=budget, quantum=3, depth=2, keep_spins=True)
     stats = srv.run_trace(trace)
     assert stats["served"] == len(trace) and stats["rejected"] == 0
     assert 2 <= stats["max_resident"] < len(trace)
     assert stats["iterations"] > 4
+    if kind == "pipelined":
+        assert srv.used == 0 and srv.arena.free_bytes() == srv.arena.size
+        assert 0.0 <= stats["gpu_idle_fraction"] < 1.0
     for req in srv.done:
         spec = {k: v for k, v in req.spec.items() if k != "arrival"}
         run = P.Run(P.make_config(**spec))
