@@ -190,6 +190,18 @@ static_assert(PA_L64_CHAIN >= 1 && PA_L64_CHAIN <= 4, "PA_L64_CHAIN: 1 .. 4");
 // run as compare and select instead, instructions that only the ALU pipe
 // executes; the carry chains are integer adds, which the compiler may move
 // to the FMA pipe.
+// PA_L64_OR_INDEX = 1: the block index base + h (base a multiple of 4, h =
+// 0 .. 3) is formed as base | h, the same value, so that it folds into the
+// xor of the round-2 word as one three-input logic op on the ALU pipe.
+#ifndef PA_L64_OR_INDEX
+#define PA_L64_OR_INDEX 0
+#endif
+#if PA_L64_OR_INDEX
+#define PA_L64_BLOCK(base, h) ((base) | (uint32_t)(h))
+#else
+#define PA_L64_BLOCK(base, h) ((base) + (uint32_t)(h))
+#endif
+
 // Philox blocks of a group of four unrolled together in the L = 64 kernel.
 #ifndef PA_L64_HUNROLL
 #define PA_L64_HUNROLL 4
@@ -251,7 +263,7 @@ __device__ __forceinline__ void row_accepts(const Keys& d, const HalfSweepGen& g
     for (uint32_t q = 0; q < 2; ++q) {
         const uint32_t base = 8u * y + 4u * q;
         const uint32_t kc = group_tests<F4, F8, PA_L64_HUNROLL>(
-            [&](int h) { return philox_block(d, gen, base + (uint32_t)h); }, one, c4, c8, t4.T,
+            [&](int h) { return philox_block(d, gen, PA_L64_BLOCK(base, h)); }, one, c4, c8, t4.T,
             t8.T);
         // site j = 4h + m: dE = 4 carry at bit 2j + 1, dE = 8 carry at bit 2j
         constexpr uint32_t EV = 0x55555555u;
@@ -545,7 +557,7 @@ __device__ __forceinline__ void row_accepts128(const Keys& d, const HalfSweepGen
     for (uint32_t q = 0; q < 4; ++q) {
         const uint32_t base = 16u * y + 4u * q;
         const uint32_t kc = group_tests<false, false, L128_HUNROLL>(
-            [&](int h) { return philox_block(d, gen, base + (uint32_t)h); }, one, t4.T, t8.T, t4.T,
+            [&](int h) { return philox_block(d, gen, PA_L64_BLOCK(base, h)); }, one, t4.T, t8.T, t4.T,
             t8.T);
         const uint32_t b4 = (~(kc >> 1) & EV) << P, b8 = (~kc & EV) << P;
         if (q == 0) {
