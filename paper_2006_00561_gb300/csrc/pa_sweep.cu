@@ -792,6 +792,28 @@ struct RSKeyRegs {
 #define PA_RS_KEYREG 0
 #endif
 
+// How the replica-sliced kernel forms its Philox products: 0 = high and low
+// halves from C++ (__umulhi, *), 1 = one mul.wide.u32 per product.
+#ifndef PA_RS_MUL_MODE
+#define PA_RS_MUL_MODE 0
+#endif
+// PA_RS_OR_SLOT = 1: the replica's slot b0 + r (b0 a multiple of 32, r < 32)
+// is formed as b0 | r, so that it folds into the xor of its Philox word.
+#ifndef PA_RS_OR_SLOT
+#define PA_RS_OR_SLOT 0
+#endif
+__device__ __forceinline__ void rs_mul(uint32_t m, uint32_t a, uint32_t& hi, uint32_t& lo) {
+#if PA_RS_MUL_MODE == 1
+    uint64_t p;
+    asm("mul.wide.u32 %0, %1, %2;" : "=l"(p) : "r"(a), "r"(m));
+    hi = (uint32_t)(p >> 32);
+    lo = (uint32_t)p;
+#else
+    hi = __umulhi(m, a);
+    lo = m * a;
+#endif
+}
+
 // One half-sweep group: sites of pairs 4k .. 4k + 3, colour c, 32 replicas.
 template <int DIM, int L, bool PMJ, typename KT>
 __device__ __forceinline__ void rs_group(uint32_t* S, const uint8_t* JS, int k, int c, uint32_t g,
@@ -824,18 +846,22 @@ __device__ __forceinline__ void rs_group(uint32_t* S, const uint8_t* JS, int k, 
     const uint32_t w1 = M1 * z2;
 #pragma unroll 2
     for (int r = 31; r >= 0; --r) {
-        const uint32_t y2 = y2s ^ (b0 + (uint32_t)r);
-        const uint32_t z0 = __umulhi(M1, y2) ^ y1 ^ K.rk0[1];  // round 2, replica half
-        const uint32_t z1 = M1 * y2;
+        // b0 is a multiple of 32 and r < 32: b0 | r is the slot b0 + r
+        const uint32_t y2 = PA_RS_OR_SLOT ? y2s ^ (b0 | (uint32_t)r) : y2s ^ (b0 + (uint32_t)r);
+        uint32_t h2, z1;
+        rs_mul(M1, y2, h2, z1);                                 // round 2, replica half
+        const uint32_t z0 = h2 ^ y1 ^ K.rk0[1];
         uint32_t c0w = w0s ^ z1;                                // round 3, replica half
         uint32_t c1w = w1;
-        uint32_t c2w = __umulhi(M0, z0) ^ z3k;
-        uint32_t c3w = M0 * z0;
+        uint32_t h3, c3w;
+        rs_mul(M0, z0, h3, c3w);
+        uint32_t c2w = h3 ^ z3k;
 #pragma unroll
         for (int rr = 3; rr < 10; ++rr) {
             const uint32_t a = c0w, b = c2w;
-            const uint32_t hiA = __umulhi(M0, a), loA = M0 * a;
-            const uint32_t hiB = __umulhi(M1, b), loB = M1 * b;
+            uint32_t hiA, loA, hiB, loB;
+            rs_mul(M0, a, hiA, loA);
+            rs_mul(M1, b, hiB, loB);
             c0w = hiB ^ c1w ^ K.rk0[rr];
             c1w = loB;
             c2w = hiA ^ c3w ^ K.rk1[rr];
