@@ -442,13 +442,18 @@ def ensemble_compare(P, steps: int, tune_cache=None, oracle_pool=None) -> dict:
         "replicas": sum(r.state()["R"] for r in runs),
     })
     if twin_job is not None:
-        o = twin_job.get()
-        g = twin_gpu["obs"]
         out["parity"]["oracle_instance"] = twin
-        out["parity"]["batched_equals_oracle"] = bool(
-            o["spins_sha"] == twin_gpu["sha"] and o["step"] == twin_gpu["step"] and
-            o["R"] == g["R"] and o["sumE"] == g["sumE"] and
-            abs(o["lnZ"] - g["lnZ"]) <= 1e-12 * abs(o["lnZ"]))
+        try:
+            o = twin_job.get(timeout=600)
+        except Exception as e:  # the comparison is reported, not allowed to end the bench
+            out["parity"]["batched_equals_oracle"] = None
+            out["parity"]["oracle_error"] = repr(e)[:200]
+        else:
+            g = twin_gpu["obs"]
+            out["parity"]["batched_equals_oracle"] = bool(
+                o["spins_sha"] == twin_gpu["sha"] and o["step"] == twin_gpu["step"] and
+                o["R"] == g["R"] and o["sumE"] == g["sumE"] and
+                abs(o["lnZ"] - g["lnZ"]) <= 1e-12 * abs(o["lnZ"]))
     batch.close()
     for r in runs:
         r.close()
@@ -597,6 +602,15 @@ def next_items_measure(P, steps: int = 5, R0: int = WORKLOAD["R0"]) -> dict:
     return out
 
 
+def arm_config(R0: int, first: int, steps: int, world: int) -> dict:
+    """The workload both arms report (the reference arm runs a bounded slice of
+    it, described in its cpu_baseline)."""
+    return {"workload": f"2D Ising L=64 bit-packed, R0=2^21 ({R0}), beta 0->1 in K=400 steps, "
+                        f"theta=10, steps {first}..{first + steps - 1}",
+            "l2": "population 2 x 1 GiB, larger than L2 (no flush needed)",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
+
+
 def run_reference(args):
     """The reference arm: the oracle as it stands, one single-threaded process
     per host core, each running W + K full PA steps of the L = 64 workload at
@@ -617,7 +631,9 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": r["seconds"] * 1e3 / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8",
-            "data": "synthetic", "config": {"workload": sample},
+            "data": "synthetic",
+            "config": arm_config(WORKLOAD["R0"], args.warmup + 1, args.steps,
+                                 int(os.environ.get("WORLD_SIZE", "1"))),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": procs, "kind": "oracle",
                              "sample": sample, "host": host_info()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -896,10 +912,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_graph / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": f"2D Ising L=64 bit-packed, R0=2^21 ({wl['R0']}), beta 0->1 in "
-                               f"K=400 steps, theta=10, steps {first}..{first + args.steps - 1}",
-                   "l2": "population 2 x 1 GiB, larger than L2 (no flush needed)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "config": arm_config(wl["R0"], first, args.steps, world),
         "resampled_replicas_per_s": resampled_per_s,
         "plain": {"value": value_plain, "ms_per_step": ms_plain / args.steps,
                   "note": "one launch per kernel per step, kernel events on"},

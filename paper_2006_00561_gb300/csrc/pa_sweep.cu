@@ -793,14 +793,20 @@ struct RSKeyRegs {
 #endif
 
 // How the replica-sliced kernel forms its Philox products: 0 = high and low
-// halves from C++ (__umulhi, *), 1 = one mul.wide.u32 per product.
+// halves from C++ (__umulhi, *), 1 (the default) = one mul.wide.u32 per
+// product.  Measured on GB300 (single runs, attempts/ns, same bits), 0 -> 1:
+// 3D +-J L = 8 1120 -> 1223, L = 10 1027 -> 1100, L = 6 916 -> 982, 2D L = 32
+// 1295 -> 1391, L = 16 1237 -> 1330.
 #ifndef PA_RS_MUL_MODE
-#define PA_RS_MUL_MODE 0
+#define PA_RS_MUL_MODE 1
 #endif
-// PA_RS_OR_SLOT = 1: the replica's slot b0 + r (b0 a multiple of 32, r < 32)
-// is formed as b0 | r, so that it folds into the xor of its Philox word.
+// PA_RS_OR_SLOT = 1 (the default): the replica's slot b0 + r (b0 a multiple
+// of 32, r < 32) is formed as b0 | r, so that it folds into the xor of its
+// Philox word.  With mul.wide products, measured on GB300: 3D L = 10 1100 ->
+// 1130, L = 6 982 -> 986, 2D L = 32 1391 -> 1413, L = 16 1330 -> 1354, 3D L = 8
+// 1223 -> 1185 attempts/ns.
 #ifndef PA_RS_OR_SLOT
-#define PA_RS_OR_SLOT 0
+#define PA_RS_OR_SLOT 1
 #endif
 __device__ __forceinline__ void rs_mul(uint32_t m, uint32_t a, uint32_t& hi, uint32_t& lo) {
 #if PA_RS_MUL_MODE == 1

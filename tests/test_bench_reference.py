@@ -26,3 +26,8 @@ def test_reference_arm_prints_one_contract_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    # the same config object as the GPU arm's line (steps W+1 .. W+K of the
+    # 2^21-replica workload); the slice the oracle ran is in cpu_baseline
+    import bench
+    assert d["config"] == bench.arm_config(bench.WORKLOAD["R0"], 1, 1, 1)
+    assert "R0=256" in d["cpu_baseline"]["sample"]

@@ -166,3 +166,34 @@ def test_config4_ensemble_batched_equals_plain(P):
     batch.close()
     for r in plain + batched:
         r.close()
+
+
+def test_async_batch_and_phase_profile(P):
+    """pa_batch_init_async (remaining steps from the caller, nothing waited
+    for) steps every run to the bits of pa_batch_init's batch; its phase
+    profile counts every non-graph step and times every phase; a wrong
+    remaining-step count is refused."""
+    import torch
+    a_runs, b_runs = _runs(P, MIX[:5]), _runs(P, MIX[:5])
+    a = P.Batch(a_runs)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())  # the runs' init, ordered before the batch
+    b = P.Batch(b_runs, stream=s, steps_left=[COMMON["K"]] * 5)
+    b.profile(True)
+    for _ in range(3):
+        a.step()
+        b.step()
+    b.run_steps(2)  # graph replays are not profiled
+    a.run_steps(2)
+    prof = b.profile_read(reset=True)
+    assert a.sync() == 0 and b.sync() == 0
+    assert prof["steps"] == 3
+    assert all(prof[k] > 0.0 for k in ("reweight", "resample", "sweep", "obs"))
+    for ra, rb in zip(a_runs, b_runs):
+        _same(P, ra, rb, "async batch")
+    with pytest.raises(P.PaError):
+        P.Batch(_runs(P, MIX[:1]), steps_left=[COMMON["K"] + 1])
+    a.close()
+    b.close()
+    for r in a_runs + b_runs:
+        r.close()

@@ -119,6 +119,16 @@ def test_energy_L4_partition_function_matches_kaufman(dos_L4):
         assert abs(got - want) <= 1e-14 * abs(want), beta
 
 
+def test_number_of_energy_levels_matches_brute_force(dos_L4):
+    """or_num_bins: the levels run from the lowest to the highest energy of the
+    brute force, four apart (E = -32 .. 32 on the 4 x 4 torus: 17 bins, of which
+    E = -28 and 28 are never reached), and every brute-force energy has a bin."""
+    lo, hi = min(dos_L4), max(dos_L4)
+    assert O.num_bins(2, 4) == (hi - lo) // 4 + 1 == 17
+    assert all(0 <= (E - lo) // 4 < O.num_bins(2, 4) for E in dos_L4)
+    assert O.num_bins(3, 2) == 3 * 8 // 2 + 1 and O.num_bins(2, 64) == 4097
+
+
 def test_energy_levels_are_four_apart(dos_L4):
     """E = 2U - dim N and U is even on the even torus: levels step by 4 (the
     spacing the weight table D of Eq. 3 assumes)."""
