@@ -1254,6 +1254,12 @@ void batch_release(pa_batch* b) {
     if (b->fork) cudaEventDestroy(b->fork);
     delete b;
 }
+
+// Shared body of pa_batch_init (steps_left == nullptr: each run's remaining
+// steps read from the device, then the uploads are waited for) and
+// pa_batch_init_async (remaining steps given by the caller, nothing waited for).
+int batch_init(pa_run* const* runs, int32_t nruns, const int32_t* steps_left, void* ws,
+               size_t bytes, void* stream, pa_batch** out);
 }  // namespace
 
 extern "C" {
@@ -1263,14 +1269,6 @@ size_t pa_batch_workspace_size(int32_t nruns) {
     size_t off[5];
     return batch_layout(nruns, off);
 }
-
-namespace {
-// Shared body of pa_batch_init (steps_left == nullptr: each run's remaining
-// steps read from the device, then the uploads are waited for) and
-// pa_batch_init_async (remaining steps given by the caller, nothing waited for).
-int batch_init(pa_run* const* runs, int32_t nruns, const int32_t* steps_left, void* ws,
-               size_t bytes, void* stream, pa_batch** out);
-}  // namespace
 
 int pa_batch_init(pa_run* const* runs, int32_t nruns, void* ws, size_t bytes, void* stream,
                   pa_batch** out) {

@@ -350,8 +350,12 @@ class PipelinedServer(Server):
             off = self.arena.alloc(need)
             if off is None:
                 break  # fragmented: wait for a retirement
-            req.run = P.Run(self._cfg(req.spec), stream=self.admit_stream,
-                            workspace=self.arena.view(off, need))
+            try:
+                req.run = P.Run(self._cfg(req.spec), stream=self.admit_stream,
+                                workspace=self.arena.view(off, need))
+            except Exception:
+                self.arena.release(off, need)
+                raise
             req.ws = (off, need)
             req.init_event = self._event()
             self._record(req.init_event, self.admit_stream)
@@ -383,9 +387,14 @@ class PipelinedServer(Server):
             off = self.arena.alloc(need)
             if off is None:
                 return False
-            self.cur_batch = P.Batch([r.run for r in active], stream=self.stream,
-                                     steps_left=[r.spec["K"] - r.enq for r in active],
-                                     workspace=self.arena.view(off, need))
+            try:
+                self.cur_batch = P.Batch([r.run for r in active], stream=self.stream,
+                                         steps_left=[r.spec["K"] - r.enq for r in active],
+                                         workspace=self.arena.view(off, need))
+            except Exception:
+                self.arena.release(off, need)
+                self.cur_batch = old
+                raise
             self.batch_ws[id(self.cur_batch)] = (off, need)
             self.batch_refs[id(self.cur_batch)] = 0
             self.cur_members = members

@@ -92,3 +92,57 @@ def test_pending_gather_blocks_other_calls_and_one_segment_is_a_plain_step(P):
             assert np.array_equal(a.dump(what), b.dump(what))
     a.close()
     b.close()
+
+
+def test_exchange_at_the_paper_workload_every_replica(P):
+    """The paper's workload (Sec. 3): 8 GPUs x 20 480 replicas of the 2D Ising
+    model at L = 64, beta 0 -> 1 in 200 steps, theta = 1, naive exchange.
+    After 90 steps on the device (the critical region, where the naive rule
+    moves the most replicas), the oracle recomputes step 91 for every replica
+    from the device's state: copy counts, copies, the exchanged slot order and
+    the sweep (spread over one spawned process per host core); the device's
+    step 91 equals it replica for replica."""
+    import multiprocessing as mpc
+    import os
+
+    from test_gpu_fullsize import _oracle_sweep_slice
+    kw = dict(dim=2, L=64, R0=8 * 20480, K=200, theta=1, seed=2006)
+    ocfg = O.make_config(**kw)
+    run = P.Run(P.make_config(layout=P.LAYOUT_PACKED, **kw))
+    N = 8
+    bounds = RD.bounds_from_loads(RD.desired_loads(kw["R0"], N))
+    for _ in range(90):
+        bounds = RD.exchange_step(run, bounds, "naive")["bounds"]
+        run.sweep(kw["theta"])
+    st0 = run.state()
+    assert st0["status_bits"] == 0 and st0["step"] == 90
+    spins0 = run.dump(P.DUMP_SPINS).reshape(st0["R"], -1)
+    ebin0 = run.dump(P.DUMP_EBIN)
+    hist0 = run.dump(P.DUMP_HIST)
+    x = RD.exchange_step(run, bounds, "naive")
+    assert x["moves"], "the naive rule moves replicas near the critical point"
+    run.sweep(kw["theta"])
+    st = run.state()
+    step = st["step"]
+    Dtab = np.array([O.weight(O.beta(ocfg, step) - O.beta(ocfg, step - 1), j)
+                     for j in range(st["bins"])])
+    S, kref, n, F = O.tau_table(hist0, Dtab, ocfg.R0)
+    assert st["S"] == S and st["kref"] == kref
+    counts = O.copy_counts(ocfg, step, ebin0, n, F)
+    assert np.array_equal(run.dump(P.DUMP_COUNTS), counts)
+    copies = np.repeat(spins0, counts, axis=0)
+    del spins0
+    perm = np.concatenate([np.arange(a, a + k) for a, k in x["segments"]])
+    pre = copies[perm]
+    del copies
+    T = [O.threshold(O.beta(ocfg, step), 4 * (c + 1)) for c in range(3)]
+    g0 = (step - 1) * kw["theta"]
+    procs = max(1, min(32, os.cpu_count() or 1))
+    cuts = np.linspace(0, pre.shape[0], procs + 1).astype(int)
+    jobs = [(kw, pre[a:b], int(a), g0, T) for a, b in zip(cuts[:-1], cuts[1:])]
+    with mpc.get_context("spawn").Pool(procs) as pool:
+        want = np.concatenate(pool.map(_oracle_sweep_slice, jobs))
+    got = run.dump(P.DUMP_SPINS).reshape(st["R"], -1)
+    bad = np.nonzero((got != want).any(axis=1))[0]
+    assert bad.size == 0, f"{bad.size} replicas differ, first {bad[:5]}"
+    run.close()
