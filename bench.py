@@ -483,7 +483,8 @@ def serving_measure(P, prefix: int = 24) -> dict:
     def summary(st):
         return {k: st.get(k) for k in ("served", "served_attempts_per_ns", "p50_latency_s",
                                        "p99_latency_s", "max_resident", "iterations", "wall_s",
-                                       "gpu_idle_fraction", "device_busy_s")}
+                                       "gpu_idle_fraction", "device_busy_s",
+                                       "device_attempts_per_ns")}
     for name, cls in (("pipelined", serve.PipelinedServer), ("sync", serve.Server)):
         srv = cls(hbm_budget=64 << 30, quantum=8)
         st = srv.run_trace([dict(t) for t in trace])

@@ -510,6 +510,11 @@ class PipelinedServer(Server):
         out = super().stats()
         out["quanta"] = self.quanta
         out["device_busy_s"] = self.busy_ms / 1e3
+        if self.keep_history and self.busy_ms > 0:
+            # the batched form's own rate on this mix: attempts over the
+            # quanta's device time
+            out["device_attempts_per_ns"] = (sum(r.attempts() for r in self.done) /
+                                             (self.busy_ms * 1e6))
         if self.first_start is not None and self.last_end is not None:
             span = self.first_start.elapsed_time(self.last_end)
             out["device_span_s"] = span / 1e3

@@ -146,3 +146,38 @@ def test_exchange_at_the_paper_workload_every_replica(P):
     bad = np.nonzero((got != want).any(axis=1))[0]
     assert bad.size == 0, f"{bad.size} replicas differ, first {bad[:5]}"
     run.close()
+
+
+def test_exchange_scan_timeout_is_reported_and_the_context_survives(P):
+    """The scan of pa_resample_begin has the resample's bounded lookback wait:
+    with tile 0's prefix withheld (test hook) the wait runs out, the sticky
+    PA_ERR_TIMEOUT is reported, the pending gather can still be finished (every
+    copy stays inside the population buffers), and a fresh run on the same
+    context then follows the oracle."""
+    import time
+    spec = dict(dim=2, L=16, layout=1, R0=5000, K=4, theta=1, seed=3)  # 3 scan tiles
+    _, gcfg = configs(P, **spec)
+    run = P.Run(gcfg)
+    run.step()
+    assert run.status() == 0
+    P.pa_debug(run.h, P.DEBUG_WITHHOLD_PREFIX)
+    t0 = time.perf_counter()
+    run.resample_begin()
+    assert run.status() == -5  # PA_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 60.0
+    run.resample_finish([(0, run.state()["R"])])
+    assert run.status() == -5
+    run.close()
+    ocfg, gcfg = configs(P, **spec)
+    orun, grun = O.Run(ocfg), P.Run(gcfg)
+    bounds = RD.bounds_from_loads(RD.desired_loads(spec["R0"], 4))
+    for i in range(1, 3):
+        assert orun.resample() == 0
+        x = RD.exchange_step(grun, bounds, "naive")
+        assert orun.permute(x["segments"]) == 0
+        bounds = x["bounds"]
+        assert orun.sweep(1) == 0
+        grun.sweep(1)
+        compare_state(P, grun, orun, i)
+    grun.close()
+    orun.close()
