@@ -43,6 +43,22 @@ __device__ __forceinline__ unsigned long long desc_make(unsigned long long flag,
     return (flag << 62) | ((unsigned long long)(epoch & 0x3fffffffu) << 32) | value;
 }
 
+// The batched kernels stage a run's descriptor in shared memory (PA_RS_STAGE
+// = 1): read from global memory, its fields could alias the kernel's own
+// global stores, so the compiler would reload them after every store.
+#ifndef PA_RS_STAGE
+#define PA_RS_STAGE 1
+#endif
+static_assert(sizeof(RunDev) % 4 == 0, "RunDev is copied in 32-bit words");
+
+// Copies *src into the shared descriptor dst with all threads of the CTA; the
+// caller synchronises before reading it.
+__device__ __forceinline__ void stage_run(const RunDev* src, RunDev& dst) {
+    const uint32_t* from = reinterpret_cast<const uint32_t*>(src);
+    uint32_t* to = reinterpret_cast<uint32_t*>(&dst);
+    for (uint32_t w = threadIdx.x; w < sizeof(RunDev) / 4; w += blockDim.x) to[w] = from[w];
+}
+
 // Reweight of one run by nblk 256-thread CTAs (plain: k_tau, batched: one
 // CTA per run of k_tau_batched).  Every CTA finds kref and S itself (the same
 // fixed order, so the same bits) and writes the tau entries of its share of
@@ -160,7 +176,14 @@ __global__ void __launch_bounds__(256) k_tau(RunDev d) { tau_run(d, blockIdx.x, 
 // reader); CTA 0 clears the batch's work counters.
 __global__ void __launch_bounds__(256) k_tau_batched(BatchDev b) {
     if (blockIdx.x == 0 && threadIdx.x < b.ncounters) b.counters[threadIdx.x] = 0u;
+#if PA_RS_STAGE
+    __shared__ RunDev s_d;
+    stage_run(&b.runs[blockIdx.x], s_d);
+    __syncthreads();
+    const RunDev& d = s_d;
+#else
     const RunDev& d = b.runs[blockIdx.x];
+#endif
     tau_run(d, 0, 1);
     __syncthreads();
     for (uint32_t k = threadIdx.x; k < (uint32_t)d.bins; k += blockDim.x) d.hist[k] = 0u;
@@ -633,6 +656,10 @@ template <int RULE>
 __global__ void __launch_bounds__(RS_THREADS) k_resample_batched(BatchDev b) {
     __shared__ ResampleSmem sm;
     __shared__ uint32_t s_run;
+#if PA_RS_STAGE
+    __shared__ RunDev s_d;
+    uint32_t have = 0xffffffffu;
+#endif
     for (;;) {
         if (threadIdx.x == 0) {
             const uint32_t g = atomicAdd(&b.counters[0], 1u);
@@ -651,7 +678,16 @@ __global__ void __launch_bounds__(RS_THREADS) k_resample_batched(BatchDev b) {
         }
         __syncthreads();
         if (s_run == 0xffffffffu) break;
+#if PA_RS_STAGE
+        if (s_run != have) {
+            stage_run(&b.runs[s_run], s_d);
+            have = s_run;
+            __syncthreads();
+        }
+        const RunDev& d = s_d;
+#else
         const RunDev& d = b.runs[s_run];
+#endif
         if (d.st->active) resample_tile<RULE>(d, sm.tile, sm);
         __syncthreads();
     }
@@ -724,7 +760,14 @@ __device__ __forceinline__ void obs_run(const RunDev& d, int nsweeps) {
 __global__ void __launch_bounds__(256) k_obs(RunDev d, int nsweeps) { obs_run(d, nsweeps); }
 
 __global__ void __launch_bounds__(256) k_obs_batched(BatchDev b) {
+#if PA_RS_STAGE
+    __shared__ RunDev s_d;
+    stage_run(&b.runs[blockIdx.x], s_d);
+    __syncthreads();
+    const RunDev& d = s_d;
+#else
     const RunDev& d = b.runs[blockIdx.x];
+#endif
     obs_run(d, d.theta);
 }
 
