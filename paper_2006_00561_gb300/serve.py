@@ -223,6 +223,9 @@ class Server:
                         "mean_latency_s": float(lat.mean())})
         if attempts is not None and wall > 0:
             out["served_attempts_per_ns"] = attempts / (wall * 1e9)
+        if wall > 0 and type(self) is Server:
+            # the device works only while the host waits in the steps phase
+            out["gpu_idle_fraction_host_estimate"] = max(0.0, 1.0 - self.phase_s["steps"] / wall)
         return out
 
 

@@ -1,6 +1,6 @@
 """Planted mistakes: each one is applied to a copy of oracle/pa_oracle.c on the
 CPU, compiled, and the pins of test_oracle_pins.py / test_oracle_pa_statistics.py
-are run against it.  Every plausible slip listed here must make a pin fail; a
+/ test_redistribute.py are run against it.  Every plausible slip listed here must make a pin fail; a
 mutant that passes means a hole in the pins."""
 from __future__ import annotations
 
@@ -100,6 +100,15 @@ MUTANTS = [
      "uint64_t v = (uint64_t)out[0] | ((uint64_t)out[1] << 32);", "multinomial"),
     ("ground_state_lnZ_wrong_sign", "r->lnZ = log(2.0) + c->beta0 *",
      "r->lnZ = log(2.0) - c->beta0 *", "heating_starts"),
+    # the exchange between virtual GPUs (or_permute)
+    ("permute_tracked_energy_left_behind", "            r->U2[dst] = r->U[from];\n        }\n"
+     "    int8_t* ts", "        }\n    int8_t* ts", "permute_moves_whole_replicas"),
+    ("permute_ignores_the_source_slot", "int64_t from = src[q] + k;", "int64_t from = dst;",
+     "permute_moves_whole_replicas"),
+    ("permute_repeats_the_segment_start", "int64_t from = src[q] + k;",
+     "int64_t from = src[q];", "permute_moves_whole_replicas"),
+    ("permute_lengths_not_checked", "    if (total != r->R) return -1;\n    int64_t dst = 0;",
+     "    int64_t dst = 0;", "permute_moves_whole_replicas"),
 ]
 
 
@@ -123,7 +132,8 @@ def test_planted_mistake_is_caught(tmp_path, name, old, new, keys):
     env = dict(os.environ, PA_ORACLE_LIB=lib)
     cmd = [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
            os.path.join(HERE, "test_oracle_pins.py"),
-           os.path.join(HERE, "test_oracle_pa_statistics.py"), "-k", keys]
+           os.path.join(HERE, "test_oracle_pa_statistics.py"),
+           os.path.join(HERE, "test_redistribute.py"), "-k", keys]
     proc = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=900, cwd=ROOT)
     tail = proc.stdout[-400:]
     assert "passed" in tail or "failed" in tail, tail + proc.stderr[-400:]
