@@ -1192,9 +1192,6 @@ uint32_t auto_chunk(uint32_t total_slots, int grid, int warps) {
     return chunk;
 }
 
-// One batched step: reweight and resample of every run on s, then the sweep
-// classes as parallel branches (fork / join through events), then the
-// observables of every run on s.
 cudaEvent_t batch_event(pa_batch* b) {
     if (!b->ev_pool.empty()) {
         cudaEvent_t e = b->ev_pool.back();
@@ -1206,15 +1203,36 @@ cudaEvent_t batch_event(pa_batch* b) {
     return e;
 }
 
+int enqueue_batch_launches(pa_batch* b, cudaStream_t s, bool timing,
+                           const std::array<cudaEvent_t, 5>& ev);
+
+// One batched step: reweight and resample of every run on s, then the sweep
+// classes as parallel branches (fork / join through events), then the
+// observables of every run on s.  With phase timing on (and s the batch's own
+// stream) the phases are bracketed by pooled events.
 int enqueue_batch_step(pa_batch* b, cudaStream_t s) {
     std::array<cudaEvent_t, 5> ev{};
     const bool timing = b->prof && s == b->stream;
+    int got = 0;
     if (timing) {
-        for (auto& e : ev) {
-            e = batch_event(b);
-            if (!e) return PA_ERR_CUDA;
+        for (; got < 5; ++got) {
+            ev[got] = batch_event(b);
+            if (!ev[got]) break;
         }
     }
+    int rc = timing && got < 5 ? PA_ERR_CUDA : enqueue_batch_launches(b, s, timing, ev);
+    if (timing) {
+        if (rc == PA_OK) {
+            b->pending.push_back(ev);
+        } else {
+            for (int k = 0; k < got; ++k) b->ev_pool.push_back(ev[k]);
+        }
+    }
+    return rc;
+}
+
+int enqueue_batch_launches(pa_batch* b, cudaStream_t s, bool timing,
+                           const std::array<cudaEvent_t, 5>& ev) {
     auto mark = [&](int k) { return timing ? cudaEventRecord(ev[k], s) : cudaSuccess; };
     CK(mark(0));
     CK(pa::launch_tau_batched(b->bd, s));
@@ -1237,7 +1255,6 @@ int enqueue_batch_step(pa_batch* b, cudaStream_t s) {
     CK(mark(3));
     CK(pa::launch_obs_batched(b->bd, s));
     CK(mark(4));
-    if (timing) b->pending.push_back(ev);
     return PA_OK;
 }
 

@@ -804,8 +804,9 @@ static int resample_wave(const void* fn, int which, uint32_t tiles) {
 // slot -> source map, levels and magnetisations) and then k_gather over the
 // whole new population; 0 (the default): one kernel that gathers tile by
 // tile.  Measured on GB300 at 2^21 replicas, L = 64, same bits: one kernel
-// 0.366 ms; two kernels 0.374 ms (16 loads in flight per thread, 2 CTAs of 256
-// per SM), 0.380 ms (4 loads, 4 CTAs), 0.385 ms (8 loads, 3 CTAs).  The split
+// 0.366 ms with 4 loads in flight per thread in its gather (0.361 ms with 6,
+// the default); two kernels 0.374 ms (16 loads in flight per thread, 2 CTAs of
+// 256 per SM), 0.380 ms (4 loads, 4 CTAs), 0.385 ms (8 loads, 3 CTAs).  The split
 // form serves the redistribution's gather (pa_resample_finish), whose slot
 // order is only known after the host has read the scan.
 #ifndef PA_RS_SPLIT
