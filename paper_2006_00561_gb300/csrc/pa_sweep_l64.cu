@@ -206,6 +206,21 @@ static_assert(PA_L64_CHAIN >= 1 && PA_L64_CHAIN <= 4, "PA_L64_CHAIN: 1 .. 4");
 #ifndef PA_L64_HUNROLL
 #define PA_L64_HUNROLL 4
 #endif
+// Groups of four blocks unrolled together (a row's colour sites are two groups
+// at L = 64 and four at L = 128).  Measured on GB300, same bits: at L = 64
+// both groups together (125 registers, no spills) run at 1674 attempts/ns
+// against 1606 one at a time (ferromagnet, 2^21 replicas), 1631 against 1575
+// (+-J, 2^20) and 1601 against 1557 (batched, 8 +-J runs of 2^17); with two
+// Philox blocks per group unrolled instead of four, 1573.  At L = 128 two of
+// the four groups together run at 1484 against 1437 (ferromagnet, 12 warps,
+// 166 registers) and 1497 against 1361 (+-J, 8 warps); all four spill.
+#ifndef PA_L64_QUNROLL
+#define PA_L64_QUNROLL 2
+#endif
+#ifndef PA_L128_QUNROLL
+#define PA_L128_QUNROLL 2
+#endif
+constexpr int L64_QUNROLL = PA_L64_QUNROLL, L128_QUNROLL = PA_L128_QUNROLL;
 
 #ifndef PA_L64_SEL_BLOCKS
 #define PA_L64_SEL_BLOCKS 0
@@ -259,7 +274,7 @@ __device__ __forceinline__ void row_accepts(const Keys& d, const HalfSweepGen& g
     constexpr bool F8 = PA_L64_CHAIN == 1 || PA_L64_CHAIN == 4;
     const uint32_t c4 = F4 ? 0u - t4.T : t4.T, c8 = F8 ? 0u - t8.T : t8.T;
     uint32_t h4[2], h8[2];
-#pragma unroll 1
+#pragma unroll L64_QUNROLL
     for (uint32_t q = 0; q < 2; ++q) {
         const uint32_t base = 8u * y + 4u * q;
         const uint32_t kc = group_tests<F4, F8, PA_L64_HUNROLL>(
@@ -518,11 +533,12 @@ __global__ void __launch_bounds__(WARPS64 * 32, PA_L64_MIN_BLOCKS) k_sweep_l64_b
 // one after the other: the sites a half-sweep flips have the active colour,
 // and the classes of active-colour sites depend only on the other colour.
 // --------------------------------------------------------------------------
-// Block warps: the ferromagnet fits 12 warps (152 registers, no spills; 2.7 %
-// faster than 8 on GB300), the +-J kernel holds eight rows of couplings more
-// and keeps 8 warps (12 spill and run 7 % slower).
+// Block warps: with two groups unrolled, the ferromagnet runs at 1508 to 1517
+// attempts/ns with 8 warps (183 registers) against 1484 with 12 (166
+// registers) on GB300, 2^19 replicas; the +-J kernel holds eight rows of
+// couplings more and keeps 8 warps (12 spill).
 #ifndef PA_L128_WARPS
-#define PA_L128_WARPS 12
+#define PA_L128_WARPS 8
 #endif
 #ifndef PA_L128_WARPS_PMJ
 #define PA_L128_WARPS_PMJ 8
@@ -553,7 +569,7 @@ __device__ __forceinline__ void row_accepts128(const Keys& d, const HalfSweepGen
     const uint32_t one = d.one;
     constexpr uint32_t EV = 0x55555555u;
     uint32_t h4[4], h8[4];
-#pragma unroll 1
+#pragma unroll L128_QUNROLL
     for (uint32_t q = 0; q < 4; ++q) {
         const uint32_t base = 16u * y + 4u * q;
         const uint32_t kc = group_tests<false, false, L128_HUNROLL>(
