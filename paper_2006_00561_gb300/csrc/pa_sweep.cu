@@ -808,6 +808,16 @@ struct RSKeyRegs {
 #ifndef PA_RS_OR_SLOT
 #define PA_RS_OR_SLOT 1
 #endif
+// Replicas of a group whose Philox blocks are unrolled together.  Measured on
+// GB300 (attempts/ns, same bits; 1, 2, 4, 8 unrolled): 3D +-J L = 6 941, 965,
+// 962, 964; L = 8 1149, 1160, 1199, 1220; L = 10 1033, 1045, 1050, 1059; 2D
+// L = 32 1370, 1419, 1427, 1422; batched, 16 3D +-J L = 8 runs 1217, 1245,
+// 1243, 1236.  Two stays the default: the batched form, which runs the
+// disorder ensembles, is fastest there.
+#ifndef PA_RS_RUNROLL
+#define PA_RS_RUNROLL 2
+#endif
+constexpr int RS_RUNROLL = PA_RS_RUNROLL;
 __device__ __forceinline__ void rs_mul(uint32_t m, uint32_t a, uint32_t& hi, uint32_t& lo) {
 #if PA_RS_MUL_MODE == 1
     uint64_t p;
@@ -850,7 +860,7 @@ __device__ __forceinline__ void rs_group(uint32_t* S, const uint8_t* JS, int k, 
     const uint32_t z3k = (M0 * y0) ^ K.rk1[2];
     const uint32_t w0s = __umulhi(M1, z2) ^ K.rk0[2];  // round 3, shared half
     const uint32_t w1 = M1 * z2;
-#pragma unroll 2
+#pragma unroll RS_RUNROLL
     for (int r = 31; r >= 0; --r) {
         // b0 is a multiple of 32 and r < 32: b0 | r is the slot b0 + r
         const uint32_t y2 = PA_RS_OR_SLOT ? y2s ^ (b0 | (uint32_t)r) : y2s ^ (b0 + (uint32_t)r);
