@@ -526,9 +526,10 @@ class PipelinedServer(Server):
 
 
 def main(argv=None):
-    """python -m paper_2006_00561_gb300.serve --requests 256 --rate 50
-    Serves the seeded request trace in real time and prints latency /
-    throughput statistics (offered vs served load) as one JSON line."""
+    """python -m paper_2006_00561_gb300.serve --requests 256 --rate 50 [--server sync]
+    Serves the seeded request trace in real time (by the pipelined server
+    unless --server sync) and prints latency / throughput statistics
+    (offered vs served load) as one JSON line."""
     import argparse
     import json
 
@@ -541,14 +542,20 @@ def main(argv=None):
     ap.add_argument("--quantum", type=int, default=8)
     ap.add_argument("--r0-exp", type=int, nargs=2, default=(12, 18))
     ap.add_argument("--k-range", type=int, nargs=2, default=(100, 300))
+    ap.add_argument("--server", choices=("pipelined", "sync"), default="pipelined")
+    ap.add_argument("--depth", type=int, default=2)
     a = ap.parse_args(argv)
     trace = workloads.serving_trace(a.requests, rate=a.rate, seed=a.seed, R0_exp=tuple(a.r0_exp),
                                     K_range=tuple(a.k_range))
     offered = sum(t["R0"] * t["L"] ** t["dim"] * t["theta"] * t["K"] for t in trace)
     span = trace[-1]["arrival"]
-    srv = Server(hbm_budget=int(a.budget_gb * (1 << 30)), quantum=a.quantum)
+    budget = int(a.budget_gb * (1 << 30))
+    if a.server == "sync":
+        srv = Server(hbm_budget=budget, quantum=a.quantum)
+    else:
+        srv = PipelinedServer(hbm_budget=budget, quantum=a.quantum, depth=a.depth)
     st = srv.run_trace(trace)
-    st.update({"requests": a.requests, "rate_per_s": a.rate, "seed": a.seed,
+    st.update({"server": a.server, "requests": a.requests, "rate_per_s": a.rate, "seed": a.seed,
                "offered_attempts": offered, "offered_attempts_per_ns": offered / (span * 1e9),
                "trace_span_s": span, "R0_exp": list(a.r0_exp), "K_range": list(a.k_range)})
     print(json.dumps(st))
