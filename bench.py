@@ -51,9 +51,9 @@ OPS_PER_ATTEMPT = 19.5
 ALU_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12
 # DRAM bytes of one sweep launch, from the ncu capture of the same kernel at
 # 2^20 replicas, four times L2 (profiles/k_sweep_l64_ising2d_L64_R2p18.md:
-# 538.2 MB read + 483.3 MB written), scaled by the replica count to 2^21.
+# 539.9 MB read + 483.6 MB written), scaled by the replica count to 2^21.
 # None whenever the kernel changes, until the next capture.
-SWEEP_TRAFFIC_BYTES_2P21 = (538.223616e6 + 483.294208e6) * 2
+SWEEP_TRAFFIC_BYTES_2P21 = (539.905792e6 + 483.599360e6) * 2
 # Slot ranges of the e2e step: each range's copy to the host (~0.7 ms at 1/8 of
 # 1 GiB) runs while the next range sweeps (~7 ms).
 E2E_CHUNKS = 8
@@ -653,8 +653,8 @@ def run_reference(args):
 
 def philox_ceiling(P, sweep_attempts_per_ns: float) -> dict:
     """The register kernels' generator alone (pa_bench_philox): the same
-    Philox blocks in k_sweep_l64's launch shape with no acceptance tests and
-    no lattice work.  A sweep attempt consumes one uniform, so the sweep
+    Philox blocks with no acceptance tests and no lattice work, one 16-warp
+    block per SM (its fastest shape; the sweep kernel runs 12 warps).  A sweep attempt consumes one uniform, so the sweep
     kernel's attempts/ns over this kernel's uniforms/ns is the fraction of the
     generator's own ceiling that the sweep reaches."""
     import torch

@@ -41,8 +41,12 @@ namespace {
 #define PA_L64_MUL_MODE 1
 #endif
 
+// Warps per block (one block per SM).  With both groups of a row unrolled,
+// measured on GB300 (attempts/ns, same bits): 16 warps (125 registers) 1671,
+// 12 warps (152) 1686, 8 warps (212) 1653 (ferromagnet, 2^21 replicas); +-J
+// 2^20: 1626, 1636, 1611; batched, 8 +-J runs of 2^17: 1597, 1632, 1604.
 #ifndef PA_L64_WARPS
-#define PA_L64_WARPS 16
+#define PA_L64_WARPS 12
 #endif
 constexpr int WARPS64 = PA_L64_WARPS;
 
@@ -836,7 +840,14 @@ struct PhiloxRateArgs {
     uint32_t* out;
 };
 
-__global__ void __launch_bounds__(WARPS64 * 32, PA_L64_MIN_BLOCKS)
+// The generator alone runs one block of PHILOX_RATE_WARPS warps per SM: on
+// GB300 16 warps draw 2135 uniforms/ns, 12 warps 2119, 8 warps 2058.
+#ifndef PA_PHILOX_RATE_WARPS
+#define PA_PHILOX_RATE_WARPS 16
+#endif
+constexpr int PHILOX_RATE_WARPS = PA_PHILOX_RATE_WARPS;
+
+__global__ void __launch_bounds__(PHILOX_RATE_WARPS * 32, 1)
     k_philox_rate(__grid_constant__ const PhiloxRateArgs a) {
     const Keys K{a.rk0, a.rk1, a.one};
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -891,7 +902,7 @@ cudaError_t launch_sweep_l64(const RunDev& d, int nsweeps, int grid, cudaStream_
     return cudaGetLastError();
 }
 
-// One 16-warp block per SM, as k_sweep_l64 runs.
+// One block per SM.
 static int philox_rate_grid() {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
@@ -899,7 +910,7 @@ static int philox_rate_grid() {
     return sms;
 }
 
-int philox_rate_threads() { return philox_rate_grid() * WARPS64 * 32; }
+int philox_rate_threads() { return philox_rate_grid() * PHILOX_RATE_WARPS * 32; }
 
 cudaError_t launch_philox_rate(uint64_t seed, uint32_t halfsweeps, uint32_t* out, cudaStream_t s) {
     const int grid = philox_rate_grid();
@@ -912,7 +923,7 @@ cudaError_t launch_philox_rate(uint64_t seed, uint32_t halfsweeps, uint32_t* out
     a.one = 1u;
     a.halfsweeps = halfsweeps;
     a.out = out;
-    k_philox_rate<<<grid, WARPS64 * 32, 0, s>>>(a);
+    k_philox_rate<<<grid, PHILOX_RATE_WARPS * 32, 0, s>>>(a);
     return cudaGetLastError();
 }
 
