@@ -858,25 +858,39 @@ def main():
             P.pa_load_ptr(run.h, P.DUMP_SPINS_RAW, host.data_ptr(), R_now, R_now * stride)
             run.step_stream(host, E2E_CHUNKS, copy_stream)
             R_now = run.observables()["R"]
+        # device-side split of every timed step: the upload (copy + measurement
+        # pass) and the streamed step with its copies out, by events on the
+        # run's stream (they add no synchronisation)
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)]
+               for _ in range(args.steps)]
         barrier()
         t0 = time.perf_counter()
         h2d = d2h = 0
         e2e_attempts = 0
-        for _ in range(args.steps):
+        for i in range(args.steps):
+            evs[i][0].record(stream)
             P.pa_load_ptr(run.h, P.DUMP_SPINS_RAW, host.data_ptr(), R_now, R_now * stride)
             h2d += R_now * stride
+            evs[i][1].record(stream)
             # the step, with the new population copied back range by range
             # while the later ranges sweep
             run.step_stream(host, E2E_CHUNKS, copy_stream)
+            evs[i][2].record(stream)
             o = run.observables()  # returns once the copies are done
             R_now = o["R"]
             e2e_attempts += R_now * N * theta
             d2h += R_now * stride + 104
         barrier()
         dt = time.perf_counter() - t0
+        up = sorted(e[0].elapsed_time(e[1]) for e in evs)
+        st_ms = sorted(e[1].elapsed_time(e[2]) for e in evs)
         dt, e2e_attempts = aggregate(dist, dt, e2e_attempts, "cuda")
         e2e = {"value": e2e_attempts / (dt * 1e9), "unit": UNIT,
                "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps,
+               "wall_ms_per_step": dt * 1e3 / args.steps,
+               "device_ms_per_step_median": {"upload": up[len(up) // 2],
+                                             "streamed_step": st_ms[len(st_ms) // 2]},
+               "upload_ms_min_max": [up[0], up[-1]],
                "path": "pa_load(pinned host population) + pa_step_stream(population back "
                        f"to pinned host in {E2E_CHUNKS} ranges, copies overlapping the sweeps) + "
                        "pa_observables every step"}

@@ -830,36 +830,57 @@ __device__ __forceinline__ void rs_mul(uint32_t m, uint32_t a, uint32_t& hi, uin
 #endif
 }
 
-// One half-sweep group: sites of pairs 4k .. 4k + 3, colour c, 32 replicas.
-template <int DIM, int L, bool PMJ, typename KT>
-__device__ __forceinline__ void rs_group(uint32_t* S, const uint8_t* JS, int k, int c, uint32_t g,
-                                         uint32_t b0, uint32_t ctag, const KT& K,
-                                         const SweepCtx& x) {
+// Groups of a lane that share one pass over the 32 replicas (PA_RS_KG = 1, 2
+// or 4, at most what the lattice's group count fills; see rs_kg below).
+// Measured on GB300 (attempts/ns, same bits; up to 1, 2, 4 groups per pass):
+// 3D +-J L = 8 1157, 1206, 1208 (two groups fill it); L = 10 1042, 1129, 1232;
+// 2D L = 32 1416, 1433, 1502; batched, 16 3D +-J L = 8 runs 1242, 1301, 1302,
+// 12 runs of L = 6, 8, 10 1120, 1149, 1168; L = 6 (27 groups, one per lane)
+// 961 in every form.
+#ifndef PA_RS_KG
+#define PA_RS_KG 4
+#endif
+
+// KG half-sweep groups of one lane: the sites of pairs 4k .. 4k + 3, colour c,
+// for k = k0, k0 + 32, .., k0 + 32 (KG - 1) (those below NGROUPS), 32
+// replicas.  Philox of the replicas' blocks, counter (2 g + colour, k, SWEEP |
+// instance, slot): round 1 multiplies only words that every block of the
+// half-sweep shares (the group index enters word 1 and the slot word 3, both
+// by xors); round 2 multiplies one group word (shared by the 32 replicas) and
+// one replica word (shared by the groups), round 3 again one of each.  The
+// group products are formed once per group, the replica products once per
+// replica for all KG groups: a block costs 14 + 2 / KG multiplies.
+template <int DIM, int L, bool PMJ, typename KT, int KG>
+__device__ __forceinline__ void rs_groups(uint32_t* S, const uint8_t* JS, int k0, int c,
+                                          uint32_t g, uint32_t b0, uint32_t ctag, const KT& K,
+                                          const SweepCtx& x) {
     using G = RSGeo<DIM, L, PMJ>;
     constexpr int NC = G::NCLS;
     constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
     const uint32_t T[3] = {x.T0, x.T1, x.T2};
     const uint32_t nT[3] = {x.nT0, x.nT1, x.nT2};
     const uint32_t two = x.one << 1;
-    uint32_t acc[4][NC];
+    uint32_t acc[KG][4][NC];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int q = 0; q < KG; ++q)
 #pragma unroll
-        for (int cl = 0; cl < NC; ++cl) acc[i][cl] = 0u;
-    // Philox of the 32 replicas' blocks, counter (2 g + colour, k, SWEEP |
-    // instance, slot): round 1 multiplies only words the 32 blocks share (the
-    // slot enters word 2 by an xor), rounds 2 and 3 multiply one shared and
-    // one replica word each; the shared products are formed once here, so a
-    // block costs 16 multiplies
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int cl = 0; cl < NC; ++cl) acc[q][i][cl] = 0u;
     const uint32_t c0 = 2u * g + (uint32_t)c;
-    const uint32_t y0 = __umulhi(M1, ctag) ^ (uint32_t)k ^ K.rk0[0];  // round 1
+    const uint32_t y0s = __umulhi(M1, ctag) ^ K.rk0[0];  // round 1, before the xor with k
     const uint32_t y1 = M1 * ctag;
     const uint32_t y2s = __umulhi(M0, c0) ^ K.rk1[0];  // word 2 before the xor with the slot
     const uint32_t y3 = M0 * c0;
-    const uint32_t z2 = __umulhi(M0, y0) ^ y3 ^ K.rk1[1];  // round 2, shared half
-    const uint32_t z3k = (M0 * y0) ^ K.rk1[2];
-    const uint32_t w0s = __umulhi(M1, z2) ^ K.rk0[2];  // round 3, shared half
-    const uint32_t w1 = M1 * z2;
+    uint32_t z3k[KG], w0s[KG], w1[KG];
+#pragma unroll
+    for (int q = 0; q < KG; ++q) {
+        const uint32_t y0 = y0s ^ (uint32_t)(k0 + 32 * q);
+        const uint32_t z2 = __umulhi(M0, y0) ^ y3 ^ K.rk1[1];  // round 2, group half
+        z3k[q] = (M0 * y0) ^ K.rk1[2];
+        w0s[q] = __umulhi(M1, z2) ^ K.rk0[2];  // round 3, group half
+        w1[q] = M1 * z2;
+    }
 #pragma unroll RS_RUNROLL
     for (int r = 31; r >= 0; --r) {
         // b0 is a multiple of 32 and r < 32: b0 | r is the slot b0 + r
@@ -867,84 +888,110 @@ __device__ __forceinline__ void rs_group(uint32_t* S, const uint8_t* JS, int k, 
         uint32_t h2, z1;
         rs_mul(M1, y2, h2, z1);                                 // round 2, replica half
         const uint32_t z0 = h2 ^ y1 ^ K.rk0[1];
-        uint32_t c0w = w0s ^ z1;                                // round 3, replica half
-        uint32_t c1w = w1;
-        uint32_t h3, c3w;
-        rs_mul(M0, z0, h3, c3w);
-        uint32_t c2w = h3 ^ z3k;
+        uint32_t h3, c3r;
+        rs_mul(M0, z0, h3, c3r);                                // round 3, replica half
 #pragma unroll
-        for (int rr = 3; rr < 10; ++rr) {
-            const uint32_t a = c0w, b = c2w;
-            uint32_t hiA, loA, hiB, loB;
-            rs_mul(M0, a, hiA, loA);
-            rs_mul(M1, b, hiB, loB);
-            c0w = hiB ^ c1w ^ K.rk0[rr];
-            c1w = loB;
-            c2w = hiA ^ c3w ^ K.rk1[rr];
-            c3w = loA;
+        for (int q = 0; q < KG; ++q) {
+            uint32_t c0w = w0s[q] ^ z1;
+            uint32_t c1w = w1[q];
+            uint32_t c2w = h3 ^ z3k[q];
+            uint32_t c3w = c3r;
+#pragma unroll
+            for (int rr = 3; rr < 10; ++rr) {
+                const uint32_t a = c0w, b = c2w;
+                uint32_t hiA, loA, hiB, loB;
+                rs_mul(M0, a, hiA, loA);
+                rs_mul(M1, b, hiB, loB);
+                c0w = hiB ^ c1w ^ K.rk0[rr];
+                c1w = loB;
+                c2w = hiA ^ c3w ^ K.rk1[rr];
+                c3w = loA;
+            }
+            const uint32_t w[4] = {c0w, c1w, c2w, c3w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int cl = 0; cl < NC; ++cl)
+                    acc[q][i][cl] = ((PA_RS_FMA >> cl) & 1)
+                                        ? rs_chain_fma(acc[q][i][cl], w[i], x.one, nT[cl], two)
+                                        : rs_chain(acc[q][i][cl], w[i], T[cl]);
         }
-        const uint32_t w[4] = {c0w, c1w, c2w, c3w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int cl = 0; cl < NC; ++cl)
-                acc[i][cl] = ((PA_RS_FMA >> cl) & 1) ? rs_chain_fma(acc[i][cl], w[i], x.one, nT[cl], two)
-                                                      : rs_chain(acc[i][cl], w[i], T[cl]);
     }
     // the FMA form reports T = 0 as "below" for every u: nothing is below 0
 #pragma unroll
     for (int cl = 0; cl < NC; ++cl)
         if (((PA_RS_FMA >> cl) & 1) && T[cl] == 0u)
 #pragma unroll
-            for (int i = 0; i < 4; ++i) acc[i][cl] = 0xffffffffu;
+            for (int q = 0; q < KG; ++q)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc[q][i][cl] = 0xffffffffu;
     // flips: count the unsatisfied bonds of every replica bit-sliced
     uint32_t full[3];
 #pragma unroll
     for (int cl = 0; cl < 3; ++cl) full[cl] = (x.full >> cl) & 1u ? 0xffffffffu : 0u;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int s = rs_site<DIM, L>(4 * k + i, c);
-        int nb[2 * DIM];
-        rs_nbrs<DIM, L>(s, nb);
-        const uint32_t W = S[rs_ix(s)];
-        uint32_t v[2 * DIM];
-        const uint32_t jp = PMJ ? (uint32_t)JS[s] : 0u;
+    for (int q = 0; q < KG; ++q) {
+        const int k = k0 + 32 * q;
+        if (KG > 1 && k >= G::NGROUPS) continue;  // a padding group: its draws go unused
 #pragma unroll
-        for (int d = 0; d < 2 * DIM; ++d) {
-            const uint32_t jm = PMJ ? (0u - ((jp >> d) & 1u)) : 0u;
-            v[d] = W ^ S[rs_ix(nb[d])] ^ jm;
+        for (int i = 0; i < 4; ++i) {
+            const int s = rs_site<DIM, L>(4 * k + i, c);
+            int nb[2 * DIM];
+            rs_nbrs<DIM, L>(s, nb);
+            const uint32_t W = S[rs_ix(s)];
+            uint32_t v[2 * DIM];
+            const uint32_t jp = PMJ ? (uint32_t)JS[s] : 0u;
+#pragma unroll
+            for (int d = 0; d < 2 * DIM; ++d) {
+                const uint32_t jm = PMJ ? (0u - ((jp >> d) & 1u)) : 0u;
+                v[d] = W ^ S[rs_ix(nb[d])] ^ jm;
+            }
+            uint32_t b0c, b1c, b2c;
+            if constexpr (DIM == 2) {
+                const uint32_t s1 = v[0] ^ v[1] ^ v[2], k1 = (v[0] & v[1]) | (v[2] & (v[0] ^ v[1]));
+                b0c = s1 ^ v[3];
+                const uint32_t k2 = s1 & v[3];
+                b1c = k1 ^ k2;
+                b2c = k1 & k2;
+            } else {
+                const uint32_t s1 = v[0] ^ v[1] ^ v[2], k1 = (v[0] & v[1]) | (v[2] & (v[0] ^ v[1]));
+                const uint32_t s2 = v[3] ^ v[4] ^ v[5], k2 = (v[3] & v[4]) | (v[5] & (v[3] ^ v[4]));
+                b0c = s1 ^ s2;
+                const uint32_t k3 = s1 & s2;
+                b1c = k1 ^ k2 ^ k3;
+                b2c = (k1 & k2) | (k3 & (k1 ^ k2));
+            }
+            uint32_t flip;
+            if constexpr (DIM == 2) {
+                const uint32_t alw = b1c | b2c;              // c_u >= 2: dE <= 0
+                const uint32_t m0 = b0c & ~b1c & ~b2c;       // c_u = 1: dE = 4
+                const uint32_t m1 = ~(b0c | b1c | b2c);      // c_u = 0: dE = 8
+                flip = alw | (m0 & (~acc[q][i][0] | full[0])) | (m1 & (~acc[q][i][1] | full[1]));
+            } else {
+                const uint32_t alw = b2c | (b1c & b0c);      // c_u >= 3
+                const uint32_t m0 = b1c & ~b0c & ~b2c;       // c_u = 2: dE = 4
+                const uint32_t m1 = b0c & ~b1c & ~b2c;       // c_u = 1: dE = 8
+                const uint32_t m2 = ~(b0c | b1c | b2c);      // c_u = 0: dE = 12
+                flip = alw | (m0 & (~acc[q][i][0] | full[0])) | (m1 & (~acc[q][i][1] | full[1])) |
+                       (m2 & (~acc[q][i][NC - 1] | full[2]));
+            }
+            S[rs_ix(s)] = W ^ flip;
         }
-        uint32_t b0c, b1c, b2c;
-        if constexpr (DIM == 2) {
-            const uint32_t s1 = v[0] ^ v[1] ^ v[2], k1 = (v[0] & v[1]) | (v[2] & (v[0] ^ v[1]));
-            b0c = s1 ^ v[3];
-            const uint32_t k2 = s1 & v[3];
-            b1c = k1 ^ k2;
-            b2c = k1 & k2;
-        } else {
-            const uint32_t s1 = v[0] ^ v[1] ^ v[2], k1 = (v[0] & v[1]) | (v[2] & (v[0] ^ v[1]));
-            const uint32_t s2 = v[3] ^ v[4] ^ v[5], k2 = (v[3] & v[4]) | (v[5] & (v[3] ^ v[4]));
-            b0c = s1 ^ s2;
-            const uint32_t k3 = s1 & s2;
-            b1c = k1 ^ k2 ^ k3;
-            b2c = (k1 & k2) | (k3 & (k1 ^ k2));
-        }
-        uint32_t flip;
-        if constexpr (DIM == 2) {
-            const uint32_t alw = b1c | b2c;              // c_u >= 2: dE <= 0
-            const uint32_t m0 = b0c & ~b1c & ~b2c;       // c_u = 1: dE = 4
-            const uint32_t m1 = ~(b0c | b1c | b2c);      // c_u = 0: dE = 8
-            flip = alw | (m0 & (~acc[i][0] | full[0])) | (m1 & (~acc[i][1] | full[1]));
-        } else {
-            const uint32_t alw = b2c | (b1c & b0c);      // c_u >= 3
-            const uint32_t m0 = b1c & ~b0c & ~b2c;       // c_u = 2: dE = 4
-            const uint32_t m1 = b0c & ~b1c & ~b2c;       // c_u = 1: dE = 8
-            const uint32_t m2 = ~(b0c | b1c | b2c);      // c_u = 0: dE = 12
-            flip = alw | (m0 & (~acc[i][0] | full[0])) | (m1 & (~acc[i][1] | full[1])) |
-                   (m2 & (~acc[i][NC - 1] | full[2]));
-        }
-        S[rs_ix(s)] = W ^ flip;
     }
+}
+
+// Groups per pass for a lattice: the largest power of two up to PA_RS_KG whose
+// passes keep the lanes as busy as one group per pass does (within 2 %): the
+// NGROUPS groups fill ceil(NGROUPS / 32 KG) passes of 32 KG slots.
+template <int NGROUPS>
+__host__ __device__ constexpr int rs_kg() {
+    int best = 1;
+    const int per1 = 32 * ((NGROUPS + 31) / 32);
+    for (int kg = 2; kg <= PA_RS_KG; kg *= 2) {
+        const int per = 32 * kg * ((NGROUPS + 32 * kg - 1) / (32 * kg));
+        if (100 * per1 >= 98 * per) best = kg;
+    }
+    return best;
 }
 
 // One chunk of 32 replicas (slots b0 .. b0 + 31, those below R valid): load
@@ -982,8 +1029,9 @@ __device__ __forceinline__ void rs_chunk(const RunDev& d, const SweepCtx& x, uin
         const uint32_t g = x.g0 + (uint32_t)t;
 #pragma unroll 1
         for (int c = 0; c < 2; ++c) {
-            for (int k = lane; k < G::NGROUPS; k += 32)
-                rs_group<DIM, L, PMJ, KT>(S, JS, k, c, g, b0, ctag, K, x);
+            constexpr int KG = rs_kg<G::NGROUPS>();
+            for (int k = lane; k < G::NGROUPS; k += 32 * KG)
+                rs_groups<DIM, L, PMJ, KT, KG>(S, JS, k, c, g, b0, ctag, K, x);
             __syncwarp();
         }
     }
