@@ -24,6 +24,7 @@ next_items = Poisson resampling, adaptive temperature steps and checkpoints
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import statistics
@@ -676,7 +677,7 @@ def philox_ceiling(P, sweep_attempts_per_ns: float) -> dict:
     rate = uniforms / (ms * 1e6)
     return {"kernel": "k_philox_rate", "uniforms_per_ns": rate, "ms_per_launch": ms,
             "uniforms_per_launch": uniforms, "sweep_fraction": sweep_attempts_per_ns / rate,
-            "note": "Philox4x32-10 blocks of k_sweep_l64 (16 multiplies each), 1 block of "
+            "note": "Philox4x32-10 blocks of k_sweep_l64 (15 multiplies each), 1 block of "
                     "16 warps per SM, outputs xor-folded: the generator's ceiling"}
 
 
@@ -686,10 +687,11 @@ def philox_ceiling(P, sweep_attempts_per_ns: float) -> dict:
 INTOPS_KINDS = (("lop3", 0, 1, 1), ("imad", 1, 1, 1), ("mad_wide", 2, 2, 1),
                 ("lop3+imad", 3, 1, 1), ("lop3+mad_wide", 4, 1.5, 1),
                 ("mul_wide+xor", 5, 3, 2))
-# Philox4x32-10 multiplies per attempt in the register sweep kernels: 16 of a
+# Philox4x32-10 multiplies per attempt in the register sweep kernels: 15 of a
 # block's 20 products are formed per block (the rest are shared by every
-# block of a half-sweep), and a block serves 4 attempts
-MULTIPLIES_PER_ATTEMPT = 4.0
+# block of a half-sweep, or formed once per run), and a block serves 4
+# attempts
+MULTIPLIES_PER_ATTEMPT = 3.75
 
 
 def int_peaks(P, iters: int = 20000, reps: int = 3) -> dict:
@@ -864,6 +866,8 @@ def main():
         evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)]
                for _ in range(args.steps)]
         barrier()
+        gc.collect()
+        gc.disable()  # no collector pause inside the host-timed loop
         t0 = time.perf_counter()
         h2d = d2h = 0
         e2e_attempts = 0
@@ -882,8 +886,12 @@ def main():
             d2h += R_now * stride + 104
         barrier()
         dt = time.perf_counter() - t0
+        gc.enable()
         up = sorted(e[0].elapsed_time(e[1]) for e in evs)
         st_ms = sorted(e[1].elapsed_time(e[2]) for e in evs)
+        # device idle between a step's end and the next upload: the host's
+        # read of the observables and its next calls
+        gaps = sorted(evs[i][2].elapsed_time(evs[i + 1][0]) for i in range(args.steps - 1))
         dt, e2e_attempts = aggregate(dist, dt, e2e_attempts, "cuda")
         e2e = {"value": e2e_attempts / (dt * 1e9), "unit": UNIT,
                "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps,
@@ -891,6 +899,7 @@ def main():
                "device_ms_per_step_median": {"upload": up[len(up) // 2],
                                              "streamed_step": st_ms[len(st_ms) // 2]},
                "upload_ms_min_max": [up[0], up[-1]],
+               "gap_ms_median_max": [gaps[len(gaps) // 2], gaps[-1]] if gaps else None,
                "path": "pa_load(pinned host population) + pa_step_stream(population back "
                        f"to pinned host in {E2E_CHUNKS} ranges, copies overlapping the sweeps) + "
                        "pa_observables every step"}
@@ -903,7 +912,9 @@ def main():
     int_peak = ipk["peak_tops"]
     sweep_rate = sweep_attempts_per_launch / (sweep_ms * 1e6)  # attempts/ns
     mult_rate = sweep_rate * MULTIPLIES_PER_ATTEMPT / 1e3  # T products/s
-    mult_peak = max(ipk["multiply_peak_t_per_s"], rng_ceiling["uniforms_per_ns"] / 1e3)
+    # the generator alone forms MULTIPLIES_PER_ATTEMPT products per uniform
+    mult_peak = max(ipk["multiply_peak_t_per_s"],
+                    rng_ceiling["uniforms_per_ns"] * MULTIPLIES_PER_ATTEMPT / 1e3)
     ens = srv = nxt = None
     if not args.no_ensemble and world == 1:
         ens = ensemble_compare(P, steps=20, oracle_pool=ens_pool)
@@ -966,7 +977,8 @@ def main():
                      "multiply_bound": {
                          "achieved_t_products_per_s": mult_rate,
                          "peak_t_products_per_s": mult_peak, "frac": mult_rate / mult_peak,
-                         "note": "the sweep's Philox multiplies (4 per attempt) against the "
+                         "note": f"the sweep's Philox multiplies ({MULTIPLIES_PER_ATTEMPT:g} per "
+                                 "attempt) against the "
                                  "fastest measured 32x32->64 product rate (mul.wide+xor chains "
                                  "or the generator alone, whichever is higher)"}},
         "int_peaks": ipk,

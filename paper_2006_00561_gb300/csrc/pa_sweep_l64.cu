@@ -18,9 +18,11 @@
 //     add with carry-in shifts it into an accumulator that holds both tests
 //     of 16 sites (two instructions per test, no predicates or selects; the
 //     FMA pipe is left to the Philox multiplies);
-//   * the Philox round keys come from the kernel parameters, and the products
-//     shared by all blocks of a half-sweep are formed once: a block costs 16
-//     of Philox's 20 multiplies.
+//   * the Philox round keys come from the kernel parameters; the products
+//     shared by all blocks of a half-sweep are formed once per half-sweep, and
+//     the round-2 block products, which depend only on the run and the block
+//     index, once per run into a shared-memory table: a block costs 15 of
+//     Philox's 20 multiplies.
 // Grid-stride (persistent) over replicas; the population size is read from
 // device memory.  The measurement epilogue is the one of the generic kernel.
 #include "pa_internal.cuh"
@@ -73,8 +75,8 @@ struct Thr {
 // word 0 by an xor, so round 2 multiplies one block word (M0 * word 0) and one
 // shared word, round 3 again one of each (M1 * word 2, M0 * word 0 shared),
 // and rounds 4..10 are the plain rounds.  The shared products are formed once
-// per half-sweep (HalfSweepGen): 16 multiplies per block.  Same bits as
-// philox().
+// per half-sweep (HalfSweepGen) and the round-2 block product once per run
+// (round2_table): 15 multiplies per block.  Same bits as philox().
 constexpr uint32_t PM0 = 0xD2511F53u, PM1 = 0xCD9E8D57u;
 
 // Round keys of the run's seed and the opaque 1 of the multiply-add tests:
@@ -84,6 +86,7 @@ struct Keys {
     const uint32_t* rk0;
     const uint32_t* rk1;
     uint32_t one;
+    const uint2* r2;  // the lane's column of the run's round-2 table (entry j at r2[32 j])
 };
 
 __device__ __forceinline__ void mul_hilo(uint32_t m, uint32_t a, uint32_t& hi, uint32_t& lo) {
@@ -102,7 +105,6 @@ __device__ __forceinline__ void mul_hilo(uint32_t m, uint32_t a, uint32_t& hi, u
 }
 
 struct HalfSweepGen {
-    uint32_t y0k;  // round-1 word 0 before the xor with c1: high half of M1 * ctag ^ key 0
     uint32_t y3k;  // round-1 word 3 (low half of M0 * c0) ^ round-2 key 1
     uint32_t z1k;  // round-2 word 1 ^ round-3 key 0
     uint32_t e2k;  // high half of M0 * (round-2 word 0) ^ round-3 key 1
@@ -115,7 +117,7 @@ __device__ __forceinline__ HalfSweepGen half_sweep_gen(const Keys& d, uint32_t c
     uint32_t ht, lt, hc, lc;
     mul_hilo(PM1, ctag, ht, lt);  // round 1
     mul_hilo(PM0, c0, hc, lc);
-    g.y0k = ht ^ d.rk0[0];
+    (void)ht;
     g.y3k = lc ^ d.rk1[1];
     const uint32_t y2 = hc ^ slot ^ d.rk1[0];
     uint32_t h2, l2;
@@ -129,14 +131,35 @@ __device__ __forceinline__ HalfSweepGen half_sweep_gen(const Keys& d, uint32_t c
     return g;
 }
 
-// Block c1 of the half-sweep.
+// The round-2 block product M0 * (hi(M1 * ctag) ^ key0 ^ c1) depends only on
+// the run (its tag, instance and key) and the block index c1, not on the
+// half-sweep or the replica: each lane forms those of its NB blocks
+// c1 = NB * lane + j once per run, into its column of a shared-memory table
+// (entry j at col[32 j], so the lanes of a warp touch consecutive words), and
+// a block then costs 15 of Philox's 20 multiplies.
+template <uint32_t NB>
+__device__ __forceinline__ void round2_table(uint2* col, uint32_t lane, uint32_t ctag,
+                                             const uint32_t* rk0) {
+    uint32_t ht, lt;
+    mul_hilo(PM1, ctag, ht, lt);  // round 1
+    const uint32_t y0k = ht ^ rk0[0];
+#pragma unroll 1
+    for (uint32_t j = 0; j < NB; ++j) {
+        uint32_t h, l;
+        mul_hilo(PM0, y0k ^ (NB * lane + j), h, l);  // round 2, block half
+        col[32u * j] = make_uint2(h, l);
+    }
+}
+
+// Block c1 of the half-sweep (c1 one of the lane's NB table blocks).
+template <uint32_t NB>
 __device__ __forceinline__ uint4 philox_block(const Keys& d, const HalfSweepGen& g, uint32_t c1) {
-    uint32_t h2, l2, h3, l3;
-    mul_hilo(PM0, g.y0k ^ c1, h2, l2);  // round 2, block half
-    mul_hilo(PM1, h2 ^ g.y3k, h3, l3);  // round 3, block half
+    const uint2 r2 = d.r2[32u * (c1 & (NB - 1u))];  // round 2, block half (table)
+    uint32_t h3, l3;
+    mul_hilo(PM1, r2.x ^ g.y3k, h3, l3);  // round 3, block half
     uint32_t c0 = h3 ^ g.z1k;
     uint32_t c1w = l3;
-    uint32_t c2 = l2 ^ g.e2k;
+    uint32_t c2 = r2.y ^ g.e2k;
     uint32_t c3 = g.e3;
 #pragma unroll
     for (int r = 3; r < 10; ++r) {
@@ -282,7 +305,7 @@ __device__ __forceinline__ void row_accepts(const Keys& d, const HalfSweepGen& g
     for (uint32_t q = 0; q < 2; ++q) {
         const uint32_t base = 8u * y + 4u * q;
         const uint32_t kc = group_tests<F4, F8, PA_L64_HUNROLL>(
-            [&](int h) { return philox_block(d, gen, PA_L64_BLOCK(base, h)); }, one, c4, c8, t4.T,
+            [&](int h) { return philox_block<16>(d, gen, PA_L64_BLOCK(base, h)); }, one, c4, c8, t4.T,
             t8.T);
         // site j = 4h + m: dE = 4 carry at bit 2j + 1, dE = 8 carry at bit 2j
         constexpr uint32_t EV = 0x55555555u;
@@ -454,7 +477,10 @@ __global__ void __launch_bounds__(WARPS64 * 32, PA_L64_MIN_BLOCKS)
     uint32_t full;
     thresholds(d, st->step, t4, t8, full);
     const uint32_t ctag = (TAG_SWEEP << 28) | d.instance;
-    const Keys K{d.rk0, d.rk1, d.one};
+    extern __shared__ uint2 s_r2[];  // WARPS64 x 16 x 32 round-2 products
+    uint2* col = s_r2 + (size_t)wib * 16 * 32 + lane;
+    round2_table<16>(col, (uint32_t)lane, ctag, d.rk0);
+    const Keys K{d.rk0, d.rk1, d.one, col};
     uint4* spins = reinterpret_cast<uint4*>(d.spins[cur]);
     RowJ ja{0, 0, 0, 0}, jb{0, 0, 0, 0};
     if constexpr (PMJ) l64_couplings(d, lane, ja, jb);
@@ -480,7 +506,10 @@ __global__ void __launch_bounds__(WARPS64 * 32, PA_L64_MIN_BLOCKS)
 template <bool PMJ>
 __global__ void __launch_bounds__(WARPS64 * 32, PA_L64_MIN_BLOCKS) k_sweep_l64_batched(BatchSweepArgs a) {
     __shared__ uint32_t s_keys[WARPS64][24];
+    extern __shared__ uint2 s_r2[];  // WARPS64 x 16 x 32 round-2 products
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint2* col = s_r2 + (size_t)wib * 16 * 32 + lane;
+    uint32_t have = 0xffffffffu;  // run whose round-2 table the warp holds
     L64Tally tally;
     for (;;) {
         uint32_t chunk = 0;
@@ -505,8 +534,12 @@ __global__ void __launch_bounds__(WARPS64 * 32, PA_L64_MIN_BLOCKS) k_sweep_l64_b
             s_keys[wib][10 + lane] = d.rk1[lane];
         }
         __syncwarp();
-        const Keys K{&s_keys[wib][0], &s_keys[wib][10], d.one};
         const uint32_t ctag = (TAG_SWEEP << 28) | d.instance;
+        if (a.run_ids[lo] != have) {
+            round2_table<16>(col, (uint32_t)lane, ctag, &s_keys[wib][0]);
+            have = a.run_ids[lo];
+        }
+        const Keys K{&s_keys[wib][0], &s_keys[wib][10], d.one, col};
         uint4* spins = reinterpret_cast<uint4*>(d.spins[cur]);
         const uint32_t first = g - a.slot_base[lo];
         RowJ ja{0, 0, 0, 0}, jb{0, 0, 0, 0};
@@ -577,7 +610,7 @@ __device__ __forceinline__ void row_accepts128(const Keys& d, const HalfSweepGen
     for (uint32_t q = 0; q < 4; ++q) {
         const uint32_t base = 16u * y + 4u * q;
         const uint32_t kc = group_tests<false, false, L128_HUNROLL>(
-            [&](int h) { return philox_block(d, gen, PA_L64_BLOCK(base, h)); }, one, t4.T, t8.T, t4.T,
+            [&](int h) { return philox_block<64>(d, gen, PA_L64_BLOCK(base, h)); }, one, t4.T, t8.T, t4.T,
             t8.T);
         const uint32_t b4 = (~(kc >> 1) & EV) << P, b8 = (~kc & EV) << P;
         if (q == 0) {
@@ -735,7 +768,10 @@ __global__ void __launch_bounds__(warps128<PMJ>() * 32, 1)
     uint32_t full;
     thresholds(d, st->step, t4, t8, full);
     const uint32_t ctag = (TAG_SWEEP << 28) | d.instance;
-    const Keys K{d.rk0, d.rk1, d.one};
+    extern __shared__ uint2 s_r2[];  // warps x 64 x 32 round-2 products
+    uint2* col = s_r2 + (size_t)wib * 64 * 32 + lane;
+    round2_table<64>(col, (uint32_t)lane, ctag, d.rk0);
+    const Keys K{d.rk0, d.rk1, d.one, col};
     uint4* spins = reinterpret_cast<uint4*>(d.spins[cur]);
     RowJ2 j[4] = {};
     if constexpr (PMJ) l128_couplings(d, lane, j);
@@ -761,7 +797,10 @@ __global__ void __launch_bounds__(warps128<PMJ>() * 32, 1)
 template <bool PMJ>
 __global__ void __launch_bounds__(warps128<PMJ>() * 32, 1) k_sweep_l128_batched(BatchSweepArgs a) {
     __shared__ uint32_t s_keys[warps128<PMJ>()][24];
+    extern __shared__ uint2 s_r2[];  // warps x 64 x 32 round-2 products
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint2* col = s_r2 + (size_t)wib * 64 * 32 + lane;
+    uint32_t have = 0xffffffffu;  // run whose round-2 table the warp holds
     L64Tally tally;
     for (;;) {
         uint32_t chunk = 0;
@@ -786,8 +825,12 @@ __global__ void __launch_bounds__(warps128<PMJ>() * 32, 1) k_sweep_l128_batched(
             s_keys[wib][10 + lane] = d.rk1[lane];
         }
         __syncwarp();
-        const Keys K{&s_keys[wib][0], &s_keys[wib][10], d.one};
         const uint32_t ctag = (TAG_SWEEP << 28) | d.instance;
+        if (a.run_ids[lo] != have) {
+            round2_table<64>(col, (uint32_t)lane, ctag, &s_keys[wib][0]);
+            have = a.run_ids[lo];
+        }
+        const Keys K{&s_keys[wib][0], &s_keys[wib][10], d.one, col};
         uint4* spins = reinterpret_cast<uint4*>(d.spins[cur]);
         const uint32_t first = g - a.slot_base[lo];
         RowJ2 j[4] = {};
@@ -828,8 +871,9 @@ int l64_block_warps(const RunDev& d) {
 
 // --------------------------------------------------------------------------
 // The generator's own ceiling in the register kernels' launch shape: the
-// Philox blocks of k_sweep_l64 (half-sweep products shared, 16 multiplies per
-// block, 16 blocks per half-sweep and lane) with nothing else done to the
+// Philox blocks of k_sweep_l64 (half-sweep products shared, round-2 block
+// products from the run's table: 15 multiplies per block; 16 blocks per
+// half-sweep and lane) with nothing else done to the
 // uniforms but an xor into one word per thread.  One warp stands for one
 // replica (slot = global warp index); half-sweep g of lane l draws blocks
 // 16 l .. 16 l + 15 of counter (2 g, block, SWEEP, slot).
@@ -849,26 +893,74 @@ constexpr int PHILOX_RATE_WARPS = PA_PHILOX_RATE_WARPS;
 
 __global__ void __launch_bounds__(PHILOX_RATE_WARPS * 32, 1)
     k_philox_rate(__grid_constant__ const PhiloxRateArgs a) {
-    const Keys K{a.rk0, a.rk1, a.one};
+    extern __shared__ uint2 s_r2[];  // PHILOX_RATE_WARPS x 16 x 32 round-2 products
+    const uint32_t lane = threadIdx.x & 31u;
+    uint2* col = s_r2 + (size_t)(threadIdx.x >> 5) * 16 * 32 + lane;
+    round2_table<16>(col, lane, TAG_SWEEP << 28, a.rk0);
+    const Keys K{a.rk0, a.rk1, a.one, col};
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t slot = tid >> 5, base = (threadIdx.x & 31u) * 16u;
+    const uint32_t slot = tid >> 5, base = lane * 16u;
     uint32_t acc = 0;
     for (uint32_t g = 0; g < a.halfsweeps; ++g) {
         const HalfSweepGen gen = half_sweep_gen(K, 2u * g, slot, TAG_SWEEP << 28);
 #pragma unroll 4
         for (uint32_t h = 0; h < 16u; ++h) {
-            const uint4 u = philox_block(K, gen, base + h);
+            const uint4 u = philox_block<16>(K, gen, base + h);
             acc ^= u.x ^ u.y ^ u.z ^ u.w;
         }
     }
     a.out[tid] = acc;
 }
 
-static int wave(const void* fn, int threads) {
+// Dynamic shared memory of the register kernels: the round-2 tables.
+constexpr size_t L64_SMEM = (size_t)WARPS64 * 16 * 32 * sizeof(uint2);
+template <bool PMJ>
+constexpr size_t l128_smem() {
+    return (size_t)warps128<PMJ>() * 64 * 32 * sizeof(uint2);
+}
+constexpr size_t PHILOX_RATE_SMEM = (size_t)PHILOX_RATE_WARPS * 16 * 32 * sizeof(uint2);
+
+// Tables above the default 48 KB need the kernel's opt-in, once per device
+// (set at the first launch, which pa_init makes outside any stream capture).
+static cudaError_t ensure_smem_optin() {
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    if ((e = cudaFuncSetAttribute(k_sweep_l64<false>, A, (int)L64_SMEM)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_sweep_l64<true>, A, (int)L64_SMEM)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_sweep_l64_batched<false>, A, (int)L64_SMEM)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_sweep_l64_batched<true>, A, (int)L64_SMEM)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_sweep_l128<false>, A, (int)l128_smem<false>())) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_sweep_l128<true>, A, (int)l128_smem<true>())) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_sweep_l128_batched<false>, A, (int)l128_smem<false>())) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_sweep_l128_batched<true>, A, (int)l128_smem<true>())) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_philox_rate, A, (int)PHILOX_RATE_SMEM)) != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) done[dev] = true;
+    return cudaSuccess;
+}
+
+static size_t l64_smem(const RunDev& d) {
+    if (!is_l128(d)) return L64_SMEM;
+    return d.model == PA_MODEL_PMJ ? l128_smem<true>() : l128_smem<false>();
+}
+
+static int wave(const void* fn, int threads, size_t smem) {
     int dev = 0, sms = 0, per_sm = 0;
+    if (ensure_smem_optin() != cudaSuccess) return 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess)
         return 0;
     return per_sm < 1 ? 0 : sms * per_sm;
 }
@@ -884,20 +976,23 @@ int l64_grid(const RunDev& d) {
     const int w = l64_block_warps(d);
     const int full = wave(pick(d, k_sweep_l64<false>, k_sweep_l64<true>, k_sweep_l128<false>,
                                k_sweep_l128<true>),
-                          w * 32);
+                          w * 32, l64_smem(d));
     if (full <= 0) return 0;
     const int64_t need = ((int64_t)d.cap + w - 1) / w;
     return (int)(need < full ? need : full);
 }
 
 cudaError_t launch_sweep_l64(const RunDev& d, int nsweeps, int grid, cudaStream_t s) {
+    const cudaError_t e = ensure_smem_optin();
+    if (e != cudaSuccess) return e;
     const bool pmj = d.model == PA_MODEL_PMJ;
+    const size_t sm = l64_smem(d);
     if (is_l128(d)) {
-        if (pmj) k_sweep_l128<true><<<grid, warps128<true>() * 32, 0, s>>>(d, nsweeps);
-        else k_sweep_l128<false><<<grid, warps128<false>() * 32, 0, s>>>(d, nsweeps);
+        if (pmj) k_sweep_l128<true><<<grid, warps128<true>() * 32, sm, s>>>(d, nsweeps);
+        else k_sweep_l128<false><<<grid, warps128<false>() * 32, sm, s>>>(d, nsweeps);
     } else {
-        if (pmj) k_sweep_l64<true><<<grid, WARPS64 * 32, 0, s>>>(d, nsweeps);
-        else k_sweep_l64<false><<<grid, WARPS64 * 32, 0, s>>>(d, nsweeps);
+        if (pmj) k_sweep_l64<true><<<grid, WARPS64 * 32, sm, s>>>(d, nsweeps);
+        else k_sweep_l64<false><<<grid, WARPS64 * 32, sm, s>>>(d, nsweeps);
     }
     return cudaGetLastError();
 }
@@ -923,7 +1018,9 @@ cudaError_t launch_philox_rate(uint64_t seed, uint32_t halfsweeps, uint32_t* out
     a.one = 1u;
     a.halfsweeps = halfsweeps;
     a.out = out;
-    k_philox_rate<<<grid, PHILOX_RATE_WARPS * 32, 0, s>>>(a);
+    const cudaError_t e = ensure_smem_optin();
+    if (e != cudaSuccess) return e;
+    k_philox_rate<<<grid, PHILOX_RATE_WARPS * 32, PHILOX_RATE_SMEM, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -932,18 +1029,21 @@ bool l64_batched_applies(const RunDev& proto) { return l64_applies(proto); }
 int l64_batched_grid(const RunDev& proto) {
     return wave(pick(proto, k_sweep_l64_batched<false>, k_sweep_l64_batched<true>,
                      k_sweep_l128_batched<false>, k_sweep_l128_batched<true>),
-                l64_block_warps(proto) * 32);
+                l64_block_warps(proto) * 32, l64_smem(proto));
 }
 
 cudaError_t launch_sweep_l64_batched(const BatchSweepArgs& a, const RunDev& proto, int grid,
                                      cudaStream_t s) {
+    const cudaError_t e = ensure_smem_optin();
+    if (e != cudaSuccess) return e;
     const bool pmj = proto.model == PA_MODEL_PMJ;
+    const size_t sm = l64_smem(proto);
     if (is_l128(proto)) {
-        if (pmj) k_sweep_l128_batched<true><<<grid, warps128<true>() * 32, 0, s>>>(a);
-        else k_sweep_l128_batched<false><<<grid, warps128<false>() * 32, 0, s>>>(a);
+        if (pmj) k_sweep_l128_batched<true><<<grid, warps128<true>() * 32, sm, s>>>(a);
+        else k_sweep_l128_batched<false><<<grid, warps128<false>() * 32, sm, s>>>(a);
     } else {
-        if (pmj) k_sweep_l64_batched<true><<<grid, WARPS64 * 32, 0, s>>>(a);
-        else k_sweep_l64_batched<false><<<grid, WARPS64 * 32, 0, s>>>(a);
+        if (pmj) k_sweep_l64_batched<true><<<grid, WARPS64 * 32, sm, s>>>(a);
+        else k_sweep_l64_batched<false><<<grid, WARPS64 * 32, sm, s>>>(a);
     }
     return cudaGetLastError();
 }
