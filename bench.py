@@ -52,9 +52,9 @@ OPS_PER_ATTEMPT = 19.5
 ALU_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12
 # DRAM bytes of one sweep launch, from the ncu capture of the same kernel at
 # 2^20 replicas, four times L2 (profiles/k_sweep_l64_ising2d_L64_R2p18.md:
-# 539.9 MB read + 483.6 MB written), scaled by the replica count to 2^21.
+# 538.3 MB read + 482.9 MB written), scaled by the replica count to 2^21.
 # None whenever the kernel changes, until the next capture.
-SWEEP_TRAFFIC_BYTES_2P21 = (539.905792e6 + 483.599360e6) * 2
+SWEEP_TRAFFIC_BYTES_2P21 = (538.259456e6 + 482.916864e6) * 2
 # Slot ranges of the e2e step: each range's copy to the host (~0.7 ms at 1/8 of
 # 1 GiB) runs while the next range sweeps (~7 ms).
 E2E_CHUNKS = 8
@@ -887,7 +887,8 @@ def main():
         barrier()
         dt = time.perf_counter() - t0
         gc.enable()
-        up = sorted(e[0].elapsed_time(e[1]) for e in evs)
+        up_steps = [e[0].elapsed_time(e[1]) for e in evs]
+        up = sorted(up_steps)
         st_ms = sorted(e[1].elapsed_time(e[2]) for e in evs)
         # device idle between a step's end and the next upload: the host's
         # read of the observables and its next calls
@@ -898,7 +899,7 @@ def main():
                "wall_ms_per_step": dt * 1e3 / args.steps,
                "device_ms_per_step_median": {"upload": up[len(up) // 2],
                                              "streamed_step": st_ms[len(st_ms) // 2]},
-               "upload_ms_min_max": [up[0], up[-1]],
+               "upload_ms_per_step": [round(x, 3) for x in up_steps],
                "gap_ms_median_max": [gaps[len(gaps) // 2], gaps[-1]] if gaps else None,
                "path": "pa_load(pinned host population) + pa_step_stream(population back "
                        f"to pinned host in {E2E_CHUNKS} ranges, copies overlapping the sweeps) + "
