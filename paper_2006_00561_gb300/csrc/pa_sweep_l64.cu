@@ -105,6 +105,7 @@ __device__ __forceinline__ void mul_hilo(uint32_t m, uint32_t a, uint32_t& hi, u
 }
 
 struct HalfSweepGen {
+    uint32_t y0k;  // round-1 word 0 before the xor with c1: high half of M1 * ctag ^ key 0
     uint32_t y3k;  // round-1 word 3 (low half of M0 * c0) ^ round-2 key 1
     uint32_t z1k;  // round-2 word 1 ^ round-3 key 0
     uint32_t e2k;  // high half of M0 * (round-2 word 0) ^ round-3 key 1
@@ -117,7 +118,7 @@ __device__ __forceinline__ HalfSweepGen half_sweep_gen(const Keys& d, uint32_t c
     uint32_t ht, lt, hc, lc;
     mul_hilo(PM1, ctag, ht, lt);  // round 1
     mul_hilo(PM0, c0, hc, lc);
-    (void)ht;
+    g.y0k = ht ^ d.rk0[0];
     g.y3k = lc ^ d.rk1[1];
     const uint32_t y2 = hc ^ slot ^ d.rk1[0];
     uint32_t h2, l2;
@@ -151,10 +152,16 @@ __device__ __forceinline__ void round2_table(uint2* col, uint32_t lane, uint32_t
     }
 }
 
-// Block c1 of the half-sweep (c1 one of the lane's NB table blocks).
+// Block c1 of the half-sweep: with NB > 0 c1 is one of the lane's NB table
+// blocks and its round-2 product comes from the table; NB = 0 forms it.
 template <uint32_t NB>
 __device__ __forceinline__ uint4 philox_block(const Keys& d, const HalfSweepGen& g, uint32_t c1) {
-    const uint2 r2 = d.r2[32u * (c1 & (NB - 1u))];  // round 2, block half (table)
+    uint2 r2;
+    if constexpr (NB > 0) {
+        r2 = d.r2[32u * (c1 & (NB - 1u))];  // round 2, block half (table)
+    } else {
+        mul_hilo(PM0, g.y0k ^ c1, r2.x, r2.y);  // round 2, block half
+    }
     uint32_t h3, l3;
     mul_hilo(PM1, r2.x ^ g.y3k, h3, l3);  // round 3, block half
     uint32_t c0 = h3 ^ g.z1k;
@@ -569,6 +576,8 @@ __global__ void __launch_bounds__(WARPS64 * 32, PA_L64_MIN_BLOCKS) k_sweep_l64_b
 // filling one 32-bit quarter of the row's masks.  Rows are updated in place
 // one after the other: the sites a half-sweep flips have the active colour,
 // and the classes of active-colour sites depend only on the other colour.
+// Each block forms its round-2 product (16 multiplies per block): the table of
+// the L = 64 kernel would hold 64 blocks per lane here.
 // --------------------------------------------------------------------------
 // Block warps: with two groups unrolled, the ferromagnet runs at 1508 to 1517
 // attempts/ns with 8 warps (183 registers) against 1484 with 12 (166
@@ -610,7 +619,7 @@ __device__ __forceinline__ void row_accepts128(const Keys& d, const HalfSweepGen
     for (uint32_t q = 0; q < 4; ++q) {
         const uint32_t base = 16u * y + 4u * q;
         const uint32_t kc = group_tests<false, false, L128_HUNROLL>(
-            [&](int h) { return philox_block<64>(d, gen, PA_L64_BLOCK(base, h)); }, one, t4.T, t8.T, t4.T,
+            [&](int h) { return philox_block<0>(d, gen, PA_L64_BLOCK(base, h)); }, one, t4.T, t8.T, t4.T,
             t8.T);
         const uint32_t b4 = (~(kc >> 1) & EV) << P, b8 = (~kc & EV) << P;
         if (q == 0) {
@@ -768,10 +777,7 @@ __global__ void __launch_bounds__(warps128<PMJ>() * 32, 1)
     uint32_t full;
     thresholds(d, st->step, t4, t8, full);
     const uint32_t ctag = (TAG_SWEEP << 28) | d.instance;
-    extern __shared__ uint2 s_r2[];  // warps x 64 x 32 round-2 products
-    uint2* col = s_r2 + (size_t)wib * 64 * 32 + lane;
-    round2_table<64>(col, (uint32_t)lane, ctag, d.rk0);
-    const Keys K{d.rk0, d.rk1, d.one, col};
+    const Keys K{d.rk0, d.rk1, d.one, nullptr};
     uint4* spins = reinterpret_cast<uint4*>(d.spins[cur]);
     RowJ2 j[4] = {};
     if constexpr (PMJ) l128_couplings(d, lane, j);
@@ -797,10 +803,7 @@ __global__ void __launch_bounds__(warps128<PMJ>() * 32, 1)
 template <bool PMJ>
 __global__ void __launch_bounds__(warps128<PMJ>() * 32, 1) k_sweep_l128_batched(BatchSweepArgs a) {
     __shared__ uint32_t s_keys[warps128<PMJ>()][24];
-    extern __shared__ uint2 s_r2[];  // warps x 64 x 32 round-2 products
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    uint2* col = s_r2 + (size_t)wib * 64 * 32 + lane;
-    uint32_t have = 0xffffffffu;  // run whose round-2 table the warp holds
     L64Tally tally;
     for (;;) {
         uint32_t chunk = 0;
@@ -826,11 +829,7 @@ __global__ void __launch_bounds__(warps128<PMJ>() * 32, 1) k_sweep_l128_batched(
         }
         __syncwarp();
         const uint32_t ctag = (TAG_SWEEP << 28) | d.instance;
-        if (a.run_ids[lo] != have) {
-            round2_table<64>(col, (uint32_t)lane, ctag, &s_keys[wib][0]);
-            have = a.run_ids[lo];
-        }
-        const Keys K{&s_keys[wib][0], &s_keys[wib][10], d.one, col};
+        const Keys K{&s_keys[wib][0], &s_keys[wib][10], d.one, nullptr};
         uint4* spins = reinterpret_cast<uint4*>(d.spins[cur]);
         const uint32_t first = g - a.slot_base[lo];
         RowJ2 j[4] = {};
@@ -914,10 +913,6 @@ __global__ void __launch_bounds__(PHILOX_RATE_WARPS * 32, 1)
 
 // Dynamic shared memory of the register kernels: the round-2 tables.
 constexpr size_t L64_SMEM = (size_t)WARPS64 * 16 * 32 * sizeof(uint2);
-template <bool PMJ>
-constexpr size_t l128_smem() {
-    return (size_t)warps128<PMJ>() * 64 * 32 * sizeof(uint2);
-}
 constexpr size_t PHILOX_RATE_SMEM = (size_t)PHILOX_RATE_WARPS * 16 * 32 * sizeof(uint2);
 
 // Tables above the default 48 KB need the kernel's opt-in, once per device
@@ -935,25 +930,14 @@ static cudaError_t ensure_smem_optin() {
         return e;
     if ((e = cudaFuncSetAttribute(k_sweep_l64_batched<true>, A, (int)L64_SMEM)) != cudaSuccess)
         return e;
-    if ((e = cudaFuncSetAttribute(k_sweep_l128<false>, A, (int)l128_smem<false>())) != cudaSuccess)
-        return e;
-    if ((e = cudaFuncSetAttribute(k_sweep_l128<true>, A, (int)l128_smem<true>())) != cudaSuccess)
-        return e;
-    if ((e = cudaFuncSetAttribute(k_sweep_l128_batched<false>, A, (int)l128_smem<false>())) !=
-        cudaSuccess)
-        return e;
-    if ((e = cudaFuncSetAttribute(k_sweep_l128_batched<true>, A, (int)l128_smem<true>())) !=
-        cudaSuccess)
-        return e;
     if ((e = cudaFuncSetAttribute(k_philox_rate, A, (int)PHILOX_RATE_SMEM)) != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) done[dev] = true;
     return cudaSuccess;
 }
 
-static size_t l64_smem(const RunDev& d) {
-    if (!is_l128(d)) return L64_SMEM;
-    return d.model == PA_MODEL_PMJ ? l128_smem<true>() : l128_smem<false>();
-}
+// The L = 128 kernels form their round-2 products: a 128 KB table per block
+// ran 0.5-1.3 % slower there on GB300 (it takes that much of the L1).
+static size_t l64_smem(const RunDev& d) { return is_l128(d) ? 0 : L64_SMEM; }
 
 static int wave(const void* fn, int threads, size_t smem) {
     int dev = 0, sms = 0, per_sm = 0;
