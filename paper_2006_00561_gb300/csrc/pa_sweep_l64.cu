@@ -247,7 +247,10 @@ static_assert(PA_L64_CHAIN >= 1 && PA_L64_CHAIN <= 4, "PA_L64_CHAIN: 1 .. 4");
 // (+-J, 2^20) and 1601 against 1557 (batched, 8 +-J runs of 2^17); with two
 // Philox blocks per group unrolled instead of four, 1573.  At L = 128 two of
 // the four groups together run at 1484 against 1437 (ferromagnet, 12 warps,
-// 166 registers) and 1497 against 1361 (+-J, 8 warps); all four spill.
+// 166 registers) and 1497 against 1361 (+-J, 8 warps); all four spill.  All
+// four groups with two blocks each unrolled (125 registers) run at 1462, 1491
+// and 1509 with 8, 12 and 16 warps (+-J 1420 at every width), against 1512 to
+// 1520 for two groups of four blocks at 8 warps.
 #ifndef PA_L64_QUNROLL
 #define PA_L64_QUNROLL 2
 #endif
