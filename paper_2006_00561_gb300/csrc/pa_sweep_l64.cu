@@ -13,7 +13,7 @@
 //     64 sites of a row is evaluated bit-sliced (a handful of word ops);
 //   * a row holds 32 sites of each colour = 8 Philox blocks, each block
 //     covering 4 sites of that row, and both acceptance tests (dE = 4 and 8)
-//     are folded into two bit masks, so no shared memory and no atomics;
+//     are folded into two bit masks in registers, with no atomics;
 //   * each test is a carry chain: the carry out of u - T is [u >= T], and an
 //     add with carry-in shifts it into an accumulator that holds both tests
 //     of 16 sites (two instructions per test, no predicates or selects; the
