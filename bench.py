@@ -677,7 +677,7 @@ def philox_ceiling(P, sweep_attempts_per_ns: float) -> dict:
     rate = uniforms / (ms * 1e6)
     return {"kernel": "k_philox_rate", "uniforms_per_ns": rate, "ms_per_launch": ms,
             "uniforms_per_launch": uniforms, "sweep_fraction": sweep_attempts_per_ns / rate,
-            "note": "Philox4x32-10 blocks of k_sweep_l64 (15 multiplies each), 1 block of "
+            "note": "Philox4x32-10 blocks of k_sweep_l64 (14 multiplies each), 1 block of "
                     "16 warps per SM, outputs xor-folded: the generator's ceiling"}
 
 
@@ -687,11 +687,11 @@ def philox_ceiling(P, sweep_attempts_per_ns: float) -> dict:
 INTOPS_KINDS = (("lop3", 0, 1, 1), ("imad", 1, 1, 1), ("mad_wide", 2, 2, 1),
                 ("lop3+imad", 3, 1, 1), ("lop3+mad_wide", 4, 1.5, 1),
                 ("mul_wide+xor", 5, 3, 2))
-# Philox4x32-10 multiplies per attempt in the register sweep kernels: 15 of a
+# Philox4x32-10 multiplies per attempt in the L = 64 sweep kernel: 14 of a
 # block's 20 products are formed per block (the rest are shared by every
-# block of a half-sweep, or formed once per run), and a block serves 4
-# attempts
-MULTIPLIES_PER_ATTEMPT = 3.75
+# block of a half-sweep, or formed once per run or per launch), and a block
+# serves 4 attempts
+MULTIPLIES_PER_ATTEMPT = 3.5
 
 
 def int_peaks(P, iters: int = 20000, reps: int = 3) -> dict:

@@ -87,6 +87,8 @@ struct Keys {
     const uint32_t* rk1;
     uint32_t one;
     const uint2* r2;  // the lane's column of the run's round-2 table (entry j at r2[32 j])
+    const uint2* t3;  // the lane's column of the step's round-3 table, or null (entry
+                      // (hs, j) at t3[512 hs + 32 j] for half-sweep hs of the launch)
 };
 
 __device__ __forceinline__ void mul_hilo(uint32_t m, uint32_t a, uint32_t& hi, uint32_t& lo) {
@@ -105,6 +107,7 @@ __device__ __forceinline__ void mul_hilo(uint32_t m, uint32_t a, uint32_t& hi, u
 }
 
 struct HalfSweepGen {
+    const uint2* t3;  // this half-sweep's slice of the lane's round-3 table column (or null)
     uint32_t y0k;  // round-1 word 0 before the xor with c1: high half of M1 * ctag ^ key 0
     uint32_t y3k;  // round-1 word 3 (low half of M0 * c0) ^ round-2 key 1
     uint32_t z1k;  // round-2 word 1 ^ round-3 key 0
@@ -115,6 +118,7 @@ struct HalfSweepGen {
 __device__ __forceinline__ HalfSweepGen half_sweep_gen(const Keys& d, uint32_t c0, uint32_t slot,
                                                       uint32_t ctag) {
     HalfSweepGen g;
+    g.t3 = nullptr;
     uint32_t ht, lt, hc, lc;
     mul_hilo(PM1, ctag, ht, lt);  // round 1
     mul_hilo(PM0, c0, hc, lc);
@@ -152,21 +156,37 @@ __device__ __forceinline__ void round2_table(uint2* col, uint32_t lane, uint32_t
     }
 }
 
+// The round-3 block product M1 * (h2(c1) ^ lo(M0 * c0) ^ key) depends only on
+// the run, the block index and the half-sweep, not on the replica: the plain
+// L = 64 kernel forms those of every block and half-sweep of its launch once
+// per CTA into a second table (T3), and a block then costs 14 multiplies.
+
 // Block c1 of the half-sweep: with NB > 0 c1 is one of the lane's NB table
-// blocks and its round-2 product comes from the table; NB = 0 forms it.
-template <uint32_t NB>
+// blocks and its round-2 product comes from the table (NB = 0 forms it); with
+// T3 its round-3 product comes from the half-sweep's slice of the step table.
+template <uint32_t NB, bool T3 = false>
 __device__ __forceinline__ uint4 philox_block(const Keys& d, const HalfSweepGen& g, uint32_t c1) {
-    uint2 r2;
-    if constexpr (NB > 0) {
-        r2 = d.r2[32u * (c1 & (NB - 1u))];  // round 2, block half (table)
+    uint32_t l2, h3, l3;
+    if constexpr (T3) {
+        static_assert(NB > 0, "the step table needs the round-2 table");
+        const uint32_t j = c1 & (NB - 1u);
+        const uint2 w = g.t3[32u * j];  // round 3, block half (step table)
+        h3 = w.x;
+        l3 = w.y;
+        l2 = d.r2[32u * j].y;  // round 2, block half (run table)
     } else {
-        mul_hilo(PM0, g.y0k ^ c1, r2.x, r2.y);  // round 2, block half
+        uint2 r2;
+        if constexpr (NB > 0) {
+            r2 = d.r2[32u * (c1 & (NB - 1u))];  // round 2, block half (table)
+        } else {
+            mul_hilo(PM0, g.y0k ^ c1, r2.x, r2.y);  // round 2, block half
+        }
+        l2 = r2.y;
+        mul_hilo(PM1, r2.x ^ g.y3k, h3, l3);  // round 3, block half
     }
-    uint32_t h3, l3;
-    mul_hilo(PM1, r2.x ^ g.y3k, h3, l3);  // round 3, block half
     uint32_t c0 = h3 ^ g.z1k;
     uint32_t c1w = l3;
-    uint32_t c2 = r2.y ^ g.e2k;
+    uint32_t c2 = l2 ^ g.e2k;
     uint32_t c3 = g.e3;
 #pragma unroll
     for (int r = 3; r < 10; ++r) {
@@ -300,7 +320,7 @@ __device__ __forceinline__ uint32_t group_tests(const Block& block, uint32_t one
 // x = 8j + 2m + P take word m of Philox block 8y + j; bit x of a4 / a8 is set
 // when that uniform is below T4 / T8.  Four blocks per iteration fill one
 // 32-bit half of each mask.
-template <int P>
+template <int P, bool T3>
 __device__ __forceinline__ void row_accepts(const Keys& d, const HalfSweepGen& gen, uint32_t y,
                                             const Thr& t4, const Thr& t8, uint64_t& a4,
                                             uint64_t& a8) {
@@ -315,7 +335,7 @@ __device__ __forceinline__ void row_accepts(const Keys& d, const HalfSweepGen& g
     for (uint32_t q = 0; q < 2; ++q) {
         const uint32_t base = 8u * y + 4u * q;
         const uint32_t kc = group_tests<F4, F8, PA_L64_HUNROLL>(
-            [&](int h) { return philox_block<16>(d, gen, PA_L64_BLOCK(base, h)); }, one, c4, c8, t4.T,
+            [&](int h) { return philox_block<16, T3>(d, gen, PA_L64_BLOCK(base, h)); }, one, c4, c8, t4.T,
             t8.T);
         // site j = 4h + m: dE = 4 carry at bit 2j + 1, dE = 8 carry at bit 2j
         constexpr uint32_t EV = 0x55555555u;
@@ -346,14 +366,14 @@ struct RowJ {
 // and below.  c_u >= 2 flips outright (dE <= 0); c_u = 1 needs u < T4; c_u = 0
 // needs u < T8.  full bit 0 / 1: T4 / T8 equal 2^32 (beta = 0), always accept.
 // A bond is unsatisfied when the spins' xor differs from its coupling bit.
-template <int P, bool PMJ>
+template <int P, bool PMJ, bool T3>
 __device__ __forceinline__ uint64_t row_flips(const Keys& d, const HalfSweepGen& gen,
                                               uint64_t own, uint64_t up, uint64_t dn, uint32_t y,
                                               const Thr& t4, const Thr& t8, uint32_t full,
                                               const RowJ& j) {
     constexpr uint64_t cm = P ? 0xAAAAAAAAAAAAAAAAull : 0x5555555555555555ull;
     uint64_t a4, a8;
-    row_accepts<P>(d, gen, y, t4, t8, a4, a8);
+    row_accepts<P, T3>(d, gen, y, t4, t8, a4, a8);
     uint64_t a = own ^ ((own >> 1) | (own << 63));  // bond to x + 1
     uint64_t b = own ^ ((own << 1) | (own >> 63));  // bond to x - 1
     uint64_t e = own ^ up;
@@ -397,7 +417,7 @@ __device__ __forceinline__ void l64_couplings(const RunDev& d, int lane, RowJ& j
 
 // One replica: theta sweeps in registers, then the measurement.  Returns U
 // (all lanes), M through the reference; writes the replica back.
-template <bool PMJ>
+template <bool PMJ, bool T3>
 __device__ __forceinline__ uint32_t l64_replica(const Keys& K, uint4* spins, uint32_t slot,
                                                 int nsweeps, uint32_t g0, uint32_t ctag,
                                                 const Thr& t4, const Thr& t8, uint32_t full,
@@ -412,18 +432,20 @@ __device__ __forceinline__ uint32_t l64_replica(const Keys& K, uint4* spins, uin
         {  // colour 0: even rows have parity 0, odd rows parity 1
             const uint64_t up = shfl64(rb, lup);  // row ya - 1
             const uint64_t dn = shfl64(ra, ldn);  // row yb + 1
-            const HalfSweepGen gen = half_sweep_gen(K, 2u * g, slot, ctag);
-            const uint64_t fa = row_flips<0, PMJ>(K, gen, ra, up, rb, ya, t4, t8, full, ja);
-            const uint64_t fb = row_flips<1, PMJ>(K, gen, rb, ra, dn, yb, t4, t8, full, jb);
+            HalfSweepGen gen = half_sweep_gen(K, 2u * g, slot, ctag);
+            if constexpr (T3) gen.t3 = K.t3 + (size_t)(2 * t) * 512;
+            const uint64_t fa = row_flips<0, PMJ, T3>(K, gen, ra, up, rb, ya, t4, t8, full, ja);
+            const uint64_t fb = row_flips<1, PMJ, T3>(K, gen, rb, ra, dn, yb, t4, t8, full, jb);
             ra ^= fa;
             rb ^= fb;
         }
         {  // colour 1
             const uint64_t up = shfl64(rb, lup);
             const uint64_t dn = shfl64(ra, ldn);
-            const HalfSweepGen gen = half_sweep_gen(K, 2u * g + 1u, slot, ctag);
-            const uint64_t fa = row_flips<1, PMJ>(K, gen, ra, up, rb, ya, t4, t8, full, ja);
-            const uint64_t fb = row_flips<0, PMJ>(K, gen, rb, ra, dn, yb, t4, t8, full, jb);
+            HalfSweepGen gen = half_sweep_gen(K, 2u * g + 1u, slot, ctag);
+            if constexpr (T3) gen.t3 = K.t3 + (size_t)(2 * t + 1) * 512;
+            const uint64_t fa = row_flips<1, PMJ, T3>(K, gen, ra, up, rb, ya, t4, t8, full, ja);
+            const uint64_t fb = row_flips<0, PMJ, T3>(K, gen, rb, ra, dn, yb, t4, t8, full, jb);
             ra ^= fa;
             rb ^= fb;
         }
@@ -475,7 +497,35 @@ __device__ __forceinline__ void thresholds(const RunDev& d, uint32_t step, Thr& 
     full = d.thr[step * 4 + 3];
 }
 
-template <bool PMJ>
+// The run's round-2 table of a CTA, entry j * 32 + l for block 16 l + j, and
+// with T3 the launch's round-3 table after it, entry (hs * 16 + j) * 32 + l for
+// block 16 l + j in half-sweep hs = 2 t + colour of sweep g0 + t (c0 = 2 g0 + hs),
+// formed by all threads of the CTA (which all serve one run).
+template <bool T3>
+__device__ __forceinline__ void cta_tables(uint2* tab, uint32_t ctag, uint32_t g0, int nsweeps,
+                                           const uint32_t* rk0, const uint32_t* rk1) {
+    uint32_t ht, lt;
+    mul_hilo(PM1, ctag, ht, lt);  // round 1
+    const uint32_t y0k = ht ^ rk0[0];
+    for (uint32_t e = threadIdx.x; e < 512u; e += blockDim.x) {
+        uint32_t h, l;
+        mul_hilo(PM0, y0k ^ (16u * (e & 31u) + (e >> 5)), h, l);  // round 2, block half
+        tab[e] = make_uint2(h, l);
+    }
+    if constexpr (T3) {
+        __syncthreads();
+        const uint32_t n = 2u * (uint32_t)nsweeps * 512u;
+        for (uint32_t e = threadIdx.x; e < n; e += blockDim.x) {
+            uint32_t hc, lc, h, l;
+            mul_hilo(PM0, 2u * g0 + (e >> 9), hc, lc);  // round 1: M0 * c0
+            mul_hilo(PM1, tab[e & 511u].x ^ lc ^ rk1[1], h, l);  // round 3, block half
+            tab[512u + e] = make_uint2(h, l);
+        }
+    }
+    __syncthreads();
+}
+
+template <bool PMJ, bool T3>
 __global__ void __launch_bounds__(WARPS64 * 32, PA_L64_MIN_BLOCKS)
     k_sweep_l64(__grid_constant__ const RunDev d, int nsweeps) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -487,10 +537,9 @@ __global__ void __launch_bounds__(WARPS64 * 32, PA_L64_MIN_BLOCKS)
     uint32_t full;
     thresholds(d, st->step, t4, t8, full);
     const uint32_t ctag = (TAG_SWEEP << 28) | d.instance;
-    extern __shared__ uint2 s_r2[];  // WARPS64 x 16 x 32 round-2 products
-    uint2* col = s_r2 + (size_t)wib * 16 * 32 + lane;
-    round2_table<16>(col, (uint32_t)lane, ctag, d.rk0);
-    const Keys K{d.rk0, d.rk1, d.one, col};
+    extern __shared__ uint2 s_tab[];  // 512 round-2 products, then (T3) 2 nsweeps x 512 round-3
+    cta_tables<T3>(s_tab, ctag, g0, nsweeps, d.rk0, d.rk1);
+    const Keys K{d.rk0, d.rk1, d.one, s_tab + lane, T3 ? s_tab + 512 + lane : nullptr};
     uint4* spins = reinterpret_cast<uint4*>(d.spins[cur]);
     RowJ ja{0, 0, 0, 0}, jb{0, 0, 0, 0};
     if constexpr (PMJ) l64_couplings(d, lane, ja, jb);
@@ -501,7 +550,7 @@ __global__ void __launch_bounds__(WARPS64 * 32, PA_L64_MIN_BLOCKS)
     for (uint32_t slot = d.slot_lo + blockIdx.x * WARPS64 + wib; slot < end; slot += nwarps) {
         int M = 0;
         const uint32_t U =
-            l64_replica<PMJ>(K, spins, slot, nsweeps, g0, ctag, t4, t8, full, lane, M, ja, jb);
+            l64_replica<PMJ, T3>(K, spins, slot, nsweeps, g0, ctag, t4, t8, full, lane, M, ja, jb);
         if (lane == 0) {
             d.ebin[cur][slot] = U >> 1;
             d.mag[cur][slot] = M;
@@ -558,7 +607,8 @@ __global__ void __launch_bounds__(WARPS64 * 32, PA_L64_MIN_BLOCKS) k_sweep_l64_b
         for (uint32_t slot = first; slot < first + a.chunk && slot < R; ++slot) {
             int M = 0;
             const uint32_t U =
-                l64_replica<PMJ>(K, spins, slot, d.theta, g0, ctag, t4, t8, full, lane, M, ja, jb);
+                l64_replica<PMJ, false>(K, spins, slot, d.theta, g0, ctag, t4, t8, full, lane, M, ja,
+                                        jb);
             if (lane == 0) {
                 d.ebin[cur][slot] = U >> 1;
                 d.mag[cur][slot] = M;
@@ -893,30 +943,56 @@ struct PhiloxRateArgs {
 #endif
 constexpr int PHILOX_RATE_WARPS = PA_PHILOX_RATE_WARPS;
 
+// Half-sweeps of one round-3 table window of the generator alone.
+constexpr uint32_t PHILOX_RATE_WIN = 48;
+
 __global__ void __launch_bounds__(PHILOX_RATE_WARPS * 32, 1)
     k_philox_rate(__grid_constant__ const PhiloxRateArgs a) {
-    extern __shared__ uint2 s_r2[];  // PHILOX_RATE_WARPS x 16 x 32 round-2 products
+    // the sweep kernel's tables: the run's round-2 products, then a window of
+    // PHILOX_RATE_WIN half-sweeps' round-3 products, rebuilt per window
+    extern __shared__ uint2 s_tab[];
     const uint32_t lane = threadIdx.x & 31u;
-    uint2* col = s_r2 + (size_t)(threadIdx.x >> 5) * 16 * 32 + lane;
-    round2_table<16>(col, lane, TAG_SWEEP << 28, a.rk0);
-    const Keys K{a.rk0, a.rk1, a.one, col};
+    const uint32_t ctag = TAG_SWEEP << 28;
+    cta_tables<false>(s_tab, ctag, 0u, 0, a.rk0, a.rk1);
+    const Keys K{a.rk0, a.rk1, a.one, s_tab + lane, s_tab + 512 + lane};
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t slot = tid >> 5, base = lane * 16u;
     uint32_t acc = 0;
-    for (uint32_t g = 0; g < a.halfsweeps; ++g) {
-        const HalfSweepGen gen = half_sweep_gen(K, 2u * g, slot, TAG_SWEEP << 28);
+    for (uint32_t gb = 0; gb < a.halfsweeps; gb += PHILOX_RATE_WIN) {
+        const uint32_t nw = min(PHILOX_RATE_WIN, a.halfsweeps - gb);
+        __syncthreads();  // the previous window is read by no one any more
+        for (uint32_t e = threadIdx.x; e < nw * 512u; e += blockDim.x) {
+            uint32_t hc, lc, h, l;
+            mul_hilo(PM0, 2u * (gb + (e >> 9)), hc, lc);  // round 1: M0 * c0, c0 = 2 g
+            mul_hilo(PM1, s_tab[e & 511u].x ^ lc ^ a.rk1[1], h, l);  // round 3, block half
+            s_tab[512u + e] = make_uint2(h, l);
+        }
+        __syncthreads();
+        for (uint32_t w = 0; w < nw; ++w) {
+            HalfSweepGen gen = half_sweep_gen(K, 2u * (gb + w), slot, ctag);
+            gen.t3 = K.t3 + (size_t)w * 512;
 #pragma unroll 4
-        for (uint32_t h = 0; h < 16u; ++h) {
-            const uint4 u = philox_block<16>(K, gen, base + h);
-            acc ^= u.x ^ u.y ^ u.z ^ u.w;
+            for (uint32_t h = 0; h < 16u; ++h) {
+                const uint4 u = philox_block<16, true>(K, gen, base + h);
+                acc ^= u.x ^ u.y ^ u.z ^ u.w;
+            }
         }
     }
     a.out[tid] = acc;
 }
 
-// Dynamic shared memory of the register kernels: the round-2 tables.
-constexpr size_t L64_SMEM = (size_t)WARPS64 * 16 * 32 * sizeof(uint2);
-constexpr size_t PHILOX_RATE_SMEM = (size_t)PHILOX_RATE_WARPS * 16 * 32 * sizeof(uint2);
+// Dynamic shared memory of the L = 64 kernels: the plain kernel's CTA-wide
+// round-2 table (512 entries) and, for launches of up to L64_T3_MAX sweeps,
+// the round-3 table after it (2 nsweeps x 512 entries); the batched kernel's
+// per-warp round-2 tables (its warps may serve different runs); the
+// generator's round-2 table and one window of round-3 products.
+constexpr int L64_T3_MAX = 26;
+constexpr size_t TAB_ROW = 512 * sizeof(uint2);
+static size_t l64_plain_smem(bool t3, int nsweeps) {
+    return t3 ? (size_t)(1 + 2 * nsweeps) * TAB_ROW : TAB_ROW;
+}
+constexpr size_t L64_BATCHED_SMEM = (size_t)WARPS64 * 16 * 32 * sizeof(uint2);
+constexpr size_t PHILOX_RATE_SMEM = (size_t)(1 + PHILOX_RATE_WIN) * TAB_ROW;
 
 // Tables above the default 48 KB need the kernel's opt-in, once per device
 // (set at the first launch, which pa_init makes outside any stream capture).
@@ -927,11 +1003,14 @@ static cudaError_t ensure_smem_optin() {
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
     const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    if ((e = cudaFuncSetAttribute(k_sweep_l64<false>, A, (int)L64_SMEM)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_sweep_l64<true>, A, (int)L64_SMEM)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_sweep_l64_batched<false>, A, (int)L64_SMEM)) != cudaSuccess)
+    const int t3max = (int)l64_plain_smem(true, L64_T3_MAX);
+    if ((e = cudaFuncSetAttribute(k_sweep_l64<false, true>, A, t3max)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_sweep_l64<true, true>, A, t3max)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_sweep_l64_batched<false>, A, (int)L64_BATCHED_SMEM)) !=
+        cudaSuccess)
         return e;
-    if ((e = cudaFuncSetAttribute(k_sweep_l64_batched<true>, A, (int)L64_SMEM)) != cudaSuccess)
+    if ((e = cudaFuncSetAttribute(k_sweep_l64_batched<true>, A, (int)L64_BATCHED_SMEM)) !=
+        cudaSuccess)
         return e;
     if ((e = cudaFuncSetAttribute(k_philox_rate, A, (int)PHILOX_RATE_SMEM)) != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) done[dev] = true;
@@ -940,7 +1019,7 @@ static cudaError_t ensure_smem_optin() {
 
 // The L = 128 kernels form their round-2 products: a 128 KB table per block
 // ran 0.5-1.3 % slower there on GB300 (it takes that much of the L1).
-static size_t l64_smem(const RunDev& d) { return is_l128(d) ? 0 : L64_SMEM; }
+static size_t l64_batched_smem(const RunDev& d) { return is_l128(d) ? 0 : L64_BATCHED_SMEM; }
 
 static int wave(const void* fn, int threads, size_t smem) {
     int dev = 0, sms = 0, per_sm = 0;
@@ -961,9 +1040,10 @@ static const void* pick(const RunDev& d, K64 f64f, K64 f64j, K128 f128f, K128 f1
 
 int l64_grid(const RunDev& d) {
     const int w = l64_block_warps(d);
-    const int full = wave(pick(d, k_sweep_l64<false>, k_sweep_l64<true>, k_sweep_l128<false>,
-                               k_sweep_l128<true>),
-                          w * 32, l64_smem(d));
+    // one CTA per SM in either form (the register budget of 12 warps)
+    const int full = wave(pick(d, k_sweep_l64<false, false>, k_sweep_l64<true, false>,
+                               k_sweep_l128<false>, k_sweep_l128<true>),
+                          w * 32, is_l128(d) ? 0 : l64_plain_smem(false, 0));
     if (full <= 0) return 0;
     const int64_t need = ((int64_t)d.cap + w - 1) / w;
     return (int)(need < full ? need : full);
@@ -973,13 +1053,17 @@ cudaError_t launch_sweep_l64(const RunDev& d, int nsweeps, int grid, cudaStream_
     const cudaError_t e = ensure_smem_optin();
     if (e != cudaSuccess) return e;
     const bool pmj = d.model == PA_MODEL_PMJ;
-    const size_t sm = l64_smem(d);
     if (is_l128(d)) {
-        if (pmj) k_sweep_l128<true><<<grid, warps128<true>() * 32, sm, s>>>(d, nsweeps);
-        else k_sweep_l128<false><<<grid, warps128<false>() * 32, sm, s>>>(d, nsweeps);
+        if (pmj) k_sweep_l128<true><<<grid, warps128<true>() * 32, 0, s>>>(d, nsweeps);
+        else k_sweep_l128<false><<<grid, warps128<false>() * 32, 0, s>>>(d, nsweeps);
+    } else if (nsweeps >= 1 && nsweeps <= L64_T3_MAX) {
+        const size_t sm = l64_plain_smem(true, nsweeps);
+        if (pmj) k_sweep_l64<true, true><<<grid, WARPS64 * 32, sm, s>>>(d, nsweeps);
+        else k_sweep_l64<false, true><<<grid, WARPS64 * 32, sm, s>>>(d, nsweeps);
     } else {
-        if (pmj) k_sweep_l64<true><<<grid, WARPS64 * 32, sm, s>>>(d, nsweeps);
-        else k_sweep_l64<false><<<grid, WARPS64 * 32, sm, s>>>(d, nsweeps);
+        const size_t sm = l64_plain_smem(false, nsweeps);
+        if (pmj) k_sweep_l64<true, false><<<grid, WARPS64 * 32, sm, s>>>(d, nsweeps);
+        else k_sweep_l64<false, false><<<grid, WARPS64 * 32, sm, s>>>(d, nsweeps);
     }
     return cudaGetLastError();
 }
@@ -1016,7 +1100,7 @@ bool l64_batched_applies(const RunDev& proto) { return l64_applies(proto); }
 int l64_batched_grid(const RunDev& proto) {
     return wave(pick(proto, k_sweep_l64_batched<false>, k_sweep_l64_batched<true>,
                      k_sweep_l128_batched<false>, k_sweep_l128_batched<true>),
-                l64_block_warps(proto) * 32, l64_smem(proto));
+                l64_block_warps(proto) * 32, l64_batched_smem(proto));
 }
 
 cudaError_t launch_sweep_l64_batched(const BatchSweepArgs& a, const RunDev& proto, int grid,
@@ -1024,7 +1108,7 @@ cudaError_t launch_sweep_l64_batched(const BatchSweepArgs& a, const RunDev& prot
     const cudaError_t e = ensure_smem_optin();
     if (e != cudaSuccess) return e;
     const bool pmj = proto.model == PA_MODEL_PMJ;
-    const size_t sm = l64_smem(proto);
+    const size_t sm = l64_batched_smem(proto);
     if (is_l128(proto)) {
         if (pmj) k_sweep_l128_batched<true><<<grid, warps128<true>() * 32, sm, s>>>(a);
         else k_sweep_l128_batched<false><<<grid, warps128<false>() * 32, sm, s>>>(a);
