@@ -212,8 +212,9 @@ int pa_step_stream(pa_run* run, void* host_dst, size_t bytes, int32_t chunks, vo
  * persistent 16-warp block per SM (the shape in which the generator alone
  * runs fastest; the sweep kernel runs 12 warps), one warp per replica, each
  * lane drawing 16 blocks per half-sweep with the half-sweep products
- * shared and the round-2 block products from a per-run table (as the sweep
- * kernel draws them), with nothing done to the uniforms but an xor into one word per
+ * shared and the round-2 and round-3 block products from shared-memory
+ * tables (as the sweep kernel draws them; the round-3 table is rebuilt every
+ * 48 half-sweeps), with nothing done to the uniforms but an xor into one word per
  * thread.  Thread t writes out_dev[t] = xor over half-sweeps g < halfsweeps
  * and blocks b = 16 (t mod 32) .. + 15 of the four words of the block with
  * counter (2g, b, SWEEP << 28, t / 32) under key `seed`.  Uniforms drawn:

@@ -19,10 +19,11 @@
 //     of 16 sites (two instructions per test, no predicates or selects; the
 //     FMA pipe is left to the Philox multiplies);
 //   * the Philox round keys come from the kernel parameters; the products
-//     shared by all blocks of a half-sweep are formed once per half-sweep, and
-//     the round-2 block products, which depend only on the run and the block
-//     index, once per run into a shared-memory table: a block costs 15 of
-//     Philox's 20 multiplies.
+//     shared by all blocks of a half-sweep are formed once per half-sweep; the
+//     round-2 block products, which depend only on the run and the block
+//     index, and the round-3 block products, which depend only on the run,
+//     the block index and the half-sweep, once per CTA into shared-memory
+//     tables: a block costs 14 of Philox's 20 multiplies.
 // Grid-stride (persistent) over replicas; the population size is read from
 // device memory.  The measurement epilogue is the one of the generic kernel.
 #include "pa_internal.cuh"
@@ -75,8 +76,10 @@ struct Thr {
 // word 0 by an xor, so round 2 multiplies one block word (M0 * word 0) and one
 // shared word, round 3 again one of each (M1 * word 2, M0 * word 0 shared),
 // and rounds 4..10 are the plain rounds.  The shared products are formed once
-// per half-sweep (HalfSweepGen) and the round-2 block product once per run
-// (round2_table): 15 multiplies per block.  Same bits as philox().
+// per half-sweep (HalfSweepGen), the round-2 block product once per run and
+// the round-3 block product once per launch (cta_tables; the batched kernel,
+// whose warps serve several runs, keeps per-warp round-2 tables,
+// round2_table): 14 multiplies per block.  Same bits as philox().
 constexpr uint32_t PM0 = 0xD2511F53u, PM1 = 0xCD9E8D57u;
 
 // Round keys of the run's seed and the opaque 1 of the multiply-add tests:
@@ -923,9 +926,9 @@ int l64_block_warps(const RunDev& d) {
 
 // --------------------------------------------------------------------------
 // The generator's own ceiling in the register kernels' launch shape: the
-// Philox blocks of k_sweep_l64 (half-sweep products shared, round-2 block
-// products from the run's table: 15 multiplies per block; 16 blocks per
-// half-sweep and lane) with nothing else done to the
+// Philox blocks of k_sweep_l64 (half-sweep products shared, round-2 and
+// round-3 block products from the tables: 14 multiplies per block; 16 blocks
+// per half-sweep and lane) with nothing else done to the
 // uniforms but an xor into one word per thread.  One warp stands for one
 // replica (slot = global warp index); half-sweep g of lane l draws blocks
 // 16 l .. 16 l + 15 of counter (2 g, block, SWEEP, slot).
