@@ -77,9 +77,9 @@ struct Thr {
 // shared word, round 3 again one of each (M1 * word 2, M0 * word 0 shared),
 // and rounds 4..10 are the plain rounds.  The shared products are formed once
 // per half-sweep (HalfSweepGen), the round-2 block product once per run and
-// the round-3 block product once per launch (cta_tables; the batched kernel,
-// whose warps serve several runs, keeps per-warp round-2 tables,
-// round2_table): 14 multiplies per block.  Same bits as philox().
+// the round-3 block product once per launch (cta_tables): 14 multiplies per
+// block; 15 in the batched kernel, whose warps serve several runs and keep
+// per-warp round-2 tables (round2_table).  Same bits as philox().
 constexpr uint32_t PM0 = 0xD2511F53u, PM1 = 0xCD9E8D57u;
 
 // Round keys of the run's seed and the opaque 1 of the multiply-add tests:
