@@ -632,8 +632,10 @@ __global__ void __launch_bounds__(WARPS64 * 32, PA_L64_MIN_BLOCKS) k_sweep_l64_b
 // filling one 32-bit quarter of the row's masks.  Rows are updated in place
 // one after the other: the sites a half-sweep flips have the active colour,
 // and the classes of active-colour sites depend only on the other colour.
-// Each block forms its round-2 product (16 multiplies per block): the table of
-// the L = 64 kernel would hold 64 blocks per lane here.
+// Each block forms its round-2 product (16 multiplies per block).  Tables of
+// them as in the L = 64 kernel ran slower on GB300: per warp (128 KB per
+// block) 1490 against 1508 attempts/ns, and one per CTA (16 KB) 1504-1507
+// (ferromagnet) and 1476-1479 against 1495-1497 (+-J).
 // --------------------------------------------------------------------------
 // Block warps: with two groups unrolled, the ferromagnet runs at 1508 to 1517
 // attempts/ns with 8 warps (183 registers) against 1484 with 12 (166
