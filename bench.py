@@ -52,9 +52,9 @@ OPS_PER_ATTEMPT = 19.5
 ALU_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12
 # DRAM bytes of one sweep launch, from the ncu capture of the same kernel at
 # 2^20 replicas, four times L2 (profiles/k_sweep_l64_ising2d_L64_R2p18.md:
-# 538.3 MB read + 482.9 MB written), scaled by the replica count to 2^21.
+# 538.5 MB read + 483.2 MB written), scaled by the replica count to 2^21.
 # None whenever the kernel changes, until the next capture.
-SWEEP_TRAFFIC_BYTES_2P21 = (538.259456e6 + 482.916864e6) * 2
+SWEEP_TRAFFIC_BYTES_2P21 = (538.521344e6 + 483.193344e6) * 2
 # Slot ranges of the e2e step: each range's copy to the host (~0.7 ms at 1/8 of
 # 1 GiB) runs while the next range sweeps (~7 ms).
 E2E_CHUNKS = 8
