@@ -47,6 +47,16 @@ def test_packed_2d_sizes(P, L):
                  seed=100 + L, instance_id=L)
 
 
+@pytest.mark.parametrize("theta,model", [(1, 0), (26, 0), (27, 0), (30, 1)])
+def test_l64_sweep_counts_around_the_step_table_limit(P, theta, model):
+    """The L = 64 register kernel reads the round-3 Philox products from a
+    table formed per launch for up to 26 sweeps and forms them itself beyond:
+    both forms, ferromagnet and +-J, follow the oracle bit for bit."""
+    extra = dict(coupling_seed=9, instance_id=4) if model else {}
+    run_lockstep(P, steps=2, dim=2, L=64, layout=1, model=model, R0=96, K=4, theta=theta,
+                 beta_max=1.0, seed=300 + theta, **extra)
+
+
 @pytest.mark.parametrize("L", [4, 8, 64])
 def test_int8_2d_sizes(P, L):
     run_lockstep(P, steps=5, dim=2, L=L, layout=0, R0=600, K=10, theta=2, beta_max=1.0,
