@@ -48,6 +48,8 @@ namespace {
 // measured on GB300 (attempts/ns, same bits): 16 warps (125 registers) 1671,
 // 12 warps (152) 1686, 8 warps (212) 1653 (ferromagnet, 2^21 replicas); +-J
 // 2^20: 1626, 1636, 1611; batched, 8 +-J runs of 2^17: 1597, 1632, 1604.
+// With the Philox tables (fewer registers) 16 warps ran at 1755 against 1749
+// (ferromagnet) and 1704 against 1712 (+-J): 12 stays.
 #ifndef PA_L64_WARPS
 #define PA_L64_WARPS 12
 #endif
